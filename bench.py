@@ -1,0 +1,326 @@
+"""Benchmark of the CE plan-realization hot path on GB300.
+
+One step = one cross-entropy iteration of Algorithm 1 on the move-and-push
+workload (N = 4096 samples, T = 1000 steps, D = 6, K = 200): Philox sample ->
+fused rollout -> elite select + refit, all on the device through the C ABI.
+Reported value: simulated steps per second (N x T / time per iteration).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs an independent replica (its own Philox
+problem id) on its own GPU: weak scaling, no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workload  # noqa: E402
+
+METRIC = "sim steps/sec (N×T) on 1 GB300 & FP32-peak fraction; CEM time-to-cost vs plain"
+UNIT = "sim-steps/s"
+CONFIG = 1  # the move-and-push workload
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def workload_desc(sc, sk, cm):
+    return (f"{cm['name']}: N={cm['N']} T={sc['T']} D={len(sk['lo'])} K={cm['K']} dt={sc['dt']} "
+            f"(one CE iteration per step, initial distribution)")
+
+
+def aggregate(value_units: float, seconds: float, world: int):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([seconds], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+        u = torch.tensor([value_units], dtype=torch.float64, device=t.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        return float(u.item()), float(t.item())
+    return value_units, seconds
+
+
+def flops_per_step(name):
+    with open(os.path.join(ROOT, "workload", "flops_per_step.json")) as f:
+        return json.load(f)[name]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(sc, sk, cm, seconds=10.0, max_reps=20):
+    """The FP64 oracle, as it stands, on this host's cores: full CE
+    iterations of the same workload until ~`seconds` have passed."""
+    import oracle
+
+    oracle.build()
+    lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+    mean, chol = (lo + hi) / 2, np.diag((hi - lo) / 4)
+    cores = os.cpu_count() or 1
+    N, T = cm["N"], sc["T"]
+    reps, t0 = 0, time.perf_counter()
+    while reps < max_reps and (time.perf_counter() - t0 < seconds or reps == 0):
+        th = oracle.sample(1, reps, 0, N, mean, chol)
+        J, cls = oracle.rollout(sc, sk, th, nthreads=cores)
+        idx = oracle.select(J.astype(np.float32), cls, cm["K"])
+        oracle.refit(th, idx, lo, hi)
+        reps += 1
+    el = time.perf_counter() - t0
+    return {"value": reps * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full CE iterations (N={N}, T={T}) of the same workload, FP64, "
+                      f"{cores} threads, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sc, sk, cm = workload.config(CONFIG, seed=args.seed)
+    import oracle
+
+    oracle.build()
+    lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+    mean, chol = (lo + hi) / 2, np.diag((hi - lo) / 4)
+    cores = os.cpu_count() or 1
+    n_sample = 512  # bounded sample of the N = 4096 batch per step
+    T = sc["T"]
+
+    def step(j):
+        th = oracle.sample(1, j, 0, n_sample, mean, chol)
+        J, cls = oracle.rollout(sc, sk, th, nthreads=cores)
+        idx = oracle.select(J.astype(np.float32), cls, min(cm["K"], n_sample))
+        oracle.refit(th, idx, lo, hi)
+
+    for j in range(args.warmup):
+        step(j)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        step(args.warmup + j)
+    el = time.perf_counter() - t0
+    v = args.steps * n_sample * T / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_desc(sc, sk, cm), "l2": "n/a (host)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n_sample} of the {cm['N']} samples per CE iteration, T={T}, FP64"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    sc, sk, cm = workload.config(CONFIG, seed=args.seed)
+    N, K, T, D = cm["N"], cm["K"], sc["T"], len(sk["lo"])
+    lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
+    mean0 = torch.tensor((lo + hi) / 2, device="cuda")
+    chol0 = torch.tensor(np.diag((hi - lo) / 4), device="cuda")
+    cov0 = chol0 @ chol0.T
+    S = P.Scene(sc, sk)
+    stream = torch.cuda.Stream()
+    theta = torch.empty((N, D), device="cuda")
+    J = torch.empty(N, device="cuda")
+    cls = torch.empty(N, dtype=torch.uint8, device="cuda")
+    mean, cov, chol = mean0.clone(), cov0.clone(), chol0.clone()
+    idx = torch.empty(K, dtype=torch.int32, device="cuda")
+    keff = torch.empty(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    problem = rank
+
+    def step(j, ev=None):
+        # every step: one CE iteration from the initial distribution
+        with torch.cuda.stream(stream):
+            mean.copy_(mean0)
+            cov.copy_(cov0)
+            chol.copy_(chol0)
+            if ev:
+                ev[0].record(stream)
+            P.cem_sample(S.h, mean, chol, args.seed, j, problem, N, theta, stream)
+            if ev:
+                ev[1].record(stream)
+            P.cem_rollout_batch(S.h, theta, N, J, cls, stream)
+            if ev:
+                ev[2].record(stream)
+            P.cem_refit(S.h, theta, J, cls, N, K, 0, mean, cov, chol, idx, keff, stream)
+            if ev:
+                ev[3].record(stream)
+
+    for j in range(args.warmup):
+        step(j)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        for j in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(j))  # evict the previous step's data from L2 (untimed)
+            step(args.warmup + j, evs[j])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    roll_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ms = sum(step_ms) / args.steps
+    units, secs = aggregate(N * T * args.steps, sum(step_ms) / 1e3, world)
+    value = units / secs
+
+    # end to end through the public API with host buffers: cem_solve, one
+    # iteration per step, distribution in from pinned host memory and the
+    # best sample / new distribution back to the host
+    init_mean = np.ascontiguousarray((lo + hi) / 2, np.float32)
+    init_cov = np.ascontiguousarray(np.diag(((hi - lo) / 4) ** 2), np.float32)
+    S.solve(args.seed, N, K, 1, init_mean=init_mean, init_cov=init_cov)  # allocate + capture
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        S.solve(args.seed, N, K, 1, init_mean=init_mean, init_cov=init_cov, start_iter=j)
+    e2e_s = time.perf_counter() - t0
+    e_units, e_secs = aggregate(N * T * args.steps, e2e_s, world)
+    h2d = 4 * D + 4 * D * D * 2 + 128 + 4  # mean, cov, chol, loop state, status
+    d2h = 128 + 4 * D + 4 * D * D + 4 + 4 + 4  # loop state, mean, cov, status, histories
+
+    if rank == 0:
+        fps = flops_per_step(cm["name"])
+        peaks, src = measured_peaks()
+        clocks = clk.summary()
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roll_avg = sum(roll_ms) / len(roll_ms)
+        achieved = fps["flops"] * N * T / (roll_avg / 1e3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(sc, sk, cm), "N": N, "T": T, "D": D, "K": K,
+                       "l2": "flushed between timed steps (256 MiB write, untimed)",
+                       "rollout_ms": roll_avg, "wall_s": wall},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
+                                       f"({src} max SM clock)",
+                         "kernel": "rollout_kernel<PUSH>",
+                         "flops_per_step": fps["flops"]},
+            "e2e": {"value": e_units / e_secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        if world == 1:
+            line["cpu_baseline"] = cpu_baseline(sc, sk, cm)
+        print(json.dumps(line), flush=True)
+    S.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

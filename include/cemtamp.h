@@ -1,0 +1,232 @@
+/*
+ * cemtamp -- C ABI of the GB300 (sm_103a) cross-entropy plan-realization
+ * library.
+ *
+ * The library implements the data-parallel hot path of "Cross-Entropy
+ * Optimization of Physically Grounded Task and Motion Plans" (arXiv
+ * 2512.11571): Algorithm 1 (Sec. III-B) iterates
+ *     sample n_env parameter vectors theta ~ N(mean, cov)      -> cem_sample
+ *     roll every sample out through the plan's controllers and a
+ *     contact-rich rigid-body simulation, score it with the plan
+ *     cost of Problem 2                                        -> cem_rollout_batch
+ *     refit mean and covariance from the top-N_e elites        -> cem_refit
+ * until the iteration budget is spent (cem_solve runs the whole loop).
+ *
+ * Conventions for every entry point:
+ *   - Pointers with a `_d` suffix are DEVICE memory owned by the caller
+ *     (for example torch tensors).  They are checked with
+ *     cudaPointerGetAttributes; a host pointer yields CEM_ERR_INVALID_ARG.
+ *     Pointers with an `_h` suffix are host memory.
+ *   - Arrays are dense row-major FP32 unless stated: theta[N][D],
+ *     mean[D], cov[D][D], chol[D][D] (lower triangular, zeros above).
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.  Calls are stream-ordered and asynchronous; only
+ *     cem_solve, cem_batch_solve, cem_surrogate_* and cem_autotune
+ *     synchronise, when they return host results.
+ *   - The library owns only the memory behind a handle; it is freed by
+ *     cem_scene_destroy / cem_batch_destroy.
+ *   - Return value 0 is success; negative values are the cem_status codes
+ *     below, with a message in cem_last_error() (thread-local).
+ *   - Limits: D <= CEM_MAX_D, N <= 2^20, K <= 1024, T <= 1,000,000.
+ *
+ * A handle may be used from one host thread at a time; calls on different
+ * handles are independent.
+ */
+#ifndef CEMTAMP_H
+#define CEMTAMP_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CEM_MAX_D 18
+#define CEM_MAX_ACTIONS 6
+#define CEM_MAX_GEOMS 16
+#define CEM_MAX_SLABS 6
+#define CEM_MAX_K 1024
+#define CEM_MAX_N (1 << 20)
+#define CEM_TRACE_W 20
+
+typedef enum {
+  CEM_OK = 0,
+  CEM_ERR_INVALID_ARG = -1,
+  CEM_ERR_CUDA = -2,
+  CEM_ERR_TIMEOUT = -3,
+  CEM_ERR_NOT_PD = -4,
+  CEM_ERR_UNSUPPORTED = -5,
+  CEM_ERR_NO_MEMORY = -6
+} cem_status;
+
+/* Scene kinds: which dynamics and cost the rollout runs. */
+typedef enum {
+  CEM_SCENE_QUADRATIC = 0, /* J = (theta - theta*)^T A (theta - theta*), no dynamics */
+  CEM_SCENE_REACH = 1,     /* planar box base, one moveTo action */
+  CEM_SCENE_PUSH = 2,      /* planar base + free block: moveTo, push */
+  CEM_SCENE_PICKPLACE = 3  /* base + 2-link arm + object: move/grasp/move/place/move */
+} cem_scene_kind;
+
+/* Action kinds of a plan skeleton (the action schemas of Eq. 2 / Eq. 8-10).
+ * theta slice per action: MOVE and PUSH (dx, dy, kp); GRASP (approach
+ * azimuth, grip-height offset); PLACE (dx, dy, dz of the release point). */
+typedef enum { CEM_ACT_MOVE = 0, CEM_ACT_PUSH = 1, CEM_ACT_GRASP = 2, CEM_ACT_PLACE = 3 } cem_action_kind;
+
+typedef enum { CEM_COST_INTERP = 0, CEM_COST_STEP = 1 } cem_cost_mode;
+typedef enum { CEM_COV_FULL = 0, CEM_COV_DIAG = 1 } cem_cov_mode;
+
+/* A convex static body is the intersection of slabs lo <= n . x <= hi,
+ * where each slab is the body's exact projection interval on the unit axis
+ * n.  Finite bodies list the world x, y, z axes first (their bounding box)
+ * and then their own face normals; half-spaces use one slab with a large
+ * lo or hi. */
+typedef struct {
+  float n[3];
+  float lo, hi;
+} cem_slab;
+
+typedef struct {
+  int32_t n_slabs;
+  int32_t collide_base;   /* base footprint collides (slabs with n_z == 0) */
+  int32_t collide_object; /* object cube collides (all slabs) */
+  int32_t reserved;
+  cem_slab slab[CEM_MAX_SLABS];
+} cem_geom;
+
+/* Scene: physical constants, geometry and goal regions (SI units).  Fields a
+ * scene kind does not use are ignored. */
+typedef struct {
+  int32_t kind;      /* cem_scene_kind */
+  int32_t T;         /* horizon in steps */
+  int32_t cost_mode; /* cem_cost_mode */
+  int32_t reserved0;
+  float dt, g, eps; /* step, gravity, success tolerance */
+  /* planar base: half extents, mass, ground friction, start pose (x,y,yaw)
+   * and velocity (vx,vy,wz), yaw PD gains */
+  float base_half[2], base_mass, base_mu, base_start[3], base_v0[3], yaw_kp, yaw_kd;
+  /* free block of the push task */
+  float block_half[2], block_mass, block_mu, block_start[3], block_v0[3];
+  /* penalty contact stiffness, damping, contact friction, force limit */
+  float k_contact, c_contact, contact_mu, force_limit;
+  /* cost weights */
+  float w_time, w_goal, w_viol, w_obj, w_base;
+  /* goal point (reach) or region centre/half size (push) */
+  float goal_center[3], goal_half[3];
+  /* pick-place object (cube half size, mass, friction, start, velocity) */
+  float obj_half, obj_mass, obj_mu, obj_start[3], obj_v0[3];
+  /* 2-link arm: link lengths, shoulder height, joint PD gains, home pose */
+  float arm_l1, arm_l2, arm_z, arm_kp, arm_kd, arm_home[2];
+  /* grasp: base stand-off distance, base gain, grip height tolerance */
+  float grasp_reach, grasp_kp, grip_tol;
+  float obj_region_c[3], obj_region_h[3], base_region_c[3], base_region_h[3];
+  int32_t goal_obj_region, goal_obj_held, goal_base_region, n_geoms;
+  cem_geom geom[CEM_MAX_GEOMS];
+  float theta_star[CEM_MAX_D];
+  float A[CEM_MAX_D * CEM_MAX_D];
+} cem_scene_desc;
+
+typedef struct {
+  int32_t kind;         /* cem_action_kind */
+  int32_t theta_offset; /* first index of the action's theta slice */
+  int32_t success_ref;  /* moveTo success measured from 0: nominal, 1: nominal + offset */
+  int32_t reserved;
+  float nominal[3]; /* nominal target (region centre) */
+  float yaw;        /* base yaw target (planar tasks) */
+} cem_action_desc;
+
+/* Plan skeleton pi = (a_1..a_k) and the box bounds of its parameters. */
+typedef struct {
+  int32_t n_actions, D;
+  cem_action_desc action[CEM_MAX_ACTIONS];
+  float lo[CEM_MAX_D], hi[CEM_MAX_D];
+} cem_skeleton_desc;
+
+typedef struct cem_ctx* cem_handle;
+
+/* Problem 2 (Sec. III-B): a scene with its dynamics f, the symbolic plan pi
+ * and the goal psi_g.  Validates and copies both descriptors to the device.
+ * Errors: CEM_ERR_INVALID_ARG (bad descriptor), CEM_ERR_UNSUPPORTED
+ * (D > 18, more than 6 actions or 16 geometries), CEM_ERR_CUDA. */
+int cem_scene_create(const cem_scene_desc* scene, const cem_skeleton_desc* skel, cem_handle* out);
+int cem_scene_destroy(cem_handle h);
+
+/* Sample step of Algorithm 1: theta_d[n] = mean_d + chol_d z_n, z_n the
+ * standard normals of Philox4x32-10 (Salmon et al., SC'11) with counter
+ * (n, c, iter, problem) and key = seed, Box-Muller on word pairs.  N = 0 is
+ * a no-op. */
+int cem_sample(cem_handle h, const float* mean_d, const float* chol_d, uint64_t seed, uint32_t iter,
+               uint32_t problem, int N, float* theta_d, void* stream);
+
+/* The same Philox words the sampler draws: words_d[N][4*ceil(D/4)] (u32). */
+int cem_philox_words(cem_handle h, uint64_t seed, uint32_t iter, uint32_t problem, int N, uint32_t* words_d,
+                     void* stream);
+
+/* Evaluate step of Algorithm 1 (Sec. III-B, Problem 2): roll out each row
+ * of theta_d (clamped to the bounds) for T steps; J_d[n] = plan cost,
+ * cls_d[n] = 0 (every action succeeded and psi_g(x_T)), 1 (every action
+ * succeeded, psi_g false), 2 (otherwise), 3 (non-finite cost). */
+int cem_rollout_batch(cem_handle h, const float* theta_d, int N, float* J_d, uint8_t* cls_d, void* stream);
+
+/* Per-step state of each rollout for `steps` steps: states_d[N][steps][20]
+ * (layout documented in DESIGN; planar: base x,y,yaw,vx,vy,w, block ditto,
+ * action; pick-place: base x,y,vx,vy, q1,q2,dq1,dq2, azimuth, object
+ * x,y,z,vx,vy,vz, attached, action, end-effector x,y,z). */
+int cem_rollout_trace(cem_handle h, const float* theta_d, int N, int steps, float* states_d, void* stream);
+
+/* Update step of Algorithm 1 with the elite rules of Sec. III-B: rank by
+ * (class, J, index); elites are the K lowest of the best class present in
+ * {0, 1} (fewer if fewer exist), else of class 2; mean/cov (1/K_eff, ridge
+ * (1e-4 range)^2) and its Cholesky factor; one elite -> cov =
+ * diag((0.05 range)^2).  mean_d/cov_d/chol_d are read-write and kept when
+ * no elite exists.  elite_idx_d (K entries, ascending key) and k_eff_d may
+ * be NULL.  Errors: CEM_ERR_UNSUPPORTED if K > 1024. */
+int cem_refit(cem_handle h, const float* theta_d, const float* J_d, const uint8_t* cls_d, int N, int K,
+              int cov_mode, float* mean_d, float* cov_d, float* chol_d, int32_t* elite_idx_d, int32_t* k_eff_d,
+              void* stream);
+
+typedef struct {
+  uint64_t seed;
+  int32_t N, K, iters, cov_mode;
+  uint32_t problem;
+  uint32_t start_iter;    /* Philox iteration of the first sample (resume) */
+  int32_t use_graph;      /* capture one CE iteration in a CUDA graph and replay it */
+  int32_t reserved;
+  const float* init_mean_h; /* D values or NULL -> midpoint of the bounds */
+  const float* init_cov_h;  /* D x D or NULL -> diag((range / 4)^2) */
+  float* best_J_hist_h;     /* iters values or NULL: best cost so far per iteration */
+  int32_t* k_eff_hist_h;    /* iters values or NULL */
+} cem_solve_params;
+
+typedef struct {
+  float best_theta[CEM_MAX_D];
+  float best_J;
+  int32_t best_class;
+  int32_t D;
+  int32_t iters_done;
+  float mean[CEM_MAX_D];
+  float cov[CEM_MAX_D * CEM_MAX_D];
+  float elapsed_ms; /* device time of the loop (CUDA events) */
+} cem_result;
+
+/* Algorithm 1 end to end on the device: the distribution starts on the host
+ * (params), every iteration runs sample -> rollout -> refit, and the best
+ * sample over all iterations plus the final mean/cov come back to the host.
+ * Synchronous. */
+int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out);
+
+/* Threads-per-block of the rollout kernel (0 = automatic). */
+int cem_set_launch(cem_handle h, int block_threads);
+/* Times candidate block sizes for this scene and N on the current device
+ * and keeps the fastest; results are cached in a text file when
+ * cache_path is not NULL.  Writes the chosen block size. */
+int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* cem_last_error(void);
+/* Library version string. */
+const char* cem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -229,7 +229,12 @@ void planar_rollout(const or_scene& s, const Prep& pp, const double* th, int T, 
     R nx = R(0.0), ny = R(0.0), dep = R(0.0), qx = R(0.0), qy = R(0.0), Fn = R(0.0);
     R rax = R(0.0), ray = R(0.0), rbx = R(0.0), rby = R(0.0);
     if (has_block) {
-      hit = sat_rect(b, s.base_half[0], s.base_half[1], k, s.block_half[0], s.block_half[1], nx, ny, dep, qx, qy);
+      // broad phase: the rectangles can only touch if their bounding circles do
+      R cdx = k.x - b.x, cdy = k.y - b.y;
+      const double rsum = std::sqrt(s.base_half[0] * s.base_half[0] + s.base_half[1] * s.base_half[1]) +
+                          std::sqrt(s.block_half[0] * s.block_half[0] + s.block_half[1] * s.block_half[1]);
+      if (cdx * cdx + cdy * cdy < R(rsum * rsum))
+        hit = sat_rect(b, s.base_half[0], s.base_half[1], k, s.block_half[0], s.block_half[1], nx, ny, dep, qx, qy);
       if (hit) {
         rax = qx - b.x; ray = qy - b.y; rbx = qx - k.x; rby = qy - k.y;
         // relative velocity of the block's contact point w.r.t. the base's

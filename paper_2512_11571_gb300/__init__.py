@@ -1,0 +1,380 @@
+"""Python binding of libcemtamp, the GB300 cross-entropy plan-realization library.
+
+Argument marshalling only: every step of the path (Philox sampling, the
+fused rollout, elite selection and refit, the device-resident CE loop) runs
+in the library's CUDA kernels.  PyTorch is used for device memory and
+streams.  The functions keep the C names of ``include/cemtamp.h``; ``Scene``
+wraps a handle.  There is no CPU fallback: importing works without a GPU,
+but every call needs the compiled library and a CUDA device and raises
+otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcemtamp.so")
+
+MAX_D, MAX_ACTIONS, MAX_GEOMS, MAX_SLABS, MAX_K, TRACE_W = 18, 6, 16, 6, 1024, 20
+SCENE_KIND = {"quadratic": 0, "reach": 1, "push": 2, "pickplace": 3}
+ACTION_KIND = {"move": 0, "push": 1, "grasp": 2, "place": 3}
+ACTION_WIDTH = {"move": 3, "push": 3, "grasp": 2, "place": 3}
+COV = {"full": 0, "diag": 1}
+STATUS = {0: "CEM_OK", -1: "CEM_ERR_INVALID_ARG", -2: "CEM_ERR_CUDA", -3: "CEM_ERR_TIMEOUT",
+          -4: "CEM_ERR_NOT_PD", -5: "CEM_ERR_UNSUPPORTED", -6: "CEM_ERR_NO_MEMORY"}
+
+EXPORTS = [
+    "cem_scene_create", "cem_scene_destroy", "cem_sample", "cem_philox_words", "cem_rollout_batch",
+    "cem_rollout_trace", "cem_refit", "cem_solve", "cem_set_launch", "cem_autotune", "cem_last_error",
+    "cem_version",
+]
+
+
+class CemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ----------------------------------------------------------- C structures
+class cem_slab(C.Structure):
+    _fields_ = [("n", C.c_float * 3), ("lo", C.c_float), ("hi", C.c_float)]
+
+
+class cem_geom(C.Structure):
+    _fields_ = [("n_slabs", C.c_int32), ("collide_base", C.c_int32), ("collide_object", C.c_int32),
+                ("reserved", C.c_int32), ("slab", cem_slab * MAX_SLABS)]
+
+
+F3 = C.c_float * 3
+F2 = C.c_float * 2
+
+
+class cem_scene_desc(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int32), ("T", C.c_int32), ("cost_mode", C.c_int32), ("reserved0", C.c_int32),
+        ("dt", C.c_float), ("g", C.c_float), ("eps", C.c_float),
+        ("base_half", F2), ("base_mass", C.c_float), ("base_mu", C.c_float), ("base_start", F3),
+        ("base_v0", F3), ("yaw_kp", C.c_float), ("yaw_kd", C.c_float),
+        ("block_half", F2), ("block_mass", C.c_float), ("block_mu", C.c_float), ("block_start", F3),
+        ("block_v0", F3),
+        ("k_contact", C.c_float), ("c_contact", C.c_float), ("contact_mu", C.c_float),
+        ("force_limit", C.c_float),
+        ("w_time", C.c_float), ("w_goal", C.c_float), ("w_viol", C.c_float), ("w_obj", C.c_float),
+        ("w_base", C.c_float),
+        ("goal_center", F3), ("goal_half", F3),
+        ("obj_half", C.c_float), ("obj_mass", C.c_float), ("obj_mu", C.c_float), ("obj_start", F3),
+        ("obj_v0", F3),
+        ("arm_l1", C.c_float), ("arm_l2", C.c_float), ("arm_z", C.c_float), ("arm_kp", C.c_float),
+        ("arm_kd", C.c_float), ("arm_home", F2),
+        ("grasp_reach", C.c_float), ("grasp_kp", C.c_float), ("grip_tol", C.c_float),
+        ("obj_region_c", F3), ("obj_region_h", F3), ("base_region_c", F3), ("base_region_h", F3),
+        ("goal_obj_region", C.c_int32), ("goal_obj_held", C.c_int32), ("goal_base_region", C.c_int32),
+        ("n_geoms", C.c_int32),
+        ("geom", cem_geom * MAX_GEOMS),
+        ("theta_star", C.c_float * MAX_D), ("A", C.c_float * (MAX_D * MAX_D)),
+    ]
+
+
+class cem_action_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("theta_offset", C.c_int32), ("success_ref", C.c_int32),
+                ("reserved", C.c_int32), ("nominal", F3), ("yaw", C.c_float)]
+
+
+class cem_skeleton_desc(C.Structure):
+    _fields_ = [("n_actions", C.c_int32), ("D", C.c_int32), ("action", cem_action_desc * MAX_ACTIONS),
+                ("lo", C.c_float * MAX_D), ("hi", C.c_float * MAX_D)]
+
+
+class cem_solve_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("N", C.c_int32), ("K", C.c_int32), ("iters", C.c_int32),
+                ("cov_mode", C.c_int32), ("problem", C.c_uint32), ("start_iter", C.c_uint32),
+                ("use_graph", C.c_int32), ("reserved", C.c_int32),
+                ("init_mean_h", C.POINTER(C.c_float)), ("init_cov_h", C.POINTER(C.c_float)),
+                ("best_J_hist_h", C.POINTER(C.c_float)), ("k_eff_hist_h", C.POINTER(C.c_int32))]
+
+
+class cem_result(C.Structure):
+    _fields_ = [("best_theta", C.c_float * MAX_D), ("best_J", C.c_float), ("best_class", C.c_int32),
+                ("D", C.c_int32), ("iters_done", C.c_int32), ("mean", C.c_float * MAX_D),
+                ("cov", C.c_float * (MAX_D * MAX_D)), ("elapsed_ms", C.c_float)]
+
+
+# ------------------------------------------------------------- marshalling
+def _set(arr, vals):
+    for i, v in enumerate(vals):
+        arr[i] = float(v)
+
+
+def pack_scene(scene: dict, skel: dict, T: int | None = None):
+    """Workload dictionaries -> (cem_scene_desc, cem_skeleton_desc)."""
+    s = cem_scene_desc()
+    s.kind = SCENE_KIND[scene["kind"]]
+    s.T = int(scene["T"] if T is None else T)
+    s.cost_mode = 1 if scene.get("cost_mode", "interp") == "step" else 0
+    s.dt, s.g, s.eps = scene["dt"], scene["g"], scene.get("eps", 0.0)
+    for key in ("base_mass", "base_mu", "yaw_kp", "yaw_kd", "block_mass", "block_mu", "k_contact",
+                "c_contact", "contact_mu", "force_limit", "w_time", "w_goal", "w_viol", "w_obj", "w_base",
+                "obj_half", "obj_mass", "obj_mu", "arm_l1", "arm_l2", "arm_z", "arm_kp", "arm_kd",
+                "grasp_reach", "grasp_kp", "grip_tol"):
+        if key in scene:
+            setattr(s, key, float(scene[key]))
+    for key in ("base_half", "base_start", "base_v0", "block_half", "block_start", "block_v0",
+                "goal_center", "goal_half", "obj_start", "obj_v0", "arm_home"):
+        if key in scene:
+            _set(getattr(s, key), scene[key])
+    for key, name in (("obj_region_center", "obj_region_c"), ("obj_region_half", "obj_region_h"),
+                      ("base_region_center", "base_region_c"), ("base_region_half", "base_region_h")):
+        if key in scene:
+            _set(getattr(s, name), scene[key])
+    for key in ("goal_obj_region", "goal_obj_held", "goal_base_region"):
+        setattr(s, key, int(bool(scene.get(key, False))))
+    geoms = scene.get("geoms", [])
+    if len(geoms) > MAX_GEOMS:
+        raise ValueError("at most 16 geometries")
+    s.n_geoms = len(geoms)
+    for gi, gm in enumerate(geoms):
+        g = s.geom[gi]
+        if len(gm["slabs"]) > MAX_SLABS:
+            raise ValueError("at most 6 slabs per geometry")
+        g.n_slabs = len(gm["slabs"])
+        g.collide_base = int(gm["base"])
+        g.collide_object = int(gm["obj"])
+        for si, (nx, ny, nz, lo, hi) in enumerate(gm["slabs"]):
+            _set(g.slab[si].n, (nx, ny, nz))
+            g.slab[si].lo = lo
+            g.slab[si].hi = hi
+    D = len(skel["lo"])
+    if D > MAX_D:
+        raise ValueError("D > 18")
+    if scene["kind"] == "quadratic":
+        _set(s.theta_star, scene["theta_star"])
+        for i in range(D * D):
+            s.A[i] = scene["A"][i]
+    k = cem_skeleton_desc()
+    k.D = D
+    acts = skel["actions"]
+    if len(acts) > MAX_ACTIONS:
+        raise ValueError("at most 6 actions")
+    k.n_actions = len(acts)
+    off = 0
+    for i, a in enumerate(acts):
+        k.action[i].kind = ACTION_KIND[a["kind"]]
+        k.action[i].theta_offset = off
+        k.action[i].success_ref = 1 if a.get("success_ref", "nominal") == "target" else 0
+        _set(k.action[i].nominal, a["nominal"])
+        k.action[i].yaw = a.get("yaw", 0.0)
+        off += ACTION_WIDTH[a["kind"]]
+    _set(k.lo, skel["lo"])
+    _set(k.hi, skel["hi"])
+    return s, k
+
+
+# ------------------------------------------------------------------ loading
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcemtamp.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libcemtamp.so is not built ({path}); run paper_2512_11571_gb300/build.py")
+    L = C.CDLL(path)
+    vp, fp, u8p, i32p, u32p = C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
+    H = C.c_void_p
+    L.cem_scene_create.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc), C.POINTER(H)]
+    L.cem_scene_destroy.argtypes = [H]
+    L.cem_sample.argtypes = [H, fp, fp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, fp, vp]
+    L.cem_philox_words.argtypes = [H, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, u32p, vp]
+    L.cem_rollout_batch.argtypes = [H, fp, C.c_int, fp, u8p, vp]
+    L.cem_rollout_trace.argtypes = [H, fp, C.c_int, C.c_int, fp, vp]
+    L.cem_refit.argtypes = [H, fp, fp, u8p, C.c_int, C.c_int, C.c_int, fp, fp, fp, i32p, i32p, vp]
+    L.cem_solve.argtypes = [H, C.POINTER(cem_solve_params), C.POINTER(cem_result)]
+    L.cem_set_launch.argtypes = [H, C.c_int]
+    L.cem_autotune.argtypes = [H, C.c_int, C.c_char_p, C.POINTER(C.c_int)]
+    L.cem_last_error.restype = C.c_char_p
+    L.cem_version.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("cem_last_error", "cem_version"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise CemError(rc, load().cem_last_error().decode())
+
+
+def _ptr(t):
+    import torch
+
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# --------------------------------------------------------- C-named wrappers
+def cem_scene_create(scene: dict, skel: dict, T: int | None = None):
+    s, k = pack_scene(scene, skel, T)
+    h = C.c_void_p()
+    _check(load().cem_scene_create(C.byref(s), C.byref(k), C.byref(h)))
+    return h
+
+
+def cem_scene_destroy(h):
+    _check(load().cem_scene_destroy(h))
+
+
+def cem_sample(h, mean, chol, seed, it, problem, N, theta, stream=None):
+    _check(load().cem_sample(h, _ptr(mean), _ptr(chol), seed, it, problem, N, _ptr(theta), _stream(stream)))
+
+
+def cem_philox_words(h, seed, it, problem, N, words, stream=None):
+    _check(load().cem_philox_words(h, seed, it, problem, N, _ptr(words), _stream(stream)))
+
+
+def cem_rollout_batch(h, theta, N, J, cls, stream=None):
+    _check(load().cem_rollout_batch(h, _ptr(theta), N, _ptr(J), _ptr(cls), _stream(stream)))
+
+
+def cem_rollout_trace(h, theta, N, steps, states, stream=None):
+    _check(load().cem_rollout_trace(h, _ptr(theta), N, steps, _ptr(states), _stream(stream)))
+
+
+def cem_refit(h, theta, J, cls, N, K, cov_mode, mean, cov, chol, elite_idx=None, k_eff=None, stream=None):
+    _check(load().cem_refit(h, _ptr(theta), _ptr(J), _ptr(cls), N, K, cov_mode, _ptr(mean), _ptr(cov),
+                            _ptr(chol), _ptr(elite_idx), _ptr(k_eff), _stream(stream)))
+
+
+def cem_solve(h, params: cem_solve_params):
+    out = cem_result()
+    _check(load().cem_solve(h, C.byref(params), C.byref(out)))
+    return out
+
+
+def cem_set_launch(h, block):
+    _check(load().cem_set_launch(h, block))
+
+
+def cem_autotune(h, N, cache_path=None):
+    b = C.c_int()
+    _check(load().cem_autotune(h, N, cache_path.encode() if cache_path else None, C.byref(b)))
+    return b.value
+
+
+# ----------------------------------------------------------- convenience
+class Scene:
+    """A scene + plan skeleton on the device (one library handle)."""
+
+    def __init__(self, scene: dict, skel: dict, T: int | None = None):
+        self.scene, self.skel = scene, skel
+        self.D = len(skel["lo"])
+        self.T = int(scene["T"] if T is None else T)
+        self.lo = np.asarray(skel["lo"], np.float32)
+        self.hi = np.asarray(skel["hi"], np.float32)
+        self.h = cem_scene_create(scene, skel, T)
+
+    def close(self):
+        if self.h is not None and _lib is not None:
+            cem_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # device tensors in, device tensors out
+    def sample(self, mean, chol, seed, it, N, problem=0, stream=None):
+        import torch
+
+        theta = torch.empty((N, self.D), dtype=torch.float32, device=mean.device)
+        cem_sample(self.h, mean, chol, seed, it, problem, N, theta, stream)
+        return theta
+
+    def philox_words(self, seed, it, N, problem=0, stream=None):
+        import torch
+
+        nc = (self.D + 3) // 4
+        w = torch.empty((N, 4 * nc), dtype=torch.int32, device="cuda")
+        cem_philox_words(self.h, seed, it, problem, N, w, stream)
+        return w
+
+    def rollout(self, theta, stream=None):
+        import torch
+
+        N = theta.shape[0]
+        J = torch.empty(N, dtype=torch.float32, device=theta.device)
+        cls = torch.empty(N, dtype=torch.uint8, device=theta.device)
+        cem_rollout_batch(self.h, theta, N, J, cls, stream)
+        return J, cls
+
+    def trace(self, theta, steps, stream=None):
+        import torch
+
+        N = theta.shape[0]
+        st = torch.empty((N, steps, TRACE_W), dtype=torch.float32, device=theta.device)
+        cem_rollout_trace(self.h, theta, N, steps, st, stream)
+        return st
+
+    def refit(self, theta, J, cls, K, mean, cov, chol, cov_mode="full", stream=None):
+        import torch
+
+        idx = torch.full((K,), -1, dtype=torch.int32, device=J.device)
+        keff = torch.zeros(1, dtype=torch.int32, device=J.device)
+        cem_refit(self.h, theta, J, cls, J.shape[0], K, COV[cov_mode], mean, cov, chol, idx, keff, stream)
+        return idx, keff
+
+    def solve(self, seed, N, K, iters, cov_mode="full", problem=0, start_iter=0, use_graph=True,
+              init_mean=None, init_cov=None):
+        p = cem_solve_params()
+        p.seed, p.N, p.K, p.iters, p.cov_mode = seed, N, K, iters, COV[cov_mode]
+        p.problem, p.start_iter, p.use_graph = problem, start_iter, int(use_graph)
+        keep = []
+        if init_mean is not None:
+            m = np.ascontiguousarray(init_mean, np.float32)
+            keep.append(m)
+            p.init_mean_h = m.ctypes.data_as(C.POINTER(C.c_float))
+        if init_cov is not None:
+            c = np.ascontiguousarray(init_cov, np.float32)
+            keep.append(c)
+            p.init_cov_h = c.ctypes.data_as(C.POINTER(C.c_float))
+        hist = np.zeros(iters, np.float32)
+        keff = np.zeros(iters, np.int32)
+        p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
+        p.k_eff_hist_h = keff.ctypes.data_as(C.POINTER(C.c_int32))
+        r = cem_solve(self.h, p)
+        D = self.D
+        return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
+                    mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                    iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff)
+
+    def set_launch(self, block):
+        cem_set_launch(self.h, block)
+
+    def autotune(self, N, cache_path=None):
+        return cem_autotune(self.h, N, cache_path)

@@ -1,0 +1,629 @@
+// C ABI of the cemtamp library: argument validation, the per-handle device
+// scene and workspaces, and the device-resident CE loop of Algorithm 1
+// (Sec. III-B) with one iteration captured in a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace cem;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(CEM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CEM_CUDA(call)                               \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Mean distance from the centre of a 2a x 2b rectangle, closed form of
+// (1/ab) * integral over [0,a]x[0,b] of sqrt(x^2 + y^2).
+double mean_radius(double a, double b) {
+  const double d = std::sqrt(a * a + b * b);
+  const double s = a * b * d / 3.0 + a * a * a / 6.0 * std::log((b + d) / a) + b * b * b / 6.0 * std::log((a + d) / b);
+  return s / (a * b);
+}
+
+int action_width(int kind) { return kind == CEM_ACT_GRASP ? 2 : 3; }
+}  // namespace
+
+struct cem_ctx {
+  cem_scene_desc desc;
+  cem_skeleton_desc skel;
+  DevScene host;
+  DevScene* scene_d = nullptr;
+  int block = 0;  // rollout threads per block (0 = heuristic)
+  // workspaces of cem_solve
+  int cap_N = 0, cap_K = 0, cap_iters = 0;
+  float* theta_d = nullptr;
+  float* J_d = nullptr;
+  uint8_t* cls_d = nullptr;
+  float* mean_d = nullptr;
+  float* cov_d = nullptr;
+  float* chol_d = nullptr;
+  int32_t* keff_d = nullptr;
+  int32_t* status_d = nullptr;
+  Track* track_d = nullptr;
+  float* hist_J_d = nullptr;
+  int32_t* hist_keff_d = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_N = -1, graph_K = -1, graph_cov = -1;
+  uint64_t graph_seed = 0;
+  uint32_t graph_problem = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int validate(const cem_scene_desc* s, const cem_skeleton_desc* k) {
+  if (!s || !k) return fail(CEM_ERR_INVALID_ARG, "scene and skeleton descriptors are required");
+  if (s->kind < CEM_SCENE_QUADRATIC || s->kind > CEM_SCENE_PICKPLACE) return fail(CEM_ERR_INVALID_ARG, "unknown scene kind");
+  if (k->D < 1 || k->D > CEM_MAX_D) return fail(CEM_ERR_UNSUPPORTED, "D must be in 1..18");
+  if (s->T < 1 || s->T > 1000000) return fail(CEM_ERR_UNSUPPORTED, "T must be in 1..1e6");
+  if (!(s->dt > 0.0f) || !std::isfinite(s->dt)) return fail(CEM_ERR_INVALID_ARG, "dt must be positive");
+  for (int d = 0; d < k->D; ++d)
+    if (!(k->lo[d] <= k->hi[d]) || !std::isfinite(k->lo[d]) || !std::isfinite(k->hi[d]))
+      return fail(CEM_ERR_INVALID_ARG, "bounds must be finite with lo <= hi");
+  if (s->kind == CEM_SCENE_QUADRATIC) return CEM_OK;
+  if (k->n_actions < 1 || k->n_actions > CEM_MAX_ACTIONS) return fail(CEM_ERR_UNSUPPORTED, "1..6 actions supported");
+  int off = 0;
+  for (int i = 0; i < k->n_actions; ++i) {
+    const cem_action_desc& a = k->action[i];
+    if (a.kind < CEM_ACT_MOVE || a.kind > CEM_ACT_PLACE) return fail(CEM_ERR_INVALID_ARG, "unknown action kind");
+    const bool planar = s->kind != CEM_SCENE_PICKPLACE;
+    if (planar && !(a.kind == CEM_ACT_MOVE || a.kind == CEM_ACT_PUSH))
+      return fail(CEM_ERR_INVALID_ARG, "planar scenes take moveTo/push actions only");
+    if (!planar && a.kind == CEM_ACT_PUSH) return fail(CEM_ERR_INVALID_ARG, "pick-place takes no push action");
+    if (a.theta_offset != off) return fail(CEM_ERR_INVALID_ARG, "theta slices must be contiguous and in order");
+    off += action_width(a.kind);
+  }
+  if (off != k->D) return fail(CEM_ERR_INVALID_ARG, "theta slices do not cover D");
+  if (s->kind == CEM_SCENE_PUSH && (k->n_actions > 2))
+    return fail(CEM_ERR_UNSUPPORTED, "push scenes have at most 2 actions");
+  if (s->n_geoms < 0 || s->n_geoms > CEM_MAX_GEOMS) return fail(CEM_ERR_UNSUPPORTED, "at most 16 geometries");
+  for (int g = 0; g < s->n_geoms; ++g)
+    if (s->geom[g].n_slabs < 0 || s->geom[g].n_slabs > CEM_MAX_SLABS)
+      return fail(CEM_ERR_UNSUPPORTED, "at most 6 slabs per geometry");
+  if (!(s->base_mass > 0.0f)) return fail(CEM_ERR_INVALID_ARG, "base mass must be positive");
+  if (s->kind == CEM_SCENE_PUSH && !(s->block_mass > 0.0f)) return fail(CEM_ERR_INVALID_ARG, "block mass must be positive");
+  if (s->kind == CEM_SCENE_PICKPLACE && !(s->obj_mass > 0.0f && s->arm_l1 > 0.0f && s->arm_l2 > 0.0f))
+    return fail(CEM_ERR_INVALID_ARG, "object mass and arm links must be positive");
+  return CEM_OK;
+}
+
+DevScene prepare(const cem_scene_desc& s, const cem_skeleton_desc& k) {
+  DevScene d;
+  std::memset(&d, 0, sizeof(d));
+  d.kind = s.kind;
+  d.T = s.T;
+  d.cost_step = s.cost_mode == CEM_COST_STEP;
+  d.D = k.D;
+  d.n_act = s.kind == CEM_SCENE_QUADRATIC ? 0 : k.n_actions;
+  d.n_geoms = s.n_geoms;
+  d.goal_obj_region = s.goal_obj_region;
+  d.goal_obj_held = s.goal_obj_held;
+  d.goal_base_region = s.goal_base_region;
+  d.dt = s.dt;
+  d.g = s.g;
+  d.eps = s.eps;
+  d.k_contact = s.k_contact;
+  d.c_contact = s.c_contact;
+  d.contact_mu = s.contact_mu;
+  d.force_limit = s.force_limit;
+  d.w_time = s.w_time;
+  d.w_goal = s.w_goal;
+  d.w_viol = s.w_viol;
+  d.w_obj = s.w_obj;
+  d.w_base = s.w_base;
+  const double dt = s.dt, g = s.g;
+  // base
+  d.bhx = s.base_half[0];
+  d.bhy = s.base_half[1];
+  d.mb = s.base_mass;
+  const double Ib = s.base_mass * (4.0 * s.base_half[0] * s.base_half[0] + 4.0 * s.base_half[1] * s.base_half[1]) / 12.0;
+  d.Ib = (float)Ib;
+  d.dt_mb = (float)(dt / s.base_mass);
+  d.dt_Ib = Ib > 0 ? (float)(dt / Ib) : 0.0f;
+  d.base_cap = (float)(s.base_mu * g * dt);
+  if (Ib > 0 && s.base_half[0] > 0 && s.base_half[1] > 0)
+    d.base_wcap = (float)(s.base_mu * s.base_mass * g * mean_radius(s.base_half[0], s.base_half[1]) * dt / Ib);
+  d.yaw_kp = s.yaw_kp;
+  d.yaw_kd = s.yaw_kd;
+  for (int i = 0; i < 3; ++i) {
+    d.base_start[i] = s.base_start[i];
+    d.base_v0[i] = s.base_v0[i];
+    d.block_start[i] = s.block_start[i];
+    d.block_v0[i] = s.block_v0[i];
+    d.goal_center[i] = s.goal_center[i];
+    d.goal_half[i] = s.goal_half[i];
+    d.obj_start[i] = s.obj_start[i];
+    d.obj_v0[i] = s.obj_v0[i];
+    d.obj_region_c[i] = s.obj_region_c[i];
+    d.obj_region_h[i] = s.obj_region_h[i];
+    d.base_region_c[i] = s.base_region_c[i];
+    d.base_region_h[i] = s.base_region_h[i];
+  }
+  // block
+  d.khx = s.block_half[0];
+  d.khy = s.block_half[1];
+  d.mk = s.block_mass;
+  if (s.block_mass > 0) {
+    const double Ik = s.block_mass * (4.0 * s.block_half[0] * s.block_half[0] + 4.0 * s.block_half[1] * s.block_half[1]) / 12.0;
+    d.Ik = (float)Ik;
+    d.dt_mk = (float)(dt / s.block_mass);
+    d.dt_Ik = (float)(dt / Ik);
+    d.block_cap = (float)(s.block_mu * g * dt);
+    d.block_wcap = (float)(s.block_mu * s.block_mass * g * mean_radius(s.block_half[0], s.block_half[1]) * dt / Ik);
+  }
+  // pick-place
+  d.oh = s.obj_half;
+  d.mo = s.obj_mass;
+  d.obj_mu = s.obj_mu;
+  d.dt_mo = s.obj_mass > 0 ? (float)(dt / s.obj_mass) : 0.0f;
+  d.obj_cap = (float)(s.obj_mu * dt);
+  d.arm_l1 = s.arm_l1;
+  d.arm_l2 = s.arm_l2;
+  d.arm_z = s.arm_z;
+  d.arm_kp = s.arm_kp;
+  d.arm_kd = s.arm_kd;
+  d.arm_home[0] = s.arm_home[0];
+  d.arm_home[1] = s.arm_home[1];
+  d.grasp_reach = s.grasp_reach;
+  d.grasp_kp = s.grasp_kp;
+  d.grip_tol = s.grip_tol;
+  // skeleton
+  for (int i = 0; i < CEM_MAX_ACTIONS && i < k.n_actions; ++i) {
+    d.act_kind[i] = k.action[i].kind;
+    d.act_off[i] = k.action[i].theta_offset;
+    d.act_ref[i] = k.action[i].success_ref;
+    for (int j = 0; j < 3; ++j) d.act_nom[i][j] = k.action[i].nominal[j];
+    d.act_yaw[i] = k.action[i].yaw;
+  }
+  for (int i = 0; i < k.D; ++i) {
+    d.lo[i] = k.lo[i];
+    d.hi[i] = k.hi[i];
+  }
+  for (int gi = 0; gi < s.n_geoms; ++gi) {
+    d.geom_nslab[gi] = s.geom[gi].n_slabs;
+    d.geom_flags[gi] = (s.geom[gi].collide_base ? 1 : 0) | (s.geom[gi].collide_object ? 2 : 0);
+    for (int si = 0; si < s.geom[gi].n_slabs; ++si) {
+      for (int j = 0; j < 3; ++j) d.slab[gi][si][j] = s.geom[gi].slab[si].n[j];
+      d.slab[gi][si][3] = s.geom[gi].slab[si].lo;
+      d.slab[gi][si][4] = s.geom[gi].slab[si].hi;
+    }
+  }
+  for (int i = 0; i < CEM_MAX_D; ++i) d.theta_star[i] = s.theta_star[i];
+  for (int i = 0; i < k.D * k.D; ++i) d.A[i] = s.A[i];
+  return d;
+}
+
+int default_block(const cem_ctx* h, int N) {
+  if (h->block > 0) return h->block;
+  // spread small batches over all SMs: one warp per CTA until every SM has
+  // work, larger CTAs after that
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int b = 32;
+  while (b < 256 && (N + 2 * b - 1) / (2 * b) >= sms) b *= 2;
+  return b;
+}
+
+void free_work(cem_ctx* h) {
+  cudaFree(h->theta_d);
+  cudaFree(h->J_d);
+  cudaFree(h->cls_d);
+  cudaFree(h->mean_d);
+  cudaFree(h->cov_d);
+  cudaFree(h->chol_d);
+  cudaFree(h->keff_d);
+  cudaFree(h->status_d);
+  cudaFree(h->track_d);
+  cudaFree(h->hist_J_d);
+  cudaFree(h->hist_keff_d);
+  h->theta_d = nullptr;
+  h->J_d = nullptr;
+  h->cls_d = nullptr;
+  h->mean_d = h->cov_d = h->chol_d = nullptr;
+  h->keff_d = h->status_d = nullptr;
+  h->track_d = nullptr;
+  h->hist_J_d = nullptr;
+  h->hist_keff_d = nullptr;
+  h->cap_N = h->cap_K = h->cap_iters = 0;
+}
+
+int ensure_work(cem_ctx* h, int N, int iters) {
+  const int D = h->skel.D;
+  if (N <= h->cap_N && iters <= h->cap_iters && h->mean_d) return CEM_OK;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  free_work(h);
+  const int n = N > 0 ? N : 1, it = iters > 0 ? iters : 1;
+  if (cudaMalloc(&h->theta_d, sizeof(float) * (size_t)n * D) != cudaSuccess ||
+      cudaMalloc(&h->J_d, sizeof(float) * (size_t)n) != cudaSuccess ||
+      cudaMalloc(&h->cls_d, (size_t)n) != cudaSuccess || cudaMalloc(&h->mean_d, sizeof(float) * D) != cudaSuccess ||
+      cudaMalloc(&h->cov_d, sizeof(float) * D * D) != cudaSuccess ||
+      cudaMalloc(&h->chol_d, sizeof(float) * D * D) != cudaSuccess ||
+      cudaMalloc(&h->keff_d, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&h->status_d, sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&h->track_d, sizeof(Track)) != cudaSuccess ||
+      cudaMalloc(&h->hist_J_d, sizeof(float) * it) != cudaSuccess ||
+      cudaMalloc(&h->hist_keff_d, sizeof(int32_t) * it) != cudaSuccess) {
+    cudaGetLastError();
+    free_work(h);
+    return fail(CEM_ERR_NO_MEMORY, "cudaMalloc of the solve workspace failed");
+  }
+  h->cap_N = n;
+  h->cap_iters = it;
+  return CEM_OK;
+}
+
+RefitArgs refit_args(const cem_ctx* h, const float* theta, const float* J, const uint8_t* cls, int N, int K,
+                     int cov_mode) {
+  RefitArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.theta = theta;
+  a.J = J;
+  a.cls = cls;
+  a.N = N;
+  a.D = h->skel.D;
+  a.K = K;
+  a.cov_mode = cov_mode;
+  for (int d = 0; d < h->skel.D; ++d) {
+    a.lo[d] = h->skel.lo[d];
+    a.hi[d] = h->skel.hi[d];
+  }
+  return a;
+}
+
+// one CE iteration on h->stream: sample -> rollout -> refit (reads and
+// advances the device-side iteration counter)
+cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N, int K, int cov_mode) {
+  cudaError_t e = launch_sample(h->mean_d, h->chol_d, seed, &h->track_d->iter, 0, problem, N, h->skel.D, h->theta_d,
+                                h->stream);
+  if (e != cudaSuccess) return e;
+  e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->stream);
+  if (e != cudaSuccess) return e;
+  RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, K, cov_mode);
+  a.mean = h->mean_d;
+  a.cov = h->cov_d;
+  a.chol = h->chol_d;
+  a.k_eff = h->keff_d;
+  a.track = h->track_d;
+  a.hist_J = h->hist_J_d;
+  a.hist_keff = h->hist_keff_d;
+  a.status = h->status_d;
+  return launch_refit(a, h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cem_last_error(void) { return g_err.c_str(); }
+const char* cem_version(void) { return "cemtamp 0.1 (sm_103a)"; }
+
+int cem_scene_create(const cem_scene_desc* scene, const cem_skeleton_desc* skel, cem_handle* out) {
+  g_err.clear();
+  if (!out) return fail(CEM_ERR_INVALID_ARG, "out handle pointer is NULL");
+  *out = nullptr;
+  int rc = validate(scene, skel);
+  if (rc != CEM_OK) return rc;
+  cem_ctx* h = new cem_ctx();
+  h->desc = *scene;
+  h->skel = *skel;
+  h->host = prepare(*scene, *skel);
+  cudaError_t e = configure_refit();
+  if (e == cudaSuccess) e = cudaMalloc(&h->scene_d, sizeof(DevScene));
+  if (e == cudaSuccess) e = cudaMemcpy(h->scene_d, &h->host, sizeof(DevScene), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cem_scene_destroy(h);
+    return cuda_fail(e, "cem_scene_create");
+  }
+  *out = h;
+  return CEM_OK;
+}
+
+int cem_scene_destroy(cem_handle h) {
+  if (!h) return CEM_OK;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  free_work(h);
+  cudaFree(h->scene_d);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+  return CEM_OK;
+}
+
+int cem_set_launch(cem_handle h, int block_threads) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))
+    return fail(CEM_ERR_INVALID_ARG, "block size must be 0 or a multiple of 32 in 32..256");
+  h->block = block_threads;
+  return CEM_OK;
+}
+
+int cem_sample(cem_handle h, const float* mean_d, const float* chol_d, uint64_t seed, uint32_t iter, uint32_t problem,
+               int N, float* theta_d, void* stream) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 0 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 0..2^20");
+  if (N == 0) return CEM_OK;
+  if (!is_device_ptr(mean_d) || !is_device_ptr(chol_d) || !is_device_ptr(theta_d))
+    return fail(CEM_ERR_INVALID_ARG, "mean, chol and theta must be device pointers");
+  cudaError_t e = launch_sample(mean_d, chol_d, seed, nullptr, iter, problem, N, h->skel.D, theta_d,
+                                (cudaStream_t)stream);
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_sample");
+}
+
+int cem_philox_words(cem_handle h, uint64_t seed, uint32_t iter, uint32_t problem, int N, uint32_t* words_d,
+                     void* stream) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 0 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 0..2^20");
+  if (N == 0) return CEM_OK;
+  if (!is_device_ptr(words_d)) return fail(CEM_ERR_INVALID_ARG, "words must be a device pointer");
+  cudaError_t e = launch_philox_words(seed, iter, problem, N, h->skel.D, words_d, (cudaStream_t)stream);
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_philox_words");
+}
+
+int cem_rollout_batch(cem_handle h, const float* theta_d, int N, float* J_d, uint8_t* cls_d, void* stream) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 0 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 0..2^20");
+  if (N == 0) return CEM_OK;
+  if (!is_device_ptr(theta_d) || !is_device_ptr(J_d) || !is_device_ptr(cls_d))
+    return fail(CEM_ERR_INVALID_ARG, "theta, J and cls must be device pointers");
+  cudaError_t e = launch_rollout(h->scene_d, h->host.kind, theta_d, N, J_d, cls_d, default_block(h, N),
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_rollout_batch");
+}
+
+int cem_rollout_trace(cem_handle h, const float* theta_d, int N, int steps, float* states_d, void* stream) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 0 || N > 65536 || steps < 0 || steps > 100000) return fail(CEM_ERR_UNSUPPORTED, "trace: N <= 65536, steps <= 1e5");
+  if (N == 0 || steps == 0) return CEM_OK;
+  if (h->host.kind == CEM_SCENE_QUADRATIC) return fail(CEM_ERR_UNSUPPORTED, "quadratic scenes have no state");
+  if (!is_device_ptr(theta_d) || !is_device_ptr(states_d))
+    return fail(CEM_ERR_INVALID_ARG, "theta and states must be device pointers");
+  cudaError_t e = launch_trace(h->scene_d, h->host.kind, theta_d, N, steps, states_d, (cudaStream_t)stream);
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_rollout_trace");
+}
+
+int cem_refit(cem_handle h, const float* theta_d, const float* J_d, const uint8_t* cls_d, int N, int K, int cov_mode,
+              float* mean_d, float* cov_d, float* chol_d, int32_t* elite_idx_d, int32_t* k_eff_d, void* stream) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 0 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 0..2^20");
+  if (K < 1 || K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..1024");
+  if (cov_mode != CEM_COV_FULL && cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
+  if (!is_device_ptr(mean_d) || !is_device_ptr(cov_d) || !is_device_ptr(chol_d))
+    return fail(CEM_ERR_INVALID_ARG, "mean, cov and chol must be device pointers");
+  if (N > 0 && (!is_device_ptr(theta_d) || !is_device_ptr(J_d) || !is_device_ptr(cls_d)))
+    return fail(CEM_ERR_INVALID_ARG, "theta, J and cls must be device pointers");
+  if ((elite_idx_d && !is_device_ptr(elite_idx_d)) || (k_eff_d && !is_device_ptr(k_eff_d)))
+    return fail(CEM_ERR_INVALID_ARG, "elite_idx and k_eff must be device pointers or NULL");
+  RefitArgs a = refit_args(h, theta_d, J_d, cls_d, N, K, cov_mode);
+  a.mean = mean_d;
+  a.cov = cov_d;
+  a.chol = chol_d;
+  a.elite_idx = elite_idx_d;
+  a.k_eff = k_eff_d;
+  cudaError_t e = launch_refit(a, (cudaStream_t)stream);
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_refit");
+}
+
+int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out) {
+  g_err.clear();
+  if (!h || !p || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  const int D = h->skel.D;
+  if (p->N < 1 || p->N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 1..2^20");
+  if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..1024");
+  if (p->iters < 1 || p->iters > 100000) return fail(CEM_ERR_UNSUPPORTED, "iters must be in 1..1e5");
+  if (p->cov_mode != CEM_COV_FULL && p->cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
+  int rc = ensure_work(h, p->N, p->iters);
+  if (rc != CEM_OK) return rc;
+  // initial distribution (host) -> device
+  std::vector<float> mean(D), cov((size_t)D * D, 0.0f), chol((size_t)D * D, 0.0f);
+  for (int d = 0; d < D; ++d) {
+    mean[d] = p->init_mean_h ? p->init_mean_h[d] : 0.5f * (h->skel.lo[d] + h->skel.hi[d]);
+    if (!p->init_cov_h) cov[d * D + d] = std::pow(0.25f * (h->skel.hi[d] - h->skel.lo[d]), 2.0f);
+  }
+  if (p->init_cov_h)
+    for (int i = 0; i < D * D; ++i) cov[i] = p->init_cov_h[i];
+  {  // host Cholesky of the initial covariance (FP64)
+    std::vector<double> L((size_t)D * D, 0.0);
+    for (int j = 0; j < D; ++j) {
+      double s = cov[j * D + j];
+      for (int k = 0; k < j; ++k) s -= L[j * D + k] * L[j * D + k];
+      if (!(s > 0.0)) return fail(CEM_ERR_NOT_PD, "initial covariance is not positive definite");
+      L[j * D + j] = std::sqrt(s);
+      for (int i = j + 1; i < D; ++i) {
+        double t = cov[i * D + j];
+        for (int k = 0; k < j; ++k) t -= L[i * D + k] * L[j * D + k];
+        L[i * D + j] = t / L[j * D + j];
+      }
+    }
+    for (int i = 0; i < D * D; ++i) chol[i] = (float)L[i];
+  }
+  Track tr;
+  std::memset(&tr, 0, sizeof(tr));
+  tr.iter = p->start_iter;
+  tr.base_iter = p->start_iter;
+  tr.best_cls = 4;
+  tr.best_J = INFINITY;
+  tr.hist_len = p->iters;
+  const int32_t zero = 0;
+  CEM_CUDA(cudaMemcpyAsync(h->mean_d, mean.data(), sizeof(float) * D, cudaMemcpyHostToDevice, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(h->cov_d, cov.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(h->track_d, &tr, sizeof(Track), cudaMemcpyHostToDevice, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(h->status_d, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  if (p->use_graph) {
+    const bool stale = !h->graph || h->graph_N != p->N || h->graph_K != p->K || h->graph_cov != p->cov_mode ||
+                       h->graph_seed != p->seed || h->graph_problem != p->problem;
+    if (stale) {
+      if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+      }
+      cudaGraph_t g;
+      CEM_CUDA(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = enqueue_iteration(h, p->seed, p->problem, p->N, p->K, p->cov_mode);
+      cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(e, "capture of the CE iteration");
+      if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&h->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      h->graph_N = p->N;
+      h->graph_K = p->K;
+      h->graph_cov = p->cov_mode;
+      h->graph_seed = p->seed;
+      h->graph_problem = p->problem;
+    }
+  }
+  CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
+  for (int j = 0; j < p->iters; ++j) {
+    if (p->use_graph) {
+      CEM_CUDA(cudaGraphLaunch(h->graph, h->stream));
+    } else {
+      cudaError_t e = enqueue_iteration(h, p->seed, p->problem, p->N, p->K, p->cov_mode);
+      if (e != cudaSuccess) return cuda_fail(e, "CE iteration");
+    }
+  }
+  CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
+  int32_t status = 0;
+  CEM_CUDA(cudaMemcpyAsync(&tr, h->track_d, sizeof(Track), cudaMemcpyDeviceToHost, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(out->mean, h->mean_d, sizeof(float) * D, cudaMemcpyDeviceToHost, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(out->cov, h->cov_d, sizeof(float) * D * D, cudaMemcpyDeviceToHost, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(&status, h->status_d, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (p->best_J_hist_h)
+    CEM_CUDA(cudaMemcpyAsync(p->best_J_hist_h, h->hist_J_d, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, h->stream));
+  if (p->k_eff_hist_h)
+    CEM_CUDA(cudaMemcpyAsync(p->k_eff_hist_h, h->hist_keff_d, sizeof(int32_t) * p->iters, cudaMemcpyDeviceToHost, h->stream));
+  CEM_CUDA(cudaStreamSynchronize(h->stream));
+  float ms = 0.0f;
+  CEM_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  out->elapsed_ms = ms;
+  out->D = D;
+  out->iters_done = (int32_t)(tr.iter - tr.base_iter);
+  out->best_J = tr.best_J;
+  out->best_class = tr.best_cls;
+  for (int d = 0; d < CEM_MAX_D; ++d) out->best_theta[d] = d < D ? tr.best_theta[d] : 0.0f;
+  if (status != 0) return fail(CEM_ERR_NOT_PD, "covariance not positive definite after the diagonal fallback");
+  return CEM_OK;
+}
+
+int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 1 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 1..2^20");
+  int dev = 0, sms = 0;
+  CEM_CUDA(cudaGetDevice(&dev));
+  CEM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  char keybuf[256];
+  std::snprintf(keybuf, sizeof(keybuf), "kind=%d T=%d D=%d A=%d G=%d N=%d sms=%d", h->host.kind, h->host.T,
+                h->host.D, h->host.n_act, h->host.n_geoms, N, sms);
+  const std::string key(keybuf);
+  if (cache_path) {  // cache lines: "<key>|<block>"
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      const size_t bar = line.rfind('|');
+      if (bar != std::string::npos && line.substr(0, bar) == key) {
+        const int b = std::atoi(line.c_str() + bar + 1);
+        if (b >= 32 && b <= 256 && b % 32 == 0) {
+          h->block = b;
+          if (block_out) *block_out = b;
+          return CEM_OK;
+        }
+      }
+    }
+  }
+  int rc = ensure_work(h, N, 1);
+  if (rc != CEM_OK) return rc;
+  // sample once from the initial distribution so the timed rollouts see
+  // realistic parameter vectors
+  const int D = h->skel.D;
+  std::vector<float> mean(D), chol((size_t)D * D, 0.0f);
+  for (int d = 0; d < D; ++d) {
+    mean[d] = 0.5f * (h->skel.lo[d] + h->skel.hi[d]);
+    chol[d * D + d] = 0.25f * (h->skel.hi[d] - h->skel.lo[d]);
+  }
+  CEM_CUDA(cudaMemcpyAsync(h->mean_d, mean.data(), sizeof(float) * D, cudaMemcpyHostToDevice, h->stream));
+  CEM_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
+  cudaError_t e = launch_sample(h->mean_d, h->chol_d, 12345, nullptr, 0, 0, N, D, h->theta_d, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune sample");
+  const int cand[] = {32, 64, 128, 256};
+  float best_ms = INFINITY;
+  int best_b = 128;
+  for (int b : cand) {
+    float tot = 0.0f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
+      e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, h->stream);
+      if (e != cudaSuccess) return cuda_fail(e, "autotune rollout");
+      CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
+      CEM_CUDA(cudaEventSynchronize(h->ev1));
+      float ms = 0.0f;
+      CEM_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+      if (rep > 0) tot += ms;  // the first launch is a warm-up
+    }
+    if (tot < best_ms) {
+      best_ms = tot;
+      best_b = b;
+    }
+  }
+  h->block = best_b;
+  if (block_out) *block_out = best_b;
+  if (h->graph) {  // the captured rollout used the old launch shape
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (cache_path) {
+    std::ofstream o(cache_path, std::ios::app);
+    o << key << "|" << best_b << "\n";
+  }
+  return CEM_OK;
+}
+
+}  // extern "C"

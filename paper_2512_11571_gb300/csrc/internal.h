@@ -1,0 +1,93 @@
+// Internal declarations of the cemtamp CUDA library (device scene layout,
+// kernel launchers, error helpers).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cemtamp.h"
+
+namespace cem {
+
+// Scene prepared for the device: the descriptor's values plus derived
+// constants (inertias, friction capacities per step, 1/m), all FP32.  One
+// copy lives in global memory per handle; kernels stage it in shared memory.
+struct DevScene {
+  int32_t kind, T, cost_step, D;
+  int32_t n_act, n_geoms, goal_obj_region, goal_obj_held;
+  int32_t goal_base_region, pad0, pad1, pad2;
+  float dt, g, eps, k_contact;
+  float c_contact, contact_mu, force_limit, w_time;
+  float w_goal, w_viol, w_obj, w_base;
+  // planar base
+  float bhx, bhy, mb, Ib;
+  float dt_mb, dt_Ib, base_cap, base_wcap;  // dt/m, dt/I, mu g dt, mu m g rbar dt / I
+  float yaw_kp, yaw_kd, base_start[3], base_v0[3];
+  // block
+  float khx, khy, mk, Ik;
+  float dt_mk, dt_Ik, block_cap, block_wcap;
+  float block_start[3], block_v0[3];
+  float goal_center[3], goal_half[3];
+  // pick-place
+  float oh, mo, obj_mu, dt_mo;
+  float obj_start[3], obj_v0[3];
+  float arm_l1, arm_l2, arm_z, arm_kp, arm_kd, arm_home[2];
+  float grasp_reach, grasp_kp, grip_tol;
+  float obj_region_c[3], obj_region_h[3], base_region_c[3], base_region_h[3];
+  float obj_cap;  // mu dt (per unit normal force)
+  // skeleton
+  int32_t act_kind[CEM_MAX_ACTIONS], act_off[CEM_MAX_ACTIONS], act_ref[CEM_MAX_ACTIONS];
+  float act_nom[CEM_MAX_ACTIONS][3], act_yaw[CEM_MAX_ACTIONS];
+  float lo[CEM_MAX_D], hi[CEM_MAX_D];
+  // geometry
+  int32_t geom_nslab[CEM_MAX_GEOMS], geom_flags[CEM_MAX_GEOMS];  // bit0 base, bit1 object
+  float slab[CEM_MAX_GEOMS][CEM_MAX_SLABS][5];
+  // quadratic
+  float theta_star[CEM_MAX_D];
+  float A[CEM_MAX_D * CEM_MAX_D];
+};
+
+// Best-ever sample and iteration counter of a device-resident CE loop.
+struct Track {
+  uint32_t iter;       // Philox iteration of the next sample
+  uint32_t base_iter;  // iteration of the first sample (history index 0)
+  int32_t best_cls;    // 4 = none yet
+  float best_J;
+  float best_theta[CEM_MAX_D];
+  int32_t hist_len;
+  int32_t pad;
+};
+
+struct RefitArgs {
+  const float* theta;
+  const float* J;
+  const uint8_t* cls;
+  int N, D, K, cov_mode;
+  float lo[CEM_MAX_D], hi[CEM_MAX_D];
+  float* mean;
+  float* cov;
+  float* chol;
+  int32_t* elite_idx;
+  int32_t* k_eff;
+  Track* track;
+  float* hist_J;
+  int32_t* hist_keff;
+  int32_t* status;  // set to CEM_ERR_NOT_PD when the covariance stays indefinite
+};
+
+// kernel launchers (stream-ordered, no synchronisation)
+cudaError_t launch_sample(const float* mean, const float* chol, uint64_t seed, const uint32_t* iter_ptr,
+                          uint32_t iter, uint32_t problem, int N, int D, float* theta, cudaStream_t st);
+cudaError_t launch_philox_words(uint64_t seed, uint32_t iter, uint32_t problem, int N, int D, uint32_t* words,
+                                cudaStream_t st);
+cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
+                           int block, cudaStream_t st);
+cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
+                         cudaStream_t st);
+cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
+// opts the refit kernel into its dynamic shared memory (once per device, before any capture)
+cudaError_t configure_refit();
+size_t refit_smem_bytes(int K, int D);
+
+}  // namespace cem

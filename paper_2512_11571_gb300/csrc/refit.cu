@@ -1,0 +1,280 @@
+// Update step of Algorithm 1 (Sec. III-B): pick the top-N_e elites and refit
+// the sampling distribution to them.
+//
+// Elite rules of Sec. III-B: samples are ranked by (class, J, index); the
+// elites are the K lowest of the best class present among {0: goal reached,
+// 1: every action succeeded} -- fewer if fewer exist ("only the n_feasible
+// samples are used") -- or, if neither class occurs, of class 2.  The new
+// distribution is the maximum-likelihood Gaussian of the elites (the
+// KL-minimising CE update of Botev et al.): mean, covariance with 1/K_eff,
+// a ridge (1e-4 range)^2; a single elite gets diag((0.05 range)^2)
+// ("artificial noise"); the diagonal mode is the independent-normal model of
+// Sec. IV-A.
+//
+// One CTA of 1024 threads per problem.  Selection is an exact MSB-first
+// radix select over 52-bit keys (32-bit order-preserving cost bits, 20-bit
+// index) with shared-memory histograms, then a bitonic sort of the K_eff
+// elites; ties are impossible because the index is part of the key.  The
+// statistics are accumulated in FP64 by groups of four threads per output
+// with a fixed reduction order (run-to-run deterministic), and one warp
+// factorises the covariance.
+#include "internal.h"
+
+namespace cem {
+namespace {
+
+constexpr int RT = 1024;
+constexpr int KEY_BITS = 52;
+
+__device__ __forceinline__ uint32_t order_bits(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// class (0..3) and 52-bit key of sample i
+__device__ __forceinline__ int classify(const float* __restrict__ J, const uint8_t* __restrict__ cls, int i,
+                                        uint64_t& key) {
+  float j = J[i];
+  int c = cls[i];
+  if (c > 3) c = 3;
+  if (!isfinite(j)) {
+    c = 3;
+    j = __int_as_float(0x7f800000);
+  }
+  j = j + 0.0f;  // -0 -> +0
+  key = ((uint64_t)order_bits(j) << 20) | (uint64_t)i;
+  return c;
+}
+
+__device__ bool cholesky_warp(double* A, int D, int lane) {
+  // right-looking, in place, lower triangle; lane i owns row i
+  for (int j = 0; j < D; ++j) {
+    double d = A[j * D + j];
+    const bool ok = d > 0.0;
+    if (!__all_sync(0xffffffffu, ok)) return false;
+    const double ljj = sqrt(d);
+    __syncwarp();
+    if (lane == j) A[j * D + j] = ljj;
+    if (lane > j && lane < D) A[lane * D + j] /= ljj;
+    __syncwarp();
+    if (lane > j && lane < D)
+      for (int k = j + 1; k <= lane; ++k) A[lane * D + k] -= A[lane * D + j] * A[k * D + j];
+    __syncwarp();
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(RT) refit_kernel(RefitArgs a) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ int cnt[4];
+  __shared__ uint32_t hist[256];
+  __shared__ int s_cstar, s_keff, s_rank, s_n, s_fail;
+  __shared__ uint64_t s_prefix, s_mask;
+  __shared__ double s_mean[CEM_MAX_D];
+  __shared__ double s_cov[CEM_MAX_D * CEM_MAX_D];
+  __shared__ double s_L[CEM_MAX_D * CEM_MAX_D];
+  const int tid = threadIdx.x, N = a.N, D = a.D;
+  if (tid < 4) cnt[tid] = 0;
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+  for (int i = tid; i < N; i += RT) {
+    uint64_t key;
+    atomicAdd(&cnt[classify(a.J, a.cls, i, key)], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int cs = cnt[0] > 0 ? 0 : cnt[1] > 0 ? 1 : cnt[2] > 0 ? 2 : -1;
+    s_cstar = cs;
+    s_keff = cs < 0 ? 0 : min(a.K, cnt[cs]);
+    s_rank = s_keff;
+    s_prefix = 0;
+    s_mask = 0;
+  }
+  __syncthreads();
+  const int cstar = s_cstar, keff = s_keff;
+  if (keff > 0) {
+    uint64_t kth = ~0ull;
+    if (keff < cnt[cstar]) {  // exact radix select of the keff-th smallest key
+      int shift = KEY_BITS;
+      while (shift > 0) {
+        const int width = shift >= 8 ? 8 : shift;
+        shift -= width;
+        for (int d = tid; d < 256; d += RT) hist[d] = 0;
+        __syncthreads();
+        const uint64_t prefix = s_prefix, mask = s_mask;
+        for (int i = tid; i < N; i += RT) {
+          uint64_t key;
+          if (classify(a.J, a.cls, i, key) == cstar && (key & mask) == prefix)
+            atomicAdd(&hist[(key >> shift) & ((1u << width) - 1)], 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+          uint32_t cum = 0;
+          int d = 0;
+          for (; d < (1 << width); ++d) {
+            if (cum + hist[d] >= (uint32_t)s_rank) break;
+            cum += hist[d];
+          }
+          s_rank -= (int)cum;
+          s_prefix |= (uint64_t)d << shift;
+          s_mask |= (uint64_t)((1u << width) - 1) << shift;
+        }
+        __syncthreads();
+      }
+      kth = s_prefix;
+    }
+    // gather the elites (unordered), then bitonic sort by key
+    int P = 1;
+    while (P < keff) P <<= 1;
+    uint64_t* keys = reinterpret_cast<uint64_t*>(dyn);
+    float* eth = reinterpret_cast<float*>(dyn + sizeof(uint64_t) * P);
+    for (int i = tid; i < P; i += RT) keys[i] = ~0ull;
+    __syncthreads();
+    for (int i = tid; i < N; i += RT) {
+      uint64_t key;
+      if (classify(a.J, a.cls, i, key) == cstar && key <= kth) {
+        const int pos = atomicAdd(&s_n, 1);
+        if (pos < P) keys[pos] = key;
+      }
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < P; i += RT) {
+          const int ixj = i ^ j;
+          if (ixj > i) {
+            const uint64_t x = keys[i], y = keys[ixj];
+            const bool asc = (i & k) == 0;
+            if ((x > y) == asc) {
+              keys[i] = y;
+              keys[ixj] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int e = tid; e < keff; e += RT) {
+      const int idx = (int)(keys[e] & 0xFFFFF);
+      if (a.elite_idx) a.elite_idx[e] = idx;
+      for (int d = 0; d < D; ++d) eth[e * D + d] = a.theta[(size_t)idx * D + d];
+    }
+    __syncthreads();
+    // statistics in FP64: 4 threads per output, fixed reduction order
+    const int grp = tid >> 2, part = tid & 3;
+    if (keff == 1) {
+      if (tid < D) s_mean[tid] = (double)eth[tid];
+      for (int i = tid; i < D * D; i += RT) {
+        const int r = i / D, c = i % D;
+        const double w = 0.05 * ((double)a.hi[r] - (double)a.lo[r]);
+        s_cov[i] = r == c ? w * w : 0.0;
+      }
+      __syncthreads();
+    } else {
+      double v = 0.0;
+      if (grp < D)
+        for (int e = part; e < keff; e += 4) v += (double)eth[e * D + grp];
+      v += __shfl_down_sync(0xffffffffu, v, 2);
+      v += __shfl_down_sync(0xffffffffu, v, 1);
+      if (grp < D && part == 0) s_mean[grp] = v / keff;
+      __syncthreads();
+      const int npair = D * (D + 1) / 2;
+      int pi = 0, pj = 0;
+      if (grp < npair) {  // pair index -> (pi, pj), pi <= pj
+        int rem = grp, r = 0;
+        while (rem >= D - r) {
+          rem -= D - r;
+          ++r;
+        }
+        pi = r;
+        pj = r + rem;
+      }
+      v = 0.0;
+      if (grp < npair) {
+        const double mi = s_mean[pi], mj = s_mean[pj];
+        for (int e = part; e < keff; e += 4) v += ((double)eth[e * D + pi] - mi) * ((double)eth[e * D + pj] - mj);
+      }
+      v += __shfl_down_sync(0xffffffffu, v, 2);
+      v += __shfl_down_sync(0xffffffffu, v, 1);
+      if (grp < npair && part == 0) {
+        double c = v / keff;
+        if (pi == pj) {
+          const double w = 1e-4 * ((double)a.hi[pi] - (double)a.lo[pi]);
+          c += w * w;
+        }
+        s_cov[pi * D + pj] = c;
+        s_cov[pj * D + pi] = c;
+      }
+      __syncthreads();
+    }
+    if (a.cov_mode == CEM_COV_DIAG)
+      for (int i = tid; i < D * D; i += RT)
+        if (i / D != i % D) s_cov[i] = 0.0;
+    __syncthreads();
+    if (tid < 32) {
+      for (int i = tid; i < D * D; i += 32) s_L[i] = (i % D) <= (i / D) ? s_cov[i] : 0.0;
+      __syncwarp();
+      bool ok = cholesky_warp(s_L, D, tid);
+      if (!ok) {  // fall back to the diagonal
+        for (int i = tid; i < D * D; i += 32) {
+          const bool dg = i / D == i % D;
+          if (!dg) s_cov[i] = 0.0;
+          s_L[i] = dg ? s_cov[i] : 0.0;
+        }
+        __syncwarp();
+        ok = cholesky_warp(s_L, D, tid);
+      }
+      if (tid == 0) s_fail = ok ? 0 : 1;
+    }
+    __syncthreads();
+    if (!s_fail) {
+      for (int i = tid; i < D; i += RT) a.mean[i] = (float)s_mean[i];
+      for (int i = tid; i < D * D; i += RT) {
+        a.cov[i] = (float)s_cov[i];
+        a.chol[i] = (i % D) <= (i / D) ? (float)s_L[i] : 0.0f;
+      }
+    } else if (tid == 0 && a.status) {
+      *a.status = CEM_ERR_NOT_PD;
+    }
+  }
+  if (tid == 0) {
+    if (a.k_eff) *a.k_eff = keff;
+    if (a.track) {
+      Track* t = a.track;
+      if (keff > 0) {
+        const int b = (int)(reinterpret_cast<uint64_t*>(dyn)[0] & 0xFFFFF);
+        const float jb = a.J[b];
+        if (cstar < t->best_cls || (cstar == t->best_cls && jb < t->best_J)) {
+          t->best_cls = cstar;
+          t->best_J = jb;
+          for (int d = 0; d < D; ++d) t->best_theta[d] = a.theta[(size_t)b * D + d];
+        }
+      }
+      const int h = (int)(t->iter - t->base_iter);
+      if (h >= 0 && h < t->hist_len) {
+        if (a.hist_J) a.hist_J[h] = t->best_J;
+        if (a.hist_keff) a.hist_keff[h] = keff;
+      }
+      t->iter += 1;
+    }
+  }
+}
+
+}  // namespace
+
+size_t refit_smem_bytes(int K, int D) {
+  int P = 1;
+  while (P < K) P <<= 1;
+  return sizeof(uint64_t) * (size_t)P + sizeof(float) * (size_t)K * D;
+}
+
+cudaError_t configure_refit() {
+  return cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)refit_smem_bytes(CEM_MAX_K, CEM_MAX_D));
+}
+
+cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {
+  refit_kernel<<<1, RT, refit_smem_bytes(a.K, a.D), st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace cem

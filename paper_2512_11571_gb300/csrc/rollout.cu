@@ -1,0 +1,655 @@
+// Evaluate step of Algorithm 1 (Sec. III-B): every sample's plan is rolled
+// out through its controllers and the rigid-body dynamics x_{t+1} =
+// f(x_t, a_i) (Eq. 1b, Problem 2) for T steps and scored with the plan cost.
+//
+// Dynamics (the paper uses IsaacGym and does not define f; this is the
+// library's model): semi-implicit Euler; ground friction as an implicit
+// Coulomb clamp of the trial velocity; one penalty contact per (body,
+// geometry) pair from the separating-axis minimum overlap,
+// F_n = max(0, k depth - c v_n); Coulomb friction between bodies as one
+// Jacobi impulse per contact capped by mu F_n dt and by the impulse that
+// stops sliding.  Action cost (Sec. IV-A): time until the action succeeds;
+// the next action starts at the step after success (Problem 1).
+//
+// GB300 mapping: one thread per rollout, the whole state in registers, the
+// scene (geometry, constants, skeleton) staged once per block in shared
+// memory, the T-step loop fused in one launch, nothing per step written to
+// HBM.  The kernel reads N*D*4 bytes and writes N*5 bytes, so it is bound by
+// the FP32 pipe and by instruction latency, not by HBM.
+#include "internal.h"
+
+namespace cem {
+namespace {
+
+constexpr int TW = CEM_TRACE_W;
+
+__device__ __forceinline__ float theta_at(const DevScene& s, const float* __restrict__ row, int i) {
+  return fminf(fmaxf(row[i], s.lo[i]), s.hi[i]);
+}
+
+// time at which an action succeeded inside step k (state t_k -> t_{k+1})
+__device__ __forceinline__ float success_time(const DevScene& s, int k, float d_prev, float d_new) {
+  if (s.cost_step) return (float)(k + 1) * s.dt;
+  float frac = 0.0f;
+  if (d_prev > s.eps) frac = (d_prev - s.eps) / (d_prev - d_new);
+  frac = fminf(fmaxf(frac, 0.0f), 1.0f);
+  return ((float)k + frac) * s.dt;
+}
+
+struct B2 {
+  float x, y, psi, vx, vy, w;
+};
+
+__device__ __forceinline__ void ground_clamp(B2& b, float cap, float wcap) {
+  const float sp = sqrtf(b.vx * b.vx + b.vy * b.vy);
+  if (sp <= cap) {
+    b.vx = 0.0f;
+    b.vy = 0.0f;
+  } else {
+    const float f = 1.0f - cap / sp;
+    b.vx *= f;
+    b.vy *= f;
+  }
+  if (fabsf(b.w) <= wcap) b.w = 0.0f;
+  else b.w = b.w > 0.0f ? b.w - wcap : b.w + wcap;
+}
+
+__device__ __forceinline__ bool inside_rect(float px, float py, float cx, float cy, float c, float s, float hx,
+                                            float hy) {
+  const float rx = px - cx, ry = py - cy;
+  const float u = rx * c + ry * s, w = ry * c - rx * s;
+  return fabsf(u) <= hx && fabsf(w) <= hy;
+}
+
+// mean of the corners of rectangle I (centre ix,iy, rotation ci,si) inside
+// rectangle R; returns how many
+__device__ __forceinline__ int corners_inside(float ix, float iy, float ci, float si, float ihx, float ihy, float rx,
+                                              float ry, float cr, float sr, float rhx, float rhy, float& mx,
+                                              float& my) {
+  int cnt = 0;
+  mx = 0.0f;
+  my = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float su = (i & 1) ? ihx : -ihx, sw = (i & 2) ? ihy : -ihy;
+    const float px = ix + su * ci - sw * si;
+    const float py = iy + su * si + sw * ci;
+    if (inside_rect(px, py, rx, ry, cr, sr, rhx, rhy)) {
+      mx += px;
+      my += py;
+      ++cnt;
+    }
+  }
+  return cnt;
+}
+
+// SAT of rectangle A (base) against rectangle B (block): normal A->B, depth,
+// contact point (mean of incident corners inside the reference body).
+__device__ __forceinline__ bool sat_rect(const B2& A, float ahx, float ahy, const B2& B, float bhx, float bhy,
+                                         float& nx, float& ny, float& depth, float& qx, float& qy) {
+  float sa, ca, sb, cb;
+  sincosf(A.psi, &sa, &ca);
+  sincosf(B.psi, &sb, &cb);
+  const float axx[4] = {ca, -sa, cb, -sb};
+  const float axy[4] = {sa, ca, sb, cb};
+  const float dx = B.x - A.x, dy = B.y - A.y;
+  int best = -1;
+  float best_ov = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float ux = axx[k], uy = axy[k];
+    const float ra = ahx * fabsf(ca * ux + sa * uy) + ahy * fabsf(ca * uy - sa * ux);
+    const float rb = bhx * fabsf(cb * ux + sb * uy) + bhy * fabsf(cb * uy - sb * ux);
+    const float sp = dx * ux + dy * uy;
+    const float ov = ra + rb - fabsf(sp);
+    if (ov <= 0.0f) return false;
+    if (best < 0 || ov < best_ov) {
+      best = k;
+      best_ov = ov;
+      nx = sp >= 0.0f ? ux : -ux;
+      ny = sp >= 0.0f ? uy : -uy;
+    }
+  }
+  depth = best_ov;
+  float mx, my;
+  int cnt;
+  if (best < 2) cnt = corners_inside(B.x, B.y, cb, sb, bhx, bhy, A.x, A.y, ca, sa, ahx, ahy, mx, my);
+  else cnt = corners_inside(A.x, A.y, ca, sa, ahx, ahy, B.x, B.y, cb, sb, bhx, bhy, mx, my);
+  if (cnt == 0) {
+    if (best < 2) cnt = corners_inside(A.x, A.y, ca, sa, ahx, ahy, B.x, B.y, cb, sb, bhx, bhy, mx, my);
+    else cnt = corners_inside(B.x, B.y, cb, sb, bhx, bhy, A.x, A.y, ca, sa, ahx, ahy, mx, my);
+  }
+  if (cnt == 0) {
+    qx = (A.x + B.x) * 0.5f;
+    qy = (A.y + B.y) * 0.5f;
+  } else {
+    qx = mx / (float)cnt;
+    qy = my / (float)cnt;
+  }
+  return true;
+}
+
+__device__ __forceinline__ float cross2(float ax, float ay, float bx, float by) { return ax * by - ay * bx; }
+
+__device__ __forceinline__ void put_trace(float* tr, int step, const float* v, int nv) {
+  float* o = tr + (size_t)step * TW;
+#pragma unroll
+  for (int i = 0; i < TW; ++i) o[i] = i < nv ? v[i] : 0.0f;
+}
+
+// ------------------------------------------------------------- reach / push
+template <bool HAS_BLOCK, bool TRACE>
+__device__ void planar_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out, int& cls_out,
+                               float* tr) {
+  B2 b{s.base_start[0], s.base_start[1], s.base_start[2], s.base_v0[0], s.base_v0[1], s.base_v0[2]};
+  B2 k{s.block_start[0], s.block_start[1], s.block_start[2], s.block_v0[0], s.block_v0[1], s.block_v0[2]};
+  const int L = s.n_act;
+  const float dt = s.dt;
+  const float rsum = sqrtf(s.bhx * s.bhx + s.bhy * s.bhy) + sqrtf(s.khx * s.khx + s.khy * s.khy);
+  int a = 0, loaded = -1;
+  float gx = 0.f, gy = 0.f, kp = 0.f, kd = 0.f, rx = 0.f, ry = 0.f, yaw_t = 0.f;
+  float t_done = (float)T * dt, viol = 0.0f;
+  for (int step = 0; step < T; ++step) {
+    const int ai = a < L ? a : L - 1;
+    if (ai != loaded) {
+      const int o = s.act_off[ai];
+      gx = s.act_nom[ai][0] + theta_at(s, row, o);
+      gy = s.act_nom[ai][1] + theta_at(s, row, o + 1);
+      kp = theta_at(s, row, o + 2);
+      kd = 2.0f * sqrtf(kp);
+      rx = s.act_ref[ai] ? gx : s.act_nom[ai][0];
+      ry = s.act_ref[ai] ? gy : s.act_nom[ai][1];
+      yaw_t = s.act_yaw[ai];
+      loaded = ai;
+    }
+    float d_prev = 0.0f;
+    if (a < L) d_prev = sqrtf((b.x - rx) * (b.x - rx) + (b.y - ry) * (b.y - ry));
+    float fx = s.mb * (kp * (gx - b.x) - kd * b.vx);
+    float fy = s.mb * (kp * (gy - b.y) - kd * b.vy);
+    float tq = s.Ib * (s.yaw_kp * (yaw_t - b.psi) - s.yaw_kd * b.w);
+    float fkx = 0.f, fky = 0.f, tk = 0.f, Fn = 0.f;
+    float rax = 0.f, ray = 0.f, rbx = 0.f, rby = 0.f, nx = 0.f, ny = 0.f;
+    bool hit = false;
+    if (HAS_BLOCK) {
+      const float cdx = k.x - b.x, cdy = k.y - b.y;
+      if (cdx * cdx + cdy * cdy < rsum * rsum) {  // bounding circles overlap
+        float dep, qx, qy;
+        hit = sat_rect(b, s.bhx, s.bhy, k, s.khx, s.khy, nx, ny, dep, qx, qy);
+        if (hit) {
+          rax = qx - b.x;
+          ray = qy - b.y;
+          rbx = qx - k.x;
+          rby = qy - k.y;
+          const float vrx = (k.vx - k.w * rby) - (b.vx - b.w * ray);
+          const float vry = (k.vy + k.w * rbx) - (b.vy + b.w * rax);
+          const float vn = vrx * nx + vry * ny;
+          Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn);
+          fkx = Fn * nx;
+          fky = Fn * ny;
+          fx -= fkx;
+          fy -= fky;
+          tq -= cross2(rax, ray, fkx, fky);
+          tk = cross2(rbx, rby, fkx, fky);
+          const float over = Fn - s.force_limit;
+          if (over > 0.0f) viol += over * dt;
+        }
+      }
+    }
+    b.vx += s.dt_mb * fx;
+    b.vy += s.dt_mb * fy;
+    b.w += s.dt_Ib * tq;
+    if (HAS_BLOCK) {
+      k.vx += s.dt_mk * fkx;
+      k.vy += s.dt_mk * fky;
+      k.w += s.dt_Ik * tk;
+      if (hit && Fn > 0.0f) {
+        const float tx = -ny, ty = nx;
+        const float vrx = (k.vx - k.w * rby) - (b.vx - b.w * ray);
+        const float vry = (k.vy + k.w * rbx) - (b.vy + b.w * rax);
+        const float vt = vrx * tx + vry * ty;
+        const float ca = cross2(rax, ray, tx, ty), cb = cross2(rbx, rby, tx, ty);
+        const float inv_m = 1.0f / s.mb + 1.0f / s.mk + ca * ca / s.Ib + cb * cb / s.Ik;
+        const float jm = fminf(s.contact_mu * dt * Fn, fabsf(vt) / inv_m);
+        const float jt = vt > 0.0f ? -jm : jm;
+        const float jx = jt * tx, jy = jt * ty;
+        k.vx += jx / s.mk;
+        k.vy += jy / s.mk;
+        k.w += cross2(rbx, rby, jx, jy) / s.Ik;
+        b.vx -= jx / s.mb;
+        b.vy -= jy / s.mb;
+        b.w -= cross2(rax, ray, jx, jy) / s.Ib;
+      }
+      ground_clamp(k, s.block_cap, s.block_wcap);
+    }
+    ground_clamp(b, s.base_cap, s.base_wcap);
+    b.x += b.vx * dt;
+    b.y += b.vy * dt;
+    b.psi += b.w * dt;
+    if (HAS_BLOCK) {
+      k.x += k.vx * dt;
+      k.y += k.vy * dt;
+      k.psi += k.w * dt;
+    }
+    if (a < L) {
+      const float d_new = sqrtf((b.x - rx) * (b.x - rx) + (b.y - ry) * (b.y - ry));
+      if (d_new <= s.eps) {
+        const float ts = success_time(s, step, d_prev, d_new);
+        if (a == L - 1) t_done = ts;
+        ++a;
+      }
+    }
+    if (TRACE) {
+      const float v[13] = {b.x, b.y, b.psi, b.vx, b.vy, b.w, k.x, k.y, k.psi, k.vx, k.vy, k.w, (float)a};
+      put_trace(tr, step, v, 13);
+    }
+  }
+  const bool complete = a == L;
+  bool goal;
+  float J;
+  if (!HAS_BLOCK) {
+    const float ex = b.x - s.goal_center[0], ey = b.y - s.goal_center[1];
+    const float dist = sqrtf(ex * ex + ey * ey);
+    goal = dist <= s.eps;
+    J = s.w_time * t_done + s.w_goal * dist;
+  } else {
+    const float ax = fabsf(k.x - s.goal_center[0]), ay = fabsf(k.y - s.goal_center[1]);
+    const float ex = fmaxf(ax - s.goal_half[0], 0.0f), ey = fmaxf(ay - s.goal_half[1], 0.0f);
+    const float dist = sqrtf(ex * ex + ey * ey);
+    goal = ax <= s.goal_half[0] && ay <= s.goal_half[1];
+    J = s.w_time * t_done + s.w_goal * dist + s.w_viol * viol;
+  }
+  J_out = J;
+  cls_out = complete ? (goal ? 0 : 1) : 2;
+  if (!isfinite(J)) cls_out = 3;
+}
+
+// --------------------------------------------------------------- pick-place
+// Minimum-overlap contact of an axis-aligned mover against static geometry g
+// (slabs).  PLANAR: base footprint, slabs with n_z == 0 only.
+template <bool PLANAR>
+__device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px, float py, float pz, float hx,
+                                             float hy, float hz, float& nx, float& ny, float& nz, float& depth) {
+  bool any = false;
+  float best = 0.0f;
+  const int ns = s.geom_nslab[g];
+  for (int i = 0; i < ns; ++i) {
+    const float* sl = s.slab[g][i];
+    if (PLANAR && sl[2] != 0.0f) continue;
+    const float r = hx * fabsf(sl[0]) + hy * fabsf(sl[1]) + hz * fabsf(sl[2]);
+    const float sp = sl[0] * px + sl[1] * py + sl[2] * pz;
+    const float ov_pos = sl[4] - (sp - r);
+    const float ov_neg = (sp + r) - sl[3];
+    if (ov_pos <= 0.0f || ov_neg <= 0.0f) return false;
+    const float ov = fminf(ov_pos, ov_neg);
+    if (!any || ov < best) {
+      best = ov;
+      any = true;
+      const float sg = ov_pos <= ov_neg ? 1.0f : -1.0f;
+      nx = sg * sl[0];
+      ny = sg * sl[1];
+      nz = sg * sl[2];
+    }
+  }
+  depth = best;
+  return any;
+}
+
+__device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, float tx, float ty, float tz,
+                                       float& beta, float& q1, float& q2) {
+  const float dx = tx - bx, dy = ty - by;
+  beta = atan2f(dy, dx);
+  float rr = sqrtf(dx * dx + dy * dy);
+  float zz = tz - s.arm_z;
+  float rho = sqrtf(rr * rr + zz * zz);
+  const float rmax = s.arm_l1 + s.arm_l2 - 1e-3f, rmin = fabsf(s.arm_l1 - s.arm_l2) + 1e-3f;
+  if (rho > rmax) {
+    const float f = rmax / rho;
+    rr *= f;
+    zz *= f;
+    rho = rmax;
+  } else if (rho < rmin) {
+    const float f = rmin / fmaxf(rho, 1e-9f);
+    rr *= f;
+    zz *= f;
+    rho = rmin;
+  }
+  float c2 = (rho * rho - (s.arm_l1 * s.arm_l1 + s.arm_l2 * s.arm_l2)) / (2.0f * s.arm_l1 * s.arm_l2);
+  c2 = fminf(fmaxf(c2, -1.0f), 1.0f);
+  q2 = -acosf(c2);
+  float s2, co2;
+  sincosf(q2, &s2, &co2);
+  q1 = atan2f(zz, rr) - atan2f(s.arm_l2 * s2, s.arm_l1 + s.arm_l2 * co2);
+}
+
+__device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, float cb, float sb, float q1, float q2,
+                                       float& ex, float& ey, float& ez) {
+  float s1, c1, s12, c12;
+  sincosf(q1, &s1, &c1);
+  sincosf(q1 + q2, &s12, &c12);
+  const float r = s.arm_l1 * c1 + s.arm_l2 * c12;
+  ez = s.arm_z + s.arm_l1 * s1 + s.arm_l2 * s12;
+  ex = bx + r * cb;
+  ey = by + r * sb;
+}
+
+template <bool TRACE>
+__device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out,
+                                  int& cls_out, float* tr) {
+  const float dt = s.dt, h = s.oh;
+  float bx = s.base_start[0], by = s.base_start[1], bvx = s.base_v0[0], bvy = s.base_v0[1];
+  float q1 = s.arm_home[0], q2 = s.arm_home[1], dq1 = 0.f, dq2 = 0.f, beta = 0.f;
+  float cbeta = 1.0f, sbeta = 0.0f;
+  float q1t = q1, q2t = q2;
+  float ox = s.obj_start[0], oy = s.obj_start[1], oz = s.obj_start[2];
+  float ovx = s.obj_v0[0], ovy = s.obj_v0[1], ovz = s.obj_v0[2];
+  bool attached = false;
+  float offx = 0.f, offy = 0.f, offz = 0.f;
+  float ex, ey, ez;
+  arm_fk(s, bx, by, cbeta, sbeta, q1, q2, ex, ey, ez);
+  const int L = s.n_act;
+  int a = 0, loaded = -1;
+  float gx = bx, gy = by, kp = 0.f, kd = 0.f;
+  float mgx = bx, mgy = by, mkp = 0.f, mkd = 0.f;
+  float rx = 0.f, ry = 0.f, caz = 1.f, saz = 0.f, hgrip = 0.f, ptx = 0.f, pty = 0.f, ptz = 0.f;
+  float t_done = (float)T * dt;
+  for (int step = 0; step < T; ++step) {
+    const int ai = a < L ? a : L - 1;
+    const int kind = s.act_kind[ai];
+    if (ai != loaded) {
+      const int o = s.act_off[ai];
+      if (kind == CEM_ACT_MOVE) {
+        mgx = s.act_nom[ai][0] + theta_at(s, row, o);
+        mgy = s.act_nom[ai][1] + theta_at(s, row, o + 1);
+        mkp = theta_at(s, row, o + 2);
+        mkd = 2.0f * sqrtf(mkp);
+        rx = s.act_ref[ai] ? mgx : s.act_nom[ai][0];
+        ry = s.act_ref[ai] ? mgy : s.act_nom[ai][1];
+      } else if (kind == CEM_ACT_GRASP) {
+        sincosf(theta_at(s, row, o), &saz, &caz);
+        hgrip = theta_at(s, row, o + 1);
+        kp = s.grasp_kp;
+        kd = 2.0f * sqrtf(kp);
+      } else if (kind == CEM_ACT_PLACE) {
+        ptx = s.act_nom[ai][0] + theta_at(s, row, o);
+        pty = s.act_nom[ai][1] + theta_at(s, row, o + 1);
+        ptz = s.act_nom[ai][2] + theta_at(s, row, o + 2);
+      }
+      loaded = ai;
+    }
+    float tx = 0.f, ty = 0.f, tz = 0.f;
+    if (kind == CEM_ACT_MOVE) {
+      gx = mgx;
+      gy = mgy;
+      kp = mkp;
+      kd = mkd;
+    } else if (kind == CEM_ACT_GRASP) {
+      tx = ox;
+      ty = oy;
+      tz = oz + hgrip;
+      gx = ox - s.grasp_reach * caz;
+      gy = oy - s.grasp_reach * saz;
+    } else {
+      tx = ptx;
+      ty = pty;
+      tz = ptz;
+      gx = mgx;
+      gy = mgy;
+      kp = mkp;
+      kd = mkd;
+    }
+    float d_prev = 0.0f;
+    if (a < L) {
+      if (kind == CEM_ACT_MOVE) d_prev = sqrtf((bx - rx) * (bx - rx) + (by - ry) * (by - ry));
+      else d_prev = sqrtf((ex - tx) * (ex - tx) + (ey - ty) * (ey - ty) + (ez - tz) * (ez - tz));
+    }
+    if (kind != CEM_ACT_MOVE) {
+      arm_ik(s, bx, by, tx, ty, tz, beta, q1t, q2t);
+      sincosf(beta, &sbeta, &cbeta);
+    }
+    // base: PD + penalty contacts with the static footprints
+    float fx = s.mb * (kp * (gx - bx) - kd * bvx);
+    float fy = s.mb * (kp * (gy - by) - kd * bvy);
+    for (int g = 0; g < s.n_geoms; ++g) {
+      if (!(s.geom_flags[g] & 1)) continue;
+      float nx, ny, nz, dep;
+      if (slab_contact<true>(s, g, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, nx, ny, nz, dep)) {
+        const float vn = bvx * nx + bvy * ny;
+        const float Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn);
+        fx += Fn * nx;
+        fy += Fn * ny;
+      }
+    }
+    bvx += s.dt_mb * fx;
+    bvy += s.dt_mb * fy;
+    {
+      const float sp = sqrtf(bvx * bvx + bvy * bvy);
+      if (sp <= s.base_cap) {
+        bvx = 0.0f;
+        bvy = 0.0f;
+      } else {
+        const float f = 1.0f - s.base_cap / sp;
+        bvx *= f;
+        bvy *= f;
+      }
+    }
+    bx += bvx * dt;
+    by += bvy * dt;
+    // arm joints
+    const float dd1 = s.arm_kp * (q1t - q1) - s.arm_kd * dq1;
+    const float dd2 = s.arm_kp * (q2t - q2) - s.arm_kd * dq2;
+    dq1 += dt * dd1;
+    dq2 += dt * dd2;
+    q1 += dt * dq1;
+    q2 += dt * dq2;
+    float nex, ney, nez;
+    arm_fk(s, bx, by, cbeta, sbeta, q1, q2, nex, ney, nez);
+    // object
+    if (attached) {
+      ox = nex + offx;
+      oy = ney + offy;
+      oz = nez + offz;
+      ovx = (nex - ex) / dt;
+      ovy = (ney - ey) / dt;
+      ovz = (nez - ez) / dt;
+    } else {
+      uint32_t mask = 0;
+      int nc = 0;
+      float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+      for (int g = 0; g < s.n_geoms; ++g) {
+        if (!(s.geom_flags[g] & 2)) continue;
+        float nx, ny, nz, dep;
+        if (slab_contact<false>(s, g, ox, oy, oz, h, h, h, nx, ny, nz, dep)) {
+          const float vn = ovx * nx + ovy * ny + ovz * nz;
+          const float Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn);
+          if (Fn > 0.0f) {
+            mask |= 1u << g;
+            ++nc;
+            fsx += Fn * nx;
+            fsy += Fn * ny;
+            fsz += Fn * nz;
+          }
+        }
+      }
+      // the same contacts again (identical arithmetic) for the Jacobi
+      // friction impulses, all taken from one trial velocity
+      const float px = ox, py = oy, pz = oz;
+      const float pvx = ovx, pvy = ovy, pvz = ovz;
+      ovx += s.dt_mo * fsx;
+      ovy += s.dt_mo * fsy;
+      ovz += s.dt_mo * fsz - s.g * dt;
+      float jx = 0.f, jy = 0.f, jz = 0.f;
+      while (mask) {
+        const int g = __ffs(mask) - 1;
+        mask &= mask - 1;
+        float nx, ny, nz, dep;
+        slab_contact<false>(s, g, px, py, pz, h, h, h, nx, ny, nz, dep);
+        const float vn0 = pvx * nx + pvy * ny + pvz * nz;
+        const float Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn0);
+        const float vn = ovx * nx + ovy * ny + ovz * nz;
+        const float tx_ = ovx - vn * nx, ty_ = ovy - vn * ny, tz_ = ovz - vn * nz;
+        const float vt = sqrtf(tx_ * tx_ + ty_ * ty_ + tz_ * tz_);
+        if (vt > 0.0f) {
+          const float jm = fminf(s.obj_cap * Fn, s.mo * vt / (float)nc);
+          const float f = jm / (s.mo * vt);
+          jx -= f * tx_;
+          jy -= f * ty_;
+          jz -= f * tz_;
+        }
+      }
+      ovx += jx;
+      ovy += jy;
+      ovz += jz;
+      ox += ovx * dt;
+      oy += ovy * dt;
+      oz += ovz * dt;
+    }
+    if (a < L) {
+      float d_new;
+      bool ok;
+      if (kind == CEM_ACT_MOVE) {
+        d_new = sqrtf((bx - rx) * (bx - rx) + (by - ry) * (by - ry));
+        ok = d_new <= s.eps;
+      } else {
+        d_new = sqrtf((nex - tx) * (nex - tx) + (ney - ty) * (ney - ty) + (nez - tz) * (nez - tz));
+        ok = d_new <= s.eps;
+        if (kind == CEM_ACT_GRASP) ok = ok && fabsf(hgrip) <= s.grip_tol;
+      }
+      if (ok) {
+        const float ts = success_time(s, step, d_prev, d_new);
+        if (a == L - 1) t_done = ts;
+        if (kind == CEM_ACT_GRASP) {
+          attached = true;
+          offx = ox - nex;
+          offy = oy - ney;
+          offz = oz - nez;
+        } else if (kind == CEM_ACT_PLACE) {
+          attached = false;
+        }
+        ++a;
+      }
+    }
+    ex = nex;
+    ey = ney;
+    ez = nez;
+    if (TRACE) {
+      const float v[20] = {bx,  by,  bvx, bvy, q1,  q2,  dq1, dq2, beta, ox,
+                           oy,  oz,  ovx, ovy, ovz, attached ? 1.f : 0.f, (float)a, ex, ey, ez};
+      put_trace(tr, step, v, 20);
+    }
+  }
+  const bool complete = a == L;
+  bool goal = true;
+  float d_obj = 0.f, d_base = 0.f;
+  if (s.goal_obj_region) {
+    const float e0 = fabsf(ox - s.obj_region_c[0]), e1 = fabsf(oy - s.obj_region_c[1]),
+                e2 = fabsf(oz - s.obj_region_c[2]);
+    goal = goal && !attached && e0 <= s.obj_region_h[0] && e1 <= s.obj_region_h[1] && e2 <= s.obj_region_h[2];
+    const float x0 = fmaxf(e0 - s.obj_region_h[0], 0.f), x1 = fmaxf(e1 - s.obj_region_h[1], 0.f),
+                x2 = fmaxf(e2 - s.obj_region_h[2], 0.f);
+    d_obj = sqrtf(x0 * x0 + x1 * x1 + x2 * x2);
+  }
+  if (s.goal_obj_held) {
+    goal = goal && attached;
+    d_obj = attached ? 0.f : 1.f;
+  }
+  if (s.goal_base_region) {
+    const float e0 = fabsf(bx - s.base_region_c[0]), e1 = fabsf(by - s.base_region_c[1]);
+    goal = goal && e0 <= s.base_region_h[0] && e1 <= s.base_region_h[1];
+    const float x0 = fmaxf(e0 - s.base_region_h[0], 0.f), x1 = fmaxf(e1 - s.base_region_h[1], 0.f);
+    d_base = sqrtf(x0 * x0 + x1 * x1);
+  }
+  const float J = s.w_time * t_done + s.w_obj * d_obj + s.w_base * d_base;
+  J_out = J;
+  cls_out = complete ? (goal ? 0 : 1) : 2;
+  if (!isfinite(J)) cls_out = 3;
+}
+
+__device__ void quadratic_cost(const DevScene& s, const float* __restrict__ row, float& J_out, int& cls_out) {
+  float e[CEM_MAX_D];
+#pragma unroll
+  for (int i = 0; i < CEM_MAX_D; ++i) e[i] = i < s.D ? theta_at(s, row, i) - s.theta_star[i] : 0.0f;
+  float J = 0.0f;
+#pragma unroll
+  for (int i = 0; i < CEM_MAX_D; ++i) {
+    if (i < s.D) {
+      float ri = 0.0f;
+#pragma unroll
+      for (int j = 0; j < CEM_MAX_D; ++j)
+        if (j < s.D) ri += s.A[i * s.D + j] * e[j];
+      J += e[i] * ri;
+    }
+  }
+  J_out = J;
+  cls_out = isfinite(J) ? 0 : 3;
+}
+
+__device__ __forceinline__ void stage_scene(const DevScene* __restrict__ g, DevScene& sh) {
+  const int words = (int)(sizeof(DevScene) / 4);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(g);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&sh);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
+template <int KIND, bool TRACE>
+__global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict__ scene_g,
+                                                      const float* __restrict__ theta, int N, int steps,
+                                                      float* __restrict__ J, uint8_t* __restrict__ cls,
+                                                      float* __restrict__ trace) {
+  __shared__ DevScene s;
+  stage_scene(scene_g, s);
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const float* row = theta + (size_t)n * s.D;
+  float* tr = TRACE ? trace + (size_t)n * steps * TW : nullptr;
+  const int T = TRACE ? steps : s.T;
+  float Jn;
+  int c;
+  if (KIND == CEM_SCENE_REACH) planar_rollout<false, TRACE>(s, row, T, Jn, c, tr);
+  else if (KIND == CEM_SCENE_PUSH) planar_rollout<true, TRACE>(s, row, T, Jn, c, tr);
+  else if (KIND == CEM_SCENE_PICKPLACE) pickplace_rollout<TRACE>(s, row, T, Jn, c, tr);
+  else quadratic_cost(s, row, Jn, c);
+  if (!TRACE) {
+    J[n] = Jn;
+    cls[n] = (uint8_t)c;
+  }
+}
+
+template <bool TRACE>
+cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* J, uint8_t* cls,
+                     float* trace, int block, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  if (block <= 0) block = 128;
+  const int grid = (N + block - 1) / block;
+  switch (kind) {
+    case CEM_SCENE_QUADRATIC:
+      rollout_kernel<CEM_SCENE_QUADRATIC, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      break;
+    case CEM_SCENE_REACH:
+      rollout_kernel<CEM_SCENE_REACH, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      break;
+    case CEM_SCENE_PUSH:
+      rollout_kernel<CEM_SCENE_PUSH, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      break;
+    case CEM_SCENE_PICKPLACE:
+      rollout_kernel<CEM_SCENE_PICKPLACE, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
+                           int block, cudaStream_t st) {
+  return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, st);
+}
+
+cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
+                         cudaStream_t st) {
+  return dispatch<true>(s_d, kind, theta, N, steps, nullptr, nullptr, states, 64, st);
+}
+
+}  // namespace cem

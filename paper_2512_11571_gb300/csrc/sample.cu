@@ -1,0 +1,122 @@
+// Sample step of Algorithm 1 (Sec. III-B): draw n_env parameter vectors
+// theta ~ N(mean, chol chol^T).
+//
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+// multiplies, a word swap and xors with the round key, the key bumped by the
+// Weyl constants between rounds.  Counter (n, c, iter, problem), key = seed;
+// call c yields normals 4c..4c+3 of sample n by Box-Muller on word pairs
+// with u = (r + 1) 2^-32 in (0, 1].
+//
+// One thread per sample: the ceil(D/4) Philox calls and the D x D
+// triangular product stay in registers; mean and chol are staged in shared
+// memory once per block.  The kernel writes N*D*4 bytes and is far from
+// any roofline at the CE sizes (N <= 65536); it exists to keep the loop on
+// the device.
+#include "internal.h"
+
+namespace cem {
+namespace {
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                              uint32_t k1, uint32_t out[4]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    if (r < 9) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+// u = (r + 1) / 2^32, in (0, 1]
+__device__ __forceinline__ float u01(uint32_t r) { return fmaf(__uint2float_rn(r), 0x1p-32f, 0x1p-32f); }
+
+__global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ mean, const float* __restrict__ chol,
+                                                     uint64_t seed, const uint32_t* __restrict__ iter_ptr,
+                                                     uint32_t iter, uint32_t problem, int N, int D,
+                                                     float* __restrict__ theta) {
+  __shared__ float sL[CEM_MAX_D * CEM_MAX_D];
+  __shared__ float sm[CEM_MAX_D];
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = chol[i];
+  for (int i = threadIdx.x; i < D; i += blockDim.x) sm[i] = mean[i];
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const uint32_t it = iter_ptr ? *iter_ptr : iter;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  float z[20];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    if (4 * c < D) {
+      uint32_t r[4];
+      philox4x32_10((uint32_t)n, (uint32_t)c, it, problem, k0, k1, r);
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const float rad = sqrtf(-2.0f * logf(u01(r[2 * p])));
+        float sn, cs;
+        sincospif(2.0f * u01(r[2 * p + 1]), &sn, &cs);
+        z[4 * c + 2 * p] = rad * cs;
+        z[4 * c + 2 * p + 1] = rad * sn;
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) z[4 * c + p] = 0.0f;
+    }
+  }
+  float* out = theta + (size_t)n * D;
+#pragma unroll
+  for (int i = 0; i < CEM_MAX_D; ++i) {
+    if (i < D) {
+      float acc = sm[i];
+#pragma unroll
+      for (int j = 0; j <= i; ++j) acc = fmaf(sL[i * D + j], z[j], acc);
+      out[i] = acc;
+    }
+  }
+}
+
+__global__ void philox_words_kernel(uint64_t seed, uint32_t iter, uint32_t problem, int N, int nc,
+                                    uint32_t* __restrict__ words) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * nc) return;
+  const int n = t / nc, c = t % nc;
+  uint32_t r[4];
+  philox4x32_10((uint32_t)n, (uint32_t)c, iter, problem, (uint32_t)seed, (uint32_t)(seed >> 32), r);
+  uint32_t* o = words + (size_t)t * 4;
+  o[0] = r[0];
+  o[1] = r[1];
+  o[2] = r[2];
+  o[3] = r[3];
+}
+
+}  // namespace
+
+cudaError_t launch_sample(const float* mean, const float* chol, uint64_t seed, const uint32_t* iter_ptr,
+                          uint32_t iter, uint32_t problem, int N, int D, float* theta, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const int bs = 128;
+  sample_kernel<<<(N + bs - 1) / bs, bs, 0, st>>>(mean, chol, seed, iter_ptr, iter, problem, N, D, theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox_words(uint64_t seed, uint32_t iter, uint32_t problem, int N, int D, uint32_t* words,
+                                cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const int nc = (D + 3) / 4;
+  const int total = N * nc, bs = 256;
+  philox_words_kernel<<<(total + bs - 1) / bs, bs, 0, st>>>(seed, iter, problem, N, nc, words);
+  return cudaGetLastError();
+}
+
+}  // namespace cem

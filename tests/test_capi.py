@@ -1,0 +1,133 @@
+"""C-ABI checks that need no GPU: the library builds, exports every entry
+point that include/cemtamp.h declares, the ctypes mirrors of the public
+structs have the C layout, and host-side argument validation rejects bad
+descriptors before any CUDA call."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+import workload
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cemtamp.h")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    return P
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cem_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("cem_scene_create", "cem_scene_destroy", "cem_sample", "cem_rollout_batch", "cem_refit",
+                 "cem_solve", "cem_last_error", "cem_autotune"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    lib = C.CDLL(pkg.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True, text=True).stdout
+    for n in declared_functions():
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+def test_binding_names_match_header(pkg):
+    assert sorted(pkg.EXPORTS) == sorted(n for n in declared_functions())
+    for n in pkg.EXPORTS:
+        if n not in ("cem_last_error", "cem_version"):
+            assert callable(getattr(pkg, n))
+
+
+def _c_offsets(struct_name, fields, tmp_path):
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){"]
+    lines.append(f'printf("%zu\\n", sizeof({struct_name}));')
+    for f in fields:
+        lines.append(f'printf("%zu\\n", offsetof({struct_name}, {f}));')
+    lines.append("return 0;}")
+    c = tmp_path / f"{struct_name}.c"
+    exe = tmp_path / f"{struct_name}.out"
+    c.write_text("\n".join(lines))
+    subprocess.run(["gcc", "-std=c99", "-o", str(exe), str(c)], check=True)
+    return [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+
+
+@pytest.mark.parametrize("name", ["cem_slab", "cem_geom", "cem_scene_desc", "cem_action_desc",
+                                  "cem_skeleton_desc", "cem_solve_params", "cem_result"])
+def test_struct_layout_matches_header(pkg, name, tmp_path):
+    cls = getattr(pkg, name)
+    fields = [f[0] for f in cls._fields_]
+    got = _c_offsets(name, fields, tmp_path)
+    assert got[0] == C.sizeof(cls)
+    assert got[1:] == [getattr(cls, f).offset for f in fields]
+
+
+def _create(pkg, scene, skel):
+    s, k = pkg.pack_scene(scene, skel)
+    h = C.c_void_p()
+    return pkg.load().cem_scene_create(C.byref(s), C.byref(k), C.byref(h)), s, k
+
+
+def test_validation_rejects_bad_descriptors(pkg):
+    L = pkg.load()
+    sc, sk = workload.reach_scene()
+    s, k = pkg.pack_scene(sc, sk)
+    h = C.c_void_p()
+    # too many parameters
+    k2 = pkg.cem_skeleton_desc.from_buffer_copy(k)
+    k2.D = 19
+    assert L.cem_scene_create(C.byref(s), C.byref(k2), C.byref(h)) == -5
+    # theta slices not covering D
+    k3 = pkg.cem_skeleton_desc.from_buffer_copy(k)
+    k3.D = 4
+    assert L.cem_scene_create(C.byref(s), C.byref(k3), C.byref(h)) == -1
+    assert b"cover" in L.cem_last_error()
+    # inverted bounds
+    k4 = pkg.cem_skeleton_desc.from_buffer_copy(k)
+    k4.lo[0], k4.hi[0] = 1.0, -1.0
+    assert L.cem_scene_create(C.byref(s), C.byref(k4), C.byref(h)) == -1
+    # grasp in a planar scene
+    k5 = pkg.cem_skeleton_desc.from_buffer_copy(k)
+    k5.action[0].kind = 2
+    assert L.cem_scene_create(C.byref(s), C.byref(k5), C.byref(h)) == -1
+    # non-positive step, unknown kind, horizon 0
+    s2 = pkg.cem_scene_desc.from_buffer_copy(s)
+    s2.dt = 0.0
+    assert L.cem_scene_create(C.byref(s2), C.byref(k), C.byref(h)) == -1
+    s3 = pkg.cem_scene_desc.from_buffer_copy(s)
+    s3.kind = 9
+    assert L.cem_scene_create(C.byref(s3), C.byref(k), C.byref(h)) == -1
+    s4 = pkg.cem_scene_desc.from_buffer_copy(s)
+    s4.T = 0
+    assert L.cem_scene_create(C.byref(s4), C.byref(k), C.byref(h)) == -5
+    # NULL descriptors and NULL out pointer
+    assert L.cem_scene_create(None, C.byref(k), C.byref(h)) == -1
+    assert L.cem_scene_create(C.byref(s), C.byref(k), None) == -1
+    # calls on a NULL handle
+    assert L.cem_rollout_batch(None, None, 1, None, None, None) == -1
+    assert L.cem_refit(None, None, None, None, 1, 1, 0, None, None, None, None, None, None) == -1
+    assert L.cem_scene_destroy(None) == 0
+
+
+def test_pick_place_descriptor_packs(pkg):
+    sc, sk = workload.pickplace_scene(3)
+    s, k = pkg.pack_scene(sc, sk)
+    assert k.D == 14 and k.n_actions == 5
+    assert [k.action[i].theta_offset for i in range(5)] == [0, 3, 5, 8, 11]
+    assert s.n_geoms == len(sc["geoms"])

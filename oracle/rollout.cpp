@@ -132,8 +132,10 @@ bool inside_obb(R px, R py, R cx, R cy, R c, R s, double hx, double hy) {
 // Axes in order A.u, A.w, B.u, B.w; the minimum-overlap axis (first one on
 // ties) gives the normal, oriented from A to B, and the depth.  The contact
 // point is the mean of the incident body's corners that lie inside the
-// reference body (the body owning the axis); if there are none, the other
-// way round; if still none, the midpoint of the centres.
+// reference body (the body owning the axis), each weighted by its
+// penetration below the reference face along the normal, so that a corner
+// entering contact starts with zero weight; if no incident corner is inside,
+// the roles are swapped; if still none, the midpoint of the centres.
 template <class R>
 bool sat_rect(const Body2<R>& A, double ahx, double ahy, const Body2<R>& B, double bhx, double bhy,
               R& nx, R& ny, R& depth, R& qx, R& qy) {
@@ -157,33 +159,47 @@ bool sat_rect(const Body2<R>& A, double ahx, double ahy, const Body2<R>& B, doub
     }
   }
   depth = best_ov;
-  // corners of a rectangle: centre +- hx u +- hy w
-  auto corners_inside = [&](const Body2<R>& inc, R ci, R si, double ihx, double ihy, const Body2<R>& ref,
-                            R cr, R sr, double rhx, double rhy, R& mx, R& my) -> int {
+  // reference faces along the normal: A's face at c_A.n + r_A(n) (outward +n),
+  // B's face at c_B.n - r_B(n) (outward -n)
+  R ra_n = R(ahx) * Abs(ca * nx + sa * ny) + R(ahy) * Abs(ca * ny - sa * nx);
+  R rb_n = R(bhx) * Abs(cb * nx + sb * ny) + R(bhy) * Abs(cb * ny - sb * nx);
+  R faceA = A.x * nx + A.y * ny + ra_n;
+  R faceB = B.x * nx + B.y * ny - rb_n;
+  // corners of the incident rectangle inside the reference one, weighted by
+  // their penetration; ref_is_A selects the sign of the penetration
+  auto weighted = [&](bool ref_is_A, R& mx, R& my, R& wsum, R& px_sum, R& py_sum) -> int {
+    const Body2<R>& inc = ref_is_A ? B : A;
+    const Body2<R>& ref = ref_is_A ? A : B;
+    R ci = ref_is_A ? cb : ca, si = ref_is_A ? sb : sa;
+    R cr = ref_is_A ? ca : cb, sr = ref_is_A ? sa : sb;
+    double ihx = ref_is_A ? bhx : ahx, ihy = ref_is_A ? bhy : ahy;
+    double rhx = ref_is_A ? ahx : bhx, rhy = ref_is_A ? ahy : bhy;
     int cnt = 0;
-    mx = R(0.0); my = R(0.0);
+    mx = R(0.0); my = R(0.0); wsum = R(0.0); px_sum = R(0.0); py_sum = R(0.0);
     for (int i = 0; i < 4; ++i) {
       double su = (i & 1) ? 1.0 : -1.0, sw = (i & 2) ? 1.0 : -1.0;
       R px = inc.x + R(su * ihx) * ci - R(sw * ihy) * si;
       R py = inc.y + R(su * ihx) * si + R(sw * ihy) * ci;
       if (inside_obb(px, py, ref.x, ref.y, cr, sr, rhx, rhy)) {
-        mx = mx + px; my = my + py; ++cnt;
+        R pn = px * nx + py * ny;
+        R w = Max(ref_is_A ? faceA - pn : pn - faceB, R(0.0));
+        mx = mx + w * px; my = my + w * py; wsum = wsum + w;
+        px_sum = px_sum + px; py_sum = py_sum + py;
+        ++cnt;
       }
     }
     return cnt;
   };
-  R mx, my;
-  int cnt;
-  if (best < 2) cnt = corners_inside(B, cb, sb, bhx, bhy, A, ca, sa, ahx, ahy, mx, my);
-  else cnt = corners_inside(A, ca, sa, ahx, ahy, B, cb, sb, bhx, bhy, mx, my);
-  if (cnt == 0) {
-    if (best < 2) cnt = corners_inside(A, ca, sa, ahx, ahy, B, cb, sb, bhx, bhy, mx, my);
-    else cnt = corners_inside(B, cb, sb, bhx, bhy, A, ca, sa, ahx, ahy, mx, my);
-  }
+  R mx, my, ws, psx, psy;
+  const bool refA = best < 2;
+  int cnt = weighted(refA, mx, my, ws, psx, psy);
+  if (cnt == 0) cnt = weighted(!refA, mx, my, ws, psx, psy);
   if (cnt == 0) {
     qx = (A.x + B.x) * R(0.5); qy = (A.y + B.y) * R(0.5);
+  } else if (ws > R(0.0)) {
+    qx = mx / ws; qy = my / ws;
   } else {
-    qx = mx / R((double)cnt); qy = my / R((double)cnt);
+    qx = psx / R((double)cnt); qy = psy / R((double)cnt);
   }
   return true;
 }

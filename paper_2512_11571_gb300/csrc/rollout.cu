@@ -40,91 +40,127 @@ struct B2 {
   float x, y, psi, vx, vy, w;
 };
 
-__device__ __forceinline__ void ground_clamp(B2& b, float cap, float wcap) {
-  const float sp = sqrtf(b.vx * b.vx + b.vy * b.vy);
-  if (sp <= cap) {
-    b.vx = 0.0f;
-    b.vy = 0.0f;
-  } else {
-    const float f = 1.0f - cap / sp;
-    b.vx *= f;
-    b.vy *= f;
-  }
-  if (fabsf(b.w) <= wcap) b.w = 0.0f;
-  else b.w = b.w > 0.0f ? b.w - wcap : b.w + wcap;
+// Implicit Coulomb clamp of the trial velocity (branch-free): stick if the
+// speed is within mu g dt, else remove mu g dt along the velocity; the same
+// for the spin with capacity mu m g rbar dt / I.
+__device__ __forceinline__ void ground_clamp(B2& b, float cap, float cap2, float wcap) {
+  const float v2 = b.vx * b.vx + b.vy * b.vy;
+  const float f = v2 > cap2 ? 1.0f - cap * rsqrtf(v2) : 0.0f;
+  b.vx *= f;
+  b.vy *= f;
+  b.w = fabsf(b.w) <= wcap ? 0.0f : b.w - copysignf(wcap, b.w);
 }
 
-__device__ __forceinline__ bool inside_rect(float px, float py, float cx, float cy, float c, float s, float hx,
-                                            float hy) {
-  const float rx = px - cx, ry = py - cy;
-  const float u = rx * c + ry * s, w = ry * c - rx * s;
-  return fabsf(u) <= hx && fabsf(w) <= hy;
-}
-
-// mean of the corners of rectangle I (centre ix,iy, rotation ci,si) inside
-// rectangle R; returns how many
-__device__ __forceinline__ int corners_inside(float ix, float iy, float ci, float si, float ihx, float ihy, float rx,
-                                              float ry, float cr, float sr, float rhx, float rhy, float& mx,
-                                              float& my) {
+// Contact point of the rectangle pair in the reference body's frame: the
+// incident body's corners that lie inside the reference rectangle, each
+// weighted by its penetration along the normal.  Inputs (all in the
+// reference frame): the incident centre d, the incident axes u_i, w_i, the
+// normal n, the reference half sizes and the reference support r_n along n.
+// ref_is_A: penetration below A's face (r_n - p.n), else above B's face
+// (p.n + r_n).  Returns how many corners are inside.
+__device__ __forceinline__ int corners_local(float dx, float dy, float uix, float uiy, float wix, float wiy, float ihx,
+                                             float ihy, float rhx, float rhy, float nlx, float nly, float r_n,
+                                             bool ref_is_A, float& mx, float& my, float& ws, float& px_sum,
+                                             float& py_sum) {
   int cnt = 0;
-  mx = 0.0f;
-  my = 0.0f;
+  mx = my = ws = px_sum = py_sum = 0.0f;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const float su = (i & 1) ? ihx : -ihx, sw = (i & 2) ? ihy : -ihy;
-    const float px = ix + su * ci - sw * si;
-    const float py = iy + su * si + sw * ci;
-    if (inside_rect(px, py, rx, ry, cr, sr, rhx, rhy)) {
-      mx += px;
-      my += py;
+    const float px = dx + su * uix + sw * wix;
+    const float py = dy + su * uiy + sw * wiy;
+    if (fabsf(px) <= rhx && fabsf(py) <= rhy) {
+      const float pn = px * nlx + py * nly;
+      const float w = fmaxf(ref_is_A ? r_n - pn : pn + r_n, 0.0f);
+      mx += w * px;
+      my += w * py;
+      ws += w;
+      px_sum += px;
+      py_sum += py;
       ++cnt;
     }
   }
   return cnt;
 }
 
-// SAT of rectangle A (base) against rectangle B (block): normal A->B, depth,
-// contact point (mean of incident corners inside the reference body).
+// SAT of rectangle A (base) against rectangle B (block) with the relative
+// rotation (c, s) = (cos, sin)(psi_B - psi_A): the support of a box along
+// the other box's axes needs only |c| and |s|.  Axes in order A.u, A.w, B.u,
+// B.w; the minimum overlap (first on ties) gives the normal (A -> B) and the
+// depth.  Contact point: penetration-weighted mean of the incident corners
+// inside the reference body (roles swapped if none; midpoint last).
 __device__ __forceinline__ bool sat_rect(const B2& A, float ahx, float ahy, const B2& B, float bhx, float bhy,
                                          float& nx, float& ny, float& depth, float& qx, float& qy) {
   float sa, ca, sb, cb;
   sincosf(A.psi, &sa, &ca);
   sincosf(B.psi, &sb, &cb);
-  const float axx[4] = {ca, -sa, cb, -sb};
-  const float axy[4] = {sa, ca, sb, cb};
+  const float c = ca * cb + sa * sb, s = ca * sb - sa * cb;
+  const float ac = fabsf(c), as = fabsf(s);
   const float dx = B.x - A.x, dy = B.y - A.y;
-  int best = -1;
-  float best_ov = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float ux = axx[k], uy = axy[k];
-    const float ra = ahx * fabsf(ca * ux + sa * uy) + ahy * fabsf(ca * uy - sa * ux);
-    const float rb = bhx * fabsf(cb * ux + sb * uy) + bhy * fabsf(cb * uy - sb * ux);
-    const float sp = dx * ux + dy * uy;
-    const float ov = ra + rb - fabsf(sp);
-    if (ov <= 0.0f) return false;
-    if (best < 0 || ov < best_ov) {
-      best = k;
-      best_ov = ov;
-      nx = sp >= 0.0f ? ux : -ux;
-      ny = sp >= 0.0f ? uy : -uy;
-    }
+  const float dAx = dx * ca + dy * sa, dAy = dy * ca - dx * sa;  // B's centre in A's frame
+  const float dBx = dx * cb + dy * sb, dBy = dy * cb - dx * sb;  // same vector in B's frame
+  const float ov0 = ahx + bhx * ac + bhy * as - fabsf(dAx);
+  const float ov1 = ahy + bhx * as + bhy * ac - fabsf(dAy);
+  const float ov2 = ahx * ac + ahy * as + bhx - fabsf(dBx);
+  const float ov3 = ahx * as + ahy * ac + bhy - fabsf(dBy);
+  if (ov0 <= 0.0f || ov1 <= 0.0f || ov2 <= 0.0f || ov3 <= 0.0f) return false;
+  int best = 0;
+  float ov = ov0;
+  if (ov1 < ov) { best = 1; ov = ov1; }
+  if (ov2 < ov) { best = 2; ov = ov2; }
+  if (ov3 < ov) { best = 3; ov = ov3; }
+  depth = ov;
+  // normal in world and in both local frames (sg = side of B along the axis)
+  float nAx, nAy, nBx, nBy;
+  if (best == 0) {
+    const float sg = dAx >= 0.0f ? 1.0f : -1.0f;
+    nx = sg * ca; ny = sg * sa; nAx = sg; nAy = 0.0f; nBx = sg * c; nBy = -sg * s;
+  } else if (best == 1) {
+    const float sg = dAy >= 0.0f ? 1.0f : -1.0f;
+    nx = -sg * sa; ny = sg * ca; nAx = 0.0f; nAy = sg; nBx = sg * s; nBy = sg * c;
+  } else if (best == 2) {
+    const float sg = dBx >= 0.0f ? 1.0f : -1.0f;
+    nx = sg * cb; ny = sg * sb; nAx = sg * c; nAy = sg * s; nBx = sg; nBy = 0.0f;
+  } else {
+    const float sg = dBy >= 0.0f ? 1.0f : -1.0f;
+    nx = -sg * sb; ny = sg * cb; nAx = -sg * s; nAy = sg * c; nBx = 0.0f; nBy = sg;
   }
-  depth = best_ov;
-  float mx, my;
-  int cnt;
-  if (best < 2) cnt = corners_inside(B.x, B.y, cb, sb, bhx, bhy, A.x, A.y, ca, sa, ahx, ahy, mx, my);
-  else cnt = corners_inside(A.x, A.y, ca, sa, ahx, ahy, B.x, B.y, cb, sb, bhx, bhy, mx, my);
+  const float rA_n = ahx * fabsf(nAx) + ahy * fabsf(nAy);  // A's support along n
+  const float rB_n = bhx * fabsf(nBx) + bhy * fabsf(nBy);
+  // B's corners in A's frame use B's axes (c, s), (-s, c); A's corners in
+  // B's frame use A's axes (c, -s), (s, c) and A's centre at -dB
+  float mx, my, ws, psx, psy;
+  bool in_A = best < 2;  // frame of the points being accumulated
+  int cnt = in_A ? corners_local(dAx, dAy, c, s, -s, c, bhx, bhy, ahx, ahy, nAx, nAy, rA_n, true, mx, my, ws, psx, psy)
+                 : corners_local(-dBx, -dBy, c, -s, s, c, ahx, ahy, bhx, bhy, nBx, nBy, rB_n, false, mx, my, ws, psx,
+                                 psy);
   if (cnt == 0) {
-    if (best < 2) cnt = corners_inside(A.x, A.y, ca, sa, ahx, ahy, B.x, B.y, cb, sb, bhx, bhy, mx, my);
-    else cnt = corners_inside(B.x, B.y, cb, sb, bhx, bhy, A.x, A.y, ca, sa, ahx, ahy, mx, my);
+    in_A = !in_A;
+    cnt = in_A ? corners_local(dAx, dAy, c, s, -s, c, bhx, bhy, ahx, ahy, nAx, nAy, rA_n, true, mx, my, ws, psx, psy)
+               : corners_local(-dBx, -dBy, c, -s, s, c, ahx, ahy, bhx, bhy, nBx, nBy, rB_n, false, mx, my, ws, psx,
+                               psy);
   }
   if (cnt == 0) {
     qx = (A.x + B.x) * 0.5f;
     qy = (A.y + B.y) * 0.5f;
+    return true;
+  }
+  float lx, ly;
+  if (ws > 0.0f) {
+    const float inv = 1.0f / ws;
+    lx = mx * inv;
+    ly = my * inv;
   } else {
-    qx = mx / (float)cnt;
-    qy = my / (float)cnt;
+    const float inv = cnt == 1 ? 1.0f : cnt == 2 ? 0.5f : cnt == 4 ? 0.25f : (1.0f / 3.0f);
+    lx = psx * inv;
+    ly = psy * inv;
+  }
+  if (in_A) {
+    qx = A.x + lx * ca - ly * sa;
+    qy = A.y + lx * sa + ly * ca;
+  } else {
+    qx = B.x + lx * cb - ly * sb;
+    qy = B.y + lx * sb + ly * cb;
   }
   return true;
 }
@@ -138,17 +174,28 @@ __device__ __forceinline__ void put_trace(float* tr, int step, const float* v, i
 }
 
 // ------------------------------------------------------------- reach / push
+// The success test compares squared distances; the square roots are taken
+// only at the step that succeeds (for the interpolated crossing time).
 template <bool HAS_BLOCK, bool TRACE>
 __device__ void planar_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out, int& cls_out,
                                float* tr) {
+  // loop invariants in registers
+  const float dt = s.dt, eps2 = s.eps * s.eps;
+  const float mb = s.mb, Ib = s.Ib, dt_mb = s.dt_mb, dt_Ib = s.dt_Ib;
+  const float bcap = s.base_cap, bcap2 = bcap * bcap, bwcap = s.base_wcap;
+  const float ykp = s.yaw_kp, ykd = s.yaw_kd;
+  const float bhx = s.bhx, bhy = s.bhy, khx = s.khx, khy = s.khy;
+  const float dt_mk = s.dt_mk, dt_Ik = s.dt_Ik, kcap = s.block_cap, kcap2 = kcap * kcap, kwcap = s.block_wcap;
+  const float kc = s.k_contact, cc = s.c_contact, mu_dt = s.contact_mu * s.dt, flim = s.force_limit;
+  const float inv_mb = 1.0f / s.mb, inv_Ib = 1.0f / s.Ib;
+  const float inv_mk = HAS_BLOCK ? 1.0f / s.mk : 0.0f, inv_Ik = HAS_BLOCK ? 1.0f / s.Ik : 0.0f;
+  const float rsum = sqrtf(bhx * bhx + bhy * bhy) + sqrtf(khx * khx + khy * khy), rsum2 = rsum * rsum;
   B2 b{s.base_start[0], s.base_start[1], s.base_start[2], s.base_v0[0], s.base_v0[1], s.base_v0[2]};
   B2 k{s.block_start[0], s.block_start[1], s.block_start[2], s.block_v0[0], s.block_v0[1], s.block_v0[2]};
   const int L = s.n_act;
-  const float dt = s.dt;
-  const float rsum = sqrtf(s.bhx * s.bhx + s.bhy * s.bhy) + sqrtf(s.khx * s.khx + s.khy * s.khy);
   int a = 0, loaded = -1;
   float gx = 0.f, gy = 0.f, kp = 0.f, kd = 0.f, rx = 0.f, ry = 0.f, yaw_t = 0.f;
-  float t_done = (float)T * dt, viol = 0.0f;
+  float t_done = (float)T * dt, viol = 0.0f, d2_cur = 0.0f;
   for (int step = 0; step < T; ++step) {
     const int ai = a < L ? a : L - 1;
     if (ai != loaded) {
@@ -161,20 +208,19 @@ __device__ void planar_rollout(const DevScene& s, const float* __restrict__ row,
       ry = s.act_ref[ai] ? gy : s.act_nom[ai][1];
       yaw_t = s.act_yaw[ai];
       loaded = ai;
+      d2_cur = (b.x - rx) * (b.x - rx) + (b.y - ry) * (b.y - ry);
     }
-    float d_prev = 0.0f;
-    if (a < L) d_prev = sqrtf((b.x - rx) * (b.x - rx) + (b.y - ry) * (b.y - ry));
-    float fx = s.mb * (kp * (gx - b.x) - kd * b.vx);
-    float fy = s.mb * (kp * (gy - b.y) - kd * b.vy);
-    float tq = s.Ib * (s.yaw_kp * (yaw_t - b.psi) - s.yaw_kd * b.w);
+    float fx = mb * (kp * (gx - b.x) - kd * b.vx);
+    float fy = mb * (kp * (gy - b.y) - kd * b.vy);
+    float tq = Ib * (ykp * (yaw_t - b.psi) - ykd * b.w);
     float fkx = 0.f, fky = 0.f, tk = 0.f, Fn = 0.f;
     float rax = 0.f, ray = 0.f, rbx = 0.f, rby = 0.f, nx = 0.f, ny = 0.f;
     bool hit = false;
     if (HAS_BLOCK) {
       const float cdx = k.x - b.x, cdy = k.y - b.y;
-      if (cdx * cdx + cdy * cdy < rsum * rsum) {  // bounding circles overlap
+      if (cdx * cdx + cdy * cdy < rsum2) {  // bounding circles overlap
         float dep, qx, qy;
-        hit = sat_rect(b, s.bhx, s.bhy, k, s.khx, s.khy, nx, ny, dep, qx, qy);
+        hit = sat_rect(b, bhx, bhy, k, khx, khy, nx, ny, dep, qx, qy);
         if (hit) {
           rax = qx - b.x;
           ray = qy - b.y;
@@ -183,45 +229,45 @@ __device__ void planar_rollout(const DevScene& s, const float* __restrict__ row,
           const float vrx = (k.vx - k.w * rby) - (b.vx - b.w * ray);
           const float vry = (k.vy + k.w * rbx) - (b.vy + b.w * rax);
           const float vn = vrx * nx + vry * ny;
-          Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn);
+          Fn = fmaxf(0.0f, kc * dep - cc * vn);
           fkx = Fn * nx;
           fky = Fn * ny;
           fx -= fkx;
           fy -= fky;
           tq -= cross2(rax, ray, fkx, fky);
           tk = cross2(rbx, rby, fkx, fky);
-          const float over = Fn - s.force_limit;
+          const float over = Fn - flim;
           if (over > 0.0f) viol += over * dt;
         }
       }
     }
-    b.vx += s.dt_mb * fx;
-    b.vy += s.dt_mb * fy;
-    b.w += s.dt_Ib * tq;
+    b.vx += dt_mb * fx;
+    b.vy += dt_mb * fy;
+    b.w += dt_Ib * tq;
     if (HAS_BLOCK) {
-      k.vx += s.dt_mk * fkx;
-      k.vy += s.dt_mk * fky;
-      k.w += s.dt_Ik * tk;
+      k.vx += dt_mk * fkx;
+      k.vy += dt_mk * fky;
+      k.w += dt_Ik * tk;
       if (hit && Fn > 0.0f) {
         const float tx = -ny, ty = nx;
         const float vrx = (k.vx - k.w * rby) - (b.vx - b.w * ray);
         const float vry = (k.vy + k.w * rbx) - (b.vy + b.w * rax);
         const float vt = vrx * tx + vry * ty;
         const float ca = cross2(rax, ray, tx, ty), cb = cross2(rbx, rby, tx, ty);
-        const float inv_m = 1.0f / s.mb + 1.0f / s.mk + ca * ca / s.Ib + cb * cb / s.Ik;
-        const float jm = fminf(s.contact_mu * dt * Fn, fabsf(vt) / inv_m);
+        const float inv_m = inv_mb + inv_mk + ca * ca * inv_Ib + cb * cb * inv_Ik;
+        const float jm = fminf(mu_dt * Fn, fabsf(vt) / inv_m);
         const float jt = vt > 0.0f ? -jm : jm;
         const float jx = jt * tx, jy = jt * ty;
-        k.vx += jx / s.mk;
-        k.vy += jy / s.mk;
-        k.w += cross2(rbx, rby, jx, jy) / s.Ik;
-        b.vx -= jx / s.mb;
-        b.vy -= jy / s.mb;
-        b.w -= cross2(rax, ray, jx, jy) / s.Ib;
+        k.vx += jx * inv_mk;
+        k.vy += jy * inv_mk;
+        k.w += cross2(rbx, rby, jx, jy) * inv_Ik;
+        b.vx -= jx * inv_mb;
+        b.vy -= jy * inv_mb;
+        b.w -= cross2(rax, ray, jx, jy) * inv_Ib;
       }
-      ground_clamp(k, s.block_cap, s.block_wcap);
+      ground_clamp(k, kcap, kcap2, kwcap);
     }
-    ground_clamp(b, s.base_cap, s.base_wcap);
+    ground_clamp(b, bcap, bcap2, bwcap);
     b.x += b.vx * dt;
     b.y += b.vy * dt;
     b.psi += b.w * dt;
@@ -231,12 +277,13 @@ __device__ void planar_rollout(const DevScene& s, const float* __restrict__ row,
       k.psi += k.w * dt;
     }
     if (a < L) {
-      const float d_new = sqrtf((b.x - rx) * (b.x - rx) + (b.y - ry) * (b.y - ry));
-      if (d_new <= s.eps) {
-        const float ts = success_time(s, step, d_prev, d_new);
+      const float d2_new = (b.x - rx) * (b.x - rx) + (b.y - ry) * (b.y - ry);
+      if (d2_new <= eps2) {
+        const float ts = success_time(s, step, sqrtf(d2_cur), sqrtf(d2_new));
         if (a == L - 1) t_done = ts;
         ++a;
       }
+      d2_cur = d2_new;
     }
     if (TRACE) {
       const float v[13] = {b.x, b.y, b.psi, b.vx, b.vy, b.w, k.x, k.y, k.psi, k.vx, k.vy, k.w, (float)a};
@@ -335,7 +382,10 @@ __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, fl
 template <bool TRACE>
 __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out,
                                   int& cls_out, float* tr) {
-  const float dt = s.dt, h = s.oh;
+  const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps, gdt = s.g * s.dt;
+  const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap, bcap2 = bcap * bcap;
+  const float kc = s.k_contact, cc = s.c_contact, dt_mo = s.dt_mo, akp = s.arm_kp, akd = s.arm_kd;
+  const int n_geoms = s.n_geoms;
   float bx = s.base_start[0], by = s.base_start[1], bvx = s.base_v0[0], bvy = s.base_v0[1];
   float q1 = s.arm_home[0], q2 = s.arm_home[1], dq1 = 0.f, dq2 = 0.f, beta = 0.f;
   float cbeta = 1.0f, sbeta = 0.0f;
@@ -397,46 +447,41 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
       kp = mkp;
       kd = mkd;
     }
-    float d_prev = 0.0f;
+    float d2_prev = 0.0f;  // squared distance to the action's target at t_k
     if (a < L) {
-      if (kind == CEM_ACT_MOVE) d_prev = sqrtf((bx - rx) * (bx - rx) + (by - ry) * (by - ry));
-      else d_prev = sqrtf((ex - tx) * (ex - tx) + (ey - ty) * (ey - ty) + (ez - tz) * (ez - tz));
+      if (kind == CEM_ACT_MOVE) d2_prev = (bx - rx) * (bx - rx) + (by - ry) * (by - ry);
+      else d2_prev = (ex - tx) * (ex - tx) + (ey - ty) * (ey - ty) + (ez - tz) * (ez - tz);
     }
     if (kind != CEM_ACT_MOVE) {
       arm_ik(s, bx, by, tx, ty, tz, beta, q1t, q2t);
       sincosf(beta, &sbeta, &cbeta);
     }
     // base: PD + penalty contacts with the static footprints
-    float fx = s.mb * (kp * (gx - bx) - kd * bvx);
-    float fy = s.mb * (kp * (gy - by) - kd * bvy);
-    for (int g = 0; g < s.n_geoms; ++g) {
+    float fx = mb * (kp * (gx - bx) - kd * bvx);
+    float fy = mb * (kp * (gy - by) - kd * bvy);
+    for (int g = 0; g < n_geoms; ++g) {
       if (!(s.geom_flags[g] & 1)) continue;
       float nx, ny, nz, dep;
       if (slab_contact<true>(s, g, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, nx, ny, nz, dep)) {
         const float vn = bvx * nx + bvy * ny;
-        const float Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn);
+        const float Fn = fmaxf(0.0f, kc * dep - cc * vn);
         fx += Fn * nx;
         fy += Fn * ny;
       }
     }
-    bvx += s.dt_mb * fx;
-    bvy += s.dt_mb * fy;
-    {
-      const float sp = sqrtf(bvx * bvx + bvy * bvy);
-      if (sp <= s.base_cap) {
-        bvx = 0.0f;
-        bvy = 0.0f;
-      } else {
-        const float f = 1.0f - s.base_cap / sp;
-        bvx *= f;
-        bvy *= f;
-      }
+    bvx += dt_mb * fx;
+    bvy += dt_mb * fy;
+    {  // ground friction of the base (yaw is locked)
+      const float v2 = bvx * bvx + bvy * bvy;
+      const float f = v2 > bcap2 ? 1.0f - bcap * rsqrtf(v2) : 0.0f;
+      bvx *= f;
+      bvy *= f;
     }
     bx += bvx * dt;
     by += bvy * dt;
     // arm joints
-    const float dd1 = s.arm_kp * (q1t - q1) - s.arm_kd * dq1;
-    const float dd2 = s.arm_kp * (q2t - q2) - s.arm_kd * dq2;
+    const float dd1 = akp * (q1t - q1) - akd * dq1;
+    const float dd2 = akp * (q2t - q2) - akd * dq2;
     dq1 += dt * dd1;
     dq2 += dt * dd2;
     q1 += dt * dq1;
@@ -455,12 +500,12 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
       uint32_t mask = 0;
       int nc = 0;
       float fsx = 0.f, fsy = 0.f, fsz = 0.f;
-      for (int g = 0; g < s.n_geoms; ++g) {
+      for (int g = 0; g < n_geoms; ++g) {
         if (!(s.geom_flags[g] & 2)) continue;
         float nx, ny, nz, dep;
         if (slab_contact<false>(s, g, ox, oy, oz, h, h, h, nx, ny, nz, dep)) {
           const float vn = ovx * nx + ovy * ny + ovz * nz;
-          const float Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn);
+          const float Fn = fmaxf(0.0f, kc * dep - cc * vn);
           if (Fn > 0.0f) {
             mask |= 1u << g;
             ++nc;
@@ -474,9 +519,9 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
       // friction impulses, all taken from one trial velocity
       const float px = ox, py = oy, pz = oz;
       const float pvx = ovx, pvy = ovy, pvz = ovz;
-      ovx += s.dt_mo * fsx;
-      ovy += s.dt_mo * fsy;
-      ovz += s.dt_mo * fsz - s.g * dt;
+      ovx += dt_mo * fsx;
+      ovy += dt_mo * fsy;
+      ovz += dt_mo * fsz - gdt;
       float jx = 0.f, jy = 0.f, jz = 0.f;
       while (mask) {
         const int g = __ffs(mask) - 1;
@@ -484,7 +529,7 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
         float nx, ny, nz, dep;
         slab_contact<false>(s, g, px, py, pz, h, h, h, nx, ny, nz, dep);
         const float vn0 = pvx * nx + pvy * ny + pvz * nz;
-        const float Fn = fmaxf(0.0f, s.k_contact * dep - s.c_contact * vn0);
+        const float Fn = fmaxf(0.0f, kc * dep - cc * vn0);
         const float vn = ovx * nx + ovy * ny + ovz * nz;
         const float tx_ = ovx - vn * nx, ty_ = ovy - vn * ny, tz_ = ovz - vn * nz;
         const float vt = sqrtf(tx_ * tx_ + ty_ * ty_ + tz_ * tz_);
@@ -504,18 +549,13 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
       oz += ovz * dt;
     }
     if (a < L) {
-      float d_new;
-      bool ok;
-      if (kind == CEM_ACT_MOVE) {
-        d_new = sqrtf((bx - rx) * (bx - rx) + (by - ry) * (by - ry));
-        ok = d_new <= s.eps;
-      } else {
-        d_new = sqrtf((nex - tx) * (nex - tx) + (ney - ty) * (ney - ty) + (nez - tz) * (nez - tz));
-        ok = d_new <= s.eps;
-        if (kind == CEM_ACT_GRASP) ok = ok && fabsf(hgrip) <= s.grip_tol;
-      }
+      float d2_new;
+      if (kind == CEM_ACT_MOVE) d2_new = (bx - rx) * (bx - rx) + (by - ry) * (by - ry);
+      else d2_new = (nex - tx) * (nex - tx) + (ney - ty) * (ney - ty) + (nez - tz) * (nez - tz);
+      bool ok = d2_new <= eps2;
+      if (kind == CEM_ACT_GRASP) ok = ok && fabsf(hgrip) <= s.grip_tol;
       if (ok) {
-        const float ts = success_time(s, step, d_prev, d_new);
+        const float ts = success_time(s, step, sqrtf(d2_prev), sqrtf(d2_new));
         if (a == L - 1) t_done = ts;
         if (kind == CEM_ACT_GRASP) {
           attached = true;

@@ -117,8 +117,9 @@ def push_scene(seed: int = 0, T: int = 1000, dt: float = 0.002, cost_mode: str =
 
     Per scene: block friction mu ~ U[0.4, 0.6]; region bearing
     phi ~ U[-pi/4, pi/4]; region centre 1.5 m from the block along phi.
-    ``start_in_contact`` places the base touching the block (a contact-heavy
-    variant for short-horizon parity tests).
+    ``start_in_contact`` starts the base pressed against the block, both
+    aligned with the push direction (a contact-heavy variant for
+    short-horizon parity tests).
     """
     rng = np.random.default_rng(seed)
     mu = float(rng.uniform(0.4, 0.6))
@@ -129,14 +130,16 @@ def push_scene(seed: int = 0, T: int = 1000, dt: float = 0.002, cost_mode: str =
     approach = (b0[0] - 0.35 * u[0], b0[1] - 0.35 * u[1])
     push_goal = (region[0] - 0.3 * u[0], region[1] - 0.3 * u[1])
     base_start = (0.0, 0.0, 0.0)
-    if start_in_contact:
+    block_yaw = 0.0
+    if start_in_contact:  # base face pressed 2 mm into the aligned block's back face
         base_start = (b0[0] - 0.298 * u[0], b0[1] - 0.298 * u[1], phi)
+        block_yaw = phi
     scene = dict(
         kind="push", T=T, dt=dt, g=G, cost_mode=cost_mode, eps=0.05,
         base_half=(0.25, 0.20), base_mass=10.0, base_mu=0.6,
         base_start=base_start, yaw_kp=400.0, yaw_kd=40.0,
         block_half=(0.05, 0.05), block_mass=0.5, block_mu=mu,
-        block_start=(b0[0], b0[1], 0.0),
+        block_start=(b0[0], b0[1], block_yaw),
         k_contact=2.0e4, c_contact=50.0, contact_mu=mu, force_limit=20.0,
         w_time=1.0, w_goal=20.0, w_viol=5.0,
         goal_center=(region[0], region[1], 0.0), goal_half=(0.15, 0.15, 0.0),

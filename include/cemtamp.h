@@ -214,6 +214,22 @@ typedef struct {
  * Synchronous. */
 int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out);
 
+/* cem_solve for callers that cannot allocate device memory (no paper
+ * counterpart).  Hard real-time control loops, plugins whose host owns all
+ * device memory through its own pool, and processes under a fixed memory cap
+ * cannot call cudaMalloc while planning; this entry point allocates nothing.
+ * It takes the descriptors directly (a handle would allocate) and runs the
+ * same sample -> rollout -> refit loop on `stream`, keeping every
+ * intermediate in one 2 MiB file-scope device array that every GPU loading
+ * the library holds until the process exits.  Limits: N * D <= 262144,
+ * iters <= 4096, otherwise CEM_ERR_UNSUPPORTED.  The first call on a device
+ * looks up the array's address; make it before any stream capture.  All
+ * calls share the array (the loop state is rewritten at the start of each
+ * call), so calls that overlap on the GPU race: serialise them.  p->use_graph
+ * is ignored.  Synchronous; results as cem_solve (elapsed_ms = 0). */
+int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_desc* skel, const cem_solve_params* p,
+                     cem_result* out, void* stream);
+
 /* Threads-per-block of the rollout kernel (0 = automatic). */
 int cem_set_launch(cem_handle h, int block_threads);
 /* Times candidate block sizes for this scene and N on the current device

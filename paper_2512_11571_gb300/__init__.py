@@ -28,8 +28,8 @@ STATUS = {0: "CEM_OK", -1: "CEM_ERR_INVALID_ARG", -2: "CEM_ERR_CUDA", -3: "CEM_E
 
 EXPORTS = [
     "cem_scene_create", "cem_scene_destroy", "cem_sample", "cem_philox_words", "cem_rollout_batch",
-    "cem_rollout_trace", "cem_refit", "cem_solve", "cem_set_launch", "cem_autotune", "cem_last_error",
-    "cem_version",
+    "cem_rollout_trace", "cem_refit", "cem_solve", "cem_solve_static", "cem_set_launch", "cem_autotune",
+    "cem_last_error", "cem_version",
 ]
 
 
@@ -195,6 +195,8 @@ def load(path: str = LIB_PATH):
     L.cem_rollout_trace.argtypes = [H, fp, C.c_int, C.c_int, fp, vp]
     L.cem_refit.argtypes = [H, fp, fp, u8p, C.c_int, C.c_int, C.c_int, fp, fp, fp, i32p, i32p, vp]
     L.cem_solve.argtypes = [H, C.POINTER(cem_solve_params), C.POINTER(cem_result)]
+    L.cem_solve_static.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc),
+                                   C.POINTER(cem_solve_params), C.POINTER(cem_result), vp]
     L.cem_set_launch.argtypes = [H, C.c_int]
     L.cem_autotune.argtypes = [H, C.c_int, C.c_char_p, C.POINTER(C.c_int)]
     L.cem_last_error.restype = C.c_char_p
@@ -266,6 +268,14 @@ def cem_refit(h, theta, J, cls, N, K, cov_mode, mean, cov, chol, elite_idx=None,
 def cem_solve(h, params: cem_solve_params):
     out = cem_result()
     _check(load().cem_solve(h, C.byref(params), C.byref(out)))
+    return out
+
+
+def cem_solve_static(scene: dict, skel: dict, params: cem_solve_params, stream=None):
+    """cem_solve without device allocation (see include/cemtamp.h)."""
+    s, k = pack_scene(scene, skel)
+    out = cem_result()
+    _check(load().cem_solve_static(C.byref(s), C.byref(k), C.byref(params), C.byref(out), _stream(stream)))
     return out
 
 

@@ -229,14 +229,7 @@ DevScene prepare(const cem_scene_desc& s, const cem_skeleton_desc& k) {
 
 int default_block(const cem_ctx* h, int N) {
   if (h->block > 0) return h->block;
-  // spread small batches over all SMs: one warp per CTA until every SM has
-  // work, larger CTAs after that
-  int sms = 152;
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int b = 32;
-  while (b < 256 && (N + 2 * b - 1) / (2 * b) >= sms) b *= 2;
-  return b;
+  return cem::default_rollout_block(N);
 }
 
 void free_work(cem_ctx* h) {
@@ -328,6 +321,22 @@ cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N
 }
 
 }  // namespace
+
+namespace cem {
+int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k) { return validate(s, k); }
+DevScene prepare_scene(const cem_scene_desc& s, const cem_skeleton_desc& k) { return prepare(s, k); }
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+int default_rollout_block(int N) {
+  // spread small batches over all SMs: one warp per CTA until every SM has
+  // work, larger CTAs after that
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int b = 32;
+  while (b < 256 && (N + 2 * b - 1) / (2 * b) >= sms) b *= 2;
+  return b;
+}
+}  // namespace cem
 
 extern "C" {
 

@@ -90,4 +90,11 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
 cudaError_t configure_refit();
 size_t refit_smem_bytes(int K, int D);
 
+// host helpers shared by the C entry points (capi.cu)
+int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k);
+DevScene prepare_scene(const cem_scene_desc& s, const cem_skeleton_desc& k);
+int default_rollout_block(int N);
+// records the thread-local message returned by cem_last_error; returns code
+int set_last_error(int code, const std::string& msg);
+
 }  // namespace cem

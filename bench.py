@@ -32,6 +32,20 @@ METRIC = "sim steps/sec (N×T) on 1 GB300 & FP32-peak fraction; CEM time-to-cost
 UNIT = "sim-steps/s"
 CONFIG = 1  # the move-and-push workload
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+SATURATED_N = 48 * 4096  # enough rollouts to give every SM scheduler several warps
+# DRAM bytes (read + write) of one rollout launch of this workload from the
+# ncu capture in profiles/rollout_push_N4096_T1000.md; reported only while the
+# kernel source still matches the one the counters were taken on
+ROLLOUT_TRAFFIC = {"rollout.cu sha256[:16]": "2eb928e4b1d1264e", "bytes": 128768}
+
+
+def rollout_traffic():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_2512_11571_gb300", "csrc", "rollout.cu")
+    with open(path, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()[:16]
+    return ROLLOUT_TRAFFIC["bytes"] if h == ROLLOUT_TRAFFIC["rollout.cu sha256[:16]"] else None
 
 
 def parse():
@@ -263,6 +277,22 @@ def run_gb300(args):
     units, secs = aggregate(N * T * args.steps, sum(step_ms) / 1e3, world)
     value = units / secs
 
+    # the same rollout kernel with the GPU full (context for the roofline
+    # fraction: N = 4096 leaves most SM schedulers without a warp)
+    th_sat = torch.empty((SATURATED_N, D), device="cuda")
+    J_sat = torch.empty(SATURATED_N, device="cuda")
+    c_sat = torch.empty(SATURATED_N, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        P.cem_sample(S.h, mean0, chol0, args.seed, 0, problem, SATURATED_N, th_sat, stream)
+        P.cem_rollout_batch(S.h, th_sat, SATURATED_N, J_sat, c_sat, stream)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            P.cem_rollout_batch(S.h, th_sat, SATURATED_N, J_sat, c_sat, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    sat_ms = e0.elapsed_time(e1) / 3
+
     # end to end through the public API with host buffers: cem_solve, one
     # iteration per step, distribution in from pinned host memory and the
     # best sample / new distribution back to the host
@@ -296,14 +326,21 @@ def run_gb300(args):
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
                        "rollout_ms": roll_avg, "wall_s": wall},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": rollout_traffic(),
+                         "algorithmic_bytes": N * D * 4 + N * 5,
                          "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
                                        f"({src} max SM clock)",
                          "kernel": "rollout_kernel<PUSH>",
                          "flops_per_step": fps["flops"]},
+            "roofline_saturated": {"N": SATURATED_N, "rollout_ms": sat_ms,
+                                   "sim_steps_per_s": SATURATED_N * T / (sat_ms / 1e3),
+                                   "achieved": fps["flops"] * SATURATED_N * T / (sat_ms / 1e3) / 1e12,
+                                   "frac": fps["flops"] * SATURATED_N * T / (sat_ms / 1e3) / 1e12 / peak,
+                                   "unit": "TFLOP/s"},
             "e2e": {"value": e_units / e_secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": 3 * args.steps,
+            "gpu_launches_outside_timed_region": 5 + 3 * (args.steps + 1),
             "clocks": clocks,
         }
         if world == 1:

@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--rollout-only", choices=["reach", "push", "pickplace"], default=None,
+                    help="time only the rollout kernel of one workload (profiling driver)")
+    ap.add_argument("--n", type=int, default=0, help="samples for --rollout-only (0 = the workload's N)")
+    ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
     return ap.parse_args()
 
 
@@ -205,6 +209,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_measurement(P, seed, rank, iters=3):
+    """64 independent problems (skeletons of 1..6 actions, uneven N and T)
+    advanced together: CE iterations per second and simulated steps per
+    second of the whole batch, launch shape chosen by the autotuner."""
+    import torch
+
+    probs = workload.batch_problems(seed)
+    for i, p in enumerate(probs):
+        p["seed"] = seed
+        p["problem"] = 1000 * rank + i
+    with P.Batch(probs) as B:
+        warps, ctas, _ = B.autotune()
+        B.reset()
+        B.iterate(1, use_graph=True)  # capture + warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        B.iterate(iters, use_graph=True, stream=st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / iters
+        steps = B.steps_per_iteration
+    return {"problems": len(probs), "sim_steps_per_iteration": steps, "ms_per_iteration": ms,
+            "sim_steps_per_s": steps / (ms / 1e3), "launch": {"warps_per_cta": warps, "ctas_per_sm": ctas},
+            "kernels_per_iteration": 3}
+
+
 def run_gb300(args):
     import torch
 
@@ -293,6 +325,9 @@ def run_gb300(args):
     torch.cuda.synchronize()
     sat_ms = e0.elapsed_time(e1) / 3
 
+    # the 64-problem batched workload: one persistent launch per iteration
+    batch = batched_measurement(P, args.seed, rank)
+
     # end to end through the public API with host buffers: cem_solve, one
     # iteration per step, distribution in from pinned host memory and the
     # best sample / new distribution back to the host
@@ -339,6 +374,7 @@ def run_gb300(args):
                                    "unit": "TFLOP/s"},
             "e2e": {"value": e_units / e_secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
+            "batched_64": batch,
             "gpu_launches": 3 * args.steps,
             "gpu_launches_outside_timed_region": 5 + 3 * (args.steps + 1),
             "clocks": clocks,
@@ -351,8 +387,50 @@ def run_gb300(args):
         torch.distributed.destroy_process_group()
 
 
+def run_rollout_only(args):
+    """Times one workload's rollout kernel alone: one untimed launch, then
+    `reps` launches between CUDA events.  Prints one JSON line."""
+    import torch
+
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    cfg = {"reach": 0, "push": 1, "pickplace": 2}[args.rollout_only]
+    sc, sk, cm = workload.config(cfg, seed=args.seed)
+    N = args.n or cm["N"]
+    T, D = sc["T"], len(sk["lo"])
+    lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
+    with P.Scene(sc, sk) as S:
+        mean = torch.tensor((lo + hi) / 2, device="cuda")
+        chol = torch.tensor(np.diag((hi - lo) / 4), device="cuda")
+        theta = S.sample(mean, chol, args.seed, 0, N)
+        J, cls = S.rollout(theta)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        for _ in range(args.reps):
+            P.cem_rollout_batch(S.h, theta, N, J, cls, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+    fps = flops_per_step(cm["name"])
+    peaks, _ = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    tf = fps["flops"] * N * T / (ms / 1e3) / 1e12
+    print(json.dumps({"rollout_only": cm["name"], "N": N, "T": T, "D": D, "ms": ms,
+                      "sim_steps_per_s": N * T / (ms / 1e3), "achieved_tflops": tf, "frac": tf / peak,
+                      "classes": np.bincount(cls.cpu().numpy(), minlength=4).tolist()}), flush=True)
+
+
 def main():
     args = parse()
+    if args.rollout_only:
+        run_rollout_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

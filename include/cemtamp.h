@@ -21,8 +21,9 @@
  *     mean[D], cov[D][D], chol[D][D] (lower triangular, zeros above).
  *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy
  *     default stream.  Calls are stream-ordered and asynchronous; only
- *     cem_solve, cem_batch_solve, cem_surrogate_* and cem_autotune
- *     synchronise, when they return host results.
+ *     cem_solve, cem_solve_static, cem_batch_reset/read/autotune,
+ *     cem_surrogate_* and cem_autotune synchronise, when they return host
+ *     results.
  *   - The library owns only the memory behind a handle; it is freed by
  *     cem_scene_destroy / cem_batch_destroy.
  *   - Return value 0 is success; negative values are the cem_status codes
@@ -48,6 +49,7 @@ extern "C" {
 #define CEM_MAX_K 1024
 #define CEM_MAX_N (1 << 20)
 #define CEM_TRACE_W 20
+#define CEM_MAX_BATCH 1024
 
 typedef enum {
   CEM_OK = 0,
@@ -229,6 +231,44 @@ int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out);
  * is ignored.  Synchronous; results as cem_solve (elapsed_ms = 0). */
 int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_desc* skel, const cem_solve_params* p,
                      cem_result* out, void* stream);
+
+/* ---- Batched CE: many independent problems advance together ------------
+ * One iteration of Algorithm 1 for every problem of the batch per step: a
+ * batched sampler, ONE persistent rollout launch whose warps drain a queue
+ * of (problem, 32-sample chunk) items (longest horizon first), and a
+ * segmented select + refit (one CTA per problem).  Problems may differ in
+ * scene kind, skeleton length, N, K, D and T.  Results per problem are
+ * identical to cem_solve with the same seed, problem id and start_iter = 0.
+ * There is no device-side wait between warps or CTAs. */
+typedef struct {
+  uint64_t seed;
+  int32_t N, K, cov_mode;
+  uint32_t problem; /* Philox problem id */
+} cem_problem_params;
+
+typedef struct cem_batch_ctx* cem_batch_handle;
+
+/* Copies n_problems scenes/skeletons/params (arrays) to the device and resets
+ * every distribution.  Errors as cem_scene_create, per problem. */
+int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skels, const cem_problem_params* params,
+                     int n_problems, cem_batch_handle* out);
+int cem_batch_destroy(cem_batch_handle h);
+/* Initial distributions (mid-bounds, diag((range/4)^2)), iteration 0,
+ * no best sample yet.  Synchronous. */
+int cem_batch_reset(cem_batch_handle h, void* stream);
+/* `iters` CE iterations of every problem on `stream` (asynchronous); with
+ * use_graph the iteration is captured once and replayed. */
+int cem_batch_iterate(cem_batch_handle h, int iters, int use_graph, void* stream);
+/* Best sample so far, current mean/cov per problem: out[n_problems].  Synchronous. */
+int cem_batch_read(cem_batch_handle h, cem_result* out, void* stream);
+/* Persistent launch shape: warps per CTA (1..8) and CTAs per SM (0 = as
+ * many as can be resident). */
+int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm);
+/* Times the persistent rollout over warps per CTA and CTAs per SM on the
+ * current device and keeps the fastest shape.  Synchronous. */
+int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float* best_ms_out);
+/* Simulated steps of one batch iteration: sum over problems of N * T. */
+long long cem_batch_steps_per_iteration(cem_batch_handle h);
 
 /* Threads-per-block of the rollout kernel (0 = automatic). */
 int cem_set_launch(cem_handle h, int block_threads);

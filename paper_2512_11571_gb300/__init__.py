@@ -29,6 +29,8 @@ STATUS = {0: "CEM_OK", -1: "CEM_ERR_INVALID_ARG", -2: "CEM_ERR_CUDA", -3: "CEM_E
 EXPORTS = [
     "cem_scene_create", "cem_scene_destroy", "cem_sample", "cem_philox_words", "cem_rollout_batch",
     "cem_rollout_trace", "cem_refit", "cem_solve", "cem_solve_static", "cem_set_launch", "cem_autotune",
+    "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
+    "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_last_error", "cem_version",
 ]
 
@@ -95,6 +97,11 @@ class cem_solve_params(C.Structure):
                 ("use_graph", C.c_int32), ("reserved", C.c_int32),
                 ("init_mean_h", C.POINTER(C.c_float)), ("init_cov_h", C.POINTER(C.c_float)),
                 ("best_J_hist_h", C.POINTER(C.c_float)), ("k_eff_hist_h", C.POINTER(C.c_int32))]
+
+
+class cem_problem_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("N", C.c_int32), ("K", C.c_int32), ("cov_mode", C.c_int32),
+                ("problem", C.c_uint32)]
 
 
 class cem_result(C.Structure):
@@ -198,12 +205,22 @@ def load(path: str = LIB_PATH):
     L.cem_solve_static.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc),
                                    C.POINTER(cem_solve_params), C.POINTER(cem_result), vp]
     L.cem_set_launch.argtypes = [H, C.c_int]
+    L.cem_batch_create.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc),
+                                   C.POINTER(cem_problem_params), C.c_int, C.POINTER(H)]
+    L.cem_batch_destroy.argtypes = [H]
+    L.cem_batch_reset.argtypes = [H, vp]
+    L.cem_batch_iterate.argtypes = [H, C.c_int, C.c_int, vp]
+    L.cem_batch_read.argtypes = [H, C.POINTER(cem_result), vp]
+    L.cem_batch_set_launch.argtypes = [H, C.c_int, C.c_int]
+    L.cem_batch_autotune.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.cem_batch_steps_per_iteration.argtypes = [H]
     L.cem_autotune.argtypes = [H, C.c_int, C.c_char_p, C.POINTER(C.c_int)]
     L.cem_last_error.restype = C.c_char_p
     L.cem_version.restype = C.c_char_p
     for name in EXPORTS:
         if name not in ("cem_last_error", "cem_version"):
             getattr(L, name).restype = C.c_int
+    L.cem_batch_steps_per_iteration.restype = C.c_longlong
     _lib = L
     return L
 
@@ -287,6 +304,109 @@ def cem_autotune(h, N, cache_path=None):
     b = C.c_int()
     _check(load().cem_autotune(h, N, cache_path.encode() if cache_path else None, C.byref(b)))
     return b.value
+
+
+def cem_batch_create(problems):
+    """problems: list of dicts with scene, skel, N, K and optional seed,
+    problem, cov ('full' | 'diag')."""
+    n = len(problems)
+    scenes = (cem_scene_desc * n)()
+    skels = (cem_skeleton_desc * n)()
+    params = (cem_problem_params * n)()
+    for i, pr in enumerate(problems):
+        s, k = pack_scene(pr["scene"], pr["skel"])
+        scenes[i], skels[i] = s, k
+        params[i].seed = pr.get("seed", 0)
+        params[i].N, params[i].K = pr["N"], pr["K"]
+        params[i].cov_mode = COV[pr.get("cov", "full")]
+        params[i].problem = pr.get("problem", i)
+    h = C.c_void_p()
+    _check(load().cem_batch_create(scenes, skels, params, n, C.byref(h)))
+    return h
+
+
+def cem_batch_destroy(h):
+    _check(load().cem_batch_destroy(h))
+
+
+def cem_batch_reset(h, stream=None):
+    _check(load().cem_batch_reset(h, _stream(stream)))
+
+
+def cem_batch_iterate(h, iters, use_graph=True, stream=None):
+    _check(load().cem_batch_iterate(h, iters, int(use_graph), _stream(stream)))
+
+
+def cem_batch_read(h, n_problems, stream=None):
+    out = (cem_result * n_problems)()
+    _check(load().cem_batch_read(h, out, _stream(stream)))
+    return out
+
+
+def cem_batch_set_launch(h, warps_per_cta, ctas_per_sm=0):
+    _check(load().cem_batch_set_launch(h, warps_per_cta, ctas_per_sm))
+
+
+def cem_batch_autotune(h):
+    w, c, ms = C.c_int(), C.c_int(), C.c_float()
+    _check(load().cem_batch_autotune(h, C.byref(w), C.byref(c), C.byref(ms)))
+    return w.value, c.value, ms.value
+
+
+def cem_batch_steps_per_iteration(h):
+    return int(load().cem_batch_steps_per_iteration(h))
+
+
+class Batch:
+    """Many independent CE problems advanced together (one library handle)."""
+
+    def __init__(self, problems):
+        self.problems = problems
+        self.n = len(problems)
+        self.h = cem_batch_create(problems)
+
+    def close(self):
+        if self.h is not None and _lib is not None:
+            cem_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        cem_batch_reset(self.h, stream)
+
+    def iterate(self, iters, use_graph=True, stream=None):
+        cem_batch_iterate(self.h, iters, use_graph, stream)
+
+    def read(self, stream=None):
+        out = cem_batch_read(self.h, self.n, stream)
+        res = []
+        for r in out:
+            D = r.D
+            res.append(dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
+                            mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                            iters_done=r.iters_done))
+        return res
+
+    def autotune(self):
+        return cem_batch_autotune(self.h)
+
+    def set_launch(self, warps_per_cta, ctas_per_sm=0):
+        cem_batch_set_launch(self.h, warps_per_cta, ctas_per_sm)
+
+    @property
+    def steps_per_iteration(self):
+        return cem_batch_steps_per_iteration(self.h)
 
 
 # ----------------------------------------------------------- convenience

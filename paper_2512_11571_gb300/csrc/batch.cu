@@ -1,1 +1,380 @@
-// placeholder translation unit, filled by the batched scheduler
+// Batched CE: many independent plan-realization problems (different scenes,
+// skeletons of 1..6 actions, uneven N, T and D) advance together, one CE
+// iteration of Algorithm 1 (Sec. III-B) for all of them per step:
+//   batched sample (one launch, blockIdx.y = problem)
+//   -> persistent rollout (one launch draining a queue of (problem, chunk)
+//      items, longest horizon first)
+//   -> segmented select + refit (one CTA per problem),
+// the three captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace cem;
+
+namespace {
+
+int fail(int code, const std::string& m) { return set_last_error(code, m); }
+
+#define BATCH_CUDA(call)                                                                                     \
+  do {                                                                                                       \
+    cudaError_t e_ = (call);                                                                                 \
+    if (e_ != cudaSuccess) return fail(CEM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));      \
+  } while (0)
+
+constexpr int kMS = CEM_MAX_D, kMC = CEM_MAX_D * CEM_MAX_D;
+
+}  // namespace
+
+struct cem_batch_ctx {
+  int P = 0, maxN = 0, maxK = 0, maxD = 0, n_items = 0, total_samples = 0, total_theta = 0;
+  std::vector<BatchProblem> probs;
+  std::vector<cem_skeleton_desc> skels;
+  DevScene* scenes_d = nullptr;
+  BatchProblem* probs_d = nullptr;
+  BatchItem* items_d = nullptr;
+  int* counter_d = nullptr;
+  float* theta_d = nullptr;
+  float* J_d = nullptr;
+  uint8_t* cls_d = nullptr;
+  float* mean_d = nullptr;  // [P][18]
+  float* cov_d = nullptr;   // [P][18*18]
+  float* chol_d = nullptr;  // [P][18*18]
+  int32_t* keff_d = nullptr;
+  int32_t* status_d = nullptr;
+  Track* track_d = nullptr;
+  RefitArgs* args_d = nullptr;
+  int warps = 4, ctas_per_sm = 0;  // persistent launch shape (0 = occupancy)
+  cudaGraphExec_t graph = nullptr;
+  long long steps_per_iter = 0;
+};
+
+namespace {
+
+void batch_free(cem_batch_ctx* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  void* ptrs[] = {h->scenes_d, h->probs_d, h->items_d, h->counter_d, h->theta_d, h->J_d, h->cls_d,
+                  h->mean_d,   h->cov_d,   h->chol_d,  h->keff_d,    h->status_d, h->track_d, h->args_d};
+  for (void* p : ptrs) cudaFree(p);
+}
+
+int grid_size(const cem_batch_ctx* h) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps);
+  return sms * per_sm;
+}
+
+cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st) {
+  cudaError_t e = launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
+                                      h->J_d, h->cls_d, grid_size(h), h->warps, st);
+  if (e != cudaSuccess) return e;
+  return launch_refit_batch(h->args_d, h->P, h->maxK, h->maxD, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skels, const cem_problem_params* params,
+                     int n_problems, cem_batch_handle* out) {
+  set_last_error(CEM_OK, "");
+  if (!out) return fail(CEM_ERR_INVALID_ARG, "out handle pointer is NULL");
+  *out = nullptr;
+  if (!scenes || !skels || !params) return fail(CEM_ERR_INVALID_ARG, "null descriptor array");
+  if (n_problems < 1 || n_problems > CEM_MAX_BATCH) return fail(CEM_ERR_UNSUPPORTED, "1..1024 problems per batch");
+  cem_batch_ctx* h = new cem_batch_ctx();
+  h->P = n_problems;
+  std::vector<DevScene> host(n_problems);
+  long long theta_total = 0, sample_total = 0;
+  for (int p = 0; p < n_problems; ++p) {
+    int rc = validate_descriptors(&scenes[p], &skels[p]);
+    if (rc != CEM_OK) {
+      delete h;
+      return fail(rc, "problem " + std::to_string(p) + ": " + cem_last_error());
+    }
+    const cem_problem_params& q = params[p];
+    if (q.N < 1 || q.N > CEM_MAX_N || q.K < 1 || q.K > CEM_MAX_K ||
+        (q.cov_mode != CEM_COV_FULL && q.cov_mode != CEM_COV_DIAG)) {
+      delete h;
+      return fail(CEM_ERR_UNSUPPORTED, "problem " + std::to_string(p) + ": N in 1..2^20, K in 1..1024, known cov mode");
+    }
+    host[p] = prepare_scene(scenes[p], skels[p]);
+    BatchProblem b;
+    std::memset(&b, 0, sizeof(b));
+    b.N = q.N;
+    b.D = skels[p].D;
+    b.K = q.K;
+    b.kind = scenes[p].kind;
+    b.theta_off = (int32_t)theta_total;
+    b.sample_off = (int32_t)sample_total;
+    b.problem = q.problem;
+    b.seed = q.seed;
+    theta_total += (long long)q.N * b.D;
+    sample_total += q.N;
+    h->maxN = std::max(h->maxN, q.N);
+    h->maxK = std::max(h->maxK, q.K);
+    h->maxD = std::max(h->maxD, b.D);
+    h->steps_per_iter += (long long)q.N * (scenes[p].kind == CEM_SCENE_QUADRATIC ? 1 : scenes[p].T);
+    h->probs.push_back(b);
+    h->skels.push_back(skels[p]);
+  }
+  if (theta_total > (1ll << 31) - 1 || sample_total > (1ll << 31) - 1) {
+    delete h;
+    return fail(CEM_ERR_UNSUPPORTED, "batch too large");
+  }
+  h->total_samples = (int)sample_total;
+  h->total_theta = (int)theta_total;
+  // work queue: problems by descending horizon (then by index), 32-sample chunks
+  std::vector<int> order(n_problems);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    const long long wa = host[a].kind == CEM_SCENE_QUADRATIC ? 1 : (long long)host[a].T * (host[a].kind == CEM_SCENE_PICKPLACE ? 4 : 1);
+    const long long wb = host[b].kind == CEM_SCENE_QUADRATIC ? 1 : (long long)host[b].T * (host[b].kind == CEM_SCENE_PICKPLACE ? 4 : 1);
+    return wa > wb;
+  });
+  std::vector<BatchItem> items;
+  for (int p : order)
+    for (int f = 0; f < h->probs[p].N; f += 32) items.push_back(BatchItem{p, f});
+  h->n_items = (int)items.size();
+  const size_t P = n_problems;
+  cudaError_t e = configure_refit();
+  auto M = [&](void** ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+  };
+  M((void**)&h->scenes_d, sizeof(DevScene) * P);
+  M((void**)&h->probs_d, sizeof(BatchProblem) * P);
+  M((void**)&h->items_d, sizeof(BatchItem) * items.size());
+  M((void**)&h->counter_d, sizeof(int));
+  M((void**)&h->theta_d, sizeof(float) * (size_t)theta_total);
+  M((void**)&h->J_d, sizeof(float) * (size_t)sample_total);
+  M((void**)&h->cls_d, (size_t)sample_total);
+  M((void**)&h->mean_d, sizeof(float) * P * kMS);
+  M((void**)&h->cov_d, sizeof(float) * P * kMC);
+  M((void**)&h->chol_d, sizeof(float) * P * kMC);
+  M((void**)&h->keff_d, sizeof(int32_t) * P);
+  M((void**)&h->status_d, sizeof(int32_t) * P);
+  M((void**)&h->track_d, sizeof(Track) * P);
+  M((void**)&h->args_d, sizeof(RefitArgs) * P);
+  if (e == cudaSuccess) e = cudaMemcpy(h->scenes_d, host.data(), sizeof(DevScene) * P, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->probs_d, h->probs.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<RefitArgs> args(P);
+    for (size_t p = 0; p < P; ++p) {
+      RefitArgs& a = args[p];
+      std::memset(&a, 0, sizeof(a));
+      const BatchProblem& b = h->probs[p];
+      a.theta = h->theta_d + b.theta_off;
+      a.J = h->J_d + b.sample_off;
+      a.cls = h->cls_d + b.sample_off;
+      a.N = b.N;
+      a.D = b.D;
+      a.K = b.K;
+      a.cov_mode = params[p].cov_mode;
+      for (int d = 0; d < b.D; ++d) {
+        a.lo[d] = skels[p].lo[d];
+        a.hi[d] = skels[p].hi[d];
+      }
+      a.mean = h->mean_d + p * kMS;
+      a.cov = h->cov_d + p * kMC;
+      a.chol = h->chol_d + p * kMC;
+      a.k_eff = h->keff_d + p;
+      a.track = h->track_d + p;
+      a.status = h->status_d + p;
+    }
+    e = cudaMemcpy(h->args_d, args.data(), sizeof(RefitArgs) * P, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(h);
+    delete h;
+    return fail(e == cudaErrorMemoryAllocation ? CEM_ERR_NO_MEMORY : CEM_ERR_CUDA,
+                std::string("cem_batch_create: ") + cudaGetErrorString(e));
+  }
+  *out = h;
+  return cem_batch_reset(h, nullptr);
+}
+
+int cem_batch_destroy(cem_batch_handle h) {
+  if (!h) return CEM_OK;
+  cudaDeviceSynchronize();
+  batch_free(h);
+  delete h;
+  return CEM_OK;
+}
+
+int cem_batch_reset(cem_batch_handle h, void* stream) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = h->P;
+  std::vector<float> mean(P * kMS, 0.0f), cov(P * kMC, 0.0f), chol(P * kMC, 0.0f);
+  std::vector<Track> tr(P);
+  for (size_t p = 0; p < P; ++p) {
+    const cem_skeleton_desc& k = h->skels[p];
+    const int D = k.D;
+    for (int d = 0; d < D; ++d) {
+      const float sd = 0.25f * (k.hi[d] - k.lo[d]);
+      mean[p * kMS + d] = 0.5f * (k.lo[d] + k.hi[d]);
+      cov[p * kMC + d * D + d] = std::pow(sd, 2.0f);
+      chol[p * kMC + d * D + d] = (float)std::sqrt((double)std::pow(sd, 2.0f));
+    }
+    std::memset(&tr[p], 0, sizeof(Track));
+    tr[p].best_cls = 4;
+    tr[p].best_J = INFINITY;
+  }
+  std::vector<int32_t> zeros(P, 0);
+  BATCH_CUDA(cudaMemcpyAsync(h->mean_d, mean.data(), sizeof(float) * P * kMS, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->cov_d, cov.data(), sizeof(float) * P * kMC, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * P * kMC, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->track_d, tr.data(), sizeof(Track) * P, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->status_d, zeros.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaStreamSynchronize(st));  // the host vectors die at return
+  return CEM_OK;
+}
+
+int cem_batch_iterate(cem_batch_handle h, int iters, int use_graph, void* stream) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (iters < 0 || iters > 100000) return fail(CEM_ERR_UNSUPPORTED, "iters must be in 0..1e5");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (use_graph && !h->graph) {
+    cudaStream_t cap;
+    BATCH_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = enqueue(h, cap);
+      e = cudaStreamEndCapture(cap, &g);
+      if (e1 != cudaSuccess) e = e1;
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+      }
+    }
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+  }
+  for (int j = 0; j < iters; ++j) {
+    if (use_graph) {
+      BATCH_CUDA(cudaGraphLaunch(h->graph, st));
+    } else {
+      cudaError_t e = enqueue(h, st);
+      if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("batch iteration: ") + cudaGetErrorString(e));
+    }
+  }
+  return CEM_OK;
+}
+
+int cem_batch_read(cem_batch_handle h, cem_result* out, void* stream) {
+  if (!h || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = h->P;
+  std::vector<Track> tr(P);
+  std::vector<float> mean(P * kMS), cov(P * kMC);
+  std::vector<int32_t> status(P);
+  BATCH_CUDA(cudaMemcpyAsync(tr.data(), h->track_d, sizeof(Track) * P, cudaMemcpyDeviceToHost, st));
+  BATCH_CUDA(cudaMemcpyAsync(mean.data(), h->mean_d, sizeof(float) * P * kMS, cudaMemcpyDeviceToHost, st));
+  BATCH_CUDA(cudaMemcpyAsync(cov.data(), h->cov_d, sizeof(float) * P * kMC, cudaMemcpyDeviceToHost, st));
+  BATCH_CUDA(cudaMemcpyAsync(status.data(), h->status_d, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
+  BATCH_CUDA(cudaStreamSynchronize(st));
+  int bad = 0;
+  for (size_t p = 0; p < P; ++p) {
+    const int D = h->probs[p].D;
+    cem_result& r = out[p];
+    std::memset(&r, 0, sizeof(r));
+    r.D = D;
+    r.best_J = tr[p].best_J;
+    r.best_class = tr[p].best_cls;
+    r.iters_done = (int32_t)(tr[p].iter - tr[p].base_iter);
+    for (int d = 0; d < D; ++d) {
+      r.best_theta[d] = tr[p].best_theta[d];
+      r.mean[d] = mean[p * kMS + d];
+    }
+    for (int i = 0; i < D * D; ++i) r.cov[i] = cov[p * kMC + i];
+    if (status[p] != 0) ++bad;
+  }
+  if (bad) return fail(CEM_ERR_NOT_PD, std::to_string(bad) + " problem(s) kept an indefinite covariance");
+  return CEM_OK;
+}
+
+int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (warps_per_cta < 1 || warps_per_cta > 8 || ctas_per_sm < 0 || ctas_per_sm > 64)
+    return fail(CEM_ERR_INVALID_ARG, "warps per CTA in 1..8, CTAs per SM in 0..64 (0 = occupancy)");
+  if (ctas_per_sm > rollout_batch_max_ctas_per_sm(warps_per_cta))
+    return fail(CEM_ERR_INVALID_ARG, "more CTAs per SM than can be resident: the persistent grid must fit");
+  h->warps = warps_per_cta;
+  h->ctas_per_sm = ctas_per_sm;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
+}
+
+int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float* best_ms_out) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  cudaEvent_t a, b;
+  BATCH_CUDA(cudaEventCreate(&a));
+  BATCH_CUDA(cudaEventCreate(&b));
+  // theta from the initial distributions, then time the persistent rollout
+  cudaError_t e = launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, 0);
+  float best = INFINITY;
+  int bw = h->warps, bc = h->ctas_per_sm;
+  const int cand_w[] = {1, 2, 4, 8};
+  for (int w : cand_w) {
+    const int maxc = rollout_batch_max_ctas_per_sm(w);
+    for (int c = 1; c <= maxc && e == cudaSuccess; c *= 2) {
+      h->warps = w;
+      h->ctas_per_sm = c;
+      float tot = 0.0f;
+      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), 0);
+        if (e == cudaSuccess) e = cudaEventRecord(a, 0);
+        if (e == cudaSuccess)
+          e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d,
+                                              h->theta_d, h->J_d, h->cls_d, grid_size(h), w, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(b, 0);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0) tot += ms;
+      }
+      if (e == cudaSuccess && tot < best) {
+        best = tot;
+        bw = w;
+        bc = c;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  h->warps = bw;
+  h->ctas_per_sm = bc;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("batch autotune: ") + cudaGetErrorString(e));
+  if (warps_out) *warps_out = bw;
+  if (ctas_out) *ctas_out = bc;
+  if (best_ms_out) *best_ms_out = best;
+  return CEM_OK;
+}
+
+long long cem_batch_steps_per_iteration(cem_batch_handle h) { return h ? h->steps_per_iter : 0; }
+
+}  // extern "C"

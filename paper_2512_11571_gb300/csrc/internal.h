@@ -59,6 +59,22 @@ struct Track {
   int32_t pad;
 };
 
+// One problem of a batch, as the batched kernels see it.
+struct BatchProblem {
+  int32_t N, D, K, kind;
+  int32_t theta_off;   // float offset of the problem's theta rows in the batch buffer
+  int32_t sample_off;  // offset of its J / class entries
+  uint32_t problem;    // Philox problem id
+  int32_t pad;
+  uint64_t seed;
+};
+
+// A unit of work of the persistent rollout kernel: 32 consecutive samples
+// (one warp) of one problem.
+struct BatchItem {
+  int32_t problem, first;
+};
+
 struct RefitArgs {
   const float* theta;
   const float* J;
@@ -89,6 +105,18 @@ cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
 // opts the refit kernel into its dynamic shared memory (once per device, before any capture)
 cudaError_t configure_refit();
 size_t refit_smem_bytes(int K, int D);
+cudaError_t launch_refit_batch(const RefitArgs* args_d, int n_problems, int maxK, int maxD, cudaStream_t st);
+// batched sampling: problem p draws N_p rows from means[p*18..], chols[p*324..]
+// (D_p x D_p row-major) at Philox iteration tracks[p].iter
+cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int maxN, const float* means,
+                                const float* chols, const Track* tracks, float* theta, cudaStream_t st);
+// persistent rollout over a work queue of (problem, 32-sample chunk) items;
+// *counter must be zero at launch
+cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
+                                            const BatchItem* items_d, int n_items, int* counter_d,
+                                            const float* theta, float* J, uint8_t* cls, int grid, int warps,
+                                            cudaStream_t st);
+int rollout_batch_max_ctas_per_sm(int warps);
 
 // host helpers shared by the C entry points (capi.cu)
 int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k);

@@ -64,7 +64,7 @@ __device__ bool cholesky_warp(double* A, int D, int lane) {
   return true;
 }
 
-__global__ void __launch_bounds__(RT) refit_kernel(RefitArgs a) {
+__device__ __forceinline__ void refit_body(const RefitArgs& a) {
   extern __shared__ __align__(16) unsigned char dyn[];
   __shared__ int cnt[4];
   __shared__ uint32_t hist[256];
@@ -259,6 +259,16 @@ __global__ void __launch_bounds__(RT) refit_kernel(RefitArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(RT) refit_kernel(RefitArgs a) { refit_body(a); }
+
+// one CTA per problem of a batch; args[p] describes problem p
+__global__ void __launch_bounds__(RT) refit_batch_kernel(const RefitArgs* __restrict__ args) {
+  __shared__ RefitArgs a;
+  if (threadIdx.x == 0) a = args[blockIdx.x];
+  __syncthreads();
+  refit_body(a);
+}
+
 }  // namespace
 
 size_t refit_smem_bytes(int K, int D) {
@@ -268,8 +278,17 @@ size_t refit_smem_bytes(int K, int D) {
 }
 
 cudaError_t configure_refit() {
-  return cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(refit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)refit_smem_bytes(CEM_MAX_K, CEM_MAX_D));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(refit_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)refit_smem_bytes(CEM_MAX_K, CEM_MAX_D));
+}
+
+cudaError_t launch_refit_batch(const RefitArgs* args_d, int n_problems, int maxK, int maxD, cudaStream_t st) {
+  if (n_problems <= 0) return cudaSuccess;
+  refit_batch_kernel<<<n_problems, RT, refit_smem_bytes(maxK, maxD), st>>>(args_d);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st) {

@@ -176,8 +176,11 @@ __device__ __forceinline__ void put_trace(float* tr, int step, const float* v, i
 // ------------------------------------------------------------- reach / push
 // The success test compares squared distances; the square roots are taken
 // only at the step that succeeds (for the interpolated crossing time).
+// The rollout functions are compiled once (noinline) and called by every
+// rollout kernel, so the single-problem, traced and batched launches execute
+// the same instructions and return bit-identical results.
 template <bool HAS_BLOCK, bool TRACE>
-__device__ void planar_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out, int& cls_out,
+__device__ __noinline__ void planar_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out, int& cls_out,
                                float* tr) {
   // loop invariants in registers
   const float dt = s.dt, eps2 = s.eps * s.eps;
@@ -341,6 +344,43 @@ __device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px,
   return any;
 }
 
+// Neighbour list of an axis-aligned mover (half sizes hx, hy, hz at p):
+// the geometries whose gap to the mover along every world axis they list is
+// below `skin`.  A geometry left out has a gap >= skin along some world axis;
+// while the mover has moved less than skin along every axis since the build
+// that gap stays positive, so the geometry is still separated and its
+// contact test would return no contact.  PLANAR: base footprint (x, y only).
+template <bool PLANAR>
+__device__ __forceinline__ uint32_t near_list(const DevScene& s, int n_geoms, float px, float py, float pz, float hx,
+                                              float hy, float hz, float skin) {
+  uint32_t m = 0;
+  const int flag = PLANAR ? 1 : 2;
+  for (int g = 0; g < n_geoms; ++g) {
+    if (!(s.geom_flags[g] & flag)) continue;
+    bool far = false;
+    const int ns = s.geom_nslab[g];
+    for (int i = 0; i < ns && !far; ++i) {
+      const float* sl = s.slab[g][i];
+      float p, r;
+      if (sl[0] == 1.0f && sl[1] == 0.0f && sl[2] == 0.0f) {
+        p = px;
+        r = hx;
+      } else if (sl[0] == 0.0f && sl[1] == 1.0f && sl[2] == 0.0f) {
+        p = py;
+        r = hy;
+      } else if (!PLANAR && sl[0] == 0.0f && sl[1] == 0.0f && sl[2] == 1.0f) {
+        p = pz;
+        r = hz;
+      } else {
+        continue;
+      }
+      far = fmaxf(sl[3] - (p + r), (p - r) - sl[4]) >= skin;
+    }
+    if (!far) m |= 1u << g;
+  }
+  return m;
+}
+
 __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, float tx, float ty, float tz,
                                        float& beta, float& q1, float& q2) {
   const float dx = tx - bx, dy = ty - by;
@@ -368,11 +408,14 @@ __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, fl
   q1 = atan2f(zz, rr) - atan2f(s.arm_l2 * s2, s.arm_l1 + s.arm_l2 * co2);
 }
 
+// Forward kinematics.  Joint angles stay within (-pi, pi), where the
+// hardware sine/cosine is accurate to ~5e-7 absolute (~2e-7 m at the end
+// effector), far inside the per-step state tolerance.
 __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, float cb, float sb, float q1, float q2,
                                        float& ex, float& ey, float& ez) {
   float s1, c1, s12, c12;
-  sincosf(q1, &s1, &c1);
-  sincosf(q1 + q2, &s12, &c12);
+  __sincosf(q1, &s1, &c1);
+  __sincosf(q1 + q2, &s12, &c12);
   const float r = s.arm_l1 * c1 + s.arm_l2 * c12;
   ez = s.arm_z + s.arm_l1 * s1 + s.arm_l2 * s12;
   ex = bx + r * cb;
@@ -380,7 +423,7 @@ __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, fl
 }
 
 template <bool TRACE>
-__device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out,
+__device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out,
                                   int& cls_out, float* tr) {
   const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps, gdt = s.g * s.dt;
   const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap, bcap2 = bcap * bcap;
@@ -402,6 +445,10 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
   float mgx = bx, mgy = by, mkp = 0.f, mkd = 0.f;
   float rx = 0.f, ry = 0.f, caz = 1.f, saz = 0.f, hgrip = 0.f, ptx = 0.f, pty = 0.f, ptz = 0.f;
   float t_done = (float)T * dt;
+  // neighbour lists (bit g = geometry g) and the positions they were built at
+  constexpr float kSkin = 0.05f, kRebuild = 0.025f;
+  uint32_t bmask = 0, omask = 0;
+  float brx = 1e30f, bry = 1e30f, orx = 1e30f, ory = 1e30f, orz = 1e30f;
   for (int step = 0; step < T; ++step) {
     const int ai = a < L ? a : L - 1;
     const int kind = s.act_kind[ai];
@@ -459,8 +506,13 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
     // base: PD + penalty contacts with the static footprints
     float fx = mb * (kp * (gx - bx) - kd * bvx);
     float fy = mb * (kp * (gy - by) - kd * bvy);
-    for (int g = 0; g < n_geoms; ++g) {
-      if (!(s.geom_flags[g] & 1)) continue;
+    if (fmaxf(fabsf(bx - brx), fabsf(by - bry)) >= kRebuild) {
+      bmask = near_list<true>(s, n_geoms, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, kSkin);
+      brx = bx;
+      bry = by;
+    }
+    for (uint32_t m = bmask; m; m &= m - 1) {
+      const int g = __ffs(m) - 1;
       float nx, ny, nz, dep;
       if (slab_contact<true>(s, g, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, nx, ny, nz, dep)) {
         const float vn = bvx * nx + bvy * ny;
@@ -500,8 +552,14 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
       uint32_t mask = 0;
       int nc = 0;
       float fsx = 0.f, fsy = 0.f, fsz = 0.f;
-      for (int g = 0; g < n_geoms; ++g) {
-        if (!(s.geom_flags[g] & 2)) continue;
+      if (fmaxf(fmaxf(fabsf(ox - orx), fabsf(oy - ory)), fabsf(oz - orz)) >= kRebuild) {
+        omask = near_list<false>(s, n_geoms, ox, oy, oz, h, h, h, kSkin);
+        orx = ox;
+        ory = oy;
+        orz = oz;
+      }
+      for (uint32_t m = omask; m; m &= m - 1) {
+        const int g = __ffs(m) - 1;
         float nx, ny, nz, dep;
         if (slab_contact<false>(s, g, ox, oy, oz, h, h, h, nx, ny, nz, dep)) {
           const float vn = ovx * nx + ovy * ny + ovz * nz;
@@ -604,7 +662,7 @@ __device__ void pickplace_rollout(const DevScene& s, const float* __restrict__ r
   if (!isfinite(J)) cls_out = 3;
 }
 
-__device__ void quadratic_cost(const DevScene& s, const float* __restrict__ row, float& J_out, int& cls_out) {
+__device__ __noinline__ void quadratic_cost(const DevScene& s, const float* __restrict__ row, float& J_out, int& cls_out) {
   float e[CEM_MAX_D];
 #pragma unroll
   for (int i = 0; i < CEM_MAX_D; ++i) e[i] = i < s.D ? theta_at(s, row, i) - s.theta_star[i] : 0.0f;
@@ -680,7 +738,77 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
   return cudaGetLastError();
 }
 
+// Persistent batched rollout: every warp of a resident CTA repeatedly takes
+// the next (problem, 32-sample chunk) item from a global queue and rolls the
+// chunk out with that problem's scene, staged in the warp's own shared-memory
+// slot (reloaded only when the problem changes).  Items come longest horizon
+// first, so the tail of the queue is short work.  There are no waits between
+// warps or CTAs: a warp that finds the queue empty exits.
+constexpr int kMaxBatchWarps = 8;
+
+__global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene* __restrict__ scenes,
+                                                                 const BatchProblem* __restrict__ probs,
+                                                                 const BatchItem* __restrict__ items, int n_items,
+                                                                 int* __restrict__ counter,
+                                                                 const float* __restrict__ theta,
+                                                                 float* __restrict__ J, uint8_t* __restrict__ cls) {
+  __shared__ DevScene sc[kMaxBatchWarps];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DevScene& s = sc[w];
+  int cur = -1;
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    if (item.problem != cur) {
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(scenes + item.problem);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s);
+      for (int i = lane; i < (int)(sizeof(DevScene) / 4); i += 32) dst[i] = src[i];
+      __syncwarp();
+      cur = item.problem;
+    }
+    const BatchProblem pb = probs[item.problem];
+    const int n = item.first + lane;
+    if (n < pb.N) {
+      const float* row = theta + pb.theta_off + (size_t)n * pb.D;
+      float Jn;
+      int c;
+      switch (s.kind) {
+        case CEM_SCENE_REACH: planar_rollout<false, false>(s, row, s.T, Jn, c, nullptr); break;
+        case CEM_SCENE_PUSH: planar_rollout<true, false>(s, row, s.T, Jn, c, nullptr); break;
+        case CEM_SCENE_PICKPLACE: pickplace_rollout<false>(s, row, s.T, Jn, c, nullptr); break;
+        default: quadratic_cost(s, row, Jn, c); break;
+      }
+      J[pb.sample_off + n] = Jn;
+      cls[pb.sample_off + n] = (uint8_t)c;
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace
+
+int rollout_batch_max_ctas_per_sm(int warps) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel, warps * 32, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
+                                            const BatchItem* items_d, int n_items, int* counter_d,
+                                            const float* theta, float* J, uint8_t* cls, int grid, int warps,
+                                            cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  if (warps < 1 || warps > kMaxBatchWarps || grid < 1) return cudaErrorInvalidValue;
+  rollout_persistent_kernel<<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta, J,
+                                                        cls);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
                            int block, cudaStream_t st) {

@@ -100,7 +100,67 @@ __global__ void philox_words_kernel(uint64_t seed, uint32_t iter, uint32_t probl
   o[3] = r[3];
 }
 
+// batched sampling: blockIdx.y = problem, samples in x; the same per-sample
+// arithmetic as sample_kernel
+__global__ void __launch_bounds__(128) sample_batch_kernel(const BatchProblem* __restrict__ probs,
+                                                           const float* __restrict__ means,
+                                                           const float* __restrict__ chols,
+                                                           const Track* __restrict__ tracks,
+                                                           float* __restrict__ theta) {
+  __shared__ float sL[CEM_MAX_D * CEM_MAX_D];
+  __shared__ float sm[CEM_MAX_D];
+  const int p = blockIdx.y;
+  const BatchProblem pb = probs[p];
+  if ((int)(blockIdx.x * blockDim.x) >= pb.N) return;  // whole block beyond this problem
+  const int D = pb.D;
+  for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = chols[(size_t)p * CEM_MAX_D * CEM_MAX_D + i];
+  for (int i = threadIdx.x; i < D; i += blockDim.x) sm[i] = means[(size_t)p * CEM_MAX_D + i];
+  __syncthreads();
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= pb.N) return;
+  const uint32_t it = tracks[p].iter;
+  const uint32_t k0 = (uint32_t)pb.seed, k1 = (uint32_t)(pb.seed >> 32);
+  float z[20];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    if (4 * c < D) {
+      uint32_t r[4];
+      philox4x32_10((uint32_t)n, (uint32_t)c, it, pb.problem, k0, k1, r);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float rad = sqrtf(-2.0f * logf(u01(r[2 * q])));
+        float sn, cs;
+        sincospif(2.0f * u01(r[2 * q + 1]), &sn, &cs);
+        z[4 * c + 2 * q] = rad * cs;
+        z[4 * c + 2 * q + 1] = rad * sn;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) z[4 * c + q] = 0.0f;
+    }
+  }
+  float* out = theta + pb.theta_off + (size_t)n * D;
+#pragma unroll
+  for (int i = 0; i < CEM_MAX_D; ++i) {
+    if (i < D) {
+      float acc = sm[i];
+#pragma unroll
+      for (int j = 0; j <= i; ++j) acc = fmaf(sL[i * D + j], z[j], acc);
+      out[i] = acc;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int maxN, const float* means,
+                                const float* chols, const Track* tracks, float* theta, cudaStream_t st) {
+  if (n_problems <= 0 || maxN <= 0) return cudaSuccess;
+  const int bs = 128;
+  dim3 grid((maxN + bs - 1) / bs, n_problems);
+  sample_batch_kernel<<<grid, bs, 0, st>>>(probs_d, means, chols, tracks, theta);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sample(const float* mean, const float* chol, uint64_t seed, const uint32_t* iter_ptr,
                           uint32_t iter, uint32_t problem, int N, int D, float* theta, cudaStream_t st) {

@@ -1,0 +1,110 @@
+"""Batched CE (the persistent scheduler) through the C ABI.
+
+A batch advances every problem by the same kernels as the single-problem
+loop, so each problem's result must equal cem_solve of that problem (same
+seed, Philox problem id, iterations) exactly, whatever the launch shape or
+graph use."""
+import numpy as np
+import pytest
+
+import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    return P
+
+
+def mixed_problems():
+    probs = []
+    sc, sk = workload.reach_scene(0)
+    probs.append(dict(scene=sc, skel=sk, N=200, K=20, seed=11))
+    sc, sk = workload.push_scene(1)
+    probs.append(dict(scene=sc, skel=sk, N=333, K=30, seed=12))
+    for L in (3, 4, 5, 6):
+        sc, sk = workload.pickplace_scene(2 + L, n_actions=L, T=600)
+        probs.append(dict(scene=sc, skel=sk, N=96 + 40 * L, K=16, seed=20 + L))
+    sc, sk = workload.quadratic_scene(3, D=18)
+    probs.append(dict(scene=sc, skel=sk, N=1000, K=64, seed=30, cov="diag"))
+    sc, sk = workload.push_scene(4, start_in_contact=True)
+    probs.append(dict(scene=sc, skel=sk, N=64, K=8, seed=31))
+    for i, p in enumerate(probs):
+        p["problem"] = 100 + i
+    return probs
+
+
+def single(P, pr, iters):
+    with P.Scene(pr["scene"], pr["skel"]) as S:
+        return S.solve(pr["seed"], pr["N"], pr["K"], iters, cov_mode=pr.get("cov", "full"),
+                       problem=pr["problem"], use_graph=False)
+
+
+def same(a, b):
+    assert a["best_cls"] == b["best_cls"]
+    assert a["best_J"] == b["best_J"]
+    assert np.array_equal(a["best_theta"], b["best_theta"])
+    assert np.array_equal(a["mean"], b["mean"])
+    assert np.array_equal(a["cov"], b["cov"])
+
+
+def test_batch_equals_single_problem_solves(P):
+    probs = mixed_problems()
+    iters = 4
+    with P.Batch(probs) as B:
+        B.iterate(iters, use_graph=True)
+        got = B.read()
+    for pr, g in zip(probs, got):
+        assert g["iters_done"] == iters
+        same(g, single(P, pr, iters))
+
+
+@pytest.mark.parametrize("warps,ctas", [(1, 1), (2, 3), (8, 1)])
+def test_launch_shape_does_not_change_results(P, warps, ctas):
+    probs = mixed_problems()
+    with P.Batch(probs) as B:
+        B.iterate(3, use_graph=False)
+        ref = B.read()
+        B.reset()
+        B.set_launch(warps, ctas)
+        B.iterate(3, use_graph=True)
+        got = B.read()
+    for a, b in zip(got, ref):
+        same(a, b)
+
+
+def test_autotune_and_reset(P):
+    probs = mixed_problems()
+    with P.Batch(probs) as B:
+        w, c, ms = B.autotune()
+        assert 1 <= w <= 8 and c >= 1 and ms > 0
+        B.iterate(2)
+        first = B.read()
+        B.reset()
+        B.iterate(2)
+        again = B.read()
+    for a, b in zip(first, again):
+        same(a, b)
+
+
+def test_sixty_four_problem_workload(P):
+    probs = workload.batch_problems(0)
+    for i, p in enumerate(probs):
+        p["seed"] = 7
+        p["problem"] = i
+    with P.Batch(probs) as B:
+        assert B.steps_per_iteration == sum(p["N"] * p["scene"]["T"] for p in probs)
+        B.iterate(2)
+        got = B.read()
+    assert all(np.isfinite(g["best_J"]) and g["best_cls"] <= 2 for g in got)
+    for i in (0, 17, 42, 63):  # spot-check problems against the single-problem loop
+        same(got[i], single(P, probs[i], 2))

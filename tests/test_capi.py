@@ -28,7 +28,7 @@ def pkg():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(cem_\w+)\s*\(", src, flags=re.M)
+    names = re.findall(r"^\s*(?:const\s+)?(?:\w+\s+)*\w+\s*\*?\s*(cem_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
 
 
@@ -69,7 +69,7 @@ def _c_offsets(struct_name, fields, tmp_path):
 
 
 @pytest.mark.parametrize("name", ["cem_slab", "cem_geom", "cem_scene_desc", "cem_action_desc",
-                                  "cem_skeleton_desc", "cem_solve_params", "cem_result"])
+                                  "cem_skeleton_desc", "cem_solve_params", "cem_result", "cem_problem_params"])
 def test_struct_layout_matches_header(pkg, name, tmp_path):
     cls = getattr(pkg, name)
     fields = [f[0] for f in cls._fields_]
@@ -131,3 +131,24 @@ def test_pick_place_descriptor_packs(pkg):
     assert k.D == 14 and k.n_actions == 5
     assert [k.action[i].theta_offset for i in range(5)] == [0, 3, 5, 8, 11]
     assert s.n_geoms == len(sc["geoms"])
+
+
+def test_batch_validation_names_the_problem(pkg):
+    L = pkg.load()
+    n = 3
+    scenes = (pkg.cem_scene_desc * n)()
+    skels = (pkg.cem_skeleton_desc * n)()
+    params = (pkg.cem_problem_params * n)()
+    for i in range(n):
+        sc, sk = workload.reach_scene()
+        scenes[i], skels[i] = pkg.pack_scene(sc, sk)
+        params[i].N, params[i].K = 64, 8
+    skels[1].D = 4  # slices no longer cover D
+    h = C.c_void_p()
+    assert L.cem_batch_create(scenes, skels, params, n, C.byref(h)) == -1
+    assert b"problem 1" in L.cem_last_error()
+    skels[1].D = 3
+    params[2].K = 5000
+    assert L.cem_batch_create(scenes, skels, params, n, C.byref(h)) == -5
+    assert L.cem_batch_create(scenes, skels, params, 0, C.byref(h)) == -5
+    assert L.cem_batch_iterate(None, 1, 1, None) == -1

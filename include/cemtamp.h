@@ -270,6 +270,54 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
 /* Simulated steps of one batch iteration: sum over problems of N * T. */
 long long cem_batch_steps_per_iteration(cem_batch_handle h);
 
+/* ---- Learned cost surrogate (not in the paper) ---------------------------
+ * An MLP score(x), x = [theta normalised to [-1, 1] by the bounds (clamped)
+ * and zero-padded to 32 | 16 scene features], `depth` hidden layers
+ * Linear + GELU of width `width`, a scalar output, then score = mu + sigma *
+ * out.  BF16 weights and activations, FP32 accumulation on the tensor cores,
+ * FP32 master weights.  Parameters are one FP32 vector: for each layer its
+ * weights (out x in, row-major) then its biases. */
+typedef struct cem_surrogate_ctx* cem_surrogate_handle;
+
+/* in_dim must be 48; width 8..1024 (multiple of 8); depth 1..8.  Weights
+ * start uniform in +-1/sqrt(fan_in) from `seed`; mu = 0, sigma = 1. */
+int cem_surrogate_create(int in_dim, int width, int depth, uint64_t seed, cem_surrogate_handle* out);
+int cem_surrogate_destroy(cem_surrogate_handle s);
+int cem_surrogate_num_params(cem_surrogate_handle s);
+/* Host copies of the FP32 parameters and of (mu, sigma); norm_h may be NULL.
+ * set_params also clears the optimiser state. */
+int cem_surrogate_set_params(cem_surrogate_handle s, const float* params_h, const float* norm_h);
+int cem_surrogate_get_params(cem_surrogate_handle s, float* params_h, float* norm_h);
+/* x_d[M][48] FP32 -> y_d[M] scores (stream-ordered). */
+int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float* y_d, void* stream);
+/* Full-batch gradient of mean((out - (t - mu)/sigma)^2) over M rows into
+ * grad_h (num_params floats) and the loss into *loss_h.  Synchronous. */
+int cem_surrogate_gradient(cem_surrogate_handle s, const float* x_d, const float* t_d, int M, float* grad_h,
+                           float* loss_h);
+/* `steps` AdamW steps (beta 0.9/0.999, eps 1e-8, decoupled decay on
+ * weights) on minibatches of `batch` rows drawn with replacement by Philox
+ * from (x_d[M][48], t_d[M]); normalize != 0 first sets (mu, sigma) to the
+ * targets' mean and standard deviation.  loss_hist_h (steps floats) may be
+ * NULL.  Synchronous. */
+int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t_d, int M, int batch, int steps,
+                        float lr, float weight_decay, uint64_t seed, int normalize, float* loss_hist_h);
+/* The surrogate's input features of N parameter vectors (FP32 x_d[N][48]). */
+int cem_surrogate_features(cem_surrogate_handle s, const float* theta_d, int N, int D, const float* lo_h,
+                           const float* hi_h, const float* scene16_h, float* x_d, void* stream);
+/* Screening: draw n_pool candidates from N(mean_d, chol_d chol_d^T) exactly
+ * as cem_sample does, score them, keep the n_keep lowest scores (ties by
+ * index) in ascending pool-index order: theta_keep_d[n_keep][D] and, if not
+ * NULL, their pool indices keep_idx_d[n_keep]. */
+int cem_surrogate_screen(cem_handle h, cem_surrogate_handle s, const float* mean_d, const float* chol_d, uint64_t seed,
+                         uint32_t iter, uint32_t problem, int n_pool, int n_keep, const float* scene16_h,
+                         float* theta_keep_d, int32_t* keep_idx_d, void* stream);
+/* Screened CE loop: as cem_solve, but each iteration samples n_pool
+ * candidates, rolls out only the p->N best-scored ones, and refits from
+ * their simulated costs (elites never come from the surrogate).
+ * Synchronous. */
+int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
+                       int n_pool, cem_result* out);
+
 /* Threads-per-block of the rollout kernel (0 = automatic). */
 int cem_set_launch(cem_handle h, int block_threads);
 /* Times candidate block sizes for this scene and N on the current device

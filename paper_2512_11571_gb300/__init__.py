@@ -31,6 +31,9 @@ EXPORTS = [
     "cem_rollout_trace", "cem_refit", "cem_solve", "cem_solve_static", "cem_set_launch", "cem_autotune",
     "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
+    "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
+    "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
+    "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened",
     "cem_last_error", "cem_version",
 ]
 
@@ -214,6 +217,20 @@ def load(path: str = LIB_PATH):
     L.cem_batch_set_launch.argtypes = [H, C.c_int, C.c_int]
     L.cem_batch_autotune.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
     L.cem_batch_steps_per_iteration.argtypes = [H]
+    fptr, i32ptr = C.POINTER(C.c_float), C.POINTER(C.c_int32)
+    L.cem_surrogate_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(H)]
+    L.cem_surrogate_destroy.argtypes = [H]
+    L.cem_surrogate_num_params.argtypes = [H]
+    L.cem_surrogate_set_params.argtypes = [H, fptr, fptr]
+    L.cem_surrogate_get_params.argtypes = [H, fptr, fptr]
+    L.cem_surrogate_forward.argtypes = [H, vp, C.c_int, vp, vp]
+    L.cem_surrogate_gradient.argtypes = [H, vp, vp, C.c_int, fptr, fptr]
+    L.cem_surrogate_train.argtypes = [H, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
+                                      C.c_int, fptr]
+    L.cem_surrogate_features.argtypes = [H, vp, C.c_int, C.c_int, fptr, fptr, fptr, vp, vp]
+    L.cem_surrogate_screen.argtypes = [H, H, vp, vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, fptr,
+                                       vp, vp, vp]
+    L.cem_solve_screened.argtypes = [H, H, fptr, C.POINTER(cem_solve_params), C.c_int, C.POINTER(cem_result)]
     L.cem_autotune.argtypes = [H, C.c_int, C.c_char_p, C.POINTER(C.c_int)]
     L.cem_last_error.restype = C.c_char_p
     L.cem_version.restype = C.c_char_p
@@ -409,6 +426,131 @@ class Batch:
         return cem_batch_steps_per_iteration(self.h)
 
 
+def _f32(a):
+    a = np.ascontiguousarray(a, np.float32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def cem_surrogate_create(in_dim=48, width=256, depth=4, seed=0):
+    h = C.c_void_p()
+    _check(load().cem_surrogate_create(in_dim, width, depth, seed, C.byref(h)))
+    return h
+
+
+def cem_surrogate_destroy(s):
+    _check(load().cem_surrogate_destroy(s))
+
+
+def cem_surrogate_num_params(s):
+    return int(load().cem_surrogate_num_params(s))
+
+
+def cem_surrogate_set_params(s, params, norm=None):
+    p, pp = _f32(params)
+    if norm is not None:
+        n, pn = _f32(norm)
+    _check(load().cem_surrogate_set_params(s, pp, pn if norm is not None else None))
+
+
+def cem_surrogate_get_params(s):
+    p = np.zeros(cem_surrogate_num_params(s), np.float32)
+    n = np.zeros(2, np.float32)
+    _check(load().cem_surrogate_get_params(s, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                           n.ctypes.data_as(C.POINTER(C.c_float))))
+    return p, n
+
+
+def cem_surrogate_forward(s, x, y, stream=None):
+    _check(load().cem_surrogate_forward(s, _ptr(x), x.shape[0], _ptr(y), _stream(stream)))
+
+
+def cem_surrogate_gradient(s, x, t):
+    g = np.zeros(cem_surrogate_num_params(s), np.float32)
+    loss = C.c_float()
+    _check(load().cem_surrogate_gradient(s, _ptr(x), _ptr(t), x.shape[0], g.ctypes.data_as(C.POINTER(C.c_float)),
+                                         C.byref(loss)))
+    return g, loss.value
+
+
+def cem_surrogate_train(s, x, t, batch, steps, lr=1e-3, weight_decay=1e-4, seed=0, normalize=True):
+    hist = np.zeros(max(steps, 1), np.float32)
+    _check(load().cem_surrogate_train(s, _ptr(x), _ptr(t), x.shape[0], batch, steps, lr, weight_decay, seed,
+                                      int(normalize), hist.ctypes.data_as(C.POINTER(C.c_float))))
+    return hist[:steps]
+
+
+def cem_surrogate_features(s, theta, lo, hi, scene16, x, stream=None):
+    lo_, plo = _f32(lo)
+    hi_, phi = _f32(hi)
+    sc_, psc = _f32(scene16)
+    _check(load().cem_surrogate_features(s, _ptr(theta), theta.shape[0], theta.shape[1], plo, phi, psc, _ptr(x),
+                                         _stream(stream)))
+
+
+def cem_surrogate_screen(h, s, mean, chol, seed, it, problem, n_pool, n_keep, scene16, theta_keep, keep_idx=None,
+                         stream=None):
+    sc_, psc = _f32(scene16)
+    _check(load().cem_surrogate_screen(h, s, _ptr(mean), _ptr(chol), seed, it, problem, n_pool, n_keep, psc,
+                                       _ptr(theta_keep), _ptr(keep_idx), _stream(stream)))
+
+
+def cem_solve_screened(h, s, scene16, params: cem_solve_params, n_pool):
+    sc_, psc = _f32(scene16)
+    out = cem_result()
+    _check(load().cem_solve_screened(h, s, psc, C.byref(params), n_pool, C.byref(out)))
+    return out
+
+
+class Surrogate:
+    """The cost surrogate MLP (one library handle)."""
+
+    def __init__(self, width=256, depth=4, seed=0):
+        self.h = cem_surrogate_create(48, width, depth, seed)
+
+    def close(self):
+        if self.h is not None and _lib is not None:
+            cem_surrogate_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, x, stream=None):
+        import torch
+
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        cem_surrogate_forward(self.h, x, y, stream)
+        return y
+
+    def train(self, x, t, batch=4096, steps=1000, lr=1e-3, weight_decay=1e-4, seed=0, normalize=True):
+        return cem_surrogate_train(self.h, x, t, batch, steps, lr, weight_decay, seed, normalize)
+
+    def features(self, theta, lo, hi, scene16, stream=None):
+        import torch
+
+        x = torch.empty((theta.shape[0], 48), dtype=torch.float32, device=theta.device)
+        cem_surrogate_features(self.h, theta, lo, hi, scene16, x, stream)
+        return x
+
+    def params(self):
+        return cem_surrogate_get_params(self.h)
+
+    def set_params(self, params, norm=None):
+        cem_surrogate_set_params(self.h, params, norm)
+
+    def gradient(self, x, t):
+        return cem_surrogate_gradient(self.h, x, t)
+
+
 # ----------------------------------------------------------- convenience
 class Scene:
     """A scene + plan skeleton on the device (one library handle)."""
@@ -505,6 +647,19 @@ class Scene:
 
     def set_launch(self, block):
         cem_set_launch(self.h, block)
+
+    def solve_screened(self, surrogate, scene16, seed, N, K, iters, n_pool, cov_mode="full", problem=0):
+        p = cem_solve_params()
+        p.seed, p.N, p.K, p.iters, p.cov_mode, p.problem = seed, N, K, iters, COV[cov_mode], problem
+        hist = np.zeros(iters, np.float32)
+        keff = np.zeros(iters, np.int32)
+        p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
+        p.k_eff_hist_h = keff.ctypes.data_as(C.POINTER(C.c_int32))
+        r = cem_solve_screened(self.h, surrogate.h, scene16, p, n_pool)
+        D = self.D
+        return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
+                    mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                    iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff)
 
     def autotune(self, N, cache_path=None):
         return cem_autotune(self.h, N, cache_path)

@@ -323,6 +323,99 @@ cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N
 }  // namespace
 
 namespace cem {
+const cem_skeleton_desc& handle_skeleton(cem_handle h) { return h->skel; }
+
+int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b) {
+  int rc = ensure_work(h, N, iters);
+  if (rc != CEM_OK) return rc;
+  b->theta = h->theta_d;
+  b->J = h->J_d;
+  b->cls = h->cls_d;
+  b->mean = h->mean_d;
+  b->cov = h->cov_d;
+  b->chol = h->chol_d;
+  b->keff = h->keff_d;
+  b->status = h->status_d;
+  b->track = h->track_d;
+  b->hist_J = h->hist_J_d;
+  b->hist_keff = h->hist_keff_d;
+  b->stream = h->stream;
+  b->ev0 = h->ev0;
+  b->ev1 = h->ev1;
+  b->scene = h->scene_d;
+  b->kind = h->host.kind;
+  b->block = default_block(h, N);
+  return CEM_OK;
+}
+
+int handle_init_distribution(cem_handle h, const cem_solve_params* p, SolveBuffers* b) {
+  const int D = h->skel.D;
+  std::vector<float> mean(D), cov((size_t)D * D, 0.0f), chol((size_t)D * D, 0.0f);
+  for (int d = 0; d < D; ++d) {
+    mean[d] = p->init_mean_h ? p->init_mean_h[d] : 0.5f * (h->skel.lo[d] + h->skel.hi[d]);
+    if (!p->init_cov_h) cov[d * D + d] = std::pow(0.25f * (h->skel.hi[d] - h->skel.lo[d]), 2.0f);
+  }
+  if (p->init_cov_h)
+    for (int i = 0; i < D * D; ++i) cov[i] = p->init_cov_h[i];
+  {  // host Cholesky of the initial covariance (FP64)
+    std::vector<double> L((size_t)D * D, 0.0);
+    for (int j = 0; j < D; ++j) {
+      double s = cov[j * D + j];
+      for (int k = 0; k < j; ++k) s -= L[j * D + k] * L[j * D + k];
+      if (!(s > 0.0)) return fail(CEM_ERR_NOT_PD, "initial covariance is not positive definite");
+      L[j * D + j] = std::sqrt(s);
+      for (int i = j + 1; i < D; ++i) {
+        double t = cov[i * D + j];
+        for (int k = 0; k < j; ++k) t -= L[i * D + k] * L[j * D + k];
+        L[i * D + j] = t / L[j * D + j];
+      }
+    }
+    for (int i = 0; i < D * D; ++i) chol[i] = (float)L[i];
+  }
+  Track tr;
+  std::memset(&tr, 0, sizeof(tr));
+  tr.iter = p->start_iter;
+  tr.base_iter = p->start_iter;
+  tr.best_cls = 4;
+  tr.best_J = INFINITY;
+  tr.hist_len = p->iters;
+  const int32_t zero = 0;
+  CEM_CUDA(cudaMemcpyAsync(b->mean, mean.data(), sizeof(float) * D, cudaMemcpyHostToDevice, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(b->cov, cov.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(b->chol, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(b->track, &tr, sizeof(Track), cudaMemcpyHostToDevice, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(b->status, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
+  // the host vectors are consumed before they go out of scope
+  CEM_CUDA(cudaStreamSynchronize(b->stream));
+  return CEM_OK;
+}
+
+int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b, cem_result* out) {
+  const int D = h->skel.D;
+  Track tr;
+  int32_t status = 0;
+  CEM_CUDA(cudaMemcpyAsync(&tr, b->track, sizeof(Track), cudaMemcpyDeviceToHost, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(out->mean, b->mean, sizeof(float) * D, cudaMemcpyDeviceToHost, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(out->cov, b->cov, sizeof(float) * D * D, cudaMemcpyDeviceToHost, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(&status, b->status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+  if (p->best_J_hist_h)
+    CEM_CUDA(cudaMemcpyAsync(p->best_J_hist_h, b->hist_J, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, b->stream));
+  if (p->k_eff_hist_h)
+    CEM_CUDA(cudaMemcpyAsync(p->k_eff_hist_h, b->hist_keff, sizeof(int32_t) * p->iters, cudaMemcpyDeviceToHost,
+                             b->stream));
+  CEM_CUDA(cudaStreamSynchronize(b->stream));
+  float ms = 0.0f;
+  CEM_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  out->elapsed_ms = ms;
+  out->D = D;
+  out->iters_done = (int32_t)(tr.iter - tr.base_iter);
+  out->best_J = tr.best_J;
+  out->best_class = tr.best_cls;
+  for (int d = 0; d < CEM_MAX_D; ++d) out->best_theta[d] = d < D ? tr.best_theta[d] : 0.0f;
+  if (status != 0) return fail(CEM_ERR_NOT_PD, "covariance not positive definite after the diagonal fallback");
+  return CEM_OK;
+}
+
 int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k) { return validate(s, k); }
 DevScene prepare_scene(const cem_scene_desc& s, const cem_skeleton_desc& k) { return prepare(s, k); }
 int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
@@ -463,49 +556,15 @@ int cem_refit(cem_handle h, const float* theta_d, const float* J_d, const uint8_
 int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out) {
   g_err.clear();
   if (!h || !p || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
-  const int D = h->skel.D;
   if (p->N < 1 || p->N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 1..2^20");
   if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..1024");
   if (p->iters < 1 || p->iters > 100000) return fail(CEM_ERR_UNSUPPORTED, "iters must be in 1..1e5");
   if (p->cov_mode != CEM_COV_FULL && p->cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
-  int rc = ensure_work(h, p->N, p->iters);
+  SolveBuffers b;
+  int rc = cem::handle_solve_buffers(h, p->N, p->iters, &b);
   if (rc != CEM_OK) return rc;
-  // initial distribution (host) -> device
-  std::vector<float> mean(D), cov((size_t)D * D, 0.0f), chol((size_t)D * D, 0.0f);
-  for (int d = 0; d < D; ++d) {
-    mean[d] = p->init_mean_h ? p->init_mean_h[d] : 0.5f * (h->skel.lo[d] + h->skel.hi[d]);
-    if (!p->init_cov_h) cov[d * D + d] = std::pow(0.25f * (h->skel.hi[d] - h->skel.lo[d]), 2.0f);
-  }
-  if (p->init_cov_h)
-    for (int i = 0; i < D * D; ++i) cov[i] = p->init_cov_h[i];
-  {  // host Cholesky of the initial covariance (FP64)
-    std::vector<double> L((size_t)D * D, 0.0);
-    for (int j = 0; j < D; ++j) {
-      double s = cov[j * D + j];
-      for (int k = 0; k < j; ++k) s -= L[j * D + k] * L[j * D + k];
-      if (!(s > 0.0)) return fail(CEM_ERR_NOT_PD, "initial covariance is not positive definite");
-      L[j * D + j] = std::sqrt(s);
-      for (int i = j + 1; i < D; ++i) {
-        double t = cov[i * D + j];
-        for (int k = 0; k < j; ++k) t -= L[i * D + k] * L[j * D + k];
-        L[i * D + j] = t / L[j * D + j];
-      }
-    }
-    for (int i = 0; i < D * D; ++i) chol[i] = (float)L[i];
-  }
-  Track tr;
-  std::memset(&tr, 0, sizeof(tr));
-  tr.iter = p->start_iter;
-  tr.base_iter = p->start_iter;
-  tr.best_cls = 4;
-  tr.best_J = INFINITY;
-  tr.hist_len = p->iters;
-  const int32_t zero = 0;
-  CEM_CUDA(cudaMemcpyAsync(h->mean_d, mean.data(), sizeof(float) * D, cudaMemcpyHostToDevice, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(h->cov_d, cov.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(h->track_d, &tr, sizeof(Track), cudaMemcpyHostToDevice, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(h->status_d, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  rc = cem::handle_init_distribution(h, p, &b);
+  if (rc != CEM_OK) return rc;
   if (p->use_graph) {
     const bool stale = !h->graph || h->graph_N != p->N || h->graph_K != p->K || h->graph_cov != p->cov_mode ||
                        h->graph_seed != p->seed || h->graph_problem != p->problem;
@@ -540,26 +599,7 @@ int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out) {
     }
   }
   CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
-  int32_t status = 0;
-  CEM_CUDA(cudaMemcpyAsync(&tr, h->track_d, sizeof(Track), cudaMemcpyDeviceToHost, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(out->mean, h->mean_d, sizeof(float) * D, cudaMemcpyDeviceToHost, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(out->cov, h->cov_d, sizeof(float) * D * D, cudaMemcpyDeviceToHost, h->stream));
-  CEM_CUDA(cudaMemcpyAsync(&status, h->status_d, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
-  if (p->best_J_hist_h)
-    CEM_CUDA(cudaMemcpyAsync(p->best_J_hist_h, h->hist_J_d, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, h->stream));
-  if (p->k_eff_hist_h)
-    CEM_CUDA(cudaMemcpyAsync(p->k_eff_hist_h, h->hist_keff_d, sizeof(int32_t) * p->iters, cudaMemcpyDeviceToHost, h->stream));
-  CEM_CUDA(cudaStreamSynchronize(h->stream));
-  float ms = 0.0f;
-  CEM_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-  out->elapsed_ms = ms;
-  out->D = D;
-  out->iters_done = (int32_t)(tr.iter - tr.base_iter);
-  out->best_J = tr.best_J;
-  out->best_class = tr.best_cls;
-  for (int d = 0; d < CEM_MAX_D; ++d) out->best_theta[d] = d < D ? tr.best_theta[d] : 0.0f;
-  if (status != 0) return fail(CEM_ERR_NOT_PD, "covariance not positive definite after the diagonal fallback");
-  return CEM_OK;
+  return cem::handle_read_result(h, p, &b, out);
 }
 
 int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {

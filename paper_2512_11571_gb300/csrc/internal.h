@@ -125,4 +125,30 @@ int default_rollout_block(int N);
 // records the thread-local message returned by cem_last_error; returns code
 int set_last_error(int code, const std::string& msg);
 
+// The device workspace of a handle's CE loop (cem_solve and the screened
+// loop share it).
+struct SolveBuffers {
+  float* theta;
+  float* J;
+  uint8_t* cls;
+  float* mean;
+  float* cov;
+  float* chol;
+  int32_t* keff;
+  int32_t* status;
+  Track* track;
+  float* hist_J;
+  int32_t* hist_keff;
+  cudaStream_t stream;
+  cudaEvent_t ev0, ev1;
+  const DevScene* scene;
+  int kind, block;
+};
+const cem_skeleton_desc& handle_skeleton(cem_handle h);
+int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b);
+// initial distribution of cem_solve_params (or the default) and a fresh loop state
+int handle_init_distribution(cem_handle h, const cem_solve_params* p, SolveBuffers* b);
+// copies the loop's results to the host, synchronises and fills *out
+int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b, cem_result* out);
+
 }  // namespace cem

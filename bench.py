@@ -59,6 +59,7 @@ def parse():
                     help="time only the rollout kernel of one workload (profiling driver)")
     ap.add_argument("--n", type=int, default=0, help="samples for --rollout-only (0 = the workload's N)")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
+    ap.add_argument("--skip-surrogate", action="store_true", help="leave out the time-to-cost comparison")
     return ap.parse_args()
 
 
@@ -237,6 +238,31 @@ def batched_measurement(P, seed, rank, iters=3):
             "kernels_per_iteration": 3}
 
 
+def time_to_cost(seed):
+    """CE time-to-cost, surrogate-screened vs plain, on the pick-place task:
+    a surrogate trained on 1,048,576 simulator rollouts (64 training scenes),
+    then plain CE (N = 16384, K = 512, 25 iterations) and screened CE (pool
+    65536, the same 16384 rollouts per iteration, 8192 of them unscreened)
+    on three held-out scenes."""
+    import time as _t
+
+    from paper_2512_11571_gb300 import screening
+
+    t0 = _t.perf_counter()
+    X, t = screening.training_set(n_scenes=64, per_scene=16384)
+    t_data = _t.perf_counter() - t0
+    t0 = _t.perf_counter()
+    sur, hist = screening.train_surrogate(X, t, steps=3000)
+    t_train = _t.perf_counter() - t0
+    del X, t
+    rows = screening.compare(sur, [seed, seed + 1, seed + 2])
+    sur.close()
+    return {"training_rollouts": 64 * 16384, "data_s": t_data, "train_s": t_train,
+            "train_loss_first_last": [float(hist[:10].mean()), float(hist[-10:].mean())], "scenes": rows,
+            "mean_plain_J": float(np.mean([r["plain_J"] for r in rows])),
+            "mean_screened_J": float(np.mean([r["screened_J"] for r in rows]))}
+
+
 def run_gb300(args):
     import torch
 
@@ -328,6 +354,9 @@ def run_gb300(args):
     # the 64-problem batched workload: one persistent launch per iteration
     batch = batched_measurement(P, args.seed, rank)
 
+    # CE time-to-cost: surrogate-screened vs plain (pick-place)
+    ttc = time_to_cost(args.seed) if rank == 0 and not args.skip_surrogate else None
+
     # end to end through the public API with host buffers: cem_solve, one
     # iteration per step, distribution in from pinned host memory and the
     # best sample / new distribution back to the host
@@ -375,6 +404,7 @@ def run_gb300(args):
             "e2e": {"value": e_units / e_secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "batched_64": batch,
+            "time_to_cost": ttc,
             "gpu_launches": 3 * args.steps,
             "gpu_launches_outside_timed_region": 5 + 3 * (args.steps + 1),
             "clocks": clocks,

@@ -28,7 +28,7 @@
  *     cem_scene_destroy / cem_batch_destroy.
  *   - Return value 0 is success; negative values are the cem_status codes
  *     below, with a message in cem_last_error() (thread-local).
- *   - Limits: D <= CEM_MAX_D, N <= 2^20, K <= 1024, T <= 1,000,000.
+ *   - Limits: D <= CEM_MAX_D, N <= 2^20, K <= 4096, T <= 1,000,000.
  *
  * A handle may be used from one host thread at a time; calls on different
  * handles are independent.
@@ -46,7 +46,7 @@ extern "C" {
 #define CEM_MAX_ACTIONS 6
 #define CEM_MAX_GEOMS 16
 #define CEM_MAX_SLABS 6
-#define CEM_MAX_K 1024
+#define CEM_MAX_K 4096
 #define CEM_MAX_N (1 << 20)
 #define CEM_TRACE_W 20
 #define CEM_MAX_BATCH 1024
@@ -181,7 +181,7 @@ int cem_rollout_trace(cem_handle h, const float* theta_d, int N, int steps, floa
  * (1e-4 range)^2) and its Cholesky factor; one elite -> cov =
  * diag((0.05 range)^2).  mean_d/cov_d/chol_d are read-write and kept when
  * no elite exists.  elite_idx_d (K entries, ascending key) and k_eff_d may
- * be NULL.  Errors: CEM_ERR_UNSUPPORTED if K > 1024. */
+ * be NULL.  Errors: CEM_ERR_UNSUPPORTED if K > 4096. */
 int cem_refit(cem_handle h, const float* theta_d, const float* J_d, const uint8_t* cls_d, int N, int K,
               int cov_mode, float* mean_d, float* cov_d, float* chol_d, int32_t* elite_idx_d, int32_t* k_eff_d,
               void* stream);
@@ -301,6 +301,9 @@ int cem_surrogate_gradient(cem_surrogate_handle s, const float* x_d, const float
  * NULL.  Synchronous. */
 int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t_d, int M, int batch, int steps,
                         float lr, float weight_decay, uint64_t seed, int normalize, float* loss_hist_h);
+/* Training target of simulated samples: t_d[n] = log(1 + J_d[n] + 10 *
+ * cls_d[n]) (non-finite costs map to log(1 + 1e6)), monotone in the CE key. */
+int cem_surrogate_targets(const float* J_d, const uint8_t* cls_d, int N, float* t_d, void* stream);
 /* The surrogate's input features of N parameter vectors (FP32 x_d[N][48]). */
 int cem_surrogate_features(cem_surrogate_handle s, const float* theta_d, int N, int D, const float* lo_h,
                            const float* hi_h, const float* scene16_h, float* x_d, void* stream);
@@ -312,11 +315,12 @@ int cem_surrogate_screen(cem_handle h, cem_surrogate_handle s, const float* mean
                          uint32_t iter, uint32_t problem, int n_pool, int n_keep, const float* scene16_h,
                          float* theta_keep_d, int32_t* keep_idx_d, void* stream);
 /* Screened CE loop: as cem_solve, but each iteration samples n_pool
- * candidates, rolls out only the p->N best-scored ones, and refits from
- * their simulated costs (elites never come from the surrogate).
- * Synchronous. */
+ * candidates and rolls out p->N of them: the first n_explore draws
+ * unscreened (exploration from the current distribution) and the
+ * p->N - n_explore best-scored of the rest; the refit uses their simulated
+ * costs only (elites never come from the surrogate).  Synchronous. */
 int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
-                       int n_pool, cem_result* out);
+                       int n_pool, int n_explore, cem_result* out);
 
 /* Threads-per-block of the rollout kernel (0 = automatic). */
 int cem_set_launch(cem_handle h, int block_threads);

@@ -18,7 +18,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcemtamp.so")
 
-MAX_D, MAX_ACTIONS, MAX_GEOMS, MAX_SLABS, MAX_K, TRACE_W = 18, 6, 16, 6, 1024, 20
+MAX_D, MAX_ACTIONS, MAX_GEOMS, MAX_SLABS, MAX_K, TRACE_W = 18, 6, 16, 6, 4096, 20
 SCENE_KIND = {"quadratic": 0, "reach": 1, "push": 2, "pickplace": 3}
 ACTION_KIND = {"move": 0, "push": 1, "grasp": 2, "place": 3}
 ACTION_WIDTH = {"move": 3, "push": 3, "grasp": 2, "place": 3}
@@ -33,7 +33,7 @@ EXPORTS = [
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
-    "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened",
+    "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
     "cem_last_error", "cem_version",
 ]
 
@@ -228,9 +228,11 @@ def load(path: str = LIB_PATH):
     L.cem_surrogate_train.argtypes = [H, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
                                       C.c_int, fptr]
     L.cem_surrogate_features.argtypes = [H, vp, C.c_int, C.c_int, fptr, fptr, fptr, vp, vp]
+    L.cem_surrogate_targets.argtypes = [vp, vp, C.c_int, vp, vp]
     L.cem_surrogate_screen.argtypes = [H, H, vp, vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, fptr,
                                        vp, vp, vp]
-    L.cem_solve_screened.argtypes = [H, H, fptr, C.POINTER(cem_solve_params), C.c_int, C.POINTER(cem_result)]
+    L.cem_solve_screened.argtypes = [H, H, fptr, C.POINTER(cem_solve_params), C.c_int, C.c_int,
+                                     C.POINTER(cem_result)]
     L.cem_autotune.argtypes = [H, C.c_int, C.c_char_p, C.POINTER(C.c_int)]
     L.cem_last_error.restype = C.c_char_p
     L.cem_version.restype = C.c_char_p
@@ -487,6 +489,10 @@ def cem_surrogate_features(s, theta, lo, hi, scene16, x, stream=None):
                                          _stream(stream)))
 
 
+def cem_surrogate_targets(J, cls, t, stream=None):
+    _check(load().cem_surrogate_targets(_ptr(J), _ptr(cls), J.shape[0], _ptr(t), _stream(stream)))
+
+
 def cem_surrogate_screen(h, s, mean, chol, seed, it, problem, n_pool, n_keep, scene16, theta_keep, keep_idx=None,
                          stream=None):
     sc_, psc = _f32(scene16)
@@ -494,10 +500,10 @@ def cem_surrogate_screen(h, s, mean, chol, seed, it, problem, n_pool, n_keep, sc
                                        _ptr(theta_keep), _ptr(keep_idx), _stream(stream)))
 
 
-def cem_solve_screened(h, s, scene16, params: cem_solve_params, n_pool):
+def cem_solve_screened(h, s, scene16, params: cem_solve_params, n_pool, n_explore=0):
     sc_, psc = _f32(scene16)
     out = cem_result()
-    _check(load().cem_solve_screened(h, s, psc, C.byref(params), n_pool, C.byref(out)))
+    _check(load().cem_solve_screened(h, s, psc, C.byref(params), n_pool, n_explore, C.byref(out)))
     return out
 
 
@@ -648,14 +654,15 @@ class Scene:
     def set_launch(self, block):
         cem_set_launch(self.h, block)
 
-    def solve_screened(self, surrogate, scene16, seed, N, K, iters, n_pool, cov_mode="full", problem=0):
+    def solve_screened(self, surrogate, scene16, seed, N, K, iters, n_pool, n_explore=0, cov_mode="full",
+                       problem=0):
         p = cem_solve_params()
         p.seed, p.N, p.K, p.iters, p.cov_mode, p.problem = seed, N, K, iters, COV[cov_mode], problem
         hist = np.zeros(iters, np.float32)
         keff = np.zeros(iters, np.int32)
         p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
         p.k_eff_hist_h = keff.ctypes.data_as(C.POINTER(C.c_int32))
-        r = cem_solve_screened(self.h, surrogate.h, scene16, p, n_pool)
+        r = cem_solve_screened(self.h, surrogate.h, scene16, p, n_pool, n_explore)
         D = self.D
         return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                     mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),

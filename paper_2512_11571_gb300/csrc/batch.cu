@@ -109,7 +109,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
     if (q.N < 1 || q.N > CEM_MAX_N || q.K < 1 || q.K > CEM_MAX_K ||
         (q.cov_mode != CEM_COV_FULL && q.cov_mode != CEM_COV_DIAG)) {
       delete h;
-      return fail(CEM_ERR_UNSUPPORTED, "problem " + std::to_string(p) + ": N in 1..2^20, K in 1..1024, known cov mode");
+      return fail(CEM_ERR_UNSUPPORTED, "problem " + std::to_string(p) + ": N in 1..2^20, K in 1..4096, known cov mode");
     }
     host[p] = prepare_scene(scenes[p], skels[p]);
     BatchProblem b;

@@ -535,7 +535,7 @@ int cem_refit(cem_handle h, const float* theta_d, const float* J_d, const uint8_
   g_err.clear();
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   if (N < 0 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 0..2^20");
-  if (K < 1 || K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..1024");
+  if (K < 1 || K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..4096");
   if (cov_mode != CEM_COV_FULL && cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
   if (!is_device_ptr(mean_d) || !is_device_ptr(cov_d) || !is_device_ptr(chol_d))
     return fail(CEM_ERR_INVALID_ARG, "mean, cov and chol must be device pointers");
@@ -557,7 +557,7 @@ int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out) {
   g_err.clear();
   if (!h || !p || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
   if (p->N < 1 || p->N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 1..2^20");
-  if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..1024");
+  if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..4096");
   if (p->iters < 1 || p->iters > 100000) return fail(CEM_ERR_UNSUPPORTED, "iters must be in 1..1e5");
   if (p->cov_mode != CEM_COV_FULL && p->cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
   SolveBuffers b;

@@ -14,7 +14,8 @@
 // One CTA of 1024 threads per problem.  Selection is an exact MSB-first
 // radix select over 52-bit keys (32-bit order-preserving cost bits, 20-bit
 // index) with shared-memory histograms, then a bitonic sort of the K_eff
-// elites; ties are impossible because the index is part of the key.  The
+// elites (<= 4096 keys in shared memory; elite rows are read through L2);
+// ties are impossible because the index is part of the key.  The
 // statistics are accumulated in FP64 by groups of four threads per output
 // with a fixed reduction order (run-to-run deterministic), and one warp
 // factorises the covariance.
@@ -127,7 +128,6 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
     int P = 1;
     while (P < keff) P <<= 1;
     uint64_t* keys = reinterpret_cast<uint64_t*>(dyn);
-    float* eth = reinterpret_cast<float*>(dyn + sizeof(uint64_t) * P);
     for (int i = tid; i < P; i += RT) keys[i] = ~0ull;
     __syncthreads();
     for (int i = tid; i < N; i += RT) {
@@ -153,16 +153,14 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
         }
         __syncthreads();
       }
-    for (int e = tid; e < keff; e += RT) {
-      const int idx = (int)(keys[e] & 0xFFFFF);
-      if (a.elite_idx) a.elite_idx[e] = idx;
-      for (int d = 0; d < D; ++d) eth[e * D + d] = a.theta[(size_t)idx * D + d];
-    }
-    __syncthreads();
+    if (a.elite_idx)
+      for (int e = tid; e < keff; e += RT) a.elite_idx[e] = (int)(keys[e] & 0xFFFFF);
+    // elite e's parameter row (read through L2; the keys stay in shared memory)
+    auto eth = [&](int e, int d) -> float { return a.theta[(size_t)(keys[e] & 0xFFFFF) * D + d]; };
     // statistics in FP64: 4 threads per output, fixed reduction order
     const int grp = tid >> 2, part = tid & 3;
     if (keff == 1) {
-      if (tid < D) s_mean[tid] = (double)eth[tid];
+      if (tid < D) s_mean[tid] = (double)eth(0, tid);
       for (int i = tid; i < D * D; i += RT) {
         const int r = i / D, c = i % D;
         const double w = 0.05 * ((double)a.hi[r] - (double)a.lo[r]);
@@ -172,7 +170,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
     } else {
       double v = 0.0;
       if (grp < D)
-        for (int e = part; e < keff; e += 4) v += (double)eth[e * D + grp];
+        for (int e = part; e < keff; e += 4) v += (double)eth(e, grp);
       v += __shfl_down_sync(0xffffffffu, v, 2);
       v += __shfl_down_sync(0xffffffffu, v, 1);
       if (grp < D && part == 0) s_mean[grp] = v / keff;
@@ -191,7 +189,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
       v = 0.0;
       if (grp < npair) {
         const double mi = s_mean[pi], mj = s_mean[pj];
-        for (int e = part; e < keff; e += 4) v += ((double)eth[e * D + pi] - mi) * ((double)eth[e * D + pj] - mj);
+        for (int e = part; e < keff; e += 4) v += ((double)eth(e, pi) - mi) * ((double)eth(e, pj) - mj);
       }
       v += __shfl_down_sync(0xffffffffu, v, 2);
       v += __shfl_down_sync(0xffffffffu, v, 1);
@@ -272,9 +270,10 @@ __global__ void __launch_bounds__(RT) refit_batch_kernel(const RefitArgs* __rest
 }  // namespace
 
 size_t refit_smem_bytes(int K, int D) {
+  (void)D;
   int P = 1;
   while (P < K) P <<= 1;
-  return sizeof(uint64_t) * (size_t)P + sizeof(float) * (size_t)K * D;
+  return sizeof(uint64_t) * (size_t)P;
 }
 
 cudaError_t configure_refit() {

@@ -126,7 +126,7 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   if (p->N < 1 || (long long)p->N * D > kMaxParams)
     return fail(CEM_ERR_UNSUPPORTED, "cem_solve_static holds at most N * D = 262144 parameters (N >= 1)");
   if (p->iters < 1 || p->iters > kMaxIters) return fail(CEM_ERR_UNSUPPORTED, "cem_solve_static runs 1..4096 iterations");
-  if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..1024");
+  if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..4096");
   if (p->cov_mode != CEM_COV_FULL && p->cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
   const Layout L = layout(p->N, D);
   if (L.end > kScratchBytes) return fail(CEM_ERR_UNSUPPORTED, "request does not fit the 2 MiB scratch array");

@@ -436,6 +436,23 @@ __global__ void __launch_bounds__(1024) topk_kernel(const float* __restrict__ sc
     }
 }
 
+// the first n_explore pool entries are kept whatever their score (unscreened
+// draws from the current distribution): give them the lowest finite score
+__global__ void force_keep_kernel(float* __restrict__ score, int n_explore) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_explore) score[i] = -3.402823466e38f;
+}
+
+// training target of a simulated sample: log(1 + J + 10 * class), which
+// orders samples like the CE key (class first) and compresses large costs
+__global__ void score_target_kernel(const float* __restrict__ J, const uint8_t* __restrict__ cls, int N,
+                                    float* __restrict__ t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const float j = J[i];
+  t[i] = isfinite(j) ? log1pf(fmaxf(j, 0.0f) + 10.0f * (float)cls[i]) : log1pf(1e6f);
+}
+
 __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ idx, int n, int D,
                                    float* __restrict__ dst) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -888,12 +905,18 @@ int ensure_pool(cem_surrogate_ctx* s, int P, int N, int D) {
 
 // pool theta (already sampled, P x D) -> scores -> indices of the N best ->
 // theta_keep (N x D), all on `st`
-cudaError_t screen_pool(cem_surrogate_ctx* s, int P, int N, int D, float* theta_keep, cudaStream_t st) {
+cudaError_t screen_pool(cem_surrogate_ctx* s, int P, int N, int n_explore, int D, float* theta_keep,
+                        cudaStream_t st) {
   features_kernel<bf16><<<(P + 127) / 128, 128, 0, st>>>(s->pool_theta, P, D, s->lohi, s->scene16, s->xin);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = forward_rows(s, P, s->pool_score, st);
   if (e != cudaSuccess) return e;
+  if (n_explore > 0) {
+    force_keep_kernel<<<(n_explore + 255) / 256, 256, 0, st>>>(s->pool_score, n_explore);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   topk_kernel<<<1, 1024, 0, st>>>(s->pool_score, P, N, s->keep_idx);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -933,19 +956,20 @@ int cem_surrogate_screen(cem_handle h, cem_surrogate_handle s, const float* mean
   rc = set_tables(s, k, scene16_h, st);
   if (rc != CEM_OK) return rc;
   SUR_CUDA(launch_sample(mean_d, chol_d, seed, nullptr, iter, problem, n_pool, k.D, s->pool_theta, st));
-  SUR_CUDA(screen_pool(s, n_pool, n_keep, k.D, theta_keep_d, st));
+  SUR_CUDA(screen_pool(s, n_pool, n_keep, 0, k.D, theta_keep_d, st));
   if (keep_idx_d)
     SUR_CUDA(cudaMemcpyAsync(keep_idx_d, s->keep_idx, sizeof(int32_t) * n_keep, cudaMemcpyDeviceToDevice, st));
   return CEM_OK;
 }
 
 int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
-                       int n_pool, cem_result* out) {
+                       int n_pool, int n_explore, cem_result* out) {
   set_last_error(CEM_OK, "");
   if (!h || !s || !scene16_h || !p || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
   if (p->N < 1 || n_pool < p->N || n_pool > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "1 <= N <= n_pool <= 2^20");
+  if (n_explore < 0 || n_explore > p->N) return fail(CEM_ERR_INVALID_ARG, "0 <= n_explore <= N");
   if (p->K < 1 || p->K > CEM_MAX_K || p->iters < 1 || p->iters > 100000)
-    return fail(CEM_ERR_UNSUPPORTED, "K in 1..1024, iters in 1..1e5");
+    return fail(CEM_ERR_UNSUPPORTED, "K in 1..4096, iters in 1..1e5");
   const cem_skeleton_desc& k = handle_skeleton(h);
   const int D = k.D, N = p->N;
   int rc = ensure_pool(s, n_pool, N, D);
@@ -982,7 +1006,7 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
   SUR_CUDA(cudaEventRecord(b.ev0, st));
   for (int j = 0; j < p->iters; ++j) {
     SUR_CUDA(launch_sample(b.mean, b.chol, p->seed, &b.track->iter, 0, p->problem, n_pool, D, s->pool_theta, st));
-    SUR_CUDA(screen_pool(s, n_pool, N, D, b.theta, st));
+    SUR_CUDA(screen_pool(s, n_pool, N, n_explore, D, b.theta, st));
     SUR_CUDA(launch_rollout(b.scene, b.kind, b.theta, N, b.J, b.cls, b.block, st));
     SUR_CUDA(launch_refit(a, st));
   }
@@ -991,3 +1015,12 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
 }
 
 }  // extern "C"
+
+extern "C" int cem_surrogate_targets(const float* J_d, const uint8_t* cls_d, int N, float* t_d, void* stream) {
+  if (N < 0) return fail(CEM_ERR_INVALID_ARG, "N must be >= 0");
+  if (N == 0) return CEM_OK;
+  if (!is_dev(J_d) || !is_dev(cls_d) || !is_dev(t_d)) return fail(CEM_ERR_INVALID_ARG, "J, cls and t must be device pointers");
+  score_target_kernel<<<(N + 255) / 256, 256, 0, (cudaStream_t)stream>>>(J_d, cls_d, N, t_d);
+  SUR_CUDA(cudaGetLastError());
+  return CEM_OK;
+}

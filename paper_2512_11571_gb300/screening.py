@@ -1,0 +1,89 @@
+"""Surrogate-screened CE on the pick-place task: training data from the
+simulator, training, and the screened-vs-plain comparison.
+
+Sequencing only: every sample, rollout, feature, target, training step and
+screening step runs in libcemtamp's kernels; torch holds device memory.
+
+Training data: for each training scene, half of the samples come from the
+initial CE distribution and half from the distribution after a few plain CE
+iterations on that scene (the region CE visits next); target =
+log(1 + J + 10 * class).  Screening keeps CE's simulation budget and elite
+rule (elites from simulated costs only) and spends the surrogate on choosing
+which candidates of a larger pool get simulated, keeping an unscreened
+exploration share so that the elite set is not confined to the surrogate's
+predicted basin.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import workload
+
+from . import COV, Scene, Surrogate, cem_surrogate_targets
+
+
+def _dev(a):
+    import torch
+
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def training_set(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surrogate=None):
+    """(X [n_scenes*per_scene, 48], t) on the device from pick-place scenes
+    seed0 .. seed0 + n_scenes - 1."""
+    import torch
+
+    own = surrogate is None
+    sur = Surrogate(64, 1) if own else surrogate
+    X, T = [], []
+    try:
+        for s in range(n_scenes):
+            sc, sk, _ = workload.config(2, seed=seed0 + s)
+            f16 = workload.scene_features(sc)
+            lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+            with Scene(sc, sk) as S:
+                r = S.solve(s, 4096, 256, warm_iters)
+                dists = [((lo + hi) / 2, np.diag((hi - lo) / 4)),
+                         (r["mean"], np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo))))]
+                for j, (m, c) in enumerate(dists):
+                    th = S.sample(_dev(m), _dev(c), 77 + s, j, per_scene // 2)
+                    J, cls = S.rollout(th)
+                    t = torch.empty_like(J)
+                    cem_surrogate_targets(J, cls, t)
+                    X.append(sur.features(th, lo, hi, f16))
+                    T.append(t)
+    finally:
+        if own:
+            sur.close()
+    return torch.cat(X), torch.cat(T)
+
+
+def train_surrogate(X, t, width=256, depth=4, steps=3000, batch=8192, lr=1e-3, seed=0):
+    sur = Surrogate(width, depth, seed=seed)
+    hist = sur.train(X, t, batch=batch, steps=steps, lr=lr, weight_decay=1e-4, seed=seed + 1)
+    return sur, hist
+
+
+def compare(sur, scene_seeds, N=16384, K=512, iters=25, n_pool=65536, n_explore=8192):
+    """Plain CE and surrogate-screened CE (same rollouts per iteration) on
+    held-out scenes: final best cost, loop time, and time to reach 1% of the
+    plain run's final cost."""
+    rows = []
+    for s in scene_seeds:
+        sc, sk, _ = workload.config(2, seed=s)
+        f16 = workload.scene_features(sc)
+        with Scene(sc, sk) as S:
+            S.solve(s, N, K, 1)  # warm-up (allocation, graph)
+            a = S.solve(s, N, K, iters)
+            b = S.solve_screened(sur, f16, seed=s, N=N, K=K, iters=iters, n_pool=n_pool, n_explore=n_explore)
+        target = 1.01 * a["best_J"]
+
+        def ttc(r):
+            t = r["elapsed_ms"] * np.arange(1, iters + 1) / iters
+            ok = np.where(r["history"] <= target)[0]
+            return float(t[ok[0]]) if len(ok) else None
+
+        rows.append(dict(scene=s, plain_J=float(a["best_J"]), plain_ms=a["elapsed_ms"], plain_cls=a["best_cls"],
+                         screened_J=float(b["best_J"]), screened_ms=b["elapsed_ms"], screened_cls=b["best_cls"],
+                         plain_ttc_ms=ttc(a), screened_ttc_ms=ttc(b)))
+    return rows

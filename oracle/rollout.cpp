@@ -245,11 +245,12 @@ void planar_rollout(const or_scene& s, const Prep& pp, const double* th, int T, 
     R nx = R(0.0), ny = R(0.0), dep = R(0.0), qx = R(0.0), qy = R(0.0), Fn = R(0.0);
     R rax = R(0.0), ray = R(0.0), rbx = R(0.0), rby = R(0.0);
     if (has_block) {
-      // broad phase: the rectangles can only touch if their bounding circles do
+      // broad phase: the rectangles can only touch if the block's bounding
+      // circle reaches the base rectangle (tested in the base frame)
       R cdx = k.x - b.x, cdy = k.y - b.y;
-      const double rsum = std::sqrt(s.base_half[0] * s.base_half[0] + s.base_half[1] * s.base_half[1]) +
-                          std::sqrt(s.block_half[0] * s.block_half[0] + s.block_half[1] * s.block_half[1]);
-      if (cdx * cdx + cdy * cdy < R(rsum * rsum))
+      R cbp = Cos(b.psi), sbp = Sin(b.psi);
+      const double rk = std::sqrt(s.block_half[0] * s.block_half[0] + s.block_half[1] * s.block_half[1]);
+      if (Abs(cdx * cbp + cdy * sbp) < R(s.base_half[0] + rk) && Abs(cdy * cbp - cdx * sbp) < R(s.base_half[1] + rk))
         hit = sat_rect(b, s.base_half[0], s.base_half[1], k, s.block_half[0], s.block_half[1], nx, ny, dep, qx, qy);
       if (hit) {
         rax = qx - b.x; ray = qy - b.y; rbx = qx - k.x; rby = qy - k.y;

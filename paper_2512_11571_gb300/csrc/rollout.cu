@@ -89,11 +89,18 @@ __device__ __forceinline__ int corners_local(float dx, float dy, float uix, floa
 // B.w; the minimum overlap (first on ties) gives the normal (A -> B) and the
 // depth.  Contact point: penetration-weighted mean of the incident corners
 // inside the reference body (roles swapped if none; midpoint last).
+// sine and cosine of a yaw angle: wrapped into [-pi, pi], where the hardware
+// unit is accurate to ~5e-7 (a spinning block's yaw grows without bound)
+__device__ __forceinline__ void yaw_sincos(float psi, float* sn, float* cs) {
+  const float w = psi - 6.28318530717958648f * rintf(psi * 0.159154943091895336f);
+  __sincosf(w, sn, cs);
+}
+
 __device__ __forceinline__ bool sat_rect(const B2& A, float ahx, float ahy, const B2& B, float bhx, float bhy,
                                          float& nx, float& ny, float& depth, float& qx, float& qy) {
   float sa, ca, sb, cb;
-  sincosf(A.psi, &sa, &ca);
-  sincosf(B.psi, &sb, &cb);
+  yaw_sincos(A.psi, &sa, &ca);
+  yaw_sincos(B.psi, &sb, &cb);
   const float c = ca * cb + sa * sb, s = ca * sb - sa * cb;
   const float ac = fabsf(c), as = fabsf(s);
   const float dx = B.x - A.x, dy = B.y - A.y;
@@ -192,7 +199,12 @@ __device__ __noinline__ void planar_rollout(const DevScene& s, const float* __re
   const float kc = s.k_contact, cc = s.c_contact, mu_dt = s.contact_mu * s.dt, flim = s.force_limit;
   const float inv_mb = 1.0f / s.mb, inv_Ib = 1.0f / s.Ib;
   const float inv_mk = HAS_BLOCK ? 1.0f / s.mk : 0.0f, inv_Ik = HAS_BLOCK ? 1.0f / s.Ik : 0.0f;
-  const float rsum = sqrtf(bhx * bhx + bhy * bhy) + sqrtf(khx * khx + khy * khy), rsum2 = rsum * rsum;
+  // broad phase: the block's bounding circle (radius rk) against the base
+  // rectangle, in the base frame; the hardware sine/cosine is off by < 1e-6,
+  // so a 1e-4 m margin keeps the test conservative (it never rejects a pair
+  // the exact test would keep)
+  const float rk = sqrtf(khx * khx + khy * khy);
+  const float reach_u = bhx + rk + 1e-4f, reach_w = bhy + rk + 1e-4f;
   B2 b{s.base_start[0], s.base_start[1], s.base_start[2], s.base_v0[0], s.base_v0[1], s.base_v0[2]};
   B2 k{s.block_start[0], s.block_start[1], s.block_start[2], s.block_v0[0], s.block_v0[1], s.block_v0[2]};
   const int L = s.n_act;
@@ -221,7 +233,9 @@ __device__ __noinline__ void planar_rollout(const DevScene& s, const float* __re
     bool hit = false;
     if (HAS_BLOCK) {
       const float cdx = k.x - b.x, cdy = k.y - b.y;
-      if (cdx * cdx + cdy * cdy < rsum2) {  // bounding circles overlap
+      float sbp, cbp;
+      yaw_sincos(b.psi, &sbp, &cbp);
+      if (fabsf(cdx * cbp + cdy * sbp) < reach_u && fabsf(cdy * cbp - cdx * sbp) < reach_w) {
         float dep, qx, qy;
         hit = sat_rect(b, bhx, bhy, k, khx, khy, nx, ny, dep, qx, qy);
         if (hit) {
@@ -381,14 +395,32 @@ __device__ __forceinline__ uint32_t near_list(const DevScene& s, int n_geoms, fl
   return m;
 }
 
+// Analytic inverse kinematics of the 2-link arm in its vertical plane
+// (elbow up), returning the plane's azimuth as (cos, sin) = (dx, dy) / |d|
+// (what the forward kinematics uses; the angle itself only for traces).
+// With s2 = sin q2 = -sqrt(1 - c2^2) and c2 = cos q2 no trigonometric call is
+// needed for the elbow; for equal links the shoulder offset
+// atan2(l2 s2, l1 + l2 c2) equals q2 / 2 (tangent half-angle identity).
+// Targets out of reach are pulled onto the reachable shell.
+template <bool WANT_ANGLE>
 __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, float tx, float ty, float tz,
-                                       float& beta, float& q1, float& q2) {
+                                       float& beta, float& cbeta, float& sbeta, float& q1, float& q2) {
   const float dx = tx - bx, dy = ty - by;
-  beta = atan2f(dy, dx);
-  float rr = sqrtf(dx * dx + dy * dy);
+  const float r2 = dx * dx + dy * dy;
+  float rr = sqrtf(r2);
+  if (rr > 0.0f) {
+    const float inv = 1.0f / rr;
+    cbeta = dx * inv;
+    sbeta = dy * inv;
+  } else {
+    cbeta = 1.0f;
+    sbeta = 0.0f;
+  }
+  if (WANT_ANGLE) beta = atan2f(dy, dx);
   float zz = tz - s.arm_z;
   float rho = sqrtf(rr * rr + zz * zz);
-  const float rmax = s.arm_l1 + s.arm_l2 - 1e-3f, rmin = fabsf(s.arm_l1 - s.arm_l2) + 1e-3f;
+  const float l1 = s.arm_l1, l2 = s.arm_l2;
+  const float rmax = l1 + l2 - 1e-3f, rmin = fabsf(l1 - l2) + 1e-3f;
   if (rho > rmax) {
     const float f = rmax / rho;
     rr *= f;
@@ -400,12 +432,16 @@ __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, fl
     zz *= f;
     rho = rmin;
   }
-  float c2 = (rho * rho - (s.arm_l1 * s.arm_l1 + s.arm_l2 * s.arm_l2)) / (2.0f * s.arm_l1 * s.arm_l2);
+  float c2 = (rho * rho - (l1 * l1 + l2 * l2)) / (2.0f * l1 * l2);
   c2 = fminf(fmaxf(c2, -1.0f), 1.0f);
   q2 = -acosf(c2);
-  float s2, co2;
-  sincosf(q2, &s2, &co2);
-  q1 = atan2f(zz, rr) - atan2f(s.arm_l2 * s2, s.arm_l1 + s.arm_l2 * co2);
+  const float a = atan2f(zz, rr);
+  if (l1 == l2) {
+    q1 = a - 0.5f * q2;
+  } else {
+    const float s2 = -sqrtf(fmaxf(1.0f - c2 * c2, 0.0f));
+    q1 = a - atan2f(l2 * s2, l1 + l2 * c2);
+  }
 }
 
 // Forward kinematics.  Joint angles stay within (-pi, pi), where the
@@ -445,8 +481,12 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
   float mgx = bx, mgy = by, mkp = 0.f, mkd = 0.f;
   float rx = 0.f, ry = 0.f, caz = 1.f, saz = 0.f, hgrip = 0.f, ptx = 0.f, pty = 0.f, ptz = 0.f;
   float t_done = (float)T * dt;
-  // neighbour lists (bit g = geometry g) and the positions they were built at
-  constexpr float kSkin = 0.05f, kRebuild = 0.025f;
+  // Neighbour lists (bit g = geometry g) and the positions they were built
+  // at.  A warp rebuilds all its lanes' lists together as soon as one lane
+  // needs it (rebuilding early is always valid), so the rebuild loop runs
+  // once per event instead of once per lane.
+  constexpr float kSkin = 0.15f, kRebuild = 0.075f;
+  const unsigned lanes = __activemask();
   uint32_t bmask = 0, omask = 0;
   float brx = 1e30f, bry = 1e30f, orx = 1e30f, ory = 1e30f, orz = 1e30f;
   for (int step = 0; step < T; ++step) {
@@ -499,14 +539,11 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
       if (kind == CEM_ACT_MOVE) d2_prev = (bx - rx) * (bx - rx) + (by - ry) * (by - ry);
       else d2_prev = (ex - tx) * (ex - tx) + (ey - ty) * (ey - ty) + (ez - tz) * (ez - tz);
     }
-    if (kind != CEM_ACT_MOVE) {
-      arm_ik(s, bx, by, tx, ty, tz, beta, q1t, q2t);
-      sincosf(beta, &sbeta, &cbeta);
-    }
+    if (kind != CEM_ACT_MOVE) arm_ik<TRACE>(s, bx, by, tx, ty, tz, beta, cbeta, sbeta, q1t, q2t);
     // base: PD + penalty contacts with the static footprints
     float fx = mb * (kp * (gx - bx) - kd * bvx);
     float fy = mb * (kp * (gy - by) - kd * bvy);
-    if (fmaxf(fabsf(bx - brx), fabsf(by - bry)) >= kRebuild) {
+    if (__any_sync(lanes, fmaxf(fabsf(bx - brx), fabsf(by - bry)) >= kRebuild)) {
       bmask = near_list<true>(s, n_geoms, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, kSkin);
       brx = bx;
       bry = by;
@@ -540,7 +577,9 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
     q2 += dt * dq2;
     float nex, ney, nez;
     arm_fk(s, bx, by, cbeta, sbeta, q1, q2, nex, ney, nez);
-    // object
+    // object (a warp-wide rebuild of the object lists, see above)
+    const bool orebuild = __any_sync(
+        lanes, !attached && fmaxf(fmaxf(fabsf(ox - orx), fabsf(oy - ory)), fabsf(oz - orz)) >= kRebuild);
     if (attached) {
       ox = nex + offx;
       oy = ney + offy;
@@ -552,7 +591,7 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
       uint32_t mask = 0;
       int nc = 0;
       float fsx = 0.f, fsy = 0.f, fsz = 0.f;
-      if (fmaxf(fmaxf(fabsf(ox - orx), fabsf(oy - ory)), fabsf(oz - orz)) >= kRebuild) {
+      if (orebuild) {
         omask = near_list<false>(s, n_geoms, ox, oy, oz, h, h, h, kSkin);
         orx = ox;
         ory = oy;

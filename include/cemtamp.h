@@ -197,6 +197,10 @@ typedef struct {
   const float* init_cov_h;  /* D x D or NULL -> diag((range / 4)^2) */
   float* best_J_hist_h;     /* iters values or NULL: best cost so far per iteration */
   int32_t* k_eff_hist_h;    /* iters values or NULL */
+  /* D x D lower Cholesky factor of init_cov_h, or NULL -> factorised on the
+   * host.  Passing the chol of a previous cem_result with its mean, cov and
+   * start_iter = iterations done resumes a run exactly. */
+  const float* init_chol_h;
 } cem_solve_params;
 
 typedef struct {
@@ -208,6 +212,7 @@ typedef struct {
   float mean[CEM_MAX_D];
   float cov[CEM_MAX_D * CEM_MAX_D];
   float elapsed_ms; /* device time of the loop (CUDA events) */
+  float chol[CEM_MAX_D * CEM_MAX_D]; /* Cholesky factor of cov (the sampler's state) */
 } cem_result;
 
 /* Algorithm 1 end to end on the device: the distribution starts on the host

@@ -99,7 +99,8 @@ class cem_solve_params(C.Structure):
                 ("cov_mode", C.c_int32), ("problem", C.c_uint32), ("start_iter", C.c_uint32),
                 ("use_graph", C.c_int32), ("reserved", C.c_int32),
                 ("init_mean_h", C.POINTER(C.c_float)), ("init_cov_h", C.POINTER(C.c_float)),
-                ("best_J_hist_h", C.POINTER(C.c_float)), ("k_eff_hist_h", C.POINTER(C.c_int32))]
+                ("best_J_hist_h", C.POINTER(C.c_float)), ("k_eff_hist_h", C.POINTER(C.c_int32)),
+                ("init_chol_h", C.POINTER(C.c_float))]
 
 
 class cem_problem_params(C.Structure):
@@ -110,7 +111,8 @@ class cem_problem_params(C.Structure):
 class cem_result(C.Structure):
     _fields_ = [("best_theta", C.c_float * MAX_D), ("best_J", C.c_float), ("best_class", C.c_int32),
                 ("D", C.c_int32), ("iters_done", C.c_int32), ("mean", C.c_float * MAX_D),
-                ("cov", C.c_float * (MAX_D * MAX_D)), ("elapsed_ms", C.c_float)]
+                ("cov", C.c_float * (MAX_D * MAX_D)), ("elapsed_ms", C.c_float),
+                ("chol", C.c_float * (MAX_D * MAX_D))]
 
 
 # ------------------------------------------------------------- marshalling
@@ -628,7 +630,7 @@ class Scene:
         return idx, keff
 
     def solve(self, seed, N, K, iters, cov_mode="full", problem=0, start_iter=0, use_graph=True,
-              init_mean=None, init_cov=None):
+              init_mean=None, init_cov=None, init_chol=None):
         p = cem_solve_params()
         p.seed, p.N, p.K, p.iters, p.cov_mode = seed, N, K, iters, COV[cov_mode]
         p.problem, p.start_iter, p.use_graph = problem, start_iter, int(use_graph)
@@ -641,6 +643,10 @@ class Scene:
             c = np.ascontiguousarray(init_cov, np.float32)
             keep.append(c)
             p.init_cov_h = c.ctypes.data_as(C.POINTER(C.c_float))
+        if init_chol is not None:
+            L = np.ascontiguousarray(init_chol, np.float32)
+            keep.append(L)
+            p.init_chol_h = L.ctypes.data_as(C.POINTER(C.c_float))
         hist = np.zeros(iters, np.float32)
         keff = np.zeros(iters, np.int32)
         p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
@@ -649,6 +655,7 @@ class Scene:
         D = self.D
         return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                     mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                    chol=np.array(r.chol[:D * D]).reshape(D, D),
                     iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff)
 
     def set_launch(self, block):
@@ -666,6 +673,7 @@ class Scene:
         D = self.D
         return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                     mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                    chol=np.array(r.chol[:D * D]).reshape(D, D),
                     iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff)
 
     def autotune(self, N, cache_path=None):

@@ -283,11 +283,12 @@ int cem_batch_read(cem_batch_handle h, cem_result* out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const size_t P = h->P;
   std::vector<Track> tr(P);
-  std::vector<float> mean(P * kMS), cov(P * kMC);
+  std::vector<float> mean(P * kMS), cov(P * kMC), chol(P * kMC);
   std::vector<int32_t> status(P);
   BATCH_CUDA(cudaMemcpyAsync(tr.data(), h->track_d, sizeof(Track) * P, cudaMemcpyDeviceToHost, st));
   BATCH_CUDA(cudaMemcpyAsync(mean.data(), h->mean_d, sizeof(float) * P * kMS, cudaMemcpyDeviceToHost, st));
   BATCH_CUDA(cudaMemcpyAsync(cov.data(), h->cov_d, sizeof(float) * P * kMC, cudaMemcpyDeviceToHost, st));
+  BATCH_CUDA(cudaMemcpyAsync(chol.data(), h->chol_d, sizeof(float) * P * kMC, cudaMemcpyDeviceToHost, st));
   BATCH_CUDA(cudaMemcpyAsync(status.data(), h->status_d, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
   BATCH_CUDA(cudaStreamSynchronize(st));
   int bad = 0;
@@ -303,7 +304,10 @@ int cem_batch_read(cem_batch_handle h, cem_result* out, void* stream) {
       r.best_theta[d] = tr[p].best_theta[d];
       r.mean[d] = mean[p * kMS + d];
     }
-    for (int i = 0; i < D * D; ++i) r.cov[i] = cov[p * kMC + i];
+    for (int i = 0; i < D * D; ++i) {
+      r.cov[i] = cov[p * kMC + i];
+      r.chol[i] = chol[p * kMC + i];
+    }
     if (status[p] != 0) ++bad;
   }
   if (bad) return fail(CEM_ERR_NOT_PD, std::to_string(bad) + " problem(s) kept an indefinite covariance");

@@ -357,7 +357,9 @@ int handle_init_distribution(cem_handle h, const cem_solve_params* p, SolveBuffe
   }
   if (p->init_cov_h)
     for (int i = 0; i < D * D; ++i) cov[i] = p->init_cov_h[i];
-  {  // host Cholesky of the initial covariance (FP64)
+  if (p->init_chol_h) {  // a resumed run: the sampler's exact state
+    for (int i = 0; i < D * D; ++i) chol[i] = p->init_chol_h[i];
+  } else {  // host Cholesky of the initial covariance (FP64)
     std::vector<double> L((size_t)D * D, 0.0);
     for (int j = 0; j < D; ++j) {
       double s = cov[j * D + j];
@@ -397,6 +399,7 @@ int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b,
   CEM_CUDA(cudaMemcpyAsync(&tr, b->track, sizeof(Track), cudaMemcpyDeviceToHost, b->stream));
   CEM_CUDA(cudaMemcpyAsync(out->mean, b->mean, sizeof(float) * D, cudaMemcpyDeviceToHost, b->stream));
   CEM_CUDA(cudaMemcpyAsync(out->cov, b->cov, sizeof(float) * D * D, cudaMemcpyDeviceToHost, b->stream));
+  CEM_CUDA(cudaMemcpyAsync(out->chol, b->chol, sizeof(float) * D * D, cudaMemcpyDeviceToHost, b->stream));
   CEM_CUDA(cudaMemcpyAsync(&status, b->status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
   if (p->best_J_hist_h)
     CEM_CUDA(cudaMemcpyAsync(p->best_J_hist_h, b->hist_J, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, b->stream));

@@ -23,8 +23,11 @@ namespace {
 
 constexpr int TW = CEM_TRACE_W;
 
+// parameter i clamped to its bounds; a NaN stays NaN (its rollout then ends
+// with a non-finite cost, class 3)
 __device__ __forceinline__ float theta_at(const DevScene& s, const float* __restrict__ row, int i) {
-  return fminf(fmaxf(row[i], s.lo[i]), s.hi[i]);
+  const float x = row[i];
+  return isnan(x) ? x : fminf(fmaxf(x, s.lo[i]), s.hi[i]);
 }
 
 // time at which an action succeeded inside step k (state t_k -> t_{k+1})

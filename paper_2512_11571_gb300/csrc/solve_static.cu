@@ -159,7 +159,9 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   }
   if (p->init_cov_h)
     for (int i = 0; i < D * D; ++i) cov[i] = p->init_cov_h[i];
-  {
+  if (p->init_chol_h) {
+    for (int i = 0; i < D * D; ++i) chol[i] = p->init_chol_h[i];
+  } else {
     double Lf[CEM_MAX_D * CEM_MAX_D] = {0.0};
     for (int j = 0; j < D; ++j) {
       double s = cov[j * D + j];
@@ -221,6 +223,7 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   STATIC_CUDA(cudaMemcpyAsync(&tr, track_d, sizeof(Track), cudaMemcpyDeviceToHost, st));
   STATIC_CUDA(cudaMemcpyAsync(out->mean, mean_d, sizeof(float) * D, cudaMemcpyDeviceToHost, st));
   STATIC_CUDA(cudaMemcpyAsync(out->cov, cov_d, sizeof(float) * D * D, cudaMemcpyDeviceToHost, st));
+  STATIC_CUDA(cudaMemcpyAsync(out->chol, chol_d, sizeof(float) * D * D, cudaMemcpyDeviceToHost, st));
   STATIC_CUDA(cudaMemcpyAsync(&status, status_d, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   if (p->best_J_hist_h)
     STATIC_CUDA(cudaMemcpyAsync(p->best_J_hist_h, hist_J_d, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, st));

@@ -375,3 +375,51 @@ def test_converged_cost_matches_oracle_cem(P, orc, cfg):
     close = np.abs(gpu - ref) / ref <= 0.02
     assert close.sum() >= 6, (gpu, ref)
     assert np.all(np.array(cls_g)[close] == np.array(cls_r)[close])
+
+
+# ---------------------------------------------------------- robustness, state
+@pytest.mark.parametrize("make", [lambda: workload.reach_scene(0), lambda: workload.push_scene(2),
+                                  lambda: workload.pickplace_scene(1, T=400)])
+def test_nan_parameters_give_class_3(P, orc, make):
+    sc, sk = make()
+    th = draw(P, sc, sk, 64, seed=4)
+    D = th.shape[1]
+    for i in range(0, 64, 4):
+        th[i, i % D] = np.nan
+    with P.Scene(sc, sk) as S:
+        J, cls = S.rollout(dev(th))
+    Jr, cr = orc.rollout(sc, sk, th.astype(np.float64))
+    assert np.array_equal(cls.cpu().numpy(), cr)
+    assert np.array_equal(np.isfinite(J.cpu().numpy()), np.isfinite(Jr))
+
+
+def test_resume_reproduces_the_run(P):
+    # the CE state is (mean, cov, chol, iteration): splitting a run at
+    # iteration 4 and resuming from the returned state changes nothing
+    sc, sk, cm = workload.config(1, seed=3)
+    with P.Scene(sc, sk) as S:
+        full = S.solve(9, cm["N"], cm["K"], 9)
+        first = S.solve(9, cm["N"], cm["K"], 4)
+        second = S.solve(9, cm["N"], cm["K"], 5, start_iter=4, init_mean=first["mean"], init_cov=first["cov"],
+                         init_chol=first["chol"])
+    assert np.array_equal(second["mean"], full["mean"])
+    assert np.array_equal(second["cov"], full["cov"])
+    assert np.array_equal(second["chol"], full["chol"])
+    best = min((first["best_cls"], first["best_J"]), (second["best_cls"], second["best_J"]))
+    assert best == (full["best_cls"], full["best_J"])
+    assert np.array_equal(np.concatenate([first["history"], np.minimum(second["history"], first["best_J"])]),
+                          full["history"]) or full["best_cls"] != 0
+
+
+def test_autotune_and_cache(P, tmp_path):
+    sc, sk, cm = workload.config(1, seed=0)
+    cache = str(tmp_path / "tune.txt")
+    with P.Scene(sc, sk) as S:
+        b = S.autotune(cm["N"], cache)
+        assert b in (32, 64, 128, 256)
+        lines = open(cache).read().strip().splitlines()
+        assert len(lines) == 1 and lines[0].endswith("|%d" % b)
+        assert S.autotune(cm["N"], cache) == b  # read back from the cache
+        assert len(open(cache).read().strip().splitlines()) == 1
+        r = S.solve(1, cm["N"], cm["K"], 2)
+    assert np.isfinite(r["best_J"])

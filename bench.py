@@ -36,7 +36,7 @@ SATURATED_N = 48 * 4096  # enough rollouts to give every SM scheduler several wa
 # DRAM bytes (read + write) of one rollout launch of this workload from the
 # ncu capture in profiles/rollout_push_N4096_T1000.md; reported only while the
 # kernel source still matches the one the counters were taken on
-ROLLOUT_TRAFFIC = {"rollout.cu sha256[:16]": "2eb928e4b1d1264e", "bytes": 128768}
+ROLLOUT_TRAFFIC = {"rollout.cu sha256[:16]": "4e2afd26087f5385", "bytes": 126208}
 
 
 def rollout_traffic():
@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--n", type=int, default=0, help="samples for --rollout-only (0 = the workload's N)")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
     ap.add_argument("--skip-surrogate", action="store_true", help="leave out the time-to-cost comparison")
+    ap.add_argument("--mlp-only", type=int, default=0,
+                    help="time only the surrogate forward on this many rows (profiling driver)")
     return ap.parse_args()
 
 
@@ -456,8 +458,42 @@ def run_rollout_only(args):
                       "classes": np.bincount(cls.cpu().numpy(), minlength=4).tolist()}), flush=True)
 
 
+def run_mlp_only(args):
+    """Times the surrogate's BF16 tensor-core forward (4 x 256-wide layers) on
+    --mlp-only rows: one untimed call, then `reps` calls between events."""
+    import torch
+
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    M = args.mlp_only
+    x = torch.rand((M, 48), device="cuda") * 2 - 1
+    with P.Surrogate(256, 4, seed=args.seed) as S:
+        y = S.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = torch.cuda.current_stream()
+        e0.record(st)
+        for _ in range(args.reps):
+            P.cem_surrogate_forward(S.h, x, y, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.reps
+    flops = 2.0 * M * (48 * 256 + 3 * 256 * 256 + 256)
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    print(json.dumps({"mlp_only": M, "ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
+                      "frac_of_bf16": flops / (ms / 1e3) / 1e12 / peak, "peak_bf16_tflops": peak,
+                      "peak_source": src}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mlp_only:
+        run_mlp_only(args)
+        return
     if args.rollout_only:
         run_rollout_only(args)
         return

@@ -460,7 +460,8 @@ def run_rollout_only(args):
 
 def run_mlp_only(args):
     """Times the surrogate's BF16 tensor-core forward (4 x 256-wide layers) on
-    --mlp-only rows: one untimed call, then `reps` calls between events."""
+    --mlp-only rows through both paths (the tiled mma.sync GEMM and the fused
+    tcgen05 kernel): one untimed call each, then `reps` calls between events."""
     import torch
 
     import paper_2512_11571_gb300 as P
@@ -470,23 +471,28 @@ def run_mlp_only(args):
     P.load()
     M = args.mlp_only
     x = torch.rand((M, 48), device="cuda") * 2 - 1
-    with P.Surrogate(256, 4, seed=args.seed) as S:
-        y = S.forward(x)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        st = torch.cuda.current_stream()
-        e0.record(st)
-        for _ in range(args.reps):
-            P.cem_surrogate_forward(S.h, x, y, st)
-        e1.record(st)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.reps
     flops = 2.0 * M * (48 * 256 + 3 * 256 * 256 + 256)
     peaks, src = measured_peaks()
     peak = peaks.get("bf16_tflops", 1900.0)
-    print(json.dumps({"mlp_only": M, "ms": ms, "tflops": flops / (ms / 1e3) / 1e12,
-                      "frac_of_bf16": flops / (ms / 1e3) / 1e12 / peak, "peak_bf16_tflops": peak,
-                      "peak_source": src}), flush=True)
+    out = {"mlp_only": M, "peak_bf16_tflops": peak, "peak_source": src}
+    with P.Surrogate(256, 4, seed=args.seed) as S:
+        for path, name in ((1, "tiled_mma_sync"), (2, "fused_tcgen05")):
+            S.set_forward_path(path)
+            y = S.forward(x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            st = torch.cuda.current_stream()
+            e0.record(st)
+            for _ in range(args.reps):
+                P.cem_surrogate_forward(S.h, x, y, st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.reps
+            tf = flops / (ms / 1e3) / 1e12
+            out[name] = {"ms": ms, "tflops": tf, "frac_of_bf16": tf / peak}
+        if S.status() != 0:
+            raise SystemExit("surrogate forward: a bounded pipeline wait expired")
+    print(json.dumps(out), flush=True)
 
 
 def main():

@@ -293,8 +293,21 @@ int cem_surrogate_num_params(cem_surrogate_handle s);
  * set_params also clears the optimiser state. */
 int cem_surrogate_set_params(cem_surrogate_handle s, const float* params_h, const float* norm_h);
 int cem_surrogate_get_params(cem_surrogate_handle s, float* params_h, float* norm_h);
-/* x_d[M][48] FP32 -> y_d[M] scores (stream-ordered). */
+/* x_d[M][48] FP32 -> y_d[M] scores (stream-ordered).  With width 256 and
+ * depth 4 this (and screening) runs one fused tcgen05 kernel per 128 rows;
+ * if one of its bounded pipeline waits expires, that CTA's scores are NaN
+ * and cem_surrogate_status reports the code. */
 int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float* y_d, void* stream);
+/* Forward path for inference: 0 automatic (tcgen05 where the shape allows),
+ * 1 the tiled mma.sync GEMM, 2 tcgen05 (CEM_ERR_UNSUPPORTED unless width 256
+ * and depth 4).  Training always uses the tiled GEMM. */
+int cem_surrogate_set_forward_path(cem_surrogate_handle s, int path);
+/* The path inference takes now: 1 tiled GEMM, 2 tcgen05; -1 for NULL. */
+int cem_surrogate_forward_path(cem_surrogate_handle s);
+/* Synchronises, writes and clears the tcgen05 forward's status word: 0, or
+ * 1 / 2 if a wait for the weight copy / the MMAs expired.  A non-zero code
+ * also makes cem_solve_screened return CEM_ERR_TIMEOUT. */
+int cem_surrogate_status(cem_surrogate_handle s, int* status_h);
 /* Full-batch gradient of mean((out - (t - mu)/sigma)^2) over M rows into
  * grad_h (num_params floats) and the loss into *loss_h.  Synchronous. */
 int cem_surrogate_gradient(cem_surrogate_handle s, const float* x_d, const float* t_d, int M, float* grad_h,

@@ -34,6 +34,7 @@ EXPORTS = [
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
+    "cem_surrogate_set_forward_path", "cem_surrogate_forward_path", "cem_surrogate_status",
     "cem_last_error", "cem_version",
 ]
 
@@ -226,6 +227,9 @@ def load(path: str = LIB_PATH):
     L.cem_surrogate_set_params.argtypes = [H, fptr, fptr]
     L.cem_surrogate_get_params.argtypes = [H, fptr, fptr]
     L.cem_surrogate_forward.argtypes = [H, vp, C.c_int, vp, vp]
+    L.cem_surrogate_set_forward_path.argtypes = [H, C.c_int]
+    L.cem_surrogate_forward_path.argtypes = [H]
+    L.cem_surrogate_status.argtypes = [H, C.POINTER(C.c_int)]
     L.cem_surrogate_gradient.argtypes = [H, vp, vp, C.c_int, fptr, fptr]
     L.cem_surrogate_train.argtypes = [H, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
                                       C.c_int, fptr]
@@ -468,6 +472,20 @@ def cem_surrogate_forward(s, x, y, stream=None):
     _check(load().cem_surrogate_forward(s, _ptr(x), x.shape[0], _ptr(y), _stream(stream)))
 
 
+def cem_surrogate_set_forward_path(s, path):
+    _check(load().cem_surrogate_set_forward_path(s, int(path)))
+
+
+def cem_surrogate_forward_path(s):
+    return int(load().cem_surrogate_forward_path(s))
+
+
+def cem_surrogate_status(s):
+    code = C.c_int(0)
+    _check(load().cem_surrogate_status(s, C.byref(code)))
+    return code.value
+
+
 def cem_surrogate_gradient(s, x, t):
     g = np.zeros(cem_surrogate_num_params(s), np.float32)
     loss = C.c_float()
@@ -538,6 +556,18 @@ class Surrogate:
         y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
         cem_surrogate_forward(self.h, x, y, stream)
         return y
+
+    def set_forward_path(self, path):
+        """0 automatic, 1 tiled mma.sync GEMM, 2 fused tcgen05 kernel."""
+        cem_surrogate_set_forward_path(self.h, path)
+
+    @property
+    def forward_path(self):
+        return cem_surrogate_forward_path(self.h)
+
+    def status(self):
+        """Reads and clears the fused kernel's status word (0 = no wait expired)."""
+        return cem_surrogate_status(self.h)
 
     def train(self, x, t, batch=4096, steps=1000, lr=1e-3, weight_decay=1e-4, seed=0, normalize=True):
         return cem_surrogate_train(self.h, x, t, batch, steps, lr, weight_decay, seed, normalize)

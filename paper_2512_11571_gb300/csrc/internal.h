@@ -151,4 +151,24 @@ int handle_init_distribution(cem_handle h, const cem_solve_params* p, SolveBuffe
 // copies the loop's results to the host, synchronises and fills *out
 int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b, cem_result* out);
 
+// ---- fused tcgen05 surrogate forward (48 -> 4 x 256 GELU -> 1)
+struct MlpTcOffsets {
+  int w[4];  // element offsets of W0..W3 in the flat BF16 parameter vector
+};
+struct MlpTcArgs {
+  const void* x;         // BF16 [M x 48] features
+  int M;
+  const void* wpack;     // canonical weight image from mlp_tc_pack
+  const float* bias[4];  // FP32 biases of the hidden layers
+  const void* w_out;     // BF16 [256] output weights
+  const float* b_out;    // FP32 output bias
+  const float* norm;     // [mu, sigma]
+  float* y;              // [M] scores
+  int* status;           // set non-zero if a bounded wait expired
+};
+bool mlp_tc_supported(int in_dim, int width, int depth);
+size_t mlp_tc_pack_bytes();
+cudaError_t mlp_tc_pack(const void* pb, const MlpTcOffsets& off, void* pack, cudaStream_t st);
+cudaError_t mlp_tc_forward(const MlpTcArgs& a, cudaStream_t st);
+
 }  // namespace cem

@@ -495,6 +495,12 @@ struct cem_surrogate_ctx {
   int32_t* keep_idx = nullptr;
   float* lohi = nullptr;
   float* scene16 = nullptr;
+  // fused tcgen05 forward: packed weights (rebuilt when the BF16 weights
+  // change), status word of its bounded waits, path selection
+  void* tc_pack = nullptr;
+  int* tc_status = nullptr;
+  bool tc_pack_valid = false;
+  int fwd_path = 0;  // 0 automatic, 1 tiled GEMM, 2 tcgen05
 };
 
 namespace {
@@ -579,6 +585,34 @@ cudaError_t forward_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st)
   output_layer_kernel<<<(M * 32 + threads - 1) / threads, threads, 0, st>>>(
       a, M, s->width, s->pb + s->w_off[L], s->p + s->b_off[L], s->norm, y, s->raw);
   return cudaGetLastError();
+}
+
+bool use_tc(const cem_surrogate_ctx* s) {
+  return s->fwd_path != 1 && mlp_tc_supported(s->in_dim, s->width, s->depth);
+}
+
+// scores of M rows already in s->xin, no activations kept: the fused tcgen05
+// kernel where the shape allows, else the tiled GEMM forward
+cudaError_t infer_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st) {
+  if (!use_tc(s)) return forward_rows(s, M, y, st);
+  if (!s->tc_pack_valid) {
+    MlpTcOffsets off;
+    for (int l = 0; l < 4; ++l) off.w[l] = s->w_off[l];
+    cudaError_t e = mlp_tc_pack(s->pb, off, s->tc_pack, st);
+    if (e != cudaSuccess) return e;
+    s->tc_pack_valid = true;
+  }
+  MlpTcArgs a;
+  a.x = s->xin;
+  a.M = M;
+  a.wpack = s->tc_pack;
+  for (int l = 0; l < 4; ++l) a.bias[l] = s->p + s->b_off[l];
+  a.w_out = s->pb + s->w_off[4];
+  a.b_out = s->p + s->b_off[4];
+  a.norm = s->norm;
+  a.y = y;
+  a.status = s->tc_status;
+  return mlp_tc_forward(a, st);
 }
 
 // gradient of mean((raw - (t - mu)/sigma)^2) for the M rows of the last forward;
@@ -727,6 +761,9 @@ int cem_surrogate_create(int in_dim, int width, int depth, uint64_t seed, cem_su
   A((void**)&s->norm, sizeof(float) * 2);
   A((void**)&s->lohi, sizeof(float) * 2 * CEM_MAX_D);
   A((void**)&s->scene16, sizeof(float) * 16);
+  if (mlp_tc_supported(in_dim, width, depth)) A(&s->tc_pack, mlp_tc_pack_bytes());
+  A((void**)&s->tc_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(s->tc_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(s->p, init.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->m1, 0, sizeof(float) * o);
   if (e == cudaSuccess) e = cudaMemset(s->m2, 0, sizeof(float) * o);
@@ -749,7 +786,7 @@ int cem_surrogate_destroy(cem_surrogate_handle s) {
   cudaDeviceSynchronize();
   sur_free_work(s);
   void* ptrs[] = {s->p, s->pb, s->g, s->m1, s->m2, s->norm, s->lohi, s->scene16,
-                  s->pool_theta, s->pool_x, s->pool_score, s->keep_idx};
+                  s->pool_theta, s->pool_x, s->pool_score, s->keep_idx, s->tc_pack, s->tc_status};
   for (void* p : ptrs) cudaFree(p);
   delete s;
   return CEM_OK;
@@ -762,6 +799,7 @@ int cem_surrogate_set_params(cem_surrogate_handle s, const float* params_h, cons
   SUR_CUDA(cudaMemcpy(s->p, params_h, sizeof(float) * s->total, cudaMemcpyHostToDevice));
   if (norm_h) SUR_CUDA(cudaMemcpy(s->norm, norm_h, sizeof(float) * 2, cudaMemcpyHostToDevice));
   to_bf16_kernel<<<(s->total + 255) / 256, 256>>>(s->p, (size_t)s->total, s->pb);
+  s->tc_pack_valid = false;
   SUR_CUDA(cudaDeviceSynchronize());
   SUR_CUDA(cudaMemset(s->m1, 0, sizeof(float) * s->total));
   SUR_CUDA(cudaMemset(s->m2, 0, sizeof(float) * s->total));
@@ -784,7 +822,26 @@ int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float
   cudaStream_t st = (cudaStream_t)stream;
   int rc = load_features(s, x_d, M, st);
   if (rc != CEM_OK) return rc;
-  SUR_CUDA(forward_rows(s, M, y_d, st));
+  SUR_CUDA(infer_rows(s, M, y_d, st));
+  return CEM_OK;
+}
+
+int cem_surrogate_set_forward_path(cem_surrogate_handle s, int path) {
+  if (!s) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (path < 0 || path > 2) return fail(CEM_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+  if (path == 2 && !mlp_tc_supported(s->in_dim, s->width, s->depth))
+    return fail(CEM_ERR_UNSUPPORTED, "the tcgen05 forward needs width 256 and depth 4");
+  s->fwd_path = path;
+  return CEM_OK;
+}
+
+int cem_surrogate_forward_path(cem_surrogate_handle s) { return s ? (use_tc(s) ? 2 : 1) : -1; }
+
+int cem_surrogate_status(cem_surrogate_handle s, int* status_h) {
+  if (!s || !status_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  SUR_CUDA(cudaDeviceSynchronize());
+  SUR_CUDA(cudaMemcpy(status_h, s->tc_status, sizeof(int), cudaMemcpyDeviceToHost));
+  SUR_CUDA(cudaMemset(s->tc_status, 0, sizeof(int)));
   return CEM_OK;
 }
 
@@ -830,6 +887,7 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   }
   const Segs segs = param_segments(s);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  s->tc_pack_valid = false;  // the BF16 weights change below
   cudaError_t e = cudaGetLastError();
   for (int it = 0; it < steps && e == cudaSuccess; ++it) {
     gather_batch_kernel<<<(batch + 255) / 256, 256>>>(Xall, t_d, M, s->in_dim, batch, seed, (uint32_t)it, s->xin,
@@ -910,7 +968,7 @@ cudaError_t screen_pool(cem_surrogate_ctx* s, int P, int N, int n_explore, int D
   features_kernel<bf16><<<(P + 127) / 128, 128, 0, st>>>(s->pool_theta, P, D, s->lohi, s->scene16, s->xin);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = forward_rows(s, P, s->pool_score, st);
+  e = infer_rows(s, P, s->pool_score, st);
   if (e != cudaSuccess) return e;
   if (n_explore > 0) {
     force_keep_kernel<<<(n_explore + 255) / 256, 256, 0, st>>>(s->pool_score, n_explore);
@@ -1011,7 +1069,15 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
     SUR_CUDA(launch_refit(a, st));
   }
   SUR_CUDA(cudaEventRecord(b.ev1, st));
-  return handle_read_result(h, p, &b, out);
+  rc = handle_read_result(h, p, &b, out);
+  if (rc != CEM_OK) return rc;
+  int tc_fail = 0;
+  SUR_CUDA(cudaMemcpy(&tc_fail, s->tc_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (tc_fail) {
+    cudaMemset(s->tc_status, 0, sizeof(int));
+    return fail(CEM_ERR_TIMEOUT, "surrogate forward: a bounded wait on the tensor-core pipeline expired");
+  }
+  return CEM_OK;
 }
 
 }  // extern "C"

@@ -1,0 +1,136 @@
+"""The fused tcgen05 surrogate forward (48 -> 4 x 256 GELU -> 1, one CTA per
+128 rows, TMEM accumulators) against the FP64 MLP oracle and against the
+tiled mma.sync GEMM path of the same library.
+
+Both GPU paths round at the same points (BF16 inputs, weights and hidden
+activations, FP32 accumulation, FP32 bias and GELU); only the order of the
+FP32 sums differs, which can flip the BF16 rounding of an activation.  The
+bars are those of the oracle comparison of the tiled path: the median error
+against the BF16-emulating oracle at FP32 summation level, the maximum at
+BF16 level."""
+import numpy as np
+import pytest
+
+import workload
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    return P
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+# 1 row, one full tile, tile +- 1 (ragged tail), many tiles with a tail,
+# and more CTAs than one wave of 152 SMs with a tail
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 1000, 65536 + 77])
+def test_tc_forward_matches_oracle(P, M):
+    params = mlp.init_params(48, 256, 4, seed=M % 997)
+    rng = np.random.default_rng(M)
+    X = rng.uniform(-1.5, 1.5, (M, 48))
+    with P.Surrogate(256, 4) as S:
+        assert S.forward_path == 2
+        S.set_params(mlp.flatten(params), np.array([0.25, 1.5]))
+        y = S.forward(dev(X)).cpu().numpy().astype(np.float64)
+        assert S.status() == 0
+    ye, _ = mlp.forward(params, X, emulate_bf16=True)
+    y64, _ = mlp.forward(params, X)
+    ye, y64 = 0.25 + 1.5 * ye, 0.25 + 1.5 * y64
+    scale = max(1.0, np.abs(y64).max())
+    assert np.all(np.isfinite(y))
+    assert np.median(np.abs(y - ye)) <= 1e-4 * scale
+    assert np.max(np.abs(y - ye)) <= 2e-2 * scale
+    assert np.max(np.abs(y - y64)) <= 5e-2 * scale
+
+
+def test_tc_matches_tiled_gemm(P):
+    M = 20000
+    params = mlp.init_params(48, 256, 4, seed=11)
+    X = np.random.default_rng(11).uniform(-1, 1, (M, 48))
+    with P.Surrogate(256, 4) as S:
+        S.set_params(mlp.flatten(params), np.array([0.0, 1.0]))
+        x = dev(X)
+        S.set_forward_path(1)
+        assert S.forward_path == 1
+        y1 = S.forward(x).cpu().numpy().astype(np.float64)
+        S.set_forward_path(2)
+        y2 = S.forward(x).cpu().numpy().astype(np.float64)
+        y2b = S.forward(x).cpu().numpy().astype(np.float64)
+        assert S.status() == 0
+    scale = max(1.0, np.abs(y1).max())
+    assert np.array_equal(y2, y2b)  # run to run bit-identical
+    d = np.abs(y1 - y2)
+    assert np.median(d) <= 1e-5 * scale
+    assert d.max() <= 2e-2 * scale
+
+
+def test_tc_follows_parameter_updates(P):
+    rng = np.random.default_rng(5)
+    X = rng.uniform(-1, 1, (8192, 48)).astype(np.float32)
+    t = (np.sin(3 * X[:, 0]) + X[:, 1] * X[:, 2]).astype(np.float32)
+    with P.Surrogate(256, 4, seed=6) as S:
+        x = dev(X)
+        y0 = S.forward(x).cpu().numpy()
+        S.train(x, dev(t), batch=1024, steps=20, lr=3e-3, seed=2)
+        y_tc = S.forward(x).cpu().numpy()
+        S.set_forward_path(1)
+        y_gemm = S.forward(x).cpu().numpy()
+        S.set_forward_path(0)
+        assert np.abs(y_tc - y0).max() > 1e-2  # the packed weights were rebuilt
+        np.testing.assert_allclose(y_tc, y_gemm, atol=2e-2 * max(1.0, np.abs(y_gemm).max()))
+        p, norm = S.params()
+        S.set_params(p * 0.5, norm)
+        y_half = S.forward(x).cpu().numpy()
+        S.set_forward_path(1)
+        y_half_gemm = S.forward(x).cpu().numpy()
+        assert S.status() == 0
+    np.testing.assert_allclose(y_half, y_half_gemm, atol=2e-2 * max(1.0, np.abs(y_half_gemm).max()))
+
+
+@pytest.mark.parametrize("n_pool,n_keep", [(65536, 8192), (1000, 129)])
+def test_tc_screen_keeps_lowest_scores(P, n_pool, n_keep):
+    sc, sk, _ = workload.config(2, seed=4)
+    f16 = workload.scene_features(sc)
+    lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+    mean = dev((lo + hi) / 2)
+    chol = dev(np.diag((hi - lo) / 4))
+    with P.Scene(sc, sk) as Sc, P.Surrogate(256, 4, seed=7) as S:
+        assert S.forward_path == 2
+        keep = torch.empty((n_keep, len(lo)), device="cuda")
+        idx = torch.empty(n_keep, dtype=torch.int32, device="cuda")
+        P.cem_surrogate_screen(Sc.h, S.h, mean, chol, 9, 1, 0, n_pool, n_keep, f16, keep, idx)
+        pool = Sc.sample(mean, chol, 9, 1, n_pool, problem=0)
+        score = S.forward(S.features(pool, lo, hi, f16)).cpu().numpy()
+        assert S.status() == 0
+    order = np.lexsort((np.arange(n_pool), score))[:n_keep]
+    expect = np.sort(order)
+    assert np.array_equal(idx.cpu().numpy(), expect)
+    assert np.array_equal(keep.cpu().numpy(), pool.cpu().numpy()[expect])
+
+
+def test_path_selection(P):
+    with P.Surrogate(64, 2) as S:
+        assert S.forward_path == 1
+        with pytest.raises(P.CemError):
+            S.set_forward_path(2)
+        with pytest.raises(P.CemError):
+            S.set_forward_path(3)
+    with P.Surrogate(256, 4) as S:
+        assert S.forward_path == 2
+        S.set_forward_path(1)
+        assert S.forward_path == 1
+        S.set_forward_path(0)
+        assert S.forward_path == 2

@@ -59,6 +59,10 @@ def parse():
                     help="time only the rollout kernel of one workload (profiling driver)")
     ap.add_argument("--n", type=int, default=0, help="samples for --rollout-only (0 = the workload's N)")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
+    ap.add_argument("--tpr", type=int, default=1,
+                    help="lanes per pick-and-place rollout for --rollout-only (1, 8 or 32)")
+    ap.add_argument("--block", type=int, default=0,
+                    help="rollout threads per CTA for --rollout-only (0 = the library's choice)")
     ap.add_argument("--skip-surrogate", action="store_true", help="leave out the time-to-cost comparison")
     ap.add_argument("--mlp-only", type=int, default=0,
                     help="time only the surrogate forward on this many rows (profiling driver)")
@@ -435,6 +439,9 @@ def run_rollout_only(args):
     T, D = sc["T"], len(sk["lo"])
     lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
     with P.Scene(sc, sk) as S:
+        if args.block:
+            P.cem_set_launch(S.h, args.block)
+        S.set_threads_per_rollout(args.tpr)
         mean = torch.tensor((lo + hi) / 2, device="cuda")
         chol = torch.tensor(np.diag((hi - lo) / 4), device="cuda")
         theta = S.sample(mean, chol, args.seed, 0, N)
@@ -453,7 +460,7 @@ def run_rollout_only(args):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     tf = fps["flops"] * N * T / (ms / 1e3) / 1e12
-    print(json.dumps({"rollout_only": cm["name"], "N": N, "T": T, "D": D, "ms": ms,
+    print(json.dumps({"rollout_only": cm["name"], "N": N, "T": T, "D": D, "block": args.block, "tpr": args.tpr, "ms": ms,
                       "sim_steps_per_s": N * T / (ms / 1e3), "achieved_tflops": tf, "frac": tf / peak,
                       "classes": np.bincount(cls.cpu().numpy(), minlength=4).tolist()}), flush=True)
 

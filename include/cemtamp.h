@@ -274,6 +274,15 @@ int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm)
 int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float* best_ms_out);
 /* Simulated steps of one batch iteration: sum over problems of N * T. */
 long long cem_batch_steps_per_iteration(cem_batch_handle h);
+/* Lanes per pick-and-place rollout in the persistent launch: 1, 8 or 32
+ * (other scene kinds always take one lane per rollout).  With 8 or 32, a
+ * lane group holds one rollout's state, splits its per-geometry contact
+ * queries and neighbour-list rebuilds, and sums the contact forces with warp
+ * shuffles in ascending geometry order: the results are bit-identical for
+ * every width.  cem_batch_autotune also searches this width. */
+int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr);
+/* The current persistent launch shape (CTAs per SM resolved when automatic). */
+int cem_batch_get_launch(cem_batch_handle h, int* warps_out, int* ctas_out, int* tpr_out);
 
 /* ---- Learned cost surrogate (not in the paper) ---------------------------
  * An MLP score(x), x = [theta normalised to [-1, 1] by the bounds (clamped)
@@ -340,11 +349,24 @@ int cem_surrogate_screen(cem_handle h, cem_surrogate_handle s, const float* mean
 int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
                        int n_pool, int n_explore, cem_result* out);
 
-/* Threads-per-block of the rollout kernel (0 = automatic). */
+/* Threads per block of the rollout kernel: 0 (automatic), 8, 16 or a
+ * multiple of 32 up to 256. */
 int cem_set_launch(cem_handle h, int block_threads);
-/* Times candidate block sizes for this scene and N on the current device
- * and keeps the fastest; results are cached in a text file when
- * cache_path is not NULL.  Writes the chosen block size. */
+/* Lanes per rollout for pick-and-place scenes: 1, 8 or 32 (other scene
+ * kinds always take one lane; the trace always one).  A group of G lanes
+ * holds one rollout's state, splits the per-geometry contact queries and
+ * neighbour-list rebuilds, and sums the contact forces with warp shuffles in
+ * ascending geometry order: J and the class are bit-identical for every G.
+ * With G > 1 a CTA of max(block, 32) threads carries block / G rollouts. */
+int cem_set_threads_per_rollout(cem_handle h, int tpr);
+/* The launch shape cem_rollout_batch uses for N samples: threads per block
+ * and lanes per rollout. */
+int cem_get_launch(cem_handle h, int N, int* block_out, int* tpr_out);
+/* Times candidate block sizes (and, for pick-and-place scenes, 1, 8 or 32
+ * lanes per rollout) for this scene and N on the current device and keeps
+ * the fastest; results are cached in a text file ("<key>|<block>|<lanes>")
+ * when cache_path is not NULL.  Writes the chosen block size; cem_get_launch
+ * reports both. */
 int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out);
 
 /* Thread-local message of the last failing call ("" if none). */

@@ -31,6 +31,7 @@ EXPORTS = [
     "cem_rollout_trace", "cem_refit", "cem_solve", "cem_solve_static", "cem_set_launch", "cem_autotune",
     "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
+    "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -220,6 +221,11 @@ def load(path: str = LIB_PATH):
     L.cem_batch_set_launch.argtypes = [H, C.c_int, C.c_int]
     L.cem_batch_autotune.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
     L.cem_batch_steps_per_iteration.argtypes = [H]
+    ip = C.POINTER(C.c_int)
+    L.cem_batch_set_threads_per_rollout.argtypes = [H, C.c_int]
+    L.cem_batch_get_launch.argtypes = [H, ip, ip, ip]
+    L.cem_set_threads_per_rollout.argtypes = [H, C.c_int]
+    L.cem_get_launch.argtypes = [H, C.c_int, ip, ip]
     fptr, i32ptr = C.POINTER(C.c_float), C.POINTER(C.c_int32)
     L.cem_surrogate_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_uint64, C.POINTER(H)]
     L.cem_surrogate_destroy.argtypes = [H]
@@ -331,6 +337,26 @@ def cem_autotune(h, N, cache_path=None):
     return b.value
 
 
+def cem_set_threads_per_rollout(h, tpr):
+    _check(load().cem_set_threads_per_rollout(h, int(tpr)))
+
+
+def cem_get_launch(h, N):
+    b, t = C.c_int(0), C.c_int(0)
+    _check(load().cem_get_launch(h, int(N), C.byref(b), C.byref(t)))
+    return b.value, t.value
+
+
+def cem_batch_set_threads_per_rollout(h, tpr):
+    _check(load().cem_batch_set_threads_per_rollout(h, int(tpr)))
+
+
+def cem_batch_get_launch(h):
+    w, c, t = C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(load().cem_batch_get_launch(h, C.byref(w), C.byref(c), C.byref(t)))
+    return w.value, c.value, t.value
+
+
 def cem_batch_create(problems):
     """problems: list of dicts with scene, skel, N, K and optional seed,
     problem, cov ('full' | 'diag')."""
@@ -425,6 +451,13 @@ class Batch:
 
     def autotune(self):
         return cem_batch_autotune(self.h)
+
+    def set_threads_per_rollout(self, tpr):
+        cem_batch_set_threads_per_rollout(self.h, tpr)
+
+    def launch(self):
+        """(warps per CTA, CTAs per SM, lanes per pick-and-place rollout)."""
+        return cem_batch_get_launch(self.h)
 
     def set_launch(self, warps_per_cta, ctas_per_sm=0):
         cem_batch_set_launch(self.h, warps_per_cta, ctas_per_sm)
@@ -690,6 +723,14 @@ class Scene:
 
     def set_launch(self, block):
         cem_set_launch(self.h, block)
+
+    def set_threads_per_rollout(self, tpr):
+        """Lanes per pick-and-place rollout: 1, 8 or 32 (bit-identical results)."""
+        cem_set_threads_per_rollout(self.h, tpr)
+
+    def launch(self, N):
+        """(threads per block, lanes per rollout) that a rollout of N samples uses."""
+        return cem_get_launch(self.h, N)
 
     def solve_screened(self, surrogate, scene16, seed, N, K, iters, n_pool, n_explore=0, cov_mode="full",
                        problem=0):

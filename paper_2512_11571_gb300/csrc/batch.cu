@@ -52,6 +52,8 @@ struct cem_batch_ctx {
   Track* track_d = nullptr;
   RefitArgs* args_d = nullptr;
   int warps = 4, ctas_per_sm = 0;  // persistent launch shape (0 = occupancy)
+  int tpr = 1;                     // lanes per pick-and-place rollout (1, 8 or 32)
+  bool has_pickplace = false;
   cudaGraphExec_t graph = nullptr;
   long long steps_per_iter = 0;
 };
@@ -69,7 +71,7 @@ void batch_free(cem_batch_ctx* h) {
 int grid_size(const cem_batch_ctx* h) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps);
+  const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr);
   return sms * per_sm;
 }
 
@@ -79,7 +81,7 @@ cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st) {
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
-                                      h->J_d, h->cls_d, grid_size(h), h->warps, st);
+                                      h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, st);
   if (e != cudaSuccess) return e;
   return launch_refit_batch(h->args_d, h->P, h->maxK, h->maxD, st);
 }
@@ -112,6 +114,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
       return fail(CEM_ERR_UNSUPPORTED, "problem " + std::to_string(p) + ": N in 1..2^20, K in 1..4096, known cov mode");
     }
     host[p] = prepare_scene(scenes[p], skels[p]);
+    if (host[p].kind == CEM_SCENE_PICKPLACE) h->has_pickplace = true;
     BatchProblem b;
     std::memset(&b, 0, sizeof(b));
     b.N = q.N;
@@ -318,7 +321,7 @@ int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm)
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   if (warps_per_cta < 1 || warps_per_cta > 8 || ctas_per_sm < 0 || ctas_per_sm > 64)
     return fail(CEM_ERR_INVALID_ARG, "warps per CTA in 1..8, CTAs per SM in 0..64 (0 = occupancy)");
-  if (ctas_per_sm > rollout_batch_max_ctas_per_sm(warps_per_cta))
+  if (ctas_per_sm > rollout_batch_max_ctas_per_sm(warps_per_cta, h->tpr))
     return fail(CEM_ERR_INVALID_ARG, "more CTAs per SM than can be resident: the persistent grid must fit");
   h->warps = warps_per_cta;
   h->ctas_per_sm = ctas_per_sm;
@@ -337,37 +340,50 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
   // theta from the initial distributions, then time the persistent rollout
   cudaError_t e = launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, 0);
   float best = INFINITY;
-  int bw = h->warps, bc = h->ctas_per_sm;
+  int bw = h->warps, bc = h->ctas_per_sm, bt = h->tpr;
   const int cand_w[] = {1, 2, 4, 8};
-  for (int w : cand_w) {
-    const int maxc = rollout_batch_max_ctas_per_sm(w);
-    for (int c = 1; c <= maxc && e == cudaSuccess; c *= 2) {
-      h->warps = w;
-      h->ctas_per_sm = c;
-      float tot = 0.0f;
-      for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-        e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), 0);
-        if (e == cudaSuccess) e = cudaEventRecord(a, 0);
-        if (e == cudaSuccess)
-          e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d,
-                                              h->theta_d, h->J_d, h->cls_d, grid_size(h), w, 0);
-        if (e == cudaSuccess) e = cudaEventRecord(b, 0);
-        if (e == cudaSuccess) e = cudaEventSynchronize(b);
-        float ms = 0.0f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-        if (rep > 0) tot += ms;
+  // lanes per pick-and-place rollout, then warps per CTA and CTAs per SM; a
+  // lane width whose first shape is over twice the best so far is dropped
+  for (int t : {1, 8, 32}) {
+    if (t > 1 && !h->has_pickplace) break;
+    bool first = true, drop = false;
+    for (int w : cand_w) {
+      const int maxc = rollout_batch_max_ctas_per_sm(w, t);
+      for (int c = 1; c <= maxc && e == cudaSuccess && !drop; c *= 2) {
+        h->warps = w;
+        h->ctas_per_sm = c;
+        h->tpr = t;
+        float tot = 0.0f;
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+          e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), 0);
+          if (e == cudaSuccess) e = cudaEventRecord(a, 0);
+          if (e == cudaSuccess)
+            e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d,
+                                                h->theta_d, h->J_d, h->cls_d, grid_size(h), w, t, 0);
+          if (e == cudaSuccess) e = cudaEventRecord(b, 0);
+          if (e == cudaSuccess) e = cudaEventSynchronize(b);
+          float ms = 0.0f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+          if (rep > 0) tot += ms;
+        }
+        if (e == cudaSuccess && tot < best) {
+          best = tot;
+          bw = w;
+          bc = c;
+          bt = t;
+        } else if (first && t > 1 && tot > 2.0f * best) {
+          drop = true;
+        }
+        first = false;
       }
-      if (e == cudaSuccess && tot < best) {
-        best = tot;
-        bw = w;
-        bc = c;
-      }
+      if (drop) break;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   h->warps = bw;
   h->ctas_per_sm = bc;
+  h->tpr = bt;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
     h->graph = nullptr;
@@ -380,5 +396,25 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
 }
 
 long long cem_batch_steps_per_iteration(cem_batch_handle h) { return h ? h->steps_per_iter : 0; }
+
+int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (tpr != 1 && tpr != 8 && tpr != 32) return fail(CEM_ERR_INVALID_ARG, "threads per rollout must be 1, 8 or 32");
+  if (h->ctas_per_sm > rollout_batch_max_ctas_per_sm(h->warps, tpr)) h->ctas_per_sm = 0;
+  h->tpr = tpr;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
+}
+
+int cem_batch_get_launch(cem_batch_handle h, int* warps_out, int* ctas_out, int* tpr_out) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (warps_out) *warps_out = h->warps;
+  if (ctas_out) *ctas_out = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr);
+  if (tpr_out) *tpr_out = h->tpr;
+  return CEM_OK;
+}
 
 }  // extern "C"

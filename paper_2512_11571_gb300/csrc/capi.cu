@@ -62,6 +62,7 @@ struct cem_ctx {
   DevScene host;
   DevScene* scene_d = nullptr;
   int block = 0;  // rollout threads per block (0 = heuristic)
+  int tpr = 1;    // lanes per pick-and-place rollout (1, 8 or 32)
   // workspaces of cem_solve
   int cap_N = 0, cap_K = 0, cap_iters = 0;
   float* theta_d = nullptr;
@@ -306,7 +307,8 @@ cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N
   cudaError_t e = launch_sample(h->mean_d, h->chol_d, seed, &h->track_d->iter, 0, problem, N, h->skel.D, h->theta_d,
                                 h->stream);
   if (e != cudaSuccess) return e;
-  e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->stream);
+  e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->tpr,
+                     h->stream);
   if (e != cudaSuccess) return e;
   RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, K, cov_mode);
   a.mean = h->mean_d;
@@ -345,6 +347,7 @@ int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b) {
   b->scene = h->scene_d;
   b->kind = h->host.kind;
   b->block = default_block(h, N);
+  b->tpr = h->tpr;
   return CEM_OK;
 }
 
@@ -479,9 +482,32 @@ int cem_scene_destroy(cem_handle h) {
 
 int cem_set_launch(cem_handle h, int block_threads) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
-  if (block_threads != 0 && (block_threads < 32 || block_threads > 256 || block_threads % 32))
-    return fail(CEM_ERR_INVALID_ARG, "block size must be 0 or a multiple of 32 in 32..256");
+  if (block_threads != 0 && block_threads != 8 && block_threads != 16 &&
+      (block_threads < 32 || block_threads > 256 || block_threads % 32))
+    return fail(CEM_ERR_INVALID_ARG, "block size must be 0, 8, 16 or a multiple of 32 in 32..256");
   h->block = block_threads;
+  if (h->graph) {  // a captured iteration keeps the launch shape it was built with
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
+}
+
+int cem_set_threads_per_rollout(cem_handle h, int tpr) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (tpr != 1 && tpr != 8 && tpr != 32) return fail(CEM_ERR_INVALID_ARG, "threads per rollout must be 1, 8 or 32");
+  h->tpr = tpr;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
+}
+
+int cem_get_launch(cem_handle h, int N, int* block_out, int* tpr_out) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (block_out) *block_out = default_block(h, N > 0 ? N : 1);
+  if (tpr_out) *tpr_out = h->host.kind == CEM_SCENE_PICKPLACE ? h->tpr : 1;
   return CEM_OK;
 }
 
@@ -516,7 +542,7 @@ int cem_rollout_batch(cem_handle h, const float* theta_d, int N, float* J_d, uin
   if (N == 0) return CEM_OK;
   if (!is_device_ptr(theta_d) || !is_device_ptr(J_d) || !is_device_ptr(cls_d))
     return fail(CEM_ERR_INVALID_ARG, "theta, J and cls must be device pointers");
-  cudaError_t e = launch_rollout(h->scene_d, h->host.kind, theta_d, N, J_d, cls_d, default_block(h, N),
+  cudaError_t e = launch_rollout(h->scene_d, h->host.kind, theta_d, N, J_d, cls_d, default_block(h, N), h->tpr,
                                  (cudaStream_t)stream);
   return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_rollout_batch");
 }
@@ -616,16 +642,25 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
   std::snprintf(keybuf, sizeof(keybuf), "kind=%d T=%d D=%d A=%d G=%d N=%d sms=%d", h->host.kind, h->host.T,
                 h->host.D, h->host.n_act, h->host.n_geoms, N, sms);
   const std::string key(keybuf);
-  if (cache_path) {  // cache lines: "<key>|<block>"
+  const bool multi_lane = h->host.kind == CEM_SCENE_PICKPLACE;
+  if (cache_path) {  // cache lines: "<key>|<block>|<threads per rollout>"
     std::ifstream in(cache_path);
     std::string line;
     while (std::getline(in, line)) {
-      const size_t bar = line.rfind('|');
+      const size_t bar = line.find('|');
       if (bar != std::string::npos && line.substr(0, bar) == key) {
-        const int b = std::atoi(line.c_str() + bar + 1);
-        if (b >= 32 && b <= 256 && b % 32 == 0) {
+        int b = 0, t = 1;
+        const int got = std::sscanf(line.c_str() + bar + 1, "%d|%d", &b, &t);
+        const bool ok_b = b == 16 || (b >= 32 && b <= 256 && b % 32 == 0);
+        const bool ok_t = t == 1 || (multi_lane && (t == 8 || t == 32) && b >= 32);
+        if (got >= 1 && ok_b && ok_t) {
           h->block = b;
+          h->tpr = t;
           if (block_out) *block_out = b;
+          if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+          }
           return CEM_OK;
         }
       }
@@ -645,27 +680,41 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
   CEM_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
   cudaError_t e = launch_sample(h->mean_d, h->chol_d, 12345, nullptr, 0, 0, N, D, h->theta_d, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "autotune sample");
-  const int cand[] = {32, 64, 128, 256};
+  // candidates: threads per CTA, and for pick-and-place also 8 or 32 lanes
+  // per rollout; a lane width whose first shape is over twice the best so
+  // far is dropped
+  const int blocks1[] = {16, 32, 64, 128, 256};
+  const int blocksG[] = {32, 64, 128, 256};
   float best_ms = INFINITY;
-  int best_b = 128;
-  for (int b : cand) {
-    float tot = 0.0f;
-    for (int rep = 0; rep < 3; ++rep) {
-      CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
-      e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, h->stream);
-      if (e != cudaSuccess) return cuda_fail(e, "autotune rollout");
-      CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
-      CEM_CUDA(cudaEventSynchronize(h->ev1));
-      float ms = 0.0f;
-      CEM_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-      if (rep > 0) tot += ms;  // the first launch is a warm-up
-    }
-    if (tot < best_ms) {
-      best_ms = tot;
-      best_b = b;
+  int best_b = 128, best_t = 1;
+  for (int t : {1, 8, 32}) {
+    if (t > 1 && !multi_lane) break;
+    const int* bl = t == 1 ? blocks1 : blocksG;
+    const int nb = t == 1 ? 5 : 4;
+    for (int i = 0; i < nb; ++i) {
+      const int b = bl[i];
+      float tot = 0.0f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
+        e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, t, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune rollout");
+        CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
+        CEM_CUDA(cudaEventSynchronize(h->ev1));
+        float ms = 0.0f;
+        CEM_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        if (rep > 0) tot += ms;  // the first launch is a warm-up
+      }
+      if (tot < best_ms) {
+        best_ms = tot;
+        best_b = b;
+        best_t = t;
+      } else if (i == 0 && t > 1 && tot > 2.0f * best_ms) {
+        break;
+      }
     }
   }
   h->block = best_b;
+  h->tpr = best_t;
   if (block_out) *block_out = best_b;
   if (h->graph) {  // the captured rollout used the old launch shape
     cudaGraphExecDestroy(h->graph);
@@ -673,7 +722,7 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
   }
   if (cache_path) {
     std::ofstream o(cache_path, std::ios::app);
-    o << key << "|" << best_b << "\n";
+    o << key << "|" << best_b << "|" << best_t << "\n";
   }
   return CEM_OK;
 }

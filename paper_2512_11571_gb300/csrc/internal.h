@@ -97,8 +97,10 @@ cudaError_t launch_sample(const float* mean, const float* chol, uint64_t seed, c
                           uint32_t iter, uint32_t problem, int N, int D, float* theta, cudaStream_t st);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t iter, uint32_t problem, int N, int D, uint32_t* words,
                                 cudaStream_t st);
+// block = threads per CTA; tpr = lanes per rollout (1, 8 or 32; used for
+// pick-and-place scenes, the other kinds always run one lane per rollout)
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
-                           int block, cudaStream_t st);
+                           int block, int tpr, cudaStream_t st);
 cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
                          cudaStream_t st);
 cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
@@ -115,8 +117,8 @@ cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
-                                            cudaStream_t st);
-int rollout_batch_max_ctas_per_sm(int warps);
+                                            int tpr, cudaStream_t st);
+int rollout_batch_max_ctas_per_sm(int warps, int tpr);
 
 // host helpers shared by the C entry points (capi.cu)
 int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k);
@@ -142,7 +144,7 @@ struct SolveBuffers {
   cudaStream_t stream;
   cudaEvent_t ev0, ev1;
   const DevScene* scene;
-  int kind, block;
+  int kind, block, tpr;
 };
 const cem_skeleton_desc& handle_skeleton(cem_handle h);
 int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b);

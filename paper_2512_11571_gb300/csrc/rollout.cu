@@ -342,10 +342,12 @@ __device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px,
   for (int i = 0; i < ns; ++i) {
     const float* sl = s.slab[g][i];
     if (PLANAR && sl[2] != 0.0f) continue;
-    const float r = hx * fabsf(sl[0]) + hy * fabsf(sl[1]) + hz * fabsf(sl[2]);
-    const float sp = sl[0] * px + sl[1] * py + sl[2] * pz;
-    const float ov_pos = sl[4] - (sp - r);
-    const float ov_neg = (sp + r) - sl[3];
+    // rounding pinned (no contraction choices left to the compiler): every
+    // lane-group width evaluates a contact with the same operations
+    const float r = __fmaf_rn(hx, fabsf(sl[0]), __fmaf_rn(hy, fabsf(sl[1]), __fmul_rn(hz, fabsf(sl[2]))));
+    const float sp = __fmaf_rn(sl[0], px, __fmaf_rn(sl[1], py, __fmul_rn(sl[2], pz)));
+    const float ov_pos = __fsub_rn(sl[4], __fsub_rn(sp, r));
+    const float ov_neg = __fsub_rn(__fadd_rn(sp, r), sl[3]);
     if (ov_pos <= 0.0f || ov_neg <= 0.0f) return false;
     const float ov = fminf(ov_pos, ov_neg);
     if (!any || ov < best) {
@@ -361,18 +363,84 @@ __device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px,
   return any;
 }
 
+// A group of G consecutive lanes (G = 1, 8 or 32) sharing one rollout: every
+// lane holds the same state and runs the same serial dynamics, the group
+// splits the per-geometry contact queries and combines their results with
+// warp shuffles.
+template <int G>
+struct Group {
+  unsigned mask;  // the group's lanes
+  int rank;       // this lane's index in the group
+  __device__ __forceinline__ Group() {
+    const int lane = threadIdx.x & 31;
+    rank = lane & (G - 1);
+    mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane - rank));
+  }
+  __device__ __forceinline__ float from(float v, int src) const { return G == 1 ? v : __shfl_sync(mask, v, src, G); }
+  __device__ __forceinline__ uint32_t any_bits(uint32_t v) const { return G == 1 ? v : __reduce_or_sync(mask, v); }
+};
+
+// position of the k-th (0-based) set bit of m
+__device__ __forceinline__ int nth_bit(uint32_t m, int k) {
+  for (int i = 0; i < k; ++i) m &= m - 1u;
+  return __ffs(m) - 1;
+}
+
+// Penalty force on the base footprint from geometry g: F_n = max(0, k depth -
+// c v_n) along the minimum-overlap normal, returned as (cx, cy) = F_n n.
+__device__ __forceinline__ bool base_force(const DevScene& s, int g, float bx, float by, float bvx, float bvy,
+                                           float kc, float cc, float& cx, float& cy) {
+  float nx, ny, nz, dep;
+  if (!slab_contact<true>(s, g, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, nx, ny, nz, dep)) return false;
+  const float vn = __fmaf_rn(bvx, nx, __fmul_rn(bvy, ny));
+  const float Fn = fmaxf(0.0f, __fsub_rn(__fmul_rn(kc, dep), __fmul_rn(cc, vn)));
+  cx = __fmul_rn(Fn, nx);
+  cy = __fmul_rn(Fn, ny);
+  return true;
+}
+
+// Normal and F_n of the object against geometry g (false: no overlap).
+__device__ __forceinline__ bool obj_force(const DevScene& s, int g, float px, float py, float pz, float vx, float vy,
+                                          float vz, float kc, float cc, float& nx, float& ny, float& nz, float& Fn) {
+  float dep;
+  if (!slab_contact<false>(s, g, px, py, pz, s.oh, s.oh, s.oh, nx, ny, nz, dep)) return false;
+  const float vn = __fmaf_rn(vx, nx, __fmaf_rn(vy, ny, __fmul_rn(vz, nz)));
+  Fn = fmaxf(0.0f, __fsub_rn(__fmul_rn(kc, dep), __fmul_rn(cc, vn)));
+  return true;
+}
+
+// Jacobi friction impulse of one of nc object contacts (normal n, force Fn)
+// from the trial velocity v: the tangential velocity removed, capped by
+// mu F_n dt; returned as the impulse per unit mass to subtract.
+__device__ __forceinline__ bool obj_friction(const DevScene& s, float nx, float ny, float nz, float Fn, float vx,
+                                             float vy, float vz, int nc, float& cx, float& cy, float& cz) {
+  const float vn = __fmaf_rn(vx, nx, __fmaf_rn(vy, ny, __fmul_rn(vz, nz)));
+  const float tx = __fmaf_rn(-vn, nx, vx), ty = __fmaf_rn(-vn, ny, vy), tz = __fmaf_rn(-vn, nz, vz);
+  const float vt = __fsqrt_rn(__fmaf_rn(tx, tx, __fmaf_rn(ty, ty, __fmul_rn(tz, tz))));
+  if (!(vt > 0.0f)) return false;
+  const float mvt = __fmul_rn(s.mo, vt);
+  const float jm = fminf(__fmul_rn(s.obj_cap, Fn), __fdiv_rn(mvt, (float)nc));
+  const float f = __fdiv_rn(jm, mvt);
+  cx = __fmul_rn(f, tx);
+  cy = __fmul_rn(f, ty);
+  cz = __fmul_rn(f, tz);
+  return true;
+}
+
 // Neighbour list of an axis-aligned mover (half sizes hx, hy, hz at p):
 // the geometries whose gap to the mover along every world axis they list is
 // below `skin`.  A geometry left out has a gap >= skin along some world axis;
 // while the mover has moved less than skin along every axis since the build
 // that gap stays positive, so the geometry is still separated and its
 // contact test would return no contact.  PLANAR: base footprint (x, y only).
-template <bool PLANAR>
+// A lane group splits the geometries (lane r tests g = r, r + G, ...) and
+// ORs the bits.
+template <bool PLANAR, int G>
 __device__ __forceinline__ uint32_t near_list(const DevScene& s, int n_geoms, float px, float py, float pz, float hx,
-                                              float hy, float hz, float skin) {
+                                              float hy, float hz, float skin, const Group<G>& grp) {
   uint32_t m = 0;
   const int flag = PLANAR ? 1 : 2;
-  for (int g = 0; g < n_geoms; ++g) {
+  for (int g = grp.rank; g < n_geoms; g += G) {
     if (!(s.geom_flags[g] & flag)) continue;
     bool far = false;
     const int ns = s.geom_nslab[g];
@@ -395,7 +463,166 @@ __device__ __forceinline__ uint32_t near_list(const DevScene& s, int n_geoms, fl
     }
     if (!far) m |= 1u << g;
   }
-  return m;
+  return grp.any_bits(m);
+}
+
+// Sum of the base's contact forces over the neighbour list `nbr`, added to
+// (fx, fy) in ascending geometry order.  G > 1: the k-th neighbour belongs to
+// lane k % G, which evaluates it; the sum then takes each contacting
+// geometry's force from its owner lane, in the same order and with the same
+// roundings as one lane alone.
+template <int G>
+__device__ __forceinline__ void base_contacts(const DevScene& s, uint32_t nbr, float bx, float by, float bvx,
+                                              float bvy, float kc, float cc, const Group<G>& grp, float& fx,
+                                              float& fy) {
+  if (G == 1) {
+    for (uint32_t m = nbr; m; m &= m - 1u) {
+      float cx, cy;
+      if (base_force(s, __ffs(m) - 1, bx, by, bvx, bvy, kc, cc, cx, cy)) {
+        fx = __fadd_rn(fx, cx);
+        fy = __fadd_rn(fy, cy);
+      }
+    }
+    return;
+  }
+  constexpr int SL = (CEM_MAX_GEOMS + G - 1) / G;
+  float cx[SL], cy[SL];
+  uint32_t hit = 0;
+  const int nn = __popc(nbr);
+#pragma unroll
+  for (int j = 0; j < SL; ++j) {
+    cx[j] = cy[j] = 0.0f;
+    const int k = grp.rank + j * G;
+    if (k < nn) {
+      const int g = nth_bit(nbr, k);
+      if (base_force(s, g, bx, by, bvx, bvy, kc, cc, cx[j], cy[j])) hit |= 1u << g;
+    }
+  }
+  for (uint32_t m = grp.any_bits(hit); m; m &= m - 1u) {
+    const int g = __ffs(m) - 1;
+    const int k = __popc(nbr & ((1u << g) - 1u));
+    const int j = k / G, src = k & (G - 1);
+    float vx = cx[0], vy = cy[0];
+#pragma unroll
+    for (int i = 1; i < SL; ++i)
+      if (j == i) {
+        vx = cx[i];
+        vy = cy[i];
+      }
+    fx = __fadd_rn(fx, grp.from(vx, src));
+    fy = __fadd_rn(fy, grp.from(vy, src));
+  }
+}
+
+// One object step against the static geometry in `nbr` (not attached):
+// penalty forces from the pre-step state, the trial velocity with gravity,
+// then one Jacobi friction impulse per contact from that trial velocity,
+// each summed in ascending geometry order.  Updates the velocity only.
+template <int G>
+__device__ __forceinline__ void object_contacts(const DevScene& s, uint32_t nbr, float ox, float oy, float oz,
+                                                float& ovx, float& ovy, float& ovz, float kc, float cc,
+                                                const Group<G>& grp) {
+  const float pvx = ovx, pvy = ovy, pvz = ovz;
+  float fsx = 0.f, fsy = 0.f, fsz = 0.f;
+  float jx = 0.f, jy = 0.f, jz = 0.f;
+  if (G == 1) {
+    uint32_t cm = 0;
+    int nc = 0;
+    for (uint32_t m = nbr; m; m &= m - 1u) {
+      const int g = __ffs(m) - 1;
+      float nx, ny, nz, Fn;
+      if (obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx, ny, nz, Fn) && Fn > 0.0f) {
+        cm |= 1u << g;
+        ++nc;
+        fsx = __fadd_rn(fsx, __fmul_rn(Fn, nx));
+        fsy = __fadd_rn(fsy, __fmul_rn(Fn, ny));
+        fsz = __fadd_rn(fsz, __fmul_rn(Fn, nz));
+      }
+    }
+    ovx = __fmaf_rn(s.dt_mo, fsx, pvx);
+    ovy = __fmaf_rn(s.dt_mo, fsy, pvy);
+    ovz = __fsub_rn(__fmaf_rn(s.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
+    // the same contacts again (identical arithmetic) for the friction
+    for (uint32_t m = cm; m; m &= m - 1u) {
+      const int g = __ffs(m) - 1;
+      float nx, ny, nz, Fn, cx, cy, cz;
+      obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx, ny, nz, Fn);
+      if (obj_friction(s, nx, ny, nz, Fn, ovx, ovy, ovz, nc, cx, cy, cz)) {
+        jx = __fsub_rn(jx, cx);
+        jy = __fsub_rn(jy, cy);
+        jz = __fsub_rn(jz, cz);
+      }
+    }
+  } else {
+    constexpr int SL = (CEM_MAX_GEOMS + G - 1) / G;
+    float nx[SL], ny[SL], nz[SL], Fn[SL];
+    uint32_t hit = 0;
+    const int nn = __popc(nbr);
+#pragma unroll
+    for (int j = 0; j < SL; ++j) {
+      nx[j] = ny[j] = nz[j] = Fn[j] = 0.0f;
+      const int k = grp.rank + j * G;
+      if (k < nn) {
+        const int g = nth_bit(nbr, k);
+        if (obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx[j], ny[j], nz[j], Fn[j]) && Fn[j] > 0.0f)
+          hit |= 1u << g;
+      }
+    }
+    const uint32_t cm = grp.any_bits(hit);
+    const int nc = __popc(cm);
+    // forces in ascending geometry order, each from its owner lane
+    for (uint32_t m = cm; m; m &= m - 1u) {
+      const int g = __ffs(m) - 1;
+      const int k = __popc(nbr & ((1u << g) - 1u));
+      const int j = k / G, src = k & (G - 1);
+      float a = 0.f, b = 0.f, c = 0.f;
+#pragma unroll
+      for (int i = 0; i < SL; ++i)
+        if (j == i) {
+          a = __fmul_rn(Fn[i], nx[i]);
+          b = __fmul_rn(Fn[i], ny[i]);
+          c = __fmul_rn(Fn[i], nz[i]);
+        }
+      fsx = __fadd_rn(fsx, grp.from(a, src));
+      fsy = __fadd_rn(fsy, grp.from(b, src));
+      fsz = __fadd_rn(fsz, grp.from(c, src));
+    }
+    ovx = __fmaf_rn(s.dt_mo, fsx, pvx);
+    ovy = __fmaf_rn(s.dt_mo, fsy, pvy);
+    ovz = __fsub_rn(__fmaf_rn(s.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
+    // friction: every owner evaluates its contacts, then the ordered sum
+    float fx[SL], fy[SL], fz[SL];
+    uint32_t fr = 0;
+#pragma unroll
+    for (int j = 0; j < SL; ++j) {
+      fx[j] = fy[j] = fz[j] = 0.0f;
+      const int k = grp.rank + j * G;
+      if (k < nn) {
+        const int g = nth_bit(nbr, k);
+        if (((cm >> g) & 1u) && obj_friction(s, nx[j], ny[j], nz[j], Fn[j], ovx, ovy, ovz, nc, fx[j], fy[j], fz[j]))
+          fr |= 1u << g;
+      }
+    }
+    for (uint32_t m = grp.any_bits(fr); m; m &= m - 1u) {
+      const int g = __ffs(m) - 1;
+      const int k = __popc(nbr & ((1u << g) - 1u));
+      const int j = k / G, src = k & (G - 1);
+      float a = fx[0], b = fy[0], c = fz[0];
+#pragma unroll
+      for (int i = 1; i < SL; ++i)
+        if (j == i) {
+          a = fx[i];
+          b = fy[i];
+          c = fz[i];
+        }
+      jx = __fsub_rn(jx, grp.from(a, src));
+      jy = __fsub_rn(jy, grp.from(b, src));
+      jz = __fsub_rn(jz, grp.from(c, src));
+    }
+  }
+  ovx = __fadd_rn(ovx, jx);
+  ovy = __fadd_rn(ovy, jy);
+  ovz = __fadd_rn(ovz, jz);
 }
 
 // Analytic inverse kinematics of the 2-link arm in its vertical plane
@@ -461,12 +688,13 @@ __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, fl
   ey = by + r * sb;
 }
 
-template <bool TRACE>
+template <int G, bool TRACE>
 __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out,
                                   int& cls_out, float* tr) {
-  const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps, gdt = s.g * s.dt;
+  const Group<G> grp;
+  const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps;
   const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap, bcap2 = bcap * bcap;
-  const float kc = s.k_contact, cc = s.c_contact, dt_mo = s.dt_mo, akp = s.arm_kp, akd = s.arm_kd;
+  const float kc = s.k_contact, cc = s.c_contact, akp = s.arm_kp, akd = s.arm_kd;
   const int n_geoms = s.n_geoms;
   float bx = s.base_start[0], by = s.base_start[1], bvx = s.base_v0[0], bvy = s.base_v0[1];
   float q1 = s.arm_home[0], q2 = s.arm_home[1], dq1 = 0.f, dq2 = 0.f, beta = 0.f;
@@ -547,20 +775,11 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
     float fx = mb * (kp * (gx - bx) - kd * bvx);
     float fy = mb * (kp * (gy - by) - kd * bvy);
     if (__any_sync(lanes, fmaxf(fabsf(bx - brx), fabsf(by - bry)) >= kRebuild)) {
-      bmask = near_list<true>(s, n_geoms, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, kSkin);
+      bmask = near_list<true, G>(s, n_geoms, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, kSkin, grp);
       brx = bx;
       bry = by;
     }
-    for (uint32_t m = bmask; m; m &= m - 1) {
-      const int g = __ffs(m) - 1;
-      float nx, ny, nz, dep;
-      if (slab_contact<true>(s, g, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, nx, ny, nz, dep)) {
-        const float vn = bvx * nx + bvy * ny;
-        const float Fn = fmaxf(0.0f, kc * dep - cc * vn);
-        fx += Fn * nx;
-        fy += Fn * ny;
-      }
-    }
+    base_contacts<G>(s, bmask, bx, by, bvx, bvy, kc, cc, grp, fx, fy);
     bvx += dt_mb * fx;
     bvy += dt_mb * fy;
     {  // ground friction of the base (yaw is locked)
@@ -591,59 +810,13 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
       ovy = (ney - ey) / dt;
       ovz = (nez - ez) / dt;
     } else {
-      uint32_t mask = 0;
-      int nc = 0;
-      float fsx = 0.f, fsy = 0.f, fsz = 0.f;
       if (orebuild) {
-        omask = near_list<false>(s, n_geoms, ox, oy, oz, h, h, h, kSkin);
+        omask = near_list<false, G>(s, n_geoms, ox, oy, oz, h, h, h, kSkin, grp);
         orx = ox;
         ory = oy;
         orz = oz;
       }
-      for (uint32_t m = omask; m; m &= m - 1) {
-        const int g = __ffs(m) - 1;
-        float nx, ny, nz, dep;
-        if (slab_contact<false>(s, g, ox, oy, oz, h, h, h, nx, ny, nz, dep)) {
-          const float vn = ovx * nx + ovy * ny + ovz * nz;
-          const float Fn = fmaxf(0.0f, kc * dep - cc * vn);
-          if (Fn > 0.0f) {
-            mask |= 1u << g;
-            ++nc;
-            fsx += Fn * nx;
-            fsy += Fn * ny;
-            fsz += Fn * nz;
-          }
-        }
-      }
-      // the same contacts again (identical arithmetic) for the Jacobi
-      // friction impulses, all taken from one trial velocity
-      const float px = ox, py = oy, pz = oz;
-      const float pvx = ovx, pvy = ovy, pvz = ovz;
-      ovx += dt_mo * fsx;
-      ovy += dt_mo * fsy;
-      ovz += dt_mo * fsz - gdt;
-      float jx = 0.f, jy = 0.f, jz = 0.f;
-      while (mask) {
-        const int g = __ffs(mask) - 1;
-        mask &= mask - 1;
-        float nx, ny, nz, dep;
-        slab_contact<false>(s, g, px, py, pz, h, h, h, nx, ny, nz, dep);
-        const float vn0 = pvx * nx + pvy * ny + pvz * nz;
-        const float Fn = fmaxf(0.0f, kc * dep - cc * vn0);
-        const float vn = ovx * nx + ovy * ny + ovz * nz;
-        const float tx_ = ovx - vn * nx, ty_ = ovy - vn * ny, tz_ = ovz - vn * nz;
-        const float vt = sqrtf(tx_ * tx_ + ty_ * ty_ + tz_ * tz_);
-        if (vt > 0.0f) {
-          const float jm = fminf(s.obj_cap * Fn, s.mo * vt / (float)nc);
-          const float f = jm / (s.mo * vt);
-          jx -= f * tx_;
-          jy -= f * ty_;
-          jz -= f * tz_;
-        }
-      }
-      ovx += jx;
-      ovy += jy;
-      ovz += jz;
+      object_contacts<G>(s, omask, ox, oy, oz, ovx, ovy, ovz, kc, cc, grp);
       ox += ovx * dt;
       oy += ovy * dt;
       oz += ovz * dt;
@@ -731,14 +904,16 @@ __device__ __forceinline__ void stage_scene(const DevScene* __restrict__ g, DevS
   __syncthreads();
 }
 
-template <int KIND, bool TRACE>
+// One rollout per group of G lanes (G > 1 only for pick-and-place); the
+// group's first lane writes the result.
+template <int KIND, bool TRACE, int G>
 __global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict__ scene_g,
                                                       const float* __restrict__ theta, int N, int steps,
                                                       float* __restrict__ J, uint8_t* __restrict__ cls,
                                                       float* __restrict__ trace) {
   __shared__ DevScene s;
   stage_scene(scene_g, s);
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = (int)((blockIdx.x * blockDim.x + threadIdx.x) / G);
   if (n >= N) return;
   const float* row = theta + (size_t)n * s.D;
   float* tr = TRACE ? trace + (size_t)n * steps * TW : nullptr;
@@ -747,9 +922,9 @@ __global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict
   int c;
   if (KIND == CEM_SCENE_REACH) planar_rollout<false, TRACE>(s, row, T, Jn, c, tr);
   else if (KIND == CEM_SCENE_PUSH) planar_rollout<true, TRACE>(s, row, T, Jn, c, tr);
-  else if (KIND == CEM_SCENE_PICKPLACE) pickplace_rollout<TRACE>(s, row, T, Jn, c, tr);
+  else if (KIND == CEM_SCENE_PICKPLACE) pickplace_rollout<G, TRACE>(s, row, T, Jn, c, tr);
   else quadratic_cost(s, row, Jn, c);
-  if (!TRACE) {
+  if (!TRACE && (G == 1 || (threadIdx.x & (G - 1)) == 0)) {
     J[n] = Jn;
     cls[n] = (uint8_t)c;
   }
@@ -757,22 +932,33 @@ __global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict
 
 template <bool TRACE>
 cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* J, uint8_t* cls,
-                     float* trace, int block, cudaStream_t st) {
+                     float* trace, int block, int tpr, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
   if (block <= 0) block = 128;
   const int grid = (N + block - 1) / block;
   switch (kind) {
     case CEM_SCENE_QUADRATIC:
-      rollout_kernel<CEM_SCENE_QUADRATIC, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      rollout_kernel<CEM_SCENE_QUADRATIC, TRACE, 1><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
       break;
     case CEM_SCENE_REACH:
-      rollout_kernel<CEM_SCENE_REACH, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      rollout_kernel<CEM_SCENE_REACH, TRACE, 1><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
       break;
     case CEM_SCENE_PUSH:
-      rollout_kernel<CEM_SCENE_PUSH, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      rollout_kernel<CEM_SCENE_PUSH, TRACE, 1><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
       break;
     case CEM_SCENE_PICKPLACE:
-      rollout_kernel<CEM_SCENE_PICKPLACE, TRACE><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      if (!TRACE && (tpr == 8 || tpr == 32)) {
+        // block threads: a multiple of 32 carrying block / tpr rollouts
+        const int bt = block < 32 ? 32 : block;
+        const long long threads = (long long)N * tpr;
+        const int g2 = (int)((threads + bt - 1) / bt);
+        if (tpr == 8)
+          rollout_kernel<CEM_SCENE_PICKPLACE, false, 8><<<g2, bt, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+        else
+          rollout_kernel<CEM_SCENE_PICKPLACE, false, 32><<<g2, bt, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      } else {
+        rollout_kernel<CEM_SCENE_PICKPLACE, TRACE, 1><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      }
       break;
     default:
       return cudaErrorInvalidValue;
@@ -788,6 +974,7 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
 // warps or CTAs: a warp that finds the queue empty exits.
 constexpr int kMaxBatchWarps = 8;
 
+template <int G>
 __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene* __restrict__ scenes,
                                                                  const BatchProblem* __restrict__ probs,
                                                                  const BatchItem* __restrict__ items, int n_items,
@@ -812,19 +999,37 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
       cur = item.problem;
     }
     const BatchProblem pb = probs[item.problem];
-    const int n = item.first + lane;
-    if (n < pb.N) {
-      const float* row = theta + pb.theta_off + (size_t)n * pb.D;
-      float Jn;
-      int c;
-      switch (s.kind) {
-        case CEM_SCENE_REACH: planar_rollout<false, false>(s, row, s.T, Jn, c, nullptr); break;
-        case CEM_SCENE_PUSH: planar_rollout<true, false>(s, row, s.T, Jn, c, nullptr); break;
-        case CEM_SCENE_PICKPLACE: pickplace_rollout<false>(s, row, s.T, Jn, c, nullptr); break;
-        default: quadratic_cost(s, row, Jn, c); break;
+    if (G > 1 && s.kind == CEM_SCENE_PICKPLACE) {
+      // G lanes per rollout: the 32-sample item in G passes of 32 / G
+      for (int sub = 0; sub < G; ++sub) {
+        const int n = item.first + sub * (32 / G) + lane / G;
+        if (n < pb.N) {
+          const float* row = theta + pb.theta_off + (size_t)n * pb.D;
+          float Jn;
+          int c;
+          pickplace_rollout<G, false>(s, row, s.T, Jn, c, nullptr);
+          if ((lane & (G - 1)) == 0) {
+            J[pb.sample_off + n] = Jn;
+            cls[pb.sample_off + n] = (uint8_t)c;
+          }
+        }
+        __syncwarp();
       }
-      J[pb.sample_off + n] = Jn;
-      cls[pb.sample_off + n] = (uint8_t)c;
+    } else {
+      const int n = item.first + lane;
+      if (n < pb.N) {
+        const float* row = theta + pb.theta_off + (size_t)n * pb.D;
+        float Jn;
+        int c;
+        switch (s.kind) {
+          case CEM_SCENE_REACH: planar_rollout<false, false>(s, row, s.T, Jn, c, nullptr); break;
+          case CEM_SCENE_PUSH: planar_rollout<true, false>(s, row, s.T, Jn, c, nullptr); break;
+          case CEM_SCENE_PICKPLACE: pickplace_rollout<1, false>(s, row, s.T, Jn, c, nullptr); break;
+          default: quadratic_cost(s, row, Jn, c); break;
+        }
+        J[pb.sample_off + n] = Jn;
+        cls[pb.sample_off + n] = (uint8_t)c;
+      }
     }
     __syncwarp();
   }
@@ -832,9 +1037,13 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
 
 }  // namespace
 
-int rollout_batch_max_ctas_per_sm(int warps) {
+int rollout_batch_max_ctas_per_sm(int warps, int tpr) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel, warps * 32, 0) != cudaSuccess) {
+  cudaError_t e;
+  if (tpr == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<8>, warps * 32, 0);
+  else if (tpr == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<32>, warps * 32, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<1>, warps * 32, 0);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -844,22 +1053,31 @@ int rollout_batch_max_ctas_per_sm(int warps) {
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
-                                            cudaStream_t st) {
+                                            int tpr, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (warps < 1 || warps > kMaxBatchWarps || grid < 1) return cudaErrorInvalidValue;
-  rollout_persistent_kernel<<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta, J,
-                                                        cls);
+  if (tpr == 8)
+    rollout_persistent_kernel<8><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
+                                                             J, cls);
+  else if (tpr == 32)
+    rollout_persistent_kernel<32><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
+                                                              J, cls);
+  else if (tpr == 1)
+    rollout_persistent_kernel<1><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
+                                                             J, cls);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
-                           int block, cudaStream_t st) {
-  return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, st);
+                           int block, int tpr, cudaStream_t st) {
+  return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, tpr, st);
 }
 
 cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
                          cudaStream_t st) {
-  return dispatch<true>(s_d, kind, theta, N, steps, nullptr, nullptr, states, 64, st);
+  return dispatch<true>(s_d, kind, theta, N, steps, nullptr, nullptr, states, 64, 1, st);
 }
 
 }  // namespace cem

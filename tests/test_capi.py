@@ -123,6 +123,8 @@ def test_validation_rejects_bad_descriptors(pkg):
     assert L.cem_rollout_batch(None, None, 1, None, None, None) == -1
     assert L.cem_refit(None, None, None, None, 1, 1, 0, None, None, None, None, None, None) == -1
     assert L.cem_scene_destroy(None) == 0
+    assert L.cem_set_threads_per_rollout(None, 8) == -1
+    assert L.cem_get_launch(None, 1, None, None) == -1
 
 
 def test_pick_place_descriptor_packs(pkg):
@@ -152,3 +154,5 @@ def test_batch_validation_names_the_problem(pkg):
     assert L.cem_batch_create(scenes, skels, params, n, C.byref(h)) == -5
     assert L.cem_batch_create(scenes, skels, params, 0, C.byref(h)) == -5
     assert L.cem_batch_iterate(None, 1, 1, None) == -1
+    assert L.cem_batch_set_threads_per_rollout(None, 8) == -1
+    assert L.cem_batch_get_launch(None, None, None, None) == -1

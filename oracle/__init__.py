@@ -74,6 +74,7 @@ class _Scene(C.Structure):
         ("act_ref_target", C.c_int32 * MAX_ACT),
         ("act_nom", (C.c_double * 3) * MAX_ACT), ("act_yaw", C.c_double * MAX_ACT),
         ("lo", C.c_double * MAX_D), ("hi", C.c_double * MAX_D),
+        ("act_region", C.c_int32 * MAX_ACT), ("act_ring", (C.c_double * 4) * MAX_ACT),
     ]
 
 
@@ -138,6 +139,12 @@ def pack(scene: dict, skel: dict, T: int | None = None) -> _Scene:
         s.act_ref_target[i] = 1 if a.get("success_ref", "nominal") == "target" else 0
         _set(s.act_nom[i], a["nominal"])
         s.act_yaw[i] = a.get("yaw", 0.0)
+        reg = a.get("region")
+        if reg is not None:  # annulus of a move goal: centre (x, y), radii (inner, outer)
+            if reg["kind"] != "ring" or a["kind"] != "move":
+                raise ValueError("only move goals take an annulus region")
+            s.act_region[i] = 1
+            _set(s.act_ring[i], [reg["center"][0], reg["center"][1], reg["radii"][0], reg["radii"][1]])
         off += width[a["kind"]]
     if acts and off != s.D:
         raise ValueError("skeleton width does not match bounds")
@@ -177,6 +184,11 @@ def lib():
             L.or_cem.argtypes = [sp, C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  dp, dp, C.POINTER(C.c_int), dp, dp, dp, dp]
             L.or_cem.restype = C.c_int
+            L.or_n_env.argtypes = [C.c_int] * 4
+            L.or_n_env.restype = C.c_int
+            L.or_cem_paper.argtypes = [sp, C.c_uint64, C.c_uint32] + [C.c_int] * 7 + [
+                dp, dp, C.POINTER(C.c_int), dp, dp, dp, i32p, i32p]
+            L.or_cem_paper.restype = C.c_int
             _lib = L
     return _lib
 
@@ -297,3 +309,31 @@ def cem(scene, skel, seed, N, K, iters, problem=0, diag=False, nthreads=0):
         raise RuntimeError(f"oracle CE loop failed: {rc}")
     return dict(best_theta=bt, best_J=bJ.value, best_cls=bc.value, mean=mean, cov=cov, history=hist,
                 k_eff=keff)
+
+
+def n_env(n0, n1, j1, j):
+    """Samples of CE iteration j under the linear schedule (Sec. IV-A)."""
+    return lib().or_n_env(n0, n1, j1, j)
+
+
+def cem_paper(scene, skel, seed, n0=3000, n1=300, j1=10, K=50, iters=20, problem=0, diag=True, nthreads=0):
+    """The paper's CE variant: uniform initial sampling in the parameter
+    regions, the n_env schedule, the independent-normal model (diag)."""
+    s = pack(scene, skel)
+    D = s.D
+    bt = np.zeros(D)
+    bJ = C.c_double()
+    bc = C.c_int()
+    mean = np.zeros(D)
+    cov = np.zeros((D, D))
+    hist = np.zeros(iters)
+    counts = np.zeros((iters, 4), np.int32)
+    ns = np.zeros(iters, np.int32)
+    rc = lib().or_cem_paper(C.byref(s), seed, problem, n0, n1, j1, K, iters, int(diag), nthreads,
+                            _p(bt, C.c_double), C.byref(bJ), C.byref(bc), _p(mean, C.c_double),
+                            _p(cov, C.c_double), _p(hist, C.c_double), _p(counts, C.c_int32),
+                            _p(ns, C.c_int32))
+    if rc != 0:
+        raise RuntimeError(f"oracle CE loop failed: {rc}")
+    return dict(best_theta=bt, best_J=bJ.value, best_cls=bc.value, mean=mean, cov=cov, history=hist,
+                class_counts=counts, n_env=ns)

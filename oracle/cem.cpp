@@ -157,3 +157,61 @@ extern "C" int or_cem(const or_scene* s, uint64_t seed, uint32_t problem, int N,
   *best_cls = bcls;
   return 0;
 }
+
+// Linear sample-count schedule of Sec. IV-A, rounded to the nearest integer
+// (halves up).
+extern "C" int or_n_env(int n0, int n1, int j1, int j) {
+  if (j1 <= 0 || j >= j1) return j1 <= 0 && j == 0 ? n0 : n1;
+  const double v = (double)n0 + (double)(n1 - n0) * (double)j / (double)j1;
+  return (int)std::floor(v + 0.5);
+}
+
+// The paper's variant of Algorithm 1 (Sec. III-B, IV-A): the initial
+// distribution is uniform inside the parameter regions (iteration 0), the
+// sampled batch shrinks by the schedule, and each later iteration samples
+// the normal model refit from the previous elites.
+extern "C" int or_cem_paper(const or_scene* s, uint64_t seed, uint32_t problem, int n0, int n1, int j1, int K,
+                            int iters, int diag, int nthreads, double* best_theta, double* best_J, int* best_cls,
+                            double* mean, double* cov, double* history, int* class_hist, int* n_hist) {
+  const int D = s->D;
+  const int nmax = std::max(n0, n1);
+  std::vector<double> mu(D, 0.0), C((size_t)D * D, 0.0), Lo((size_t)D * D, 0.0);
+  std::vector<double> th((size_t)nmax * D), J(nmax);
+  std::vector<uint8_t> cl(nmax);
+  std::vector<float> Jf(nmax);
+  std::vector<int32_t> idx(std::max(K, 1));
+  int bcls = 4;
+  float bJf = INFINITY;
+  double bJ = INFINITY;
+  std::vector<double> bth(D, 0.0);
+  for (int j = 0; j < iters; ++j) {
+    const int N = or_n_env(n0, n1, j1, j);
+    if (j == 0) or_sample_uniform(s, seed, problem, N, th.data());
+    else or_sample(seed, (uint32_t)j, problem, N, D, mu.data(), Lo.data(), th.data());
+    or_rollout(s, th.data(), N, J.data(), cl.data(), nthreads);
+    for (int n = 0; n < N; ++n) Jf[n] = (float)J[n];
+    const int k_eff = or_select(Jf.data(), cl.data(), N, K, idx.data());
+    if (k_eff > 0) {
+      const int b = idx[0];
+      if (cl[b] < bcls || (cl[b] == bcls && Jf[b] < bJf)) {
+        bcls = cl[b]; bJf = Jf[b]; bJ = J[b];
+        for (int d = 0; d < D; ++d) bth[d] = th[(size_t)b * D + d];
+      }
+      const int rc = or_refit(th.data(), N, D, idx.data(), k_eff, s->lo, s->hi, diag, mu.data(), C.data(), Lo.data());
+      if (rc != 0) return rc;
+    } else if (j == 0) {
+      return -4;  // no sample to start the normal model from
+    }
+    if (history) history[j] = bJ;
+    if (n_hist) n_hist[j] = N;
+    if (class_hist) {
+      for (int c = 0; c < 4; ++c) class_hist[4 * j + c] = 0;
+      for (int n = 0; n < N; ++n) class_hist[4 * j + cl[n]] += 1;
+    }
+  }
+  for (int d = 0; d < D; ++d) { best_theta[d] = bth[d]; mean[d] = mu[d]; }
+  for (int i = 0; i < D * D; ++i) cov[i] = C[i];
+  *best_J = bJ;
+  *best_cls = bcls;
+  return 0;
+}

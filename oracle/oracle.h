@@ -68,6 +68,11 @@ typedef struct {
   int32_t n_act, act_kind[OR_MAX_ACT], act_off[OR_MAX_ACT], act_ref_target[OR_MAX_ACT];
   double act_nom[OR_MAX_ACT][3], act_yaw[OR_MAX_ACT];
   double lo[OR_MAX_D], hi[OR_MAX_D];
+  /* initial sampling region of each action (Sec. III-B, IV-A): 0 = the box
+   * [lo, hi] of its parameters, 1 = an annulus for a move goal's (dx, dy):
+   * act_ring = (centre x, centre y, inner radius, outer radius) */
+  int32_t act_region[OR_MAX_ACT];
+  double act_ring[OR_MAX_ACT][4];
 } or_scene;
 
 typedef struct {
@@ -85,8 +90,13 @@ void or_philox_words(uint64_t seed, uint32_t iter, uint32_t problem, int N, int 
 void or_normals(uint64_t seed, uint32_t iter, uint32_t problem, int N, int D, double* z);
 void or_sample(uint64_t seed, uint32_t iter, uint32_t problem, int N, int D, const double* mean,
                const double* chol, double* theta);
-/* Uniform initial sampling inside the bounds (paper's iteration-0 rule). */
+/* Uniform initial sampling inside each parameter's region (paper's
+ * iteration-0 rule): the box [lo, hi], or area-uniform in an annulus for a
+ * move goal flagged act_region = 1. */
 void or_sample_uniform(const or_scene* s, uint64_t seed, uint32_t problem, int N, double* theta);
+/* Samples of CE iteration j under the linear schedule: n0 at j = 0 to n1 at
+ * j = j1, constant after (Sec. IV-A: 3000 -> 300 by iteration 10). */
+int or_n_env(int n0, int n1, int j1, int j);
 /* Roll out N parameter vectors; nthreads <= 0 -> hardware concurrency. */
 void or_rollout(const or_scene* s, const double* theta, int N, double* J, uint8_t* cls, int nthreads);
 /* Per-step state trace of one rollout: states[(steps) * OR_TRACE_W]. */
@@ -105,6 +115,13 @@ double or_mean_radius(double a, double b);
 int or_cem(const or_scene* s, uint64_t seed, uint32_t problem, int N, int K, int iters, int diag,
            int nthreads, double* best_theta, double* best_J, int* best_cls, double* mean,
            double* cov, double* history, double* keff_hist);
+/* The paper's CE variant (Sec. III-B, IV-A): iteration 0 draws n0 samples
+ * uniformly in the parameter regions, iteration j >= 1 draws or_n_env(j)
+ * Gaussian samples (Philox iteration j) from the refit; class_hist[4 j + c]
+ * = samples of class c in iteration j, n_hist[j] = samples drawn. */
+int or_cem_paper(const or_scene* s, uint64_t seed, uint32_t problem, int n0, int n1, int j1, int K, int iters,
+                 int diag, int nthreads, double* best_theta, double* best_J, int* best_cls, double* mean,
+                 double* cov, double* history, int* class_hist, int* n_hist);
 #ifdef __cplusplus
 }
 #endif

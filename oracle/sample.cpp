@@ -82,17 +82,31 @@ extern "C" void or_sample(uint64_t seed, uint32_t iter, uint32_t problem, int N,
     }
 }
 
-// Iteration-0 rule of Sec. III-B / IV-A: uniform inside the parameter bounds.
-// Uses the raw Philox words of iteration 0xFFFFFFFF so it never collides with
-// a Gaussian iteration.
+// Iteration-0 rule of Sec. III-B / IV-A: uniform inside each parameter's
+// region.  Uses the raw Philox words of iteration 0xFFFFFFFF so it never
+// collides with a Gaussian iteration; word d serves parameter d.
+//  * box: theta_d = lo_d + u_d (hi_d - lo_d);
+//  * annulus r <= |p - c| <= R for a move goal p = nominal + (dx, dy):
+//    uniform in area means P(|p - c| <= rho) = (rho^2 - r^2) / (R^2 - r^2), so
+//    rho = sqrt(r^2 + u_d (R^2 - r^2)) and the angle is 2 pi u_{d+1}.
 extern "C" void or_sample_uniform(const or_scene* s, uint64_t seed, uint32_t problem, int N,
                                   double* theta) {
   const int D = s->D, nc = n_calls(D);
   std::vector<uint32_t> w((size_t)N * nc * 4);
   or_philox_words(seed, 0xFFFFFFFFu, problem, N, D, w.data());
-  for (int n = 0; n < N; ++n)
-    for (int d = 0; d < D; ++d) {
-      double u = uniform_open0(w[(size_t)n * nc * 4 + d]);
-      theta[(size_t)n * D + d] = s->lo[d] + u * (s->hi[d] - s->lo[d]);
+  for (int n = 0; n < N; ++n) {
+    const uint32_t* r = w.data() + (size_t)n * nc * 4;
+    double* th = theta + (size_t)n * D;
+    for (int d = 0; d < D; ++d) th[d] = s->lo[d] + uniform_open0(r[d]) * (s->hi[d] - s->lo[d]);
+    for (int a = 0; a < s->n_act; ++a) {
+      if (s->act_region[a] != 1) continue;
+      const int o = s->act_off[a];
+      const double cx = s->act_ring[a][0], cy = s->act_ring[a][1];
+      const double ri = s->act_ring[a][2], ro = s->act_ring[a][3];
+      const double rho = std::sqrt(ri * ri + uniform_open0(r[o]) * (ro * ro - ri * ri));
+      const double phi = 2.0 * M_PI * uniform_open0(r[o + 1]);
+      th[o] = cx + rho * std::cos(phi) - s->act_nom[a][0];
+      th[o + 1] = cy + rho * std::sin(phi) - s->act_nom[a][1];
     }
+  }
 }

@@ -181,14 +181,22 @@ def _pp_boxes(rng, n=3, half=0.2, height=0.4):
 
 
 def pickplace_scene(seed: int = 0, n_actions: int = 5, T: int = 3000, dt: float = 0.002,
-                    cost_mode: str = "interp", obstacle: str = "ramp"):
+                    cost_mode: str = "interp", obstacle: str = "ramp", regions: str = "box"):
     """Pick-and-place with a ramp (or box) obstacle between two tables.
 
     Per scene: ramp slope ~ U[15, 30] deg, object friction mu ~ U[0.2, 0.4],
     three 0.4 m obstacle boxes at seeded non-overlapping poses in the
     6 x 4 m arena.  ``n_actions`` in 3..6 truncates or extends the 5-action
     skeleton (used by the 64-problem batch).
+
+    ``regions="paper"`` gives the two table approaches annulus regions around
+    their tables for uniform initial sampling (the paper's Table_1 / Table_2
+    rings, radii scaled to these 0.6 m tables and the 4 m arena: 0.65..0.9 m),
+    with the move bounds widened to contain them; the other parameters keep
+    their boxes (the Exit box is the paper's 1 x 1 m rectangle).
     """
+    if regions not in ("box", "paper"):
+        raise ValueError("regions is 'box' or 'paper'")
     if not 3 <= n_actions <= 6:
         raise ValueError("pick-place skeletons have 3..6 actions")
     rng = np.random.default_rng(seed)
@@ -235,15 +243,24 @@ def pickplace_scene(seed: int = 0, n_actions: int = 5, T: int = 3000, dt: float 
     )
     mv = lambda nom: dict(kind="move", nominal=(nom[0], nom[1], 0.0), yaw=0.0, success_ref="target")
     acts, lo, hi = [], [], []
+    ring = lambda t: dict(kind="ring", center=(t[0], t[1]), radii=(0.65, 0.9))
     # moveTo(Start, Table1)
     acts.append(mv((TABLE1[0], TABLE1[1] - 0.7)))
-    lo += [-0.6, -0.6, 5.0]; hi += [0.6, 0.6, 50.0]
+    if regions == "paper":
+        acts[-1]["region"] = ring(TABLE1)
+        lo += [-0.9, -0.6, 5.0]; hi += [0.9, 1.6, 50.0]
+    else:
+        lo += [-0.6, -0.6, 5.0]; hi += [0.6, 0.6, 50.0]
     # grasp(Cube): approach azimuth and grip-height offset
     acts.append(dict(kind="grasp", nominal=scene["obj_start"], yaw=0.0, success_ref="target"))
     lo += [-math.pi, -0.06]; hi += [math.pi, 0.06]
     # moveTo(Table1, Table2)
     acts.append(mv((0.9, 0.9)))
-    lo += [-1.3, -1.0, 5.0]; hi += [1.3, 1.0, 50.0]
+    if regions == "paper":
+        acts[-1]["region"] = ring(TABLE2)
+        lo += [-1.3, -1.0, 5.0]; hi += [1.4, 1.0, 50.0]
+    else:
+        lo += [-1.3, -1.0, 5.0]; hi += [1.3, 1.0, 50.0]
     if n_actions >= 4:  # place(Target)
         acts.append(dict(kind="place", nominal=(t2[0], t2[1], t2[4] + oh), yaw=0.0, success_ref="target"))
         lo += [-1.1, -0.3, 0.0]; hi += [0.3, 0.3, 0.5]

@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--block", type=int, default=0,
                     help="rollout threads per CTA for --rollout-only (0 = the library's choice)")
     ap.add_argument("--skip-surrogate", action="store_true", help="leave out the time-to-cost comparison")
+    ap.add_argument("--paper-ce", type=int, default=0,
+                    help="run the paper's CE variant on the ramp and box pick-place scenes over this many "
+                         "seeds and print the per-iteration success-rate and best-cost curves")
     ap.add_argument("--mlp-only", type=int, default=0,
                     help="time only the surrogate forward on this many rows (profiling driver)")
     return ap.parse_args()
@@ -502,8 +505,45 @@ def run_mlp_only(args):
     print(json.dumps(out), flush=True)
 
 
+def run_paper_ce(args):
+    """The paper's CE variant (uniform start in annulus / box regions, n_env
+    3000 -> 300 by iteration 10, N_e = 50, independent normal, 20
+    iterations) on the pick-place ramp and box scenes, one scene seed per
+    run: per-iteration success rate (class-0 share of the samples, Fig. 5),
+    the median best cost so far, and the loop's device time."""
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    out = {"paper_ce": {"n0": 3000, "n1": 300, "j1": 10, "K": 50, "iters": 20, "cov": "diag",
+                        "seeds": args.paper_ce}}
+    for obstacle in ("ramp", "box"):
+        rates, best, ms, cls = [], [], [], []
+        for seed in range(args.paper_ce):
+            sc, sk = workload.pickplace_scene(seed, obstacle=obstacle, regions="paper")
+            with P.Scene(sc, sk) as S:
+                r = S.solve_paper(seed)
+            rates.append(r["class_counts"][:, 0] / r["n_env"])
+            best.append(np.where(np.isfinite(r["history"]), r["history"], np.nan))
+            ms.append(r["elapsed_ms"])
+            cls.append(int(r["best_cls"]))
+        rates, best = np.array(rates), np.array(best)
+        out[obstacle] = {
+            "success_rate_mean": np.round(rates.mean(0), 5).tolist(),
+            "best_J_median": np.round(np.nanmedian(best, 0), 4).tolist(),
+            "final_best_class": cls,
+            "loop_ms_mean": float(np.mean(ms)),
+            "samples_per_loop": int(sum(3000 - 270 * min(j, 10) for j in range(20))),
+        }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.paper_ce:
+        run_paper_ce(args)
+        return
     if args.mlp_only:
         run_mlp_only(args)
         return

@@ -131,9 +131,11 @@ typedef struct {
   int32_t kind;         /* cem_action_kind */
   int32_t theta_offset; /* first index of the action's theta slice */
   int32_t success_ref;  /* moveTo success measured from 0: nominal, 1: nominal + offset */
-  int32_t reserved;
+  int32_t init_region;  /* initial sampling region (Sec. III-B): 0 the box of the action's
+                           bounds, 1 (moveTo only) an annulus for the goal (dx, dy) */
   float nominal[3]; /* nominal target (region centre) */
   float yaw;        /* base yaw target (planar tasks) */
+  float region[4];  /* init_region 1: annulus centre x, y (world), inner and outer radius */
 } cem_action_desc;
 
 /* Plan skeleton pi = (a_1..a_k) and the box bounds of its parameters. */
@@ -158,6 +160,14 @@ int cem_scene_destroy(cem_handle h);
  * a no-op. */
 int cem_sample(cem_handle h, const float* mean_d, const float* chol_d, uint64_t seed, uint32_t iter,
                uint32_t problem, int N, float* theta_d, void* stream);
+
+/* The initial distribution of Sec. III-B: N vectors uniform inside each
+ * parameter's region -- the box [lo, hi], or for a moveTo goal with
+ * init_region 1 the annulus r <= |p - c| <= R, area-uniform (radius
+ * sqrt(r^2 + u (R^2 - r^2)), angle 2 pi u').  Parameter d uses word d of the
+ * Philox block (n, d / 4, 0xFFFFFFFF, problem) with u = (word + 1) 2^-32;
+ * theta_d[N][D] is not clamped. */
+int cem_sample_uniform(cem_handle h, uint64_t seed, uint32_t problem, int N, float* theta_d, void* stream);
 
 /* The same Philox words the sampler draws: words_d[N][4*ceil(D/4)] (u32). */
 int cem_philox_words(cem_handle h, uint64_t seed, uint32_t iter, uint32_t problem, int N, uint32_t* words_d,
@@ -201,6 +211,9 @@ typedef struct {
    * host.  Passing the chol of a previous cem_result with its mean, cov and
    * start_iter = iterations done resumes a run exactly. */
   const float* init_chol_h;
+  /* iters x 4 values or NULL: samples of class 0..3 in each iteration
+   * (class 0 / n_env is the success rate of Fig. 5) */
+  int32_t* class_count_hist_h;
 } cem_solve_params;
 
 typedef struct {
@@ -220,6 +233,29 @@ typedef struct {
  * sample over all iterations plus the final mean/cov come back to the host.
  * Synchronous. */
 int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out);
+
+/* The paper's CE variant (Sec. III-B, IV-A): iteration 0 draws n0 samples
+ * with cem_sample_uniform, iteration j >= 1 draws n_env(j) samples from the
+ * normal model refit at j - 1 (Philox iteration j), where n_env falls
+ * linearly from n0 at j = 0 to n1 at j = j1 (rounded to nearest, halves up)
+ * and stays at n1; K = N_e elites per refit; cov_mode CEM_COV_DIAG is the
+ * paper's independent normal.  Histories as in cem_solve_params, plus the
+ * samples drawn per iteration.  Not graph-captured (the batch size
+ * changes).  Synchronous. */
+typedef struct {
+  uint64_t seed;
+  int32_t n0, n1, j1; /* the schedule; n0, n1 in 1..2^20, j1 >= 0 */
+  int32_t K, iters, cov_mode;
+  uint32_t problem;
+  int32_t reserved;
+  float* best_J_hist_h;         /* iters values or NULL */
+  int32_t* k_eff_hist_h;        /* iters values or NULL */
+  int32_t* class_count_hist_h;  /* iters x 4 values or NULL */
+  int32_t* n_env_hist_h;        /* iters values or NULL */
+} cem_paper_params;
+int cem_solve_paper(cem_handle h, const cem_paper_params* p, cem_result* out);
+/* n_env of iteration j under the schedule (n0, n1, j1) (host function). */
+int cem_n_env(int n0, int n1, int j1, int j);
 
 /* cem_solve for callers that cannot allocate device memory (no paper
  * counterpart).  Hard real-time control loops, plugins whose host owns all

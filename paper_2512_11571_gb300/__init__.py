@@ -32,6 +32,7 @@ EXPORTS = [
     "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
+    "cem_solve_paper", "cem_sample_uniform", "cem_n_env",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -88,7 +89,7 @@ class cem_scene_desc(C.Structure):
 
 class cem_action_desc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("theta_offset", C.c_int32), ("success_ref", C.c_int32),
-                ("reserved", C.c_int32), ("nominal", F3), ("yaw", C.c_float)]
+                ("init_region", C.c_int32), ("nominal", F3), ("yaw", C.c_float), ("region", C.c_float * 4)]
 
 
 class cem_skeleton_desc(C.Structure):
@@ -102,7 +103,15 @@ class cem_solve_params(C.Structure):
                 ("use_graph", C.c_int32), ("reserved", C.c_int32),
                 ("init_mean_h", C.POINTER(C.c_float)), ("init_cov_h", C.POINTER(C.c_float)),
                 ("best_J_hist_h", C.POINTER(C.c_float)), ("k_eff_hist_h", C.POINTER(C.c_int32)),
-                ("init_chol_h", C.POINTER(C.c_float))]
+                ("init_chol_h", C.POINTER(C.c_float)), ("class_count_hist_h", C.POINTER(C.c_int32))]
+
+
+class cem_paper_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("n0", C.c_int32), ("n1", C.c_int32), ("j1", C.c_int32),
+                ("K", C.c_int32), ("iters", C.c_int32), ("cov_mode", C.c_int32), ("problem", C.c_uint32),
+                ("reserved", C.c_int32),
+                ("best_J_hist_h", C.POINTER(C.c_float)), ("k_eff_hist_h", C.POINTER(C.c_int32)),
+                ("class_count_hist_h", C.POINTER(C.c_int32)), ("n_env_hist_h", C.POINTER(C.c_int32))]
 
 
 class cem_problem_params(C.Structure):
@@ -181,6 +190,10 @@ def pack_scene(scene: dict, skel: dict, T: int | None = None):
         k.action[i].success_ref = 1 if a.get("success_ref", "nominal") == "target" else 0
         _set(k.action[i].nominal, a["nominal"])
         k.action[i].yaw = a.get("yaw", 0.0)
+        reg = a.get("region")
+        if reg is not None:  # annulus of a moveTo goal for the initial sampling
+            k.action[i].init_region = 1 if reg["kind"] == "ring" else -1
+            _set(k.action[i].region, [reg["center"][0], reg["center"][1], reg["radii"][0], reg["radii"][1]])
         off += ACTION_WIDTH[a["kind"]]
     _set(k.lo, skel["lo"])
     _set(k.hi, skel["hi"])
@@ -209,6 +222,9 @@ def load(path: str = LIB_PATH):
     L.cem_rollout_trace.argtypes = [H, fp, C.c_int, C.c_int, fp, vp]
     L.cem_refit.argtypes = [H, fp, fp, u8p, C.c_int, C.c_int, C.c_int, fp, fp, fp, i32p, i32p, vp]
     L.cem_solve.argtypes = [H, C.POINTER(cem_solve_params), C.POINTER(cem_result)]
+    L.cem_solve_paper.argtypes = [H, C.POINTER(cem_paper_params), C.POINTER(cem_result)]
+    L.cem_sample_uniform.argtypes = [H, C.c_uint64, C.c_uint32, C.c_int, vp, vp]
+    L.cem_n_env.argtypes = [C.c_int] * 4
     L.cem_solve_static.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc),
                                    C.POINTER(cem_solve_params), C.POINTER(cem_result), vp]
     L.cem_set_launch.argtypes = [H, C.c_int]
@@ -317,6 +333,20 @@ def cem_solve(h, params: cem_solve_params):
     out = cem_result()
     _check(load().cem_solve(h, C.byref(params), C.byref(out)))
     return out
+
+
+def cem_solve_paper(h, params: cem_paper_params):
+    out = cem_result()
+    _check(load().cem_solve_paper(h, C.byref(params), C.byref(out)))
+    return out
+
+
+def cem_sample_uniform(h, seed, problem, N, theta, stream=None):
+    _check(load().cem_sample_uniform(h, seed, problem, N, _ptr(theta), _stream(stream)))
+
+
+def cem_n_env(n0, n1, j1, j):
+    return int(load().cem_n_env(n0, n1, j1, j))
 
 
 def cem_solve_static(scene: dict, skel: dict, params: cem_solve_params, stream=None):
@@ -712,14 +742,46 @@ class Scene:
             p.init_chol_h = L.ctypes.data_as(C.POINTER(C.c_float))
         hist = np.zeros(iters, np.float32)
         keff = np.zeros(iters, np.int32)
+        counts = np.zeros((iters, 4), np.int32)
         p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
         p.k_eff_hist_h = keff.ctypes.data_as(C.POINTER(C.c_int32))
+        p.class_count_hist_h = counts.ctypes.data_as(C.POINTER(C.c_int32))
         r = cem_solve(self.h, p)
         D = self.D
         return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                     mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
                     chol=np.array(r.chol[:D * D]).reshape(D, D),
-                    iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff)
+                    iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff,
+                    class_counts=counts)
+
+    def solve_paper(self, seed, n0=3000, n1=300, j1=10, K=50, iters=20, cov_mode="diag", problem=0):
+        """The paper's CE variant (Sec. III-B, IV-A): uniform initial samples in
+        the parameter regions, n_env falling linearly n0 -> n1 by iteration j1,
+        the independent-normal model."""
+        p = cem_paper_params()
+        p.seed, p.n0, p.n1, p.j1, p.K, p.iters = seed, n0, n1, j1, K, iters
+        p.cov_mode, p.problem = COV[cov_mode], problem
+        hist = np.zeros(iters, np.float32)
+        keff = np.zeros(iters, np.int32)
+        counts = np.zeros((iters, 4), np.int32)
+        ns = np.zeros(iters, np.int32)
+        p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
+        p.k_eff_hist_h = keff.ctypes.data_as(C.POINTER(C.c_int32))
+        p.class_count_hist_h = counts.ctypes.data_as(C.POINTER(C.c_int32))
+        p.n_env_hist_h = ns.ctypes.data_as(C.POINTER(C.c_int32))
+        r = cem_solve_paper(self.h, p)
+        D = self.D
+        return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
+                    mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                    iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff,
+                    class_counts=counts, n_env=ns)
+
+    def sample_uniform(self, seed, N, problem=0, stream=None):
+        import torch
+
+        theta = torch.empty((N, self.D), dtype=torch.float32, device="cuda")
+        cem_sample_uniform(self.h, seed, problem, N, theta, stream)
+        return theta
 
     def set_launch(self, block):
         cem_set_launch(self.h, block)

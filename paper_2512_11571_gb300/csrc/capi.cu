@@ -76,6 +76,7 @@ struct cem_ctx {
   Track* track_d = nullptr;
   float* hist_J_d = nullptr;
   int32_t* hist_keff_d = nullptr;
+  int32_t* hist_cnt_d = nullptr;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_N = -1, graph_K = -1, graph_cov = -1;
@@ -106,6 +107,13 @@ int validate(const cem_scene_desc* s, const cem_skeleton_desc* k) {
       return fail(CEM_ERR_INVALID_ARG, "planar scenes take moveTo/push actions only");
     if (!planar && a.kind == CEM_ACT_PUSH) return fail(CEM_ERR_INVALID_ARG, "pick-place takes no push action");
     if (a.theta_offset != off) return fail(CEM_ERR_INVALID_ARG, "theta slices must be contiguous and in order");
+    if (a.init_region != 0 && a.init_region != 1) return fail(CEM_ERR_INVALID_ARG, "init_region must be 0 or 1");
+    if (a.init_region == 1) {
+      if (a.kind != CEM_ACT_MOVE) return fail(CEM_ERR_INVALID_ARG, "only moveTo goals take an annulus region");
+      if (!(a.region[2] >= 0.0f && a.region[3] > a.region[2]) || !std::isfinite(a.region[0]) ||
+          !std::isfinite(a.region[1]) || !std::isfinite(a.region[3]))
+        return fail(CEM_ERR_INVALID_ARG, "annulus needs finite centre and 0 <= inner < outer radius");
+    }
     off += action_width(a.kind);
   }
   if (off != k->D) return fail(CEM_ERR_INVALID_ARG, "theta slices do not cover D");
@@ -209,6 +217,8 @@ DevScene prepare(const cem_scene_desc& s, const cem_skeleton_desc& k) {
     d.act_ref[i] = k.action[i].success_ref;
     for (int j = 0; j < 3; ++j) d.act_nom[i][j] = k.action[i].nominal[j];
     d.act_yaw[i] = k.action[i].yaw;
+    d.act_region[i] = k.action[i].init_region;
+    for (int j = 0; j < 4; ++j) d.act_ring[i][j] = k.action[i].region[j];
   }
   for (int i = 0; i < k.D; ++i) {
     d.lo[i] = k.lo[i];
@@ -245,6 +255,7 @@ void free_work(cem_ctx* h) {
   cudaFree(h->track_d);
   cudaFree(h->hist_J_d);
   cudaFree(h->hist_keff_d);
+  cudaFree(h->hist_cnt_d);
   h->theta_d = nullptr;
   h->J_d = nullptr;
   h->cls_d = nullptr;
@@ -253,6 +264,7 @@ void free_work(cem_ctx* h) {
   h->track_d = nullptr;
   h->hist_J_d = nullptr;
   h->hist_keff_d = nullptr;
+  h->hist_cnt_d = nullptr;
   h->cap_N = h->cap_K = h->cap_iters = 0;
 }
 
@@ -273,7 +285,8 @@ int ensure_work(cem_ctx* h, int N, int iters) {
       cudaMalloc(&h->keff_d, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&h->status_d, sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&h->track_d, sizeof(Track)) != cudaSuccess ||
       cudaMalloc(&h->hist_J_d, sizeof(float) * it) != cudaSuccess ||
-      cudaMalloc(&h->hist_keff_d, sizeof(int32_t) * it) != cudaSuccess) {
+      cudaMalloc(&h->hist_keff_d, sizeof(int32_t) * it) != cudaSuccess ||
+      cudaMalloc(&h->hist_cnt_d, sizeof(int32_t) * 4 * it) != cudaSuccess) {
     cudaGetLastError();
     free_work(h);
     return fail(CEM_ERR_NO_MEMORY, "cudaMalloc of the solve workspace failed");
@@ -318,6 +331,7 @@ cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N
   a.track = h->track_d;
   a.hist_J = h->hist_J_d;
   a.hist_keff = h->hist_keff_d;
+  a.hist_cnt = h->hist_cnt_d;
   a.status = h->status_d;
   return launch_refit(a, h->stream);
 }
@@ -341,6 +355,7 @@ int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b) {
   b->track = h->track_d;
   b->hist_J = h->hist_J_d;
   b->hist_keff = h->hist_keff_d;
+  b->hist_cnt = h->hist_cnt_d;
   b->stream = h->stream;
   b->ev0 = h->ev0;
   b->ev1 = h->ev1;
@@ -409,6 +424,9 @@ int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b,
   if (p->k_eff_hist_h)
     CEM_CUDA(cudaMemcpyAsync(p->k_eff_hist_h, b->hist_keff, sizeof(int32_t) * p->iters, cudaMemcpyDeviceToHost,
                              b->stream));
+  if (p->class_count_hist_h)
+    CEM_CUDA(cudaMemcpyAsync(p->class_count_hist_h, b->hist_cnt, sizeof(int32_t) * 4 * p->iters,
+                             cudaMemcpyDeviceToHost, b->stream));
   CEM_CUDA(cudaStreamSynchronize(b->stream));
   float ms = 0.0f;
   CEM_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
@@ -629,6 +647,81 @@ int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out) {
   }
   CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
   return cem::handle_read_result(h, p, &b, out);
+}
+
+int cem_n_env(int n0, int n1, int j1, int j) {
+  if (j1 <= 0) return j <= 0 ? n0 : n1;
+  if (j >= j1) return n1;
+  if (j <= 0) return n0;
+  // n0 + (n1 - n0) j / j1 = num / j1 > 0, rounded half up in integers
+  const long long num = (long long)n0 * j1 + (long long)(n1 - n0) * j;
+  return (int)((2 * num + j1) / (2LL * j1));
+}
+
+int cem_sample_uniform(cem_handle h, uint64_t seed, uint32_t problem, int N, float* theta_d, void* stream) {
+  g_err.clear();
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (N < 0 || N > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "N must be in 0..2^20");
+  if (N == 0) return CEM_OK;
+  if (!is_device_ptr(theta_d)) return fail(CEM_ERR_INVALID_ARG, "theta must be a device pointer");
+  cudaError_t e = launch_sample_uniform(h->scene_d, seed, problem, N, h->skel.D, theta_d, (cudaStream_t)stream);
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_sample_uniform");
+}
+
+int cem_solve_paper(cem_handle h, const cem_paper_params* p, cem_result* out) {
+  g_err.clear();
+  if (!h || !p || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  if (p->n0 < 1 || p->n0 > CEM_MAX_N || p->n1 < 1 || p->n1 > CEM_MAX_N || p->j1 < 0)
+    return fail(CEM_ERR_UNSUPPORTED, "n0, n1 must be in 1..2^20 and j1 >= 0");
+  if (p->K < 1 || p->K > CEM_MAX_K) return fail(CEM_ERR_UNSUPPORTED, "K must be in 1..4096");
+  if (p->iters < 1 || p->iters > 100000) return fail(CEM_ERR_UNSUPPORTED, "iters must be in 1..1e5");
+  if (p->cov_mode != CEM_COV_FULL && p->cov_mode != CEM_COV_DIAG) return fail(CEM_ERR_INVALID_ARG, "unknown cov mode");
+  const int nmax = p->n0 > p->n1 ? p->n0 : p->n1;
+  cem_solve_params q;
+  std::memset(&q, 0, sizeof(q));
+  q.seed = p->seed;
+  q.N = nmax;
+  q.K = p->K;
+  q.iters = p->iters;
+  q.cov_mode = p->cov_mode;
+  q.problem = p->problem;
+  q.best_J_hist_h = p->best_J_hist_h;
+  q.k_eff_hist_h = p->k_eff_hist_h;
+  q.class_count_hist_h = p->class_count_hist_h;
+  SolveBuffers b;
+  int rc = cem::handle_solve_buffers(h, nmax, p->iters, &b);
+  if (rc != CEM_OK) return rc;
+  // loop state reset; iteration 0 does not read the Gaussian (its samples are uniform)
+  rc = cem::handle_init_distribution(h, &q, &b);
+  if (rc != CEM_OK) return rc;
+  const int D = h->skel.D;
+  CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
+  for (int j = 0; j < p->iters; ++j) {
+    const int N = cem_n_env(p->n0, p->n1, p->j1, j);
+    if (p->n_env_hist_h) p->n_env_hist_h[j] = N;
+    cudaError_t e = j == 0 ? launch_sample_uniform(h->scene_d, p->seed, p->problem, N, D, h->theta_d, h->stream)
+                           : launch_sample(h->mean_d, h->chol_d, p->seed, &h->track_d->iter, 0, p->problem, N, D,
+                                           h->theta_d, h->stream);
+    if (e == cudaSuccess)
+      e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->tpr,
+                         h->stream);
+    if (e == cudaSuccess) {
+      RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, p->K, p->cov_mode);
+      a.mean = h->mean_d;
+      a.cov = h->cov_d;
+      a.chol = h->chol_d;
+      a.k_eff = h->keff_d;
+      a.track = h->track_d;
+      a.hist_J = h->hist_J_d;
+      a.hist_keff = h->hist_keff_d;
+      a.hist_cnt = h->hist_cnt_d;
+      a.status = h->status_d;
+      e = launch_refit(a, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "paper CE iteration");
+  }
+  CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
+  return cem::handle_read_result(h, &q, &b, out);
 }
 
 int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {

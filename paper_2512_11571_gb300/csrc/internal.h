@@ -38,7 +38,9 @@ struct DevScene {
   float obj_cap;  // mu dt (per unit normal force)
   // skeleton
   int32_t act_kind[CEM_MAX_ACTIONS], act_off[CEM_MAX_ACTIONS], act_ref[CEM_MAX_ACTIONS];
+  int32_t act_region[CEM_MAX_ACTIONS];  // initial sampling region: 0 box, 1 annulus
   float act_nom[CEM_MAX_ACTIONS][3], act_yaw[CEM_MAX_ACTIONS];
+  float act_ring[CEM_MAX_ACTIONS][4];   // annulus centre x, y, inner, outer radius
   float lo[CEM_MAX_D], hi[CEM_MAX_D];
   // geometry
   int32_t geom_nslab[CEM_MAX_GEOMS], geom_flags[CEM_MAX_GEOMS];  // bit0 base, bit1 object
@@ -89,7 +91,8 @@ struct RefitArgs {
   Track* track;
   float* hist_J;
   int32_t* hist_keff;
-  int32_t* status;  // set to CEM_ERR_NOT_PD when the covariance stays indefinite
+  int32_t* hist_cnt;  // [hist_len][4] samples per class and iteration (may be null)
+  int32_t* status;    // set to CEM_ERR_NOT_PD when the covariance stays indefinite
 };
 
 // kernel launchers (stream-ordered, no synchronisation)
@@ -97,6 +100,9 @@ cudaError_t launch_sample(const float* mean, const float* chol, uint64_t seed, c
                           uint32_t iter, uint32_t problem, int N, int D, float* theta, cudaStream_t st);
 cudaError_t launch_philox_words(uint64_t seed, uint32_t iter, uint32_t problem, int N, int D, uint32_t* words,
                                 cudaStream_t st);
+// uniform initial sampling inside the regions of the scene's skeleton
+cudaError_t launch_sample_uniform(const DevScene* s_d, uint64_t seed, uint32_t problem, int N, int D, float* theta,
+                                  cudaStream_t st);
 // block = threads per CTA; tpr = lanes per rollout (1, 8 or 32; used for
 // pick-and-place scenes, the other kinds always run one lane per rollout)
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
@@ -141,6 +147,7 @@ struct SolveBuffers {
   Track* track;
   float* hist_J;
   int32_t* hist_keff;
+  int32_t* hist_cnt;
   cudaStream_t stream;
   cudaEvent_t ev0, ev1;
   const DevScene* scene;

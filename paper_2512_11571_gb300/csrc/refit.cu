@@ -251,6 +251,8 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
       if (h >= 0 && h < t->hist_len) {
         if (a.hist_J) a.hist_J[h] = t->best_J;
         if (a.hist_keff) a.hist_keff[h] = keff;
+        if (a.hist_cnt)
+          for (int c = 0; c < 4; ++c) a.hist_cnt[4 * h + c] = cnt[c];
       }
       t->iter += 1;
     }

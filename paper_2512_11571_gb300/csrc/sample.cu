@@ -100,6 +100,62 @@ __global__ void philox_words_kernel(uint64_t seed, uint32_t iter, uint32_t probl
   o[3] = r[3];
 }
 
+// Initial distribution of Sec. III-B: uniform inside each parameter's
+// region.  Parameter d takes word d of the Philox block (n, d / 4,
+// 0xFFFFFFFF, problem); a box parameter is lo + u (hi - lo), an annulus goal
+// (dx, dy) of a moveTo is the area-uniform point c + rho (cos, sin)(2 pi u')
+// with rho = sqrt(r^2 + u (R^2 - r^2)), less the action's nominal target.
+__global__ void __launch_bounds__(128) sample_uniform_kernel(const DevScene* __restrict__ s, uint64_t seed,
+                                                             uint32_t problem, int N, int D,
+                                                             float* __restrict__ theta) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  float u[20];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    if (4 * c < D) {
+      uint32_t r[4];
+      philox4x32_10((uint32_t)n, (uint32_t)c, 0xFFFFFFFFu, problem, k0, k1, r);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) u[4 * c + p] = u01(r[p]);
+    } else {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) u[4 * c + p] = 0.0f;
+    }
+  }
+  float th[CEM_MAX_D];
+#pragma unroll
+  for (int d = 0; d < CEM_MAX_D; ++d) th[d] = d < D ? fmaf(u[d], s->hi[d] - s->lo[d], s->lo[d]) : 0.0f;
+  for (int a = 0; a < s->n_act; ++a) {
+    if (s->act_region[a] != 1) continue;
+    const int o = s->act_off[a];
+    const float ri = s->act_ring[a][2], ro = s->act_ring[a][3];
+    float uo = 0.0f, uo1 = 0.0f;
+#pragma unroll
+    for (int d = 0; d < CEM_MAX_D - 1; ++d)
+      if (d == o) {
+        uo = u[d];
+        uo1 = u[d + 1];
+      }
+    const float rho = sqrtf(fmaf(uo, ro * ro - ri * ri, ri * ri));
+    float sn, cs;
+    sincospif(2.0f * uo1, &sn, &cs);
+    const float px = fmaf(rho, cs, s->act_ring[a][0]) - s->act_nom[a][0];
+    const float py = fmaf(rho, sn, s->act_ring[a][1]) - s->act_nom[a][1];
+#pragma unroll
+    for (int d = 0; d < CEM_MAX_D - 1; ++d)
+      if (d == o) {
+        th[d] = px;
+        th[d + 1] = py;
+      }
+  }
+  float* out = theta + (size_t)n * D;
+#pragma unroll
+  for (int d = 0; d < CEM_MAX_D; ++d)
+    if (d < D) out[d] = th[d];
+}
+
 // batched sampling: blockIdx.y = problem, samples in x; the same per-sample
 // arithmetic as sample_kernel
 __global__ void __launch_bounds__(128) sample_batch_kernel(const BatchProblem* __restrict__ probs,
@@ -167,6 +223,14 @@ cudaError_t launch_sample(const float* mean, const float* chol, uint64_t seed, c
   if (N <= 0) return cudaSuccess;
   const int bs = 128;
   sample_kernel<<<(N + bs - 1) / bs, bs, 0, st>>>(mean, chol, seed, iter_ptr, iter, problem, N, D, theta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_uniform(const DevScene* s_d, uint64_t seed, uint32_t problem, int N, int D, float* theta,
+                                  cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const int bs = 128;
+  sample_uniform_kernel<<<(N + bs - 1) / bs, bs, 0, st>>>(s_d, seed, problem, N, D, theta);
   return cudaGetLastError();
 }
 

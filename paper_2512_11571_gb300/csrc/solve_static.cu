@@ -47,7 +47,7 @@ __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // byte offsets of the regions inside g_scratch
 struct Layout {
-  size_t scene, track, status, keff, mean, cov, chol, hist_J, hist_keff, J, cls, theta, end;
+  size_t scene, track, status, keff, mean, cov, chol, hist_J, hist_keff, hist_cnt, J, cls, theta, end;
 };
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -73,6 +73,8 @@ Layout layout(int N, int D) {
   o = up256(o + sizeof(float) * kMaxIters);
   L.hist_keff = o;
   o = up256(o + sizeof(int32_t) * kMaxIters);
+  L.hist_cnt = o;
+  o = up256(o + sizeof(int32_t) * 4 * kMaxIters);
   L.J = o;
   o = up256(o + sizeof(float) * (size_t)N);
   L.cls = o;
@@ -144,6 +146,7 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   float* chol_d = reinterpret_cast<float*>(base + L.chol);
   float* hist_J_d = reinterpret_cast<float*>(base + L.hist_J);
   int32_t* hist_keff_d = reinterpret_cast<int32_t*>(base + L.hist_keff);
+  int32_t* hist_cnt_d = reinterpret_cast<int32_t*>(base + L.hist_cnt);
   float* J_d = reinterpret_cast<float*>(base + L.J);
   uint8_t* cls_d = reinterpret_cast<uint8_t*>(base + L.cls);
   float* theta_d = reinterpret_cast<float*>(base + L.theta);
@@ -212,6 +215,7 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   a.track = track_d;
   a.hist_J = hist_J_d;
   a.hist_keff = hist_keff_d;
+  a.hist_cnt = hist_cnt_d;
   a.status = status_d;
   const int block = default_rollout_block(p->N);
   for (int j = 0; j < p->iters; ++j) {
@@ -229,6 +233,9 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
     STATIC_CUDA(cudaMemcpyAsync(p->best_J_hist_h, hist_J_d, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, st));
   if (p->k_eff_hist_h)
     STATIC_CUDA(cudaMemcpyAsync(p->k_eff_hist_h, hist_keff_d, sizeof(int32_t) * p->iters, cudaMemcpyDeviceToHost, st));
+  if (p->class_count_hist_h)
+    STATIC_CUDA(cudaMemcpyAsync(p->class_count_hist_h, hist_cnt_d, sizeof(int32_t) * 4 * p->iters,
+                                cudaMemcpyDeviceToHost, st));
   STATIC_CUDA(cudaStreamSynchronize(st));
   out->elapsed_ms = 0.0f;
   out->D = D;

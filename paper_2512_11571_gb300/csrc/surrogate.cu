@@ -1060,6 +1060,7 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
   a.track = b.track;
   a.hist_J = b.hist_J;
   a.hist_keff = b.hist_keff;
+  a.hist_cnt = b.hist_cnt;
   a.status = b.status;
   SUR_CUDA(cudaEventRecord(b.ev0, st));
   for (int j = 0; j < p->iters; ++j) {

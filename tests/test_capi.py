@@ -69,7 +69,8 @@ def _c_offsets(struct_name, fields, tmp_path):
 
 
 @pytest.mark.parametrize("name", ["cem_slab", "cem_geom", "cem_scene_desc", "cem_action_desc",
-                                  "cem_skeleton_desc", "cem_solve_params", "cem_result", "cem_problem_params"])
+                                  "cem_skeleton_desc", "cem_solve_params", "cem_result", "cem_problem_params",
+                                  "cem_paper_params"])
 def test_struct_layout_matches_header(pkg, name, tmp_path):
     cls = getattr(pkg, name)
     fields = [f[0] for f in cls._fields_]
@@ -125,6 +126,33 @@ def test_validation_rejects_bad_descriptors(pkg):
     assert L.cem_scene_destroy(None) == 0
     assert L.cem_set_threads_per_rollout(None, 8) == -1
     assert L.cem_get_launch(None, 1, None, None) == -1
+    assert L.cem_solve_paper(None, None, None) == -1
+    assert L.cem_sample_uniform(None, 1, 0, 4, None, None) == -1
+    # initial-sampling regions: an annulus only on a moveTo goal, 0 <= inner < outer
+    k6 = pkg.cem_skeleton_desc.from_buffer_copy(k)
+    k6.action[0].init_region = 2
+    assert L.cem_scene_create(C.byref(s), C.byref(k6), C.byref(h)) == -1
+    k7 = pkg.cem_skeleton_desc.from_buffer_copy(k)
+    k7.action[0].init_region = 1
+    k7.action[0].region[:] = [0.0, 0.0, 0.5, 0.5]
+    assert L.cem_scene_create(C.byref(s), C.byref(k7), C.byref(h)) == -1
+    assert b"annulus" in L.cem_last_error()
+
+
+def test_n_env_schedule_matches_oracle(pkg):
+    """The library's integer schedule against the oracle's (Sec. IV-A)."""
+    import oracle
+
+    for n0, n1, j1 in ((3000, 300, 10), (10, 0 + 1, 4), (100, 400, 3), (777, 65, 7), (5, 5, 2), (500, 50, 0)):
+        for j in range(14):
+            assert pkg.cem_n_env(n0, n1, j1, j) == oracle.n_env(n0, n1, j1, j), (n0, n1, j1, j)
+
+
+def test_paper_regions_pack(pkg):
+    sc, sk = workload.pickplace_scene(0, regions="paper")
+    s, k = pkg.pack_scene(sc, sk)
+    assert [k.action[i].init_region for i in range(5)] == [1, 0, 1, 0, 0]
+    assert list(k.action[0].region) == pytest.approx([-1.6, 0.9, 0.65, 0.9])
 
 
 def test_pick_place_descriptor_packs(pkg):

@@ -347,6 +347,12 @@ int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float
  * 1 the tiled mma.sync GEMM, 2 tcgen05 (CEM_ERR_UNSUPPORTED unless width 256
  * and depth 4).  Training always uses the tiled GEMM. */
 int cem_surrogate_set_forward_path(cem_surrogate_handle s, int path);
+/* Failure-detection test hook: while on != 0, tcgen05 forwards leave their
+ * first weight-copy barrier without its arrival, so every CTA's first
+ * pipeline wait runs out after 1 s with nothing in flight; the CTA then
+ * frees its TMEM, writes NaN scores and sets status 1.  The context stays
+ * usable; switch it off (0) for normal forwards. */
+int cem_surrogate_test_expire_wait(cem_surrogate_handle s, int on);
 /* The path inference takes now: 1 tiled GEMM, 2 tcgen05; -1 for NULL. */
 int cem_surrogate_forward_path(cem_surrogate_handle s);
 /* Synchronises, writes and clears the tcgen05 forward's status word: 0, or

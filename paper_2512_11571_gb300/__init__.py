@@ -32,7 +32,7 @@ EXPORTS = [
     "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
-    "cem_solve_paper", "cem_sample_uniform", "cem_n_env",
+    "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -251,6 +251,7 @@ def load(path: str = LIB_PATH):
     L.cem_surrogate_forward.argtypes = [H, vp, C.c_int, vp, vp]
     L.cem_surrogate_set_forward_path.argtypes = [H, C.c_int]
     L.cem_surrogate_forward_path.argtypes = [H]
+    L.cem_surrogate_test_expire_wait.argtypes = [H, C.c_int]
     L.cem_surrogate_status.argtypes = [H, C.POINTER(C.c_int)]
     L.cem_surrogate_gradient.argtypes = [H, vp, vp, C.c_int, fptr, fptr]
     L.cem_surrogate_train.argtypes = [H, vp, vp, C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
@@ -627,6 +628,10 @@ class Surrogate:
     @property
     def forward_path(self):
         return cem_surrogate_forward_path(self.h)
+
+    def test_expire_wait(self, on):
+        """Failure-detection hook: make the tcgen05 forward's first wait run out."""
+        _check(load().cem_surrogate_test_expire_wait(self.h, int(bool(on))))
 
     def status(self):
         """Reads and clears the fused kernel's status word (0 = no wait expired)."""

@@ -174,6 +174,7 @@ struct MlpTcArgs {
   const float* norm;     // [mu, sigma]
   float* y;              // [M] scores
   int* status;           // set non-zero if a bounded wait expired
+  int expire_test;       // failure-detection test: skip the first weight copy so its wait runs out
 };
 bool mlp_tc_supported(int in_dim, int width, int depth);
 size_t mlp_tc_pack_bytes();

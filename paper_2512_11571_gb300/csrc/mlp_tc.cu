@@ -197,7 +197,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (tid == 0) bulk_load(sW, wpack + w_offset(0), operand_bytes(WIDTH, IN), bar_w);
+  // (the failure-detection test leaves the barrier without its arrival, so
+  // nothing completes it and the first wait runs out with nothing in flight)
+  if (tid == 0 && !a.expire_test) bulk_load(sW, wpack + w_offset(0), operand_bytes(WIDTH, IN), bar_w);
   // input tile: 128 rows of 48 BF16 features, 16-byte pieces into the
   // canonical layout; rows past M are zero
   for (int i = tid; i < TM * (IN / 8); i += THREADS) {

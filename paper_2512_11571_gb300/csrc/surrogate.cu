@@ -501,6 +501,7 @@ struct cem_surrogate_ctx {
   int* tc_status = nullptr;
   bool tc_pack_valid = false;
   int fwd_path = 0;  // 0 automatic, 1 tiled GEMM, 2 tcgen05
+  int expire_test = 0;
 };
 
 namespace {
@@ -612,6 +613,7 @@ cudaError_t infer_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st) {
   a.norm = s->norm;
   a.y = y;
   a.status = s->tc_status;
+  a.expire_test = s->expire_test;
   return mlp_tc_forward(a, st);
 }
 
@@ -832,6 +834,12 @@ int cem_surrogate_set_forward_path(cem_surrogate_handle s, int path) {
   if (path == 2 && !mlp_tc_supported(s->in_dim, s->width, s->depth))
     return fail(CEM_ERR_UNSUPPORTED, "the tcgen05 forward needs width 256 and depth 4");
   s->fwd_path = path;
+  return CEM_OK;
+}
+
+int cem_surrogate_test_expire_wait(cem_surrogate_handle s, int on) {
+  if (!s) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  s->expire_test = on ? 1 : 0;
   return CEM_OK;
 }
 

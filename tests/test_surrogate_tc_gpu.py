@@ -8,6 +8,8 @@ FP32 sums differs, which can flip the BF16 rounding of an activation.  The
 bars are those of the oracle comparison of the tiled path: the median error
 against the BF16-emulating oracle at FP32 summation level, the maximum at
 BF16 level."""
+import time
+
 import numpy as np
 import pytest
 
@@ -134,3 +136,35 @@ def test_path_selection(P):
         assert S.forward_path == 1
         S.set_forward_path(0)
         assert S.forward_path == 2
+
+
+def test_expired_wait_reports_and_recovers(P):
+    """Failure detection without a GPU fault: the test hook leaves the first
+    weight copy's barrier without its arrival, so each CTA's first pipeline
+    wait runs out after 1 s with nothing in flight.  The rows come back NaN,
+    the status reads 1, the screened loop reports CEM_ERR_TIMEOUT, and the
+    next forward on the same context is normal and bit-identical."""
+    params = mlp.init_params(48, 256, 4, seed=3)
+    X = np.random.default_rng(3).uniform(-1, 1, (200, 48))
+    with P.Surrogate(256, 4) as S:
+        S.set_params(mlp.flatten(params), np.array([0.0, 1.0]))
+        x = dev(X)
+        good = S.forward(x).cpu().numpy()
+        assert S.status() == 0
+        S.test_expire_wait(True)
+        t0 = time.time()
+        bad = S.forward(x).cpu().numpy()
+        elapsed = time.time() - t0
+        assert S.status() == 1
+        assert np.all(np.isnan(bad))
+        assert 0.9 < elapsed < 30.0
+        sc, sk, _ = workload.config(2, seed=1, T=200)
+        with P.Scene(sc, sk) as Sc:
+            with pytest.raises(P.CemError) as err:
+                Sc.solve_screened(S, workload.scene_features(sc), seed=1, N=128, K=16, iters=1, n_pool=256)
+            assert err.value.code == -3
+        assert S.status() == 0  # the screened loop read and cleared it
+        S.test_expire_wait(False)
+        again = S.forward(x).cpu().numpy()
+        assert S.status() == 0
+    assert np.array_equal(again, good)

@@ -184,6 +184,14 @@ def lib():
             L.or_cem.argtypes = [sp, C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                  dp, dp, C.POINTER(C.c_int), dp, dp, dp, dp]
             L.or_cem.restype = C.c_int
+            L.or_dr_factors.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_double, C.c_double,
+                                        dp, dp]
+            L.or_rollout_dr.argtypes = [sp, dp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_uint64,
+                                        C.c_uint32, C.c_uint32, dp, u8p, C.c_int]
+            L.or_cem_dr.argtypes = [sp, C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, C.c_double, C.c_uint64, C.c_int, dp, dp, C.POINTER(C.c_int),
+                                    dp, dp, dp]
+            L.or_cem_dr.restype = C.c_int
             L.or_n_env.argtypes = [C.c_int] * 4
             L.or_n_env.restype = C.c_int
             L.or_cem_paper.argtypes = [sp, C.c_uint64, C.c_uint32] + [C.c_int] * 7 + [
@@ -337,3 +345,39 @@ def cem_paper(scene, skel, seed, n0=3000, n1=300, j1=10, K=50, iters=20, problem
         raise RuntimeError(f"oracle CE loop failed: {rc}")
     return dict(best_theta=bt, best_J=bJ.value, best_cls=bc.value, mean=mean, cov=cov, history=hist,
                 class_counts=counts, n_env=ns)
+
+
+def dr_factors(seed, it, problem, M, dmu, dm):
+    """Friction and mass scales of the M randomised environments of iteration it."""
+    smu, sm = np.zeros(M), np.zeros(M)
+    lib().or_dr_factors(seed, it, problem, M, dmu, dm, _p(smu, C.c_double), _p(sm, C.c_double))
+    return smu, sm
+
+
+def rollout_dr(scene, skel, theta, M, dmu, dm, seed, it=0, problem=0, T=None, nthreads=0):
+    """Mean cost and worst class of each sample over M randomised environments."""
+    s = pack(scene, skel, T)
+    th = np.ascontiguousarray(theta, np.float64).reshape(-1, s.D)
+    N = th.shape[0]
+    J = np.zeros(N, np.float64)
+    cls = np.zeros(N, np.uint8)
+    lib().or_rollout_dr(C.byref(s), _p(th, C.c_double), N, M, dmu, dm, seed, it, problem, _p(J, C.c_double),
+                        _p(cls, C.c_uint8), nthreads)
+    return J, cls
+
+
+def cem_dr(scene, skel, seed, N, K, iters, M, dmu, dm, dr_seed, problem=0, diag=False, nthreads=0):
+    s = pack(scene, skel)
+    D = s.D
+    bt = np.zeros(D)
+    bJ = C.c_double()
+    bc = C.c_int()
+    mean = np.zeros(D)
+    cov = np.zeros((D, D))
+    hist = np.zeros(iters)
+    rc = lib().or_cem_dr(C.byref(s), seed, problem, N, K, iters, int(diag), M, dmu, dm, dr_seed, nthreads,
+                         _p(bt, C.c_double), C.byref(bJ), C.byref(bc), _p(mean, C.c_double),
+                         _p(cov, C.c_double), _p(hist, C.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle CE loop failed: {rc}")
+    return dict(best_theta=bt, best_J=bJ.value, best_cls=bc.value, mean=mean, cov=cov, history=hist)

@@ -215,3 +215,48 @@ extern "C" int or_cem_paper(const or_scene* s, uint64_t seed, uint32_t problem, 
   *best_cls = bcls;
   return 0;
 }
+
+// Algorithm 1 with domain-randomised evaluation: iteration j scores every
+// sample by its mean cost (and worst class) over the M environments of
+// iteration j; sampling, selection and refit are those of or_cem.
+extern "C" int or_cem_dr(const or_scene* s, uint64_t seed, uint32_t problem, int N, int K, int iters, int diag,
+                         int M, double dmu, double dm, uint64_t dr_seed, int nthreads, double* best_theta,
+                         double* best_J, int* best_cls, double* mean, double* cov, double* history) {
+  const int D = s->D;
+  std::vector<double> mu(D), C((size_t)D * D, 0.0), Lo((size_t)D * D, 0.0);
+  for (int d = 0; d < D; ++d) {
+    mu[d] = 0.5 * (s->lo[d] + s->hi[d]);
+    const double sd = 0.25 * (s->hi[d] - s->lo[d]);
+    C[d * D + d] = sd * sd;
+    Lo[d * D + d] = sd;
+  }
+  std::vector<double> th((size_t)N * D), J(N);
+  std::vector<uint8_t> cl(N);
+  std::vector<float> Jf(N);
+  std::vector<int32_t> idx(std::max(K, 1));
+  int bcls = 4;
+  float bJf = INFINITY;
+  double bJ = INFINITY;
+  std::vector<double> bth(D, 0.0);
+  for (int j = 0; j < iters; ++j) {
+    or_sample(seed, (uint32_t)j, problem, N, D, mu.data(), Lo.data(), th.data());
+    or_rollout_dr(s, th.data(), N, M, dmu, dm, dr_seed, (uint32_t)j, problem, J.data(), cl.data(), nthreads);
+    for (int n = 0; n < N; ++n) Jf[n] = (float)J[n];
+    const int k_eff = or_select(Jf.data(), cl.data(), N, K, idx.data());
+    if (k_eff > 0) {
+      const int b = idx[0];
+      if (cl[b] < bcls || (cl[b] == bcls && Jf[b] < bJf)) {
+        bcls = cl[b]; bJf = Jf[b]; bJ = J[b];
+        for (int d = 0; d < D; ++d) bth[d] = th[(size_t)b * D + d];
+      }
+      const int rc = or_refit(th.data(), N, D, idx.data(), k_eff, s->lo, s->hi, diag, mu.data(), C.data(), Lo.data());
+      if (rc != 0) return rc;
+    }
+    if (history) history[j] = bJ;
+  }
+  for (int d = 0; d < D; ++d) { best_theta[d] = bth[d]; mean[d] = mu[d]; }
+  for (int i = 0; i < D * D; ++i) cov[i] = C[i];
+  *best_J = bJ;
+  *best_cls = bcls;
+  return 0;
+}

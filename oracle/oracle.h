@@ -99,6 +99,13 @@ void or_sample_uniform(const or_scene* s, uint64_t seed, uint32_t problem, int N
 int or_n_env(int n0, int n1, int j1, int j);
 /* Roll out N parameter vectors; nthreads <= 0 -> hardware concurrency. */
 void or_rollout(const or_scene* s, const double* theta, int N, double* J, uint8_t* cls, int nthreads);
+/* Domain randomisation factors of CE iteration iter: friction scale smu[M]
+ * and manipulated-body mass scale sm[M] (Philox block (m, 256, iter, problem)). */
+void or_dr_factors(uint64_t seed, uint32_t iter, uint32_t problem, int M, double dmu, double dm, double* smu,
+                   double* sm);
+/* Rollouts under M randomised environments: J = mean, class = worst. */
+void or_rollout_dr(const or_scene* s, const double* theta, int N, int M, double dmu, double dm, uint64_t seed,
+                   uint32_t iter, uint32_t problem, double* J, uint8_t* cls, int nthreads);
 /* Per-step state trace of one rollout: states[(steps) * OR_TRACE_W]. */
 void or_rollout_trace(const or_scene* s, const double* theta, int steps, double* states);
 /* Flop tally of one rollout (added into *ops); returns the step count. */
@@ -115,6 +122,11 @@ double or_mean_radius(double a, double b);
 int or_cem(const or_scene* s, uint64_t seed, uint32_t problem, int N, int K, int iters, int diag,
            int nthreads, double* best_theta, double* best_J, int* best_cls, double* mean,
            double* cov, double* history, double* keff_hist);
+/* or_cem with every iteration's rollouts domain-randomised (or_rollout_dr
+ * with the loop's iteration index). */
+int or_cem_dr(const or_scene* s, uint64_t seed, uint32_t problem, int N, int K, int iters, int diag, int M,
+              double dmu, double dm, uint64_t dr_seed, int nthreads, double* best_theta, double* best_J,
+              int* best_cls, double* mean, double* cov, double* history);
 /* The paper's CE variant (Sec. III-B, IV-A): iteration 0 draws n0 samples
  * uniformly in the parameter regions, iteration j >= 1 draws or_n_env(j)
  * Gaussian samples (Philox iteration j) from the refit; class_hist[4 j + c]

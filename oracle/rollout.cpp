@@ -667,3 +667,55 @@ extern "C" int or_rollout_count(const or_scene* s, const double* theta, or_ops* 
   ops->transc += g_ops.transc;
   return s->kind == OR_QUAD ? 1 : s->T;
 }
+
+// Domain randomisation (Sec. IV-C: plans made robust to bounded uncertainty
+// in friction or mass).  Environment m of CE iteration `iter` scales every
+// friction coefficient by s_mu = 1 + dmu (2 u0 - 1) and the manipulated
+// body's mass by s_m = 1 + dm (2 u1 - 1), with (u0, u1) from the first two
+// words of the Philox block (m, 256, iter, problem) under key `seed` and
+// u = (word + 1) 2^-32.  All samples of an iteration share the environments.
+extern "C" void or_dr_factors(uint64_t seed, uint32_t iter, uint32_t problem, int M, double dmu, double dm,
+                              double* smu, double* sm) {
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int m = 0; m < M; ++m) {
+    const uint32_t ctr[4] = {(uint32_t)m, 256u, iter, problem};
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    const double u0 = ((double)r[0] + 1.0) * 0x1p-32, u1 = ((double)r[1] + 1.0) * 0x1p-32;
+    smu[m] = 1.0 + dmu * (2.0 * u0 - 1.0);
+    sm[m] = 1.0 + dm * (2.0 * u1 - 1.0);
+  }
+}
+
+// Every sample in each of the M environments: J = mean over environments,
+// class = the worst (largest) class over environments, so a plan counts as
+// feasible only if it succeeds in all of them.
+extern "C" void or_rollout_dr(const or_scene* s, const double* theta, int N, int M, double dmu, double dm,
+                              uint64_t seed, uint32_t iter, uint32_t problem, double* J, uint8_t* cls,
+                              int nthreads) {
+  std::vector<double> smu(M), sm(M), Jm(N);
+  std::vector<uint8_t> cm(N);
+  or_dr_factors(seed, iter, problem, M, dmu, dm, smu.data(), sm.data());
+  for (int n = 0; n < N; ++n) {
+    J[n] = 0.0;
+    cls[n] = 0;
+  }
+  for (int m = 0; m < M; ++m) {
+    or_scene e = *s;
+    e.base_mu *= smu[m];
+    e.block_mu *= smu[m];
+    e.contact_mu *= smu[m];
+    e.obj_mu *= smu[m];
+    e.block_mass *= sm[m];
+    e.obj_mass *= sm[m];
+    or_rollout(&e, theta, N, Jm.data(), cm.data(), nthreads);
+    for (int n = 0; n < N; ++n) {
+      J[n] += Jm[n];
+      cls[n] = std::max(cls[n], cm[n]);
+    }
+  }
+  for (int n = 0; n < N; ++n) {
+    J[n] /= (double)M;
+    if (!std::isfinite(J[n])) cls[n] = 3;
+  }
+}

@@ -540,6 +540,10 @@ def cem_surrogate_set_forward_path(s, path):
     _check(load().cem_surrogate_set_forward_path(s, int(path)))
 
 
+def cem_surrogate_test_expire_wait(s, on):
+    _check(load().cem_surrogate_test_expire_wait(s, int(bool(on))))
+
+
 def cem_surrogate_forward_path(s):
     return int(load().cem_surrogate_forward_path(s))
 
@@ -631,7 +635,7 @@ class Surrogate:
 
     def test_expire_wait(self, on):
         """Failure-detection hook: make the tcgen05 forward's first wait run out."""
-        _check(load().cem_surrogate_test_expire_wait(self.h, int(bool(on))))
+        cem_surrogate_test_expire_wait(self.h, on)
 
     def status(self):
         """Reads and clears the fused kernel's status word (0 = no wait expired)."""

@@ -394,6 +394,22 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
 /* Threads per block of the rollout kernel: 0 (automatic), 8, 16 or a
  * multiple of 32 up to 256. */
 int cem_set_launch(cem_handle h, int block_threads);
+/* Domain randomisation (Sec. IV-C: plans robust to bounded uncertainty in
+ * friction or mass).  Every sample is rolled out in M environments (M = 1,
+ * 2, 4, 8, 16 or 32): environment m scales every friction coefficient by
+ * 1 + delta_mu (2u - 1) and the manipulated body's (block, object) mass by
+ * 1 + delta_mass (2u' - 1), with u, u' = (word + 1) 2^-32 from the first two
+ * words of the Philox block (m, 256, iteration, problem) under `seed`.  All
+ * samples of an iteration share the M environments; the CE loops (cem_solve,
+ * cem_solve_paper, cem_solve_screened) draw fresh ones each iteration (their
+ * iteration and problem id), cem_rollout_batch uses iteration 0 and
+ * problem 0.  A sample's cost is its mean over the environments and its class
+ * the worst one (feasible only if feasible everywhere).  The M environments
+ * of a sample run on M adjacent lanes (one lane each, whatever the lanes per
+ * rollout setting) and are combined by warp shuffles.  M = 1 with both
+ * spreads 0 switches it off.  Spreads in [0, 1).  Not applied to batches,
+ * traces, the autotuner or cem_solve_static. */
+int cem_set_randomization(cem_handle h, int M, float delta_mu, float delta_mass, uint64_t seed);
 /* Lanes per rollout for pick-and-place scenes: 1, 8 or 32 (other scene
  * kinds always take one lane; the trace always one).  A group of G lanes
  * holds one rollout's state, splits the per-geometry contact queries and

@@ -33,6 +33,7 @@ EXPORTS = [
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
     "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
+    "cem_set_randomization",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -225,6 +226,7 @@ def load(path: str = LIB_PATH):
     L.cem_solve_paper.argtypes = [H, C.POINTER(cem_paper_params), C.POINTER(cem_result)]
     L.cem_sample_uniform.argtypes = [H, C.c_uint64, C.c_uint32, C.c_int, vp, vp]
     L.cem_n_env.argtypes = [C.c_int] * 4
+    L.cem_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
     L.cem_solve_static.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc),
                                    C.POINTER(cem_solve_params), C.POINTER(cem_result), vp]
     L.cem_set_launch.argtypes = [H, C.c_int]
@@ -344,6 +346,10 @@ def cem_solve_paper(h, params: cem_paper_params):
 
 def cem_sample_uniform(h, seed, problem, N, theta, stream=None):
     _check(load().cem_sample_uniform(h, seed, problem, N, _ptr(theta), _stream(stream)))
+
+
+def cem_set_randomization(h, M, delta_mu, delta_mass, seed):
+    _check(load().cem_set_randomization(h, int(M), float(delta_mu), float(delta_mass), int(seed)))
 
 
 def cem_n_env(n0, n1, j1, j):
@@ -794,6 +800,11 @@ class Scene:
 
     def set_launch(self, block):
         cem_set_launch(self.h, block)
+
+    def set_randomization(self, M=1, delta_mu=0.0, delta_mass=0.0, seed=0):
+        """Domain randomisation: mean cost / worst class over M environments with
+        friction and manipulated-body mass scaled within +-delta (off: M=1, 0, 0)."""
+        cem_set_randomization(self.h, M, delta_mu, delta_mass, seed)
 
     def set_threads_per_rollout(self, tpr):
         """Lanes per pick-and-place rollout: 1, 8 or 32 (bit-identical results)."""

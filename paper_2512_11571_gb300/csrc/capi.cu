@@ -63,6 +63,8 @@ struct cem_ctx {
   DevScene* scene_d = nullptr;
   int block = 0;  // rollout threads per block (0 = heuristic)
   int tpr = 1;    // lanes per pick-and-place rollout (1, 8 or 32)
+  bool dr_on = false;  // domain randomisation (cem_set_randomization)
+  DrArgs dr{};         // its settings; iteration and problem are filled per launch
   // workspaces of cem_solve
   int cap_N = 0, cap_K = 0, cap_iters = 0;
   float* theta_d = nullptr;
@@ -316,12 +318,24 @@ RefitArgs refit_args(const cem_ctx* h, const float* theta, const float* J, const
 
 // one CE iteration on h->stream: sample -> rollout -> refit (reads and
 // advances the device-side iteration counter)
+// the handle's randomisation for one launch: environments of the device
+// loop's current iteration (iter_ptr) or of iteration `iter`
+const DrArgs* dr_for(cem_ctx* h, DrArgs& tmp, uint32_t problem, const uint32_t* iter_ptr, uint32_t iter) {
+  if (!h->dr_on) return nullptr;
+  tmp = h->dr;
+  tmp.problem = problem;
+  tmp.iter = iter;
+  tmp.iter_ptr = iter_ptr;
+  return &tmp;
+}
+
 cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N, int K, int cov_mode) {
   cudaError_t e = launch_sample(h->mean_d, h->chol_d, seed, &h->track_d->iter, 0, problem, N, h->skel.D, h->theta_d,
                                 h->stream);
   if (e != cudaSuccess) return e;
+  DrArgs tmp;
   e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->tpr,
-                     h->stream);
+                     dr_for(h, tmp, problem, &h->track_d->iter, 0), h->stream);
   if (e != cudaSuccess) return e;
   RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, K, cov_mode);
   a.mean = h->mean_d;
@@ -363,6 +377,7 @@ int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b) {
   b->kind = h->host.kind;
   b->block = default_block(h, N);
   b->tpr = h->tpr;
+  b->dr = h->dr_on ? &h->dr : nullptr;
   return CEM_OK;
 }
 
@@ -511,6 +526,24 @@ int cem_set_launch(cem_handle h, int block_threads) {
   return CEM_OK;
 }
 
+int cem_set_randomization(cem_handle h, int M, float delta_mu, float delta_mass, uint64_t seed) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (M < 1 || M > 32 || (M & (M - 1))) return fail(CEM_ERR_INVALID_ARG, "M must be 1, 2, 4, 8, 16 or 32");
+  if (!(delta_mu >= 0.0f && delta_mu < 1.0f) || !(delta_mass >= 0.0f && delta_mass < 1.0f))
+    return fail(CEM_ERR_INVALID_ARG, "spreads must lie in [0, 1)");
+  h->dr_on = !(M == 1 && delta_mu == 0.0f && delta_mass == 0.0f);
+  h->dr = DrArgs{};
+  h->dr.M = M;
+  h->dr.dmu = delta_mu;
+  h->dr.dm = delta_mass;
+  h->dr.seed = seed;
+  if (h->graph) {  // a captured iteration keeps the rollout it was built with
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
+}
+
 int cem_set_threads_per_rollout(cem_handle h, int tpr) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   if (tpr != 1 && tpr != 8 && tpr != 32) return fail(CEM_ERR_INVALID_ARG, "threads per rollout must be 1, 8 or 32");
@@ -560,7 +593,9 @@ int cem_rollout_batch(cem_handle h, const float* theta_d, int N, float* J_d, uin
   if (N == 0) return CEM_OK;
   if (!is_device_ptr(theta_d) || !is_device_ptr(J_d) || !is_device_ptr(cls_d))
     return fail(CEM_ERR_INVALID_ARG, "theta, J and cls must be device pointers");
+  DrArgs tmp;
   cudaError_t e = launch_rollout(h->scene_d, h->host.kind, theta_d, N, J_d, cls_d, default_block(h, N), h->tpr,
+                                 dr_for(h, tmp, 0, nullptr, 0),
                                  (cudaStream_t)stream);
   return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_rollout_batch");
 }
@@ -702,9 +737,10 @@ int cem_solve_paper(cem_handle h, const cem_paper_params* p, cem_result* out) {
     cudaError_t e = j == 0 ? launch_sample_uniform(h->scene_d, p->seed, p->problem, N, D, h->theta_d, h->stream)
                            : launch_sample(h->mean_d, h->chol_d, p->seed, &h->track_d->iter, 0, p->problem, N, D,
                                            h->theta_d, h->stream);
+    DrArgs tmp;
     if (e == cudaSuccess)
       e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->tpr,
-                         h->stream);
+                         dr_for(h, tmp, p->problem, &h->track_d->iter, 0), h->stream);
     if (e == cudaSuccess) {
       RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, p->K, p->cov_mode);
       a.mean = h->mean_d;
@@ -789,7 +825,7 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
       float tot = 0.0f;
       for (int rep = 0; rep < 3; ++rep) {
         CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
-        e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, t, h->stream);
+        e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, t, nullptr, h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "autotune rollout");
         CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
         CEM_CUDA(cudaEventSynchronize(h->ev1));

@@ -103,10 +103,25 @@ cudaError_t launch_philox_words(uint64_t seed, uint32_t iter, uint32_t problem, 
 // uniform initial sampling inside the regions of the scene's skeleton
 cudaError_t launch_sample_uniform(const DevScene* s_d, uint64_t seed, uint32_t problem, int N, int D, float* theta,
                                   cudaStream_t st);
+// Domain randomisation of a rollout launch: M environments per sample (a
+// power of two <= 32) scaling friction by 1 + dmu (2u - 1) and the
+// manipulated body's mass by 1 + dm (2u' - 1), u, u' from the Philox block
+// (m, 256, iteration, problem) under `seed`; the iteration is *iter_ptr when
+// set (a device loop), else `iter`.
+struct DrArgs {
+  int M;
+  float dmu, dm;
+  uint32_t problem, iter;
+  uint64_t seed;
+  const uint32_t* iter_ptr;
+};
+
 // block = threads per CTA; tpr = lanes per rollout (1, 8 or 32; used for
-// pick-and-place scenes, the other kinds always run one lane per rollout)
+// pick-and-place scenes, the other kinds always run one lane per rollout);
+// dr = domain randomisation or null (then tpr applies; with dr, one lane per
+// environment)
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
-                           int block, int tpr, cudaStream_t st);
+                           int block, int tpr, const DrArgs* dr, cudaStream_t st);
 cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
                          cudaStream_t st);
 cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
@@ -152,6 +167,7 @@ struct SolveBuffers {
   cudaEvent_t ev0, ev1;
   const DevScene* scene;
   int kind, block, tpr;
+  const DrArgs* dr;  // the handle's domain randomisation (null when off)
 };
 const cem_skeleton_desc& handle_skeleton(cem_handle h);
 int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b);

@@ -17,6 +17,7 @@
 // HBM.  The kernel reads N*D*4 bytes and writes N*5 bytes, so it is bound by
 // the FP32 pipe and by instruction latency, not by HBM.
 #include "internal.h"
+#include "philox.cuh"
 
 namespace cem {
 namespace {
@@ -189,19 +190,23 @@ __device__ __forceinline__ void put_trace(float* tr, int step, const float* v, i
 // The rollout functions are compiled once (noinline) and called by every
 // rollout kernel, so the single-problem, traced and batched launches execute
 // the same instructions and return bit-identical results.
+// smu / sm: friction and manipulated-body mass scales of a randomised
+// environment (exactly 1 otherwise, which leaves every value unchanged).
 template <bool HAS_BLOCK, bool TRACE>
-__device__ __noinline__ void planar_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out, int& cls_out,
-                               float* tr) {
+__device__ __noinline__ void planar_rollout(const DevScene& s, const float* __restrict__ row, int T, float smu, float sm,
+                                            float& J_out, int& cls_out, float* tr) {
   // loop invariants in registers
   const float dt = s.dt, eps2 = s.eps * s.eps;
   const float mb = s.mb, Ib = s.Ib, dt_mb = s.dt_mb, dt_Ib = s.dt_Ib;
-  const float bcap = s.base_cap, bcap2 = bcap * bcap, bwcap = s.base_wcap;
+  const float bcap = s.base_cap * smu, bcap2 = bcap * bcap, bwcap = s.base_wcap * smu;
   const float ykp = s.yaw_kp, ykd = s.yaw_kd;
   const float bhx = s.bhx, bhy = s.bhy, khx = s.khx, khy = s.khy;
-  const float dt_mk = s.dt_mk, dt_Ik = s.dt_Ik, kcap = s.block_cap, kcap2 = kcap * kcap, kwcap = s.block_wcap;
-  const float kc = s.k_contact, cc = s.c_contact, mu_dt = s.contact_mu * s.dt, flim = s.force_limit;
+  // the block's spin capacity mu m g rbar dt / I does not depend on its mass (I is proportional to m)
+  const float dt_mk = s.dt_mk / sm, dt_Ik = s.dt_Ik / sm, kcap = s.block_cap * smu, kcap2 = kcap * kcap;
+  const float kwcap = s.block_wcap * smu;
+  const float kc = s.k_contact, cc = s.c_contact, mu_dt = s.contact_mu * smu * s.dt, flim = s.force_limit;
   const float inv_mb = 1.0f / s.mb, inv_Ib = 1.0f / s.Ib;
-  const float inv_mk = HAS_BLOCK ? 1.0f / s.mk : 0.0f, inv_Ik = HAS_BLOCK ? 1.0f / s.Ik : 0.0f;
+  const float inv_mk = HAS_BLOCK ? 1.0f / (s.mk * sm) : 0.0f, inv_Ik = HAS_BLOCK ? 1.0f / (s.Ik * sm) : 0.0f;
   // broad phase: the block's bounding circle (radius rk) against the base
   // rectangle, in the base frame; the hardware sine/cosine is off by < 1e-6,
   // so a 1e-4 m margin keeps the test conservative (it never rejects a pair
@@ -412,14 +417,20 @@ __device__ __forceinline__ bool obj_force(const DevScene& s, int g, float px, fl
 // Jacobi friction impulse of one of nc object contacts (normal n, force Fn)
 // from the trial velocity v: the tangential velocity removed, capped by
 // mu F_n dt; returned as the impulse per unit mass to subtract.
-__device__ __forceinline__ bool obj_friction(const DevScene& s, float nx, float ny, float nz, float Fn, float vx,
+// The object's friction and mass terms of one (possibly randomised)
+// environment: cap = mu dt, its mass, dt / mass.
+struct ObjPhys {
+  float cap, mo, dt_mo;
+};
+
+__device__ __forceinline__ bool obj_friction(const ObjPhys& op, float nx, float ny, float nz, float Fn, float vx,
                                              float vy, float vz, int nc, float& cx, float& cy, float& cz) {
   const float vn = __fmaf_rn(vx, nx, __fmaf_rn(vy, ny, __fmul_rn(vz, nz)));
   const float tx = __fmaf_rn(-vn, nx, vx), ty = __fmaf_rn(-vn, ny, vy), tz = __fmaf_rn(-vn, nz, vz);
   const float vt = __fsqrt_rn(__fmaf_rn(tx, tx, __fmaf_rn(ty, ty, __fmul_rn(tz, tz))));
   if (!(vt > 0.0f)) return false;
-  const float mvt = __fmul_rn(s.mo, vt);
-  const float jm = fminf(__fmul_rn(s.obj_cap, Fn), __fdiv_rn(mvt, (float)nc));
+  const float mvt = __fmul_rn(op.mo, vt);
+  const float jm = fminf(__fmul_rn(op.cap, Fn), __fdiv_rn(mvt, (float)nc));
   const float f = __fdiv_rn(jm, mvt);
   cx = __fmul_rn(f, tx);
   cy = __fmul_rn(f, ty);
@@ -519,7 +530,8 @@ __device__ __forceinline__ void base_contacts(const DevScene& s, uint32_t nbr, f
 // then one Jacobi friction impulse per contact from that trial velocity,
 // each summed in ascending geometry order.  Updates the velocity only.
 template <int G>
-__device__ __forceinline__ void object_contacts(const DevScene& s, uint32_t nbr, float ox, float oy, float oz,
+__device__ __forceinline__ void object_contacts(const DevScene& s, const ObjPhys& op, uint32_t nbr, float ox,
+                                                float oy, float oz,
                                                 float& ovx, float& ovy, float& ovz, float kc, float cc,
                                                 const Group<G>& grp) {
   const float pvx = ovx, pvy = ovy, pvz = ovz;
@@ -539,15 +551,15 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, uint32_t nbr,
         fsz = __fadd_rn(fsz, __fmul_rn(Fn, nz));
       }
     }
-    ovx = __fmaf_rn(s.dt_mo, fsx, pvx);
-    ovy = __fmaf_rn(s.dt_mo, fsy, pvy);
-    ovz = __fsub_rn(__fmaf_rn(s.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
+    ovx = __fmaf_rn(op.dt_mo, fsx, pvx);
+    ovy = __fmaf_rn(op.dt_mo, fsy, pvy);
+    ovz = __fsub_rn(__fmaf_rn(op.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
     // the same contacts again (identical arithmetic) for the friction
     for (uint32_t m = cm; m; m &= m - 1u) {
       const int g = __ffs(m) - 1;
       float nx, ny, nz, Fn, cx, cy, cz;
       obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx, ny, nz, Fn);
-      if (obj_friction(s, nx, ny, nz, Fn, ovx, ovy, ovz, nc, cx, cy, cz)) {
+      if (obj_friction(op, nx, ny, nz, Fn, ovx, ovy, ovz, nc, cx, cy, cz)) {
         jx = __fsub_rn(jx, cx);
         jy = __fsub_rn(jy, cy);
         jz = __fsub_rn(jz, cz);
@@ -587,9 +599,9 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, uint32_t nbr,
       fsy = __fadd_rn(fsy, grp.from(b, src));
       fsz = __fadd_rn(fsz, grp.from(c, src));
     }
-    ovx = __fmaf_rn(s.dt_mo, fsx, pvx);
-    ovy = __fmaf_rn(s.dt_mo, fsy, pvy);
-    ovz = __fsub_rn(__fmaf_rn(s.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
+    ovx = __fmaf_rn(op.dt_mo, fsx, pvx);
+    ovy = __fmaf_rn(op.dt_mo, fsy, pvy);
+    ovz = __fsub_rn(__fmaf_rn(op.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
     // friction: every owner evaluates its contacts, then the ordered sum
     float fx[SL], fy[SL], fz[SL];
     uint32_t fr = 0;
@@ -599,7 +611,7 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, uint32_t nbr,
       const int k = grp.rank + j * G;
       if (k < nn) {
         const int g = nth_bit(nbr, k);
-        if (((cm >> g) & 1u) && obj_friction(s, nx[j], ny[j], nz[j], Fn[j], ovx, ovy, ovz, nc, fx[j], fy[j], fz[j]))
+        if (((cm >> g) & 1u) && obj_friction(op, nx[j], ny[j], nz[j], Fn[j], ovx, ovy, ovz, nc, fx[j], fy[j], fz[j]))
           fr |= 1u << g;
       }
     }
@@ -689,11 +701,12 @@ __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, fl
 }
 
 template <int G, bool TRACE>
-__device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float& J_out,
-                                  int& cls_out, float* tr) {
+__device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* __restrict__ row, int T, float smu,
+                                               float sm, float& J_out, int& cls_out, float* tr) {
   const Group<G> grp;
   const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps;
-  const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap, bcap2 = bcap * bcap;
+  const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap * smu, bcap2 = bcap * bcap;
+  const ObjPhys op{s.obj_cap * smu, s.mo * sm, s.dt_mo / sm};
   const float kc = s.k_contact, cc = s.c_contact, akp = s.arm_kp, akd = s.arm_kd;
   const int n_geoms = s.n_geoms;
   float bx = s.base_start[0], by = s.base_start[1], bvx = s.base_v0[0], bvy = s.base_v0[1];
@@ -816,7 +829,7 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
         ory = oy;
         orz = oz;
       }
-      object_contacts<G>(s, omask, ox, oy, oz, ovx, ovy, ovz, kc, cc, grp);
+      object_contacts<G>(s, op, omask, ox, oy, oz, ovx, ovy, ovz, kc, cc, grp);
       ox += ovx * dt;
       oy += ovy * dt;
       oz += ovz * dt;
@@ -920,13 +933,52 @@ __global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict
   const int T = TRACE ? steps : s.T;
   float Jn;
   int c;
-  if (KIND == CEM_SCENE_REACH) planar_rollout<false, TRACE>(s, row, T, Jn, c, tr);
-  else if (KIND == CEM_SCENE_PUSH) planar_rollout<true, TRACE>(s, row, T, Jn, c, tr);
-  else if (KIND == CEM_SCENE_PICKPLACE) pickplace_rollout<G, TRACE>(s, row, T, Jn, c, tr);
+  if (KIND == CEM_SCENE_REACH) planar_rollout<false, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
+  else if (KIND == CEM_SCENE_PUSH) planar_rollout<true, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
+  else if (KIND == CEM_SCENE_PICKPLACE) pickplace_rollout<G, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
   else quadratic_cost(s, row, Jn, c);
   if (!TRACE && (G == 1 || (threadIdx.x & (G - 1)) == 0)) {
     J[n] = Jn;
     cls[n] = (uint8_t)c;
+  }
+}
+
+// Domain-randomised rollouts: M consecutive lanes (M a power of two <= 32)
+// roll one sample out in the M environments of the iteration, then combine
+// by shuffles: the mean cost (an xor-butterfly sum, identical in every lane)
+// and the worst class; the group's first lane writes.
+template <int KIND>
+__global__ void __launch_bounds__(256) rollout_dr_kernel(const DevScene* __restrict__ scene_g,
+                                                         const float* __restrict__ theta, int N,
+                                                         float* __restrict__ J, uint8_t* __restrict__ cls,
+                                                         const DrArgs dr) {
+  __shared__ DevScene s;
+  stage_scene(scene_g, s);
+  const int M = dr.M;
+  const int t = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int n = t / M, m = t & (M - 1);
+  if (n >= N) return;  // all M lanes of a sample leave together
+  const uint32_t it = dr.iter_ptr ? *dr.iter_ptr : dr.iter;
+  uint32_t r[4];
+  philox4x32_10((uint32_t)m, 256u, it, dr.problem, (uint32_t)dr.seed, (uint32_t)(dr.seed >> 32), r);
+  const float smu = fmaf(dr.dmu, fmaf(2.0f, u01(r[0]), -1.0f), 1.0f);
+  const float sm = fmaf(dr.dm, fmaf(2.0f, u01(r[1]), -1.0f), 1.0f);
+  const float* row = theta + (size_t)n * s.D;
+  float Jn;
+  int c;
+  if (KIND == CEM_SCENE_REACH) planar_rollout<false, false>(s, row, s.T, smu, sm, Jn, c, nullptr);
+  else if (KIND == CEM_SCENE_PUSH) planar_rollout<true, false>(s, row, s.T, smu, sm, Jn, c, nullptr);
+  else pickplace_rollout<1, false>(s, row, s.T, smu, sm, Jn, c, nullptr);
+  const int lane = threadIdx.x & 31;
+  const unsigned gmask = M == 32 ? 0xffffffffu : (((1u << M) - 1u) << (lane & ~(M - 1)));
+  for (int o = 1; o < M; o <<= 1) {
+    Jn += __shfl_xor_sync(gmask, Jn, o);
+    c = max(c, __shfl_xor_sync(gmask, c, o));
+  }
+  if (m == 0) {
+    const float mean = Jn * (1.0f / (float)M);
+    J[n] = mean;
+    cls[n] = (uint8_t)(isfinite(mean) ? c : 3);
   }
 }
 
@@ -1007,7 +1059,7 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
           const float* row = theta + pb.theta_off + (size_t)n * pb.D;
           float Jn;
           int c;
-          pickplace_rollout<G, false>(s, row, s.T, Jn, c, nullptr);
+          pickplace_rollout<G, false>(s, row, s.T, 1.0f, 1.0f, Jn, c, nullptr);
           if ((lane & (G - 1)) == 0) {
             J[pb.sample_off + n] = Jn;
             cls[pb.sample_off + n] = (uint8_t)c;
@@ -1022,9 +1074,9 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
         float Jn;
         int c;
         switch (s.kind) {
-          case CEM_SCENE_REACH: planar_rollout<false, false>(s, row, s.T, Jn, c, nullptr); break;
-          case CEM_SCENE_PUSH: planar_rollout<true, false>(s, row, s.T, Jn, c, nullptr); break;
-          case CEM_SCENE_PICKPLACE: pickplace_rollout<1, false>(s, row, s.T, Jn, c, nullptr); break;
+          case CEM_SCENE_REACH: planar_rollout<false, false>(s, row, s.T, 1.0f, 1.0f, Jn, c, nullptr); break;
+          case CEM_SCENE_PUSH: planar_rollout<true, false>(s, row, s.T, 1.0f, 1.0f, Jn, c, nullptr); break;
+          case CEM_SCENE_PICKPLACE: pickplace_rollout<1, false>(s, row, s.T, 1.0f, 1.0f, Jn, c, nullptr); break;
           default: quadratic_cost(s, row, Jn, c); break;
         }
         J[pb.sample_off + n] = Jn;
@@ -1071,8 +1123,27 @@ cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const Batc
 }
 
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
-                           int block, int tpr, cudaStream_t st) {
-  return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, tpr, st);
+                           int block, int tpr, const DrArgs* dr, cudaStream_t st) {
+  if (!dr || kind == CEM_SCENE_QUADRATIC) return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, tpr, st);
+  if (N <= 0) return cudaSuccess;
+  if (dr->M < 1 || dr->M > 32 || (dr->M & (dr->M - 1))) return cudaErrorInvalidValue;
+  const int bt = block < 32 ? 32 : block;  // whole warps, so environment groups stay aligned
+  const long long threads = (long long)N * dr->M;
+  const int grid = (int)((threads + bt - 1) / bt);
+  switch (kind) {
+    case CEM_SCENE_REACH:
+      rollout_dr_kernel<CEM_SCENE_REACH><<<grid, bt, 0, st>>>(s_d, theta, N, J, cls, *dr);
+      break;
+    case CEM_SCENE_PUSH:
+      rollout_dr_kernel<CEM_SCENE_PUSH><<<grid, bt, 0, st>>>(s_d, theta, N, J, cls, *dr);
+      break;
+    case CEM_SCENE_PICKPLACE:
+      rollout_dr_kernel<CEM_SCENE_PICKPLACE><<<grid, bt, 0, st>>>(s_d, theta, N, J, cls, *dr);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,

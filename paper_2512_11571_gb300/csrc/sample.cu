@@ -13,34 +13,10 @@
 // any roofline at the CE sizes (N <= 65536); it exists to keep the loop on
 // the device.
 #include "internal.h"
+#include "philox.cuh"
 
 namespace cem {
 namespace {
-
-__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                              uint32_t k1, uint32_t out[4]) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
-    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-    c0 = n0;
-    c1 = lo1;
-    c2 = n2;
-    c3 = lo0;
-    if (r < 9) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-  }
-  out[0] = c0;
-  out[1] = c1;
-  out[2] = c2;
-  out[3] = c3;
-}
-
-// u = (r + 1) / 2^32, in (0, 1]
-__device__ __forceinline__ float u01(uint32_t r) { return fmaf(__uint2float_rn(r), 0x1p-32f, 0x1p-32f); }
 
 __global__ void __launch_bounds__(256) sample_kernel(const float* __restrict__ mean, const float* __restrict__ chol,
                                                      uint64_t seed, const uint32_t* __restrict__ iter_ptr,

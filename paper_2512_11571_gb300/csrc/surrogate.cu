@@ -1074,7 +1074,13 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
   for (int j = 0; j < p->iters; ++j) {
     SUR_CUDA(launch_sample(b.mean, b.chol, p->seed, &b.track->iter, 0, p->problem, n_pool, D, s->pool_theta, st));
     SUR_CUDA(screen_pool(s, n_pool, N, n_explore, D, b.theta, st));
-    SUR_CUDA(launch_rollout(b.scene, b.kind, b.theta, N, b.J, b.cls, b.block, b.tpr, st));
+    DrArgs dr;
+    if (b.dr) {
+      dr = *b.dr;
+      dr.problem = p->problem;
+      dr.iter_ptr = &b.track->iter;
+    }
+    SUR_CUDA(launch_rollout(b.scene, b.kind, b.theta, N, b.J, b.cls, b.block, b.tpr, b.dr ? &dr : nullptr, st));
     SUR_CUDA(launch_refit(a, st));
   }
   SUR_CUDA(cudaEventRecord(b.ev1, st));

@@ -1,0 +1,107 @@
+"""Domain randomisation on the GPU (Sec. IV-C) against the oracle.
+
+M adjacent lanes roll one sample out in the M environments of the
+iteration (friction scaled by 1 + dmu (2u - 1), manipulated-body mass by
+1 + dm (2u' - 1)) and combine by shuffles into the mean cost and the worst
+class.  Degenerate settings must reproduce the plain rollout bit for bit;
+real spreads are compared with the oracle's FP64 environments at the
+tolerances of the plain rollout parity (contact-free reach at full horizon,
+contact tasks at 200 steps), and the randomised CE loop converges like the
+oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    return P
+
+
+def thetas(sk, N, seed):
+    lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+    return np.random.default_rng(seed).uniform(lo, hi, (N, len(lo))).astype(np.float32)
+
+
+def gpu_rollout(P, S, th):
+    J, cls = S.rollout(torch.as_tensor(th).cuda())
+    torch.cuda.synchronize()
+    return J.cpu().numpy(), cls.cpu().numpy()
+
+
+@pytest.mark.parametrize("task", ["reach", "push", "pickplace"])
+def test_zero_spread_reproduces_the_plain_rollout(P, task):
+    sc, sk = {"reach": workload.reach_scene(0), "push": workload.push_scene(1, T=500),
+              "pickplace": workload.pickplace_scene(1, T=600)}[task]
+    th = thetas(sk, 1000, 1)
+    with P.Scene(sc, sk) as S:
+        J0, c0 = gpu_rollout(P, S, th)
+        S.set_randomization(4, 0.0, 0.0, seed=9)  # four identical environments
+        J4, c4 = gpu_rollout(P, S, th)
+        S.set_randomization(1, 0.0, 0.0)  # off
+        J1, c1 = gpu_rollout(P, S, th)
+    assert np.array_equal(J4.view(np.uint32), J0.view(np.uint32)) and np.array_equal(c4, c0)
+    assert np.array_equal(J1.view(np.uint32), J0.view(np.uint32)) and np.array_equal(c1, c0)
+
+
+@pytest.mark.parametrize("task,T,M", [("reach", None, 8), ("push", 200, 4), ("pickplace", 200, 32), ("push", 200, 1)])
+def test_randomised_cost_matches_oracle(P, task, T, M):
+    sc, sk = {"reach": workload.reach_scene(2), "push": workload.push_scene(3),
+              "pickplace": workload.pickplace_scene(4)}[task]
+    th = thetas(sk, 333, 2)  # ragged against warps and environment groups
+    with P.Scene(sc, sk, T=T) as S:
+        S.set_randomization(M, 0.3, 0.4, seed=1234)
+        J, c = gpu_rollout(P, S, th)
+    Jo, co = oracle.rollout_dr(sc, sk, th.astype(np.float64), M, 0.3, 0.4, seed=1234, it=0, problem=0, T=T)
+    rel = np.abs(J - Jo) / np.maximum(np.abs(Jo), 1e-3)
+    # samples on a success threshold may flip in one environment (FP32 vs FP64
+    # trajectories), exactly as in the plain parity; they must stay rare
+    ok = (rel <= 1e-3) & (c == co)
+    assert ok.mean() >= 0.97, (task, ok.mean())
+
+
+def test_cem_with_randomisation_converges_like_the_oracle(P):
+    close = 0
+    for seed in range(4):
+        sc, sk = workload.push_scene(seed)
+        with P.Scene(sc, sk) as S:
+            S.set_randomization(4, 0.25, 0.25, seed=77)
+            r = S.solve(seed, 512, 32, 6, use_graph=True)
+        o = oracle.cem_dr(sc, sk, seed, 512, 32, 6, M=4, dmu=0.25, dm=0.25, dr_seed=77)
+        if r["best_cls"] == o["best_cls"] and abs(r["best_J"] - o["best_J"]) <= 0.02 * abs(o["best_J"]):
+            close += 1
+    assert close >= 3
+
+
+def test_graph_follows_randomisation_changes(P):
+    sc, sk = workload.push_scene(2, T=400)
+    with P.Scene(sc, sk) as S:
+        plain = S.solve(3, 256, 16, 3, use_graph=True)
+        S.set_randomization(8, 0.5, 0.5, seed=5)
+        g = S.solve(3, 256, 16, 3, use_graph=True)
+        e = S.solve(3, 256, 16, 3, use_graph=False)
+        S.set_randomization(1, 0.0, 0.0)
+        again = S.solve(3, 256, 16, 3, use_graph=True)
+    assert g["best_J"] == e["best_J"] and np.array_equal(g["mean"], e["mean"])
+    assert not np.array_equal(g["mean"], plain["mean"])
+    assert again["best_J"] == plain["best_J"] and np.array_equal(again["mean"], plain["mean"])
+
+
+def test_randomisation_validation(P):
+    sc, sk = workload.reach_scene(0)
+    with P.Scene(sc, sk) as S:
+        for M, dmu, dm in ((3, 0.1, 0.1), (64, 0.1, 0.1), (0, 0.0, 0.0), (4, 1.0, 0.0), (4, 0.0, -0.1)):
+            with pytest.raises(P.CemError):
+                S.set_randomization(M, dmu, dm)

@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--rollout-only", choices=["reach", "push", "pickplace"], default=None,
                     help="time only the rollout kernel of one workload (profiling driver)")
-    ap.add_argument("--n", type=int, default=0, help="samples for --rollout-only (0 = the workload's N)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="samples for --rollout-only (0 = the workload's N) and per plan for --multiplan (0 = 4096)")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
     ap.add_argument("--tpr", type=int, default=1,
                     help="lanes per pick-and-place rollout for --rollout-only (1, 8 or 32)")
@@ -70,6 +71,9 @@ def parse():
     ap.add_argument("--dr-gain", type=int, default=0,
                     help="optimise the move-and-push task with and without domain randomisation on this many "
                          "seeds and score both plans under fresh randomised environments")
+    ap.add_argument("--multiplan", type=int, default=0,
+                    help="multi-plan search on this many pick-place scenes (four candidate plans each): "
+                         "every plan to the end vs successive halving")
     ap.add_argument("--mlp-only", type=int, default=0,
                     help="time only the surrogate forward on this many rows (profiling driver)")
     return ap.parse_args()
@@ -583,8 +587,40 @@ def run_dr_gain(args):
     print(json.dumps(out), flush=True)
 
 
+def run_multiplan(args):
+    """Four candidate plans per pick-place scene (direct, and three 6-action
+    plans through waypoints) realised in one batch, N = 4096, K = 200, 20
+    iterations: every plan for all iterations vs successive halving every 5
+    iterations.  Reports the chosen plan and cost of both, the simulated
+    steps and the wall time (host clock around the synchronous call)."""
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    rows = []
+    N = args.n or 4096
+    for seed in range(args.multiplan):
+        sc, plans = workload.pickplace_plans(seed)
+        row = {}
+        for name, halving in (("all_plans", 0), ("halving", 5)):
+            P.cem_multiplan_solve(sc, plans, seed=seed, N=N, K=200, iters=1)  # warm-up
+            t0 = time.perf_counter()
+            res, best = P.cem_multiplan_solve(sc, plans, seed=seed, N=N, K=200, iters=20, halving_iters=halving)
+            ms = (time.perf_counter() - t0) * 1e3
+            row[name] = {"best_plan": best, "best_J": float(res[best]["best_J"]), "best_cls": int(res[best]["best_cls"]),
+                         "iters_per_plan": [r["iters_run"] for r in res],
+                         "sim_steps": int(sum(r["iters_run"] for r in res) * N * sc["T"]), "ms": ms}
+        rows.append(row)
+    out = {"multiplan": {"plans": 4, "N": N, "K": 200, "iters": 20, "halving_iters": 5, "scenes": rows}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.multiplan:
+        run_multiplan(args)
+        return
     if args.dr_gain:
         run_dr_gain(args)
         return

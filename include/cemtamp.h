@@ -310,6 +310,11 @@ int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm)
 int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float* best_ms_out);
 /* Simulated steps of one batch iteration: sum over problems of N * T. */
 long long cem_batch_steps_per_iteration(cem_batch_handle h);
+/* Which problems take part in the next iterations (active_h[n_problems],
+ * non-zero = active).  An inactive problem is not sampled, rolled out or
+ * refit: its distribution, best sample and iteration count stay as they
+ * are.  cem_batch_reset makes every problem active again. */
+int cem_batch_set_active(cem_batch_handle h, const int32_t* active_h);
 /* Lanes per pick-and-place rollout in the persistent launch: 1, 8 or 32
  * (other scene kinds always take one lane per rollout).  With 8 or 32, a
  * lane group holds one rollout's state, splits its per-geometry contact
@@ -319,6 +324,28 @@ long long cem_batch_steps_per_iteration(cem_batch_handle h);
 int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr);
 /* The current persistent launch shape (CTAs per SM resolved when automatic). */
 int cem_batch_get_launch(cem_batch_handle h, int* warps_out, int* ctas_out, int* tpr_out);
+
+/* ---- Multi-plan search (Sec. III: the optimiser could search several
+ * candidate plans at once; Sec. V: evaluating many plans is expensive) ----
+ * One scene, n_plans candidate skeletons, each realised by Algorithm 1 as a
+ * problem of one batch (problem id = plan index, common seed, N, K).  With
+ * halving_iters > 0 the budget is spent by successive halving: every
+ * halving_iters iterations the active plans are ranked by their best
+ * (class, cost, plan index) and the better half (at least `keep`) stays
+ * active; eliminated plans stop where they are.  per_plan_out[n_plans] gets
+ * every plan's result (each identical to cem_solve of that plan for the
+ * iterations it ran), iters_out[n_plans] (may be NULL) those iteration
+ * counts, *best_plan_out the plan with the lowest (class, cost, index).
+ * Synchronous. */
+typedef struct {
+  uint64_t seed;
+  int32_t N, K, iters, cov_mode;
+  int32_t halving_iters; /* 0: every plan runs all iterations */
+  int32_t keep;          /* plans kept at least (0 -> 1) */
+} cem_multiplan_params;
+int cem_multiplan_solve(const cem_scene_desc* scene, const cem_skeleton_desc* plans, int n_plans,
+                        const cem_multiplan_params* p, cem_result* per_plan_out, int32_t* iters_out,
+                        int32_t* best_plan_out);
 
 /* ---- Learned cost surrogate (not in the paper) ---------------------------
  * An MLP score(x), x = [theta normalised to [-1, 1] by the bounds (clamped)

@@ -34,6 +34,7 @@ EXPORTS = [
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
     "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
     "cem_set_randomization",
+    "cem_batch_set_active", "cem_multiplan_solve",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -118,6 +119,11 @@ class cem_paper_params(C.Structure):
 class cem_problem_params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("N", C.c_int32), ("K", C.c_int32), ("cov_mode", C.c_int32),
                 ("problem", C.c_uint32)]
+
+
+class cem_multiplan_params(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("N", C.c_int32), ("K", C.c_int32), ("iters", C.c_int32),
+                ("cov_mode", C.c_int32), ("halving_iters", C.c_int32), ("keep", C.c_int32)]
 
 
 class cem_result(C.Structure):
@@ -227,6 +233,10 @@ def load(path: str = LIB_PATH):
     L.cem_sample_uniform.argtypes = [H, C.c_uint64, C.c_uint32, C.c_int, vp, vp]
     L.cem_n_env.argtypes = [C.c_int] * 4
     L.cem_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
+    L.cem_batch_set_active.argtypes = [H, C.POINTER(C.c_int32)]
+    L.cem_multiplan_solve.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc), C.c_int,
+                                      C.POINTER(cem_multiplan_params), C.POINTER(cem_result),
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.cem_solve_static.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc),
                                    C.POINTER(cem_solve_params), C.POINTER(cem_result), vp]
     L.cem_set_launch.argtypes = [H, C.c_int]
@@ -413,6 +423,38 @@ def cem_batch_create(problems):
     return h
 
 
+def cem_batch_set_active(h, active):
+    a = np.ascontiguousarray(np.asarray(active, np.int32))
+    _check(load().cem_batch_set_active(h, a.ctypes.data_as(C.POINTER(C.c_int32))))
+
+
+def cem_multiplan_solve(scene: dict, plans: list, seed, N, K, iters, halving_iters=0, keep=1, cov_mode="full"):
+    """Realise every candidate plan (skeleton) of one scene in one batch, with
+    optional successive halving; returns (per-plan result dicts, best plan)."""
+    n = len(plans)
+    skels = (cem_skeleton_desc * n)()
+    s0 = None
+    for i, sk in enumerate(plans):
+        s, k = pack_scene(scene, sk)
+        s0 = s if s0 is None else s0
+        skels[i] = k
+    p = cem_multiplan_params()
+    p.seed, p.N, p.K, p.iters, p.cov_mode = seed, N, K, iters, COV[cov_mode]
+    p.halving_iters, p.keep = halving_iters, keep
+    out = (cem_result * n)()
+    its = np.zeros(n, np.int32)
+    best = C.c_int32(-1)
+    _check(load().cem_multiplan_solve(C.byref(s0), skels, n, C.byref(p), out,
+                                      its.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(best)))
+    res = []
+    for i in range(n):
+        r, D = out[i], out[i].D
+        res.append(dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
+                        mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                        iters_done=r.iters_done, iters_run=int(its[i])))
+    return res, best.value
+
+
 def cem_batch_destroy(h):
     _check(load().cem_batch_destroy(h))
 
@@ -491,6 +533,10 @@ class Batch:
 
     def set_threads_per_rollout(self, tpr):
         cem_batch_set_threads_per_rollout(self.h, tpr)
+
+    def set_active(self, active):
+        """Which problems take part in the next iterations (reset: all)."""
+        cem_batch_set_active(self.h, active)
 
     def launch(self):
         """(warps per CTA, CTAs per SM, lanes per pick-and-place rollout)."""

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -53,6 +54,7 @@ struct cem_batch_ctx {
   RefitArgs* args_d = nullptr;
   int warps = 4, ctas_per_sm = 0;  // persistent launch shape (0 = occupancy)
   int tpr = 1;                     // lanes per pick-and-place rollout (1, 8 or 32)
+  std::vector<int> order;          // problems by descending work (the queue order)
   bool has_pickplace = false;
   cudaGraphExec_t graph = nullptr;
   long long steps_per_iter = 0;
@@ -73,6 +75,33 @@ int grid_size(const cem_batch_ctx* h) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr);
   return sms * per_sm;
+}
+
+// Which problems take part in the next iterations: flags on the device
+// problem table and refit arguments, and a work queue of the active
+// problems' chunks only (same order).  A captured graph holds the old queue
+// length, so it is dropped.
+int set_active(cem_batch_ctx* h, const std::vector<int>& active) {
+  std::vector<BatchItem> items;
+  for (int p : h->order) {
+    h->probs[p].active = active[p] ? 1 : 0;
+    if (active[p])
+      for (int f = 0; f < h->probs[p].N; f += 32) items.push_back(BatchItem{p, f});
+  }
+  BATCH_CUDA(cudaMemcpy(h->probs_d, h->probs.data(), sizeof(BatchProblem) * h->P, cudaMemcpyHostToDevice));
+  for (int p = 0; p < h->P; ++p) {
+    const int32_t skip = active[p] ? 0 : 1;
+    BATCH_CUDA(cudaMemcpy(reinterpret_cast<char*>(h->args_d + p) + offsetof(RefitArgs, skip), &skip, sizeof(skip),
+                          cudaMemcpyHostToDevice));
+  }
+  if (!items.empty())
+    BATCH_CUDA(cudaMemcpy(h->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+  h->n_items = (int)items.size();
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
 }
 
 cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st) {
@@ -125,6 +154,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
     b.sample_off = (int32_t)sample_total;
     b.problem = q.problem;
     b.seed = q.seed;
+    b.active = 1;
     theta_total += (long long)q.N * b.D;
     sample_total += q.N;
     h->maxN = std::max(h->maxN, q.N);
@@ -148,6 +178,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
     const long long wb = host[b].kind == CEM_SCENE_QUADRATIC ? 1 : (long long)host[b].T * (host[b].kind == CEM_SCENE_PICKPLACE ? 4 : 1);
     return wa > wb;
   });
+  h->order = order;
   std::vector<BatchItem> items;
   for (int p : order)
     for (int f = 0; f < h->probs[p].N; f += 32) items.push_back(BatchItem{p, f});
@@ -222,6 +253,12 @@ int cem_batch_destroy(cem_batch_handle h) {
 
 int cem_batch_reset(cem_batch_handle h, void* stream) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  bool all = true;
+  for (const BatchProblem& b : h->probs) all = all && b.active;
+  if (!all) {  // every problem takes part again
+    const int rc = set_active(h, std::vector<int>(h->P, 1));
+    if (rc != CEM_OK) return rc;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t P = h->P;
   std::vector<float> mean(P * kMS, 0.0f), cov(P * kMC, 0.0f), chol(P * kMC, 0.0f);
@@ -396,6 +433,77 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
 }
 
 long long cem_batch_steps_per_iteration(cem_batch_handle h) { return h ? h->steps_per_iter : 0; }
+
+int cem_batch_set_active(cem_batch_handle h, const int32_t* active_h) {
+  if (!h || !active_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  std::vector<int> a(h->P);
+  for (int p = 0; p < h->P; ++p) a[p] = active_h[p] ? 1 : 0;
+  return set_active(h, a);
+}
+
+int cem_multiplan_solve(const cem_scene_desc* scene, const cem_skeleton_desc* plans, int n_plans,
+                        const cem_multiplan_params* p, cem_result* per_plan_out, int32_t* iters_out,
+                        int32_t* best_plan_out) {
+  set_last_error(CEM_OK, "");
+  if (!scene || !plans || !p || !per_plan_out) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  if (n_plans < 1 || n_plans > CEM_MAX_BATCH) return fail(CEM_ERR_UNSUPPORTED, "1..1024 plans");
+  if (p->iters < 1 || p->iters > 100000 || p->halving_iters < 0 || p->keep < 0)
+    return fail(CEM_ERR_UNSUPPORTED, "iters in 1..1e5, halving_iters >= 0, keep >= 0");
+  std::vector<cem_scene_desc> scenes(n_plans, *scene);
+  std::vector<cem_problem_params> pp(n_plans);
+  for (int i = 0; i < n_plans; ++i) {
+    std::memset(&pp[i], 0, sizeof(pp[i]));
+    pp[i].seed = p->seed;
+    pp[i].N = p->N;
+    pp[i].K = p->K;
+    pp[i].cov_mode = p->cov_mode;
+    pp[i].problem = (uint32_t)i;
+  }
+  cem_batch_handle h = nullptr;
+  int rc = cem_batch_create(scenes.data(), plans, pp.data(), n_plans, &h);
+  if (rc != CEM_OK) return rc;
+  std::vector<int> active(n_plans, 1), ran(n_plans, 0);
+  std::vector<cem_result> res(n_plans);
+  const int keep = p->keep > 0 ? p->keep : 1;
+  auto key_less = [&](int a, int b) {  // (class, best cost, plan index) ascending
+    if (res[a].best_class != res[b].best_class) return res[a].best_class < res[b].best_class;
+    if (res[a].best_J != res[b].best_J) return res[a].best_J < res[b].best_J;
+    return a < b;
+  };
+  int done = 0;
+  while (rc == CEM_OK && done < p->iters) {
+    const int step = p->halving_iters > 0 ? std::min(p->halving_iters, p->iters - done) : p->iters - done;
+    rc = cem_batch_iterate(h, step, 1, nullptr);
+    if (rc != CEM_OK) break;
+    done += step;
+    for (int i = 0; i < n_plans; ++i) ran[i] += active[i] ? step : 0;
+    int n_active = 0;
+    for (int a : active) n_active += a;
+    if (p->halving_iters > 0 && done < p->iters && n_active > keep) {
+      rc = cem_batch_read(h, res.data(), nullptr);
+      if (rc != CEM_OK) break;
+      std::vector<int> alive;
+      for (int i = 0; i < n_plans; ++i)
+        if (active[i]) alive.push_back(i);
+      std::sort(alive.begin(), alive.end(), key_less);
+      const int survivors = std::max(keep, (n_active + 1) / 2);
+      for (size_t r = (size_t)survivors; r < alive.size(); ++r) active[alive[r]] = 0;
+      rc = set_active(h, active);
+    }
+  }
+  if (rc == CEM_OK) rc = cem_batch_read(h, res.data(), nullptr);
+  cem_batch_destroy(h);
+  if (rc != CEM_OK) return rc;
+  int best = 0;
+  for (int i = 1; i < n_plans; ++i)
+    if (key_less(i, best)) best = i;
+  for (int i = 0; i < n_plans; ++i) {
+    per_plan_out[i] = res[i];
+    if (iters_out) iters_out[i] = ran[i];
+  }
+  if (best_plan_out) *best_plan_out = best;
+  return CEM_OK;
+}
 
 int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");

@@ -67,7 +67,7 @@ struct BatchProblem {
   int32_t theta_off;   // float offset of the problem's theta rows in the batch buffer
   int32_t sample_off;  // offset of its J / class entries
   uint32_t problem;    // Philox problem id
-  int32_t pad;
+  int32_t active;      // 0: the problem is left out of sampling, rollouts and refits
   uint64_t seed;
 };
 
@@ -93,6 +93,7 @@ struct RefitArgs {
   int32_t* hist_keff;
   int32_t* hist_cnt;  // [hist_len][4] samples per class and iteration (may be null)
   int32_t* status;    // set to CEM_ERR_NOT_PD when the covariance stays indefinite
+  int32_t skip;       // batched refit: 1 leaves this problem untouched (eliminated plan)
 };
 
 // kernel launchers (stream-ordered, no synchronisation)

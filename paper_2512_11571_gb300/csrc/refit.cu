@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(RT) refit_batch_kernel(const RefitArgs* __rest
   __shared__ RefitArgs a;
   if (threadIdx.x == 0) a = args[blockIdx.x];
   __syncthreads();
+  if (a.skip) return;  // an eliminated plan keeps its state
   refit_body(a);
 }
 

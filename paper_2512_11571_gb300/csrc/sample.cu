@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128) sample_batch_kernel(const BatchProblem* _
   __shared__ float sm[CEM_MAX_D];
   const int p = blockIdx.y;
   const BatchProblem pb = probs[p];
-  if ((int)(blockIdx.x * blockDim.x) >= pb.N) return;  // whole block beyond this problem
+  if (!pb.active || (int)(blockIdx.x * blockDim.x) >= pb.N) return;  // inactive, or past this problem
   const int D = pb.D;
   for (int i = threadIdx.x; i < D * D; i += blockDim.x) sL[i] = chols[(size_t)p * CEM_MAX_D * CEM_MAX_D + i];
   for (int i = threadIdx.x; i < D; i += blockDim.x) sm[i] = means[(size_t)p * CEM_MAX_D + i];

@@ -284,6 +284,20 @@ def pickplace_scene(seed: int = 0, n_actions: int = 5, T: int = 3000, dt: float 
     return scene, skel
 
 
+def pickplace_plans(seed: int = 0, T: int = 3000, obstacle: str = "ramp"):
+    """One pick-place scene and four candidate plans (skeletons) for it: the
+    direct 5-action plan, and 6-action plans through a waypoint south of the
+    tables, in the far north-west corner, and in the far south-east corner
+    (the last two are long detours).  All four share the scene's goals."""
+    scene, direct = pickplace_scene(seed, n_actions=5, T=T, obstacle=obstacle)
+    plans = [direct]
+    for wp in ((0.0, -0.6), (-2.4, 1.6), (2.4, -1.5)):
+        _, sk = pickplace_scene(seed, n_actions=6, T=T, obstacle=obstacle)
+        sk["actions"][4] = dict(sk["actions"][4], nominal=(wp[0], wp[1], 0.0))
+        plans.append(sk)
+    return scene, plans
+
+
 def quadratic_scene(seed: int = 0, D: int = 6):
     """J = (theta - theta*)^T A (theta - theta*) with a seeded SPD A.
 

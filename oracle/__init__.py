@@ -22,7 +22,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SOURCES = ["sample.cpp", "rollout.cpp", "cem.cpp"]
+SOURCES = ["sample.cpp", "rollout.cpp", "cem.cpp", "plan2d.cpp"]
 
 MAX_D, MAX_ACT, MAX_GEOM, MAX_SLAB, TRACE_W = 18, 6, 16, 6, 20
 KIND = {"quadratic": 0, "reach": 1, "push": 2, "pickplace": 3}
@@ -32,7 +32,7 @@ ACT = {"move": 0, "push": 1, "grasp": 2, "place": 3}
 def build(force: bool = False) -> str:
     """Compile liboracle.so with g++ (portable flags: x86 and Arm)."""
     srcs = [os.path.join(HERE, s) for s in SOURCES]
-    newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(HERE, "oracle.h")])
+    newest = max(os.path.getmtime(p) for p in srcs + [os.path.join(HERE, "oracle.h"), os.path.join(HERE, "plan2d.h")])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
@@ -75,6 +75,8 @@ class _Scene(C.Structure):
         ("act_nom", (C.c_double * 3) * MAX_ACT), ("act_yaw", C.c_double * MAX_ACT),
         ("lo", C.c_double * MAX_D), ("hi", C.c_double * MAX_D),
         ("act_region", C.c_int32 * MAX_ACT), ("act_ring", (C.c_double * 4) * MAX_ACT),
+        ("base_ctrl", C.c_int32), ("base_infl", C.c_double), ("wp_switch", C.c_double), ("pid_ki", C.c_double),
+        ("pid_irad", C.c_double), ("pid_imax", C.c_double),
     ]
 
 
@@ -113,6 +115,10 @@ def pack(scene: dict, skel: dict, T: int | None = None) -> _Scene:
             _set(getattr(s, name), scene[key])
     for key in ("goal_obj_region", "goal_obj_held", "goal_base_region"):
         setattr(s, key, int(bool(scene.get(key, False))))
+    if scene.get("base_controller", "pd") == "astar":  # A* waypoints + PID (Sec. IV-A)
+        s.base_ctrl = 1
+        s.base_infl, s.wp_switch = scene["base_inflate"], scene["wp_switch"]
+        s.pid_ki, s.pid_irad, s.pid_imax = scene["pid_ki"], scene["pid_irad"], scene["pid_imax"]
     geoms = scene.get("geoms", [])
     if len(geoms) > MAX_GEOM:
         raise ValueError("too many geometries")
@@ -193,6 +199,10 @@ def lib():
                                     dp, dp, dp]
             L.or_cem_dr.restype = C.c_int
             L.or_n_env.argtypes = [C.c_int] * 4
+            L.or_base_corners.argtypes = [sp, dp, C.c_int]
+            L.or_base_corners.restype = C.c_int
+            L.or_plan_path.argtypes = [sp, C.c_double, C.c_double, C.c_double, C.c_double, dp, C.c_int]
+            L.or_plan_path.restype = C.c_int
             L.or_n_env.restype = C.c_int
             L.or_cem_paper.argtypes = [sp, C.c_uint64, C.c_uint32] + [C.c_int] * 7 + [
                 dp, dp, C.POINTER(C.c_int), dp, dp, dp, i32p, i32p]
@@ -381,3 +391,20 @@ def cem_dr(scene, skel, seed, N, K, iters, M, dmu, dm, dr_seed, problem=0, diag=
     if rc != 0:
         raise RuntimeError(f"oracle CE loop failed: {rc}")
     return dict(best_theta=bt, best_J=bJ.value, best_cls=bc.value, mean=mean, cov=cov, history=hist)
+
+
+def base_corners(scene, skel):
+    """Corners of the base planner's visibility graph, shape (n, 2)."""
+    s = pack(scene, skel)
+    xy = np.zeros(2 * 64)
+    n = lib().or_base_corners(C.byref(s), _p(xy, C.c_double), 64)
+    return xy[:2 * min(n, 64)].reshape(-1, 2)
+
+
+def plan_path(scene, skel, start, goal):
+    """A* waypoints of the base from start to goal (ending with the goal)."""
+    s = pack(scene, skel)
+    xy = np.zeros(2 * 64)
+    n = lib().or_plan_path(C.byref(s), float(start[0]), float(start[1]), float(goal[0]), float(goal[1]),
+                           _p(xy, C.c_double), 64)
+    return xy[:2 * min(n, 64)].reshape(-1, 2)

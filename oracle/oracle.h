@@ -38,6 +38,7 @@
 #define OR_MAX_GEOM 16
 #define OR_MAX_SLAB 6
 #define OR_TRACE_W 20
+#define OR_MAX_CORNERS 48
 
 enum { OR_QUAD = 0, OR_REACH = 1, OR_PUSH = 2, OR_PICKPLACE = 3 };
 enum { OR_MOVE = 0, OR_PUSH_ACT = 1, OR_GRASP = 2, OR_PLACE = 3 };
@@ -73,6 +74,13 @@ typedef struct {
    * act_ring = (centre x, centre y, inner radius, outer radius) */
   int32_t act_region[OR_MAX_ACT];
   double act_ring[OR_MAX_ACT][4];
+  /* moveTo controller of the pick-place base (Sec. IV-A): 0 = PD to the
+   * goal; 1 = A* waypoints (base_infl = footprint growth) tracked by PD,
+   * advancing within wp_switch of a waypoint, with an integral term
+   * (gain pid_ki * kp, active within pid_irad of the goal, |I| <= pid_imax
+   * per axis) on the final one */
+  int32_t base_ctrl;
+  double base_infl, wp_switch, pid_ki, pid_irad, pid_imax;
 } or_scene;
 
 typedef struct {
@@ -116,6 +124,12 @@ int or_select(const float* J, const uint8_t* cls, int N, int K, int32_t* idx);
 /* Refit mean/cov/chol (FP64) from elites; returns 0, or -4 if not PD. */
 int or_refit(const double* theta, int N, int D, const int32_t* idx, int k_eff, const double* lo,
              const double* hi, int diag, double* mean, double* cov, double* chol);
+/* Corners of the base planner's visibility graph: xy[2 i], xy[2 i + 1];
+ * returns their number (the first `cap` are written). */
+int or_base_corners(const or_scene* s, double* xy, int cap);
+/* A* waypoints of the base from (sx, sy) to (gx, gy), ending with the goal;
+ * returns their number (the first `cap` are written). */
+int or_plan_path(const or_scene* s, double sx, double sy, double gx, double gy, double* xy, int cap);
 /* Mean distance from the centre over a (2a x 2b) rectangle (numerical). */
 double or_mean_radius(double a, double b);
 /* Full CE loop (Algorithm 1), FP64.  history[iters] = best J so far. */

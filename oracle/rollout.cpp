@@ -17,6 +17,7 @@
 //     succeeded (here: seconds), the next action starts the step after
 //     success (Problem 1), plus the end cost of each task.
 #include "oracle.h"
+#include "plan2d.h"
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -67,6 +68,7 @@ inline double Val(double a) { return a; }
 // Scene-derived constants computed once per call (not per step).
 struct Prep {
   double Ib, Ik, rbar_b, rbar_k;
+  BaseGraph base;  // planner graph (pick-place with the A* base controller)
 };
 
 Prep prepare(const or_scene& s) {
@@ -76,6 +78,7 @@ Prep prepare(const or_scene& s) {
   p.Ik = s.block_mass * (4 * s.block_half[0] * s.block_half[0] + 4 * s.block_half[1] * s.block_half[1]) / 12.0;
   p.rbar_b = or_mean_radius(s.base_half[0], s.base_half[1]);
   p.rbar_k = s.kind == OR_PUSH ? or_mean_radius(s.block_half[0], s.block_half[1]) : 0.0;
+  if (s.kind == OR_PICKPLACE && s.base_ctrl == 1) base_graph(s, p.base);
   return p;
 }
 
@@ -395,7 +398,8 @@ void arm_fk(const or_scene& s, R bx, R by, R beta, R q1, R q2, R& ex, R& ey, R& 
 }
 
 template <class R>
-void pickplace_rollout(const or_scene& s, const double* th, int T, R& J_out, int& cls_out, double* trace) {
+void pickplace_rollout(const or_scene& s, const Prep& pp, const double* th, int T, R& J_out, int& cls_out,
+                       double* trace) {
   const double dt = s.dt, m = s.base_mass, mo = s.obj_mass, h = s.obj_half;
   R bx = R(s.base_start[0]), by = R(s.base_start[1]), bvx = R(s.base_v0[0]), bvy = R(s.base_v0[1]);
   R q1 = R(s.arm_home[0]), q2 = R(s.arm_home[1]), dq1 = R(0.0), dq2 = R(0.0), beta = R(0.0);
@@ -414,6 +418,11 @@ void pickplace_rollout(const or_scene& s, const double* th, int T, R& J_out, int
   R caz = R(1.0), saz = R(0.0), hgrip = R(0.0);       // grasp parameters
   R ptx = R(0.0), pty = R(0.0), ptz = R(0.0);         // place target
   R t_done = R(T * dt);
+  // A* base controller: waypoints of the current moveTo and the integral term
+  double wpx[OR_MAX_CORNERS + 2], wpy[OR_MAX_CORNERS + 2];
+  int nwp = 0, wi = 0;
+  R Ix = R(0.0), Iy = R(0.0);
+  const bool astar = s.base_ctrl == 1;
   for (int step = 0; step < T; ++step) {
     const int ai = a < L ? a : L - 1;
     const int kind = s.act_kind[ai];
@@ -426,6 +435,11 @@ void pickplace_rollout(const or_scene& s, const double* th, int T, R& J_out, int
         mkd = R(2.0) * Sqrt(mkp);
         rx = s.act_ref_target[ai] ? mgx : R(s.act_nom[ai][0]);
         ry = s.act_ref_target[ai] ? mgy : R(s.act_nom[ai][1]);
+        if (astar) {  // plan from where the base is now
+          nwp = plan_path(pp.base, Val(bx), Val(by), Val(mgx), Val(mgy), wpx, wpy, OR_MAX_CORNERS + 2);
+          wi = 0;
+          Ix = Iy = R(0.0);
+        }
       } else if (kind == OR_GRASP) {
         caz = Cos(R(th[o])); saz = Sin(R(th[o]));
         hgrip = R(th[o + 1]);
@@ -439,8 +453,27 @@ void pickplace_rollout(const or_scene& s, const double* th, int T, R& J_out, int
     }
     // targets of this step
     R tx = R(0.0), ty = R(0.0), tz = R(0.0);
+    R fix = R(0.0), fiy = R(0.0);  // integral force term per unit mass
     if (kind == OR_MOVE) {
       gx = mgx; gy = mgy; kp = mkp; kd = mkd;
+      if (astar) {
+        // advance past every waypoint already within the switching radius
+        while (wi < nwp - 1 && std::hypot(Val(bx) - wpx[wi], Val(by) - wpy[wi]) < s.wp_switch) ++wi;
+        if (wi < nwp - 1) {  // an intermediate waypoint: PD towards it
+          gx = R(wpx[wi]); gy = R(wpy[wi]);
+          Ix = Iy = R(0.0);
+        } else {  // the goal: PID, integrating the error near it
+          const R ex_ = mgx - bx, ey_ = mgy - by;
+          if (Val(Sqrt(ex_ * ex_ + ey_ * ey_)) < s.pid_irad) {
+            Ix = Min(Max(Ix + ex_ * R(dt), R(-s.pid_imax)), R(s.pid_imax));
+            Iy = Min(Max(Iy + ey_ * R(dt), R(-s.pid_imax)), R(s.pid_imax));
+          } else {
+            Ix = Iy = R(0.0);
+          }
+          fix = R(s.pid_ki) * kp * Ix;
+          fiy = R(s.pid_ki) * kp * Iy;
+        }
+      }
     } else if (kind == OR_GRASP) {
       tx = ox; ty = oy; tz = oz + hgrip;
       gx = ox - R(s.grasp_reach) * caz;
@@ -458,6 +491,10 @@ void pickplace_rollout(const or_scene& s, const double* th, int T, R& J_out, int
     // base: PD + penalty contacts against the static footprints
     R fx = R(m) * (kp * (gx - bx) - kd * bvx);
     R fy = R(m) * (kp * (gy - by) - kd * bvy);
+    if (astar && kind == OR_MOVE) {
+      fx = fx + R(m) * fix;
+      fy = fy + R(m) * fiy;
+    }
     for (int gi = 0; gi < s.n_geoms; ++gi) {
       if (!s.geom_base[gi]) continue;
       R nx, ny, nz, dep;
@@ -601,7 +638,7 @@ void rollout_one(const or_scene& s, const Prep& pp, const double* theta, int T, 
     case OR_QUAD: quadratic_cost(s, th, J, cls); break;
     case OR_REACH:
     case OR_PUSH: planar_rollout(s, pp, th, T, J, cls, trace); break;
-    case OR_PICKPLACE: pickplace_rollout(s, th, T, J, cls, trace); break;
+    case OR_PICKPLACE: pickplace_rollout(s, pp, th, T, J, cls, trace); break;
     default: J = R(NAN); cls = 3;
   }
 }

@@ -181,7 +181,8 @@ def _pp_boxes(rng, n=3, half=0.2, height=0.4):
 
 
 def pickplace_scene(seed: int = 0, n_actions: int = 5, T: int = 3000, dt: float = 0.002,
-                    cost_mode: str = "interp", obstacle: str = "ramp", regions: str = "box"):
+                    cost_mode: str = "interp", obstacle: str = "ramp", regions: str = "box",
+                    controller: str = "pd"):
     """Pick-and-place with a ramp (or box) obstacle between two tables.
 
     Per scene: ramp slope ~ U[15, 30] deg, object friction mu ~ U[0.2, 0.4],
@@ -194,9 +195,17 @@ def pickplace_scene(seed: int = 0, n_actions: int = 5, T: int = 3000, dt: float 
     rings, radii scaled to these 0.6 m tables and the 4 m arena: 0.65..0.9 m),
     with the move bounds widened to contain them; the other parameters keep
     their boxes (the Exit box is the paper's 1 x 1 m rectangle).
+
+    ``controller="astar"`` drives every moveTo of the base along A* waypoints
+    (footprints grown by the base's half-diagonal) tracked by PD, switching
+    within 0.25 m, with an integral term (gain 2 kp, active within 0.3 m of
+    the goal, |I| <= 0.5 m s) on the final one, as in the paper's experiments;
+    the default "pd" drives straight at the goal.
     """
     if regions not in ("box", "paper"):
         raise ValueError("regions is 'box' or 'paper'")
+    if controller not in ("pd", "astar"):
+        raise ValueError("controller is 'pd' or 'astar'")
     if not 3 <= n_actions <= 6:
         raise ValueError("pick-place skeletons have 3..6 actions")
     rng = np.random.default_rng(seed)
@@ -241,6 +250,9 @@ def pickplace_scene(seed: int = 0, n_actions: int = 5, T: int = 3000, dt: float 
         geoms=geoms,
         slope=slope, ramp_top=z_hi, boxes=boxes,
     )
+    if controller == "astar":
+        scene.update(base_controller="astar", base_inflate=math.hypot(0.25, 0.20), wp_switch=0.25,
+                     pid_ki=2.0, pid_irad=0.3, pid_imax=0.5)
     mv = lambda nom: dict(kind="move", nominal=(nom[0], nom[1], 0.0), yaw=0.0, success_ref="target")
     acts, lo, hi = [], [], []
     ring = lambda t: dict(kind="ring", center=(t[0], t[1]), radii=(0.65, 0.9))

@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
     ap.add_argument("--tpr", type=int, default=1,
                     help="lanes per pick-and-place rollout for --rollout-only (1, 8 or 32)")
+    ap.add_argument("--controller", choices=["pd", "astar"], default="pd",
+                    help="moveTo controller of the pick-place base for --rollout-only pickplace")
     ap.add_argument("--block", type=int, default=0,
                     help="rollout threads per CTA for --rollout-only (0 = the library's choice)")
     ap.add_argument("--skip-surrogate", action="store_true", help="leave out the time-to-cost comparison")
@@ -444,7 +446,8 @@ def run_rollout_only(args):
     build.build()
     P.load()
     cfg = {"reach": 0, "push": 1, "pickplace": 2}[args.rollout_only]
-    sc, sk, cm = workload.config(cfg, seed=args.seed)
+    kw = {"controller": args.controller} if cfg == 2 else {}
+    sc, sk, cm = workload.config(cfg, seed=args.seed, **kw)
     N = args.n or cm["N"]
     T, D = sc["T"], len(sk["lo"])
     lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
@@ -470,7 +473,7 @@ def run_rollout_only(args):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     tf = fps["flops"] * N * T / (ms / 1e3) / 1e12
-    print(json.dumps({"rollout_only": cm["name"], "N": N, "T": T, "D": D, "block": args.block, "tpr": args.tpr, "ms": ms,
+    print(json.dumps({"rollout_only": cm["name"], "N": N, "T": T, "D": D, "block": args.block, "tpr": args.tpr, "controller": args.controller if cfg == 2 else None, "ms": ms,
                       "sim_steps_per_s": N * T / (ms / 1e3), "achieved_tflops": tf, "frac": tf / peak,
                       "classes": np.bincount(cls.cpu().numpy(), minlength=4).tolist()}), flush=True)
 

@@ -50,6 +50,7 @@ extern "C" {
 #define CEM_MAX_N (1 << 20)
 #define CEM_TRACE_W 20
 #define CEM_MAX_BATCH 1024
+#define CEM_MAX_CORNERS 48 /* corners of the base planner's visibility graph */
 
 typedef enum {
   CEM_OK = 0,
@@ -125,6 +126,18 @@ typedef struct {
   cem_geom geom[CEM_MAX_GEOMS];
   float theta_star[CEM_MAX_D];
   float A[CEM_MAX_D * CEM_MAX_D];
+  /* moveTo controller of the pick-place base (Sec. IV-A: A* paths tracked by
+   * a PID controller).  0: PD straight at the goal.  1: A* over the
+   * visibility graph of the base footprints (slabs with n_z == 0 of bodies
+   * with collide_base) grown by base_inflate along their normals (corners
+   * pushed 1 mm out, at most CEM_MAX_CORNERS; a footprint holding an
+   * endpoint is used ungrown, or skipped, for that endpoint's edges),
+   * planned when the action starts; waypoints tracked by PD, advancing
+   * within wp_switch of one, the goal by PID with integral gain
+   * pid_ki * kp, integrating only within pid_irad of the goal, |I| <=
+   * pid_imax per axis. */
+  int32_t base_controller;
+  float base_inflate, wp_switch, pid_ki, pid_irad, pid_imax;
 } cem_scene_desc;
 
 typedef struct {
@@ -254,6 +267,12 @@ typedef struct {
   int32_t* n_env_hist_h;        /* iters values or NULL */
 } cem_paper_params;
 int cem_solve_paper(cem_handle h, const cem_paper_params* p, cem_result* out);
+/* The A* path the pick-place base follows from (sx, sy) to (gx, gy) in a
+ * scene with base_controller 1 (the rollout's planner, run on the device):
+ * *n_out waypoints after the start, ending with the goal, the first `cap`
+ * written to xy_h[2 i], xy_h[2 i + 1].  CEM_ERR_UNSUPPORTED without the A*
+ * controller.  Synchronous. */
+int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* xy_h, int cap, int* n_out);
 /* n_env of iteration j under the schedule (n0, n1, j1) (host function). */
 int cem_n_env(int n0, int n1, int j1, int j);
 

@@ -34,7 +34,7 @@ EXPORTS = [
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
     "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
     "cem_set_randomization",
-    "cem_batch_set_active", "cem_multiplan_solve",
+    "cem_batch_set_active", "cem_multiplan_solve", "cem_base_path",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -86,6 +86,8 @@ class cem_scene_desc(C.Structure):
         ("n_geoms", C.c_int32),
         ("geom", cem_geom * MAX_GEOMS),
         ("theta_star", C.c_float * MAX_D), ("A", C.c_float * (MAX_D * MAX_D)),
+        ("base_controller", C.c_int32), ("base_inflate", C.c_float), ("wp_switch", C.c_float),
+        ("pid_ki", C.c_float), ("pid_irad", C.c_float), ("pid_imax", C.c_float),
     ]
 
 
@@ -180,6 +182,10 @@ def pack_scene(scene: dict, skel: dict, T: int | None = None):
     D = len(skel["lo"])
     if D > MAX_D:
         raise ValueError("D > 18")
+    if scene.get("base_controller", "pd") == "astar":  # A* waypoints + PID (Sec. IV-A)
+        s.base_controller = 1
+        s.base_inflate, s.wp_switch = scene["base_inflate"], scene["wp_switch"]
+        s.pid_ki, s.pid_irad, s.pid_imax = scene["pid_ki"], scene["pid_irad"], scene["pid_imax"]
     if scene["kind"] == "quadratic":
         _set(s.theta_star, scene["theta_star"])
         for i in range(D * D):
@@ -234,6 +240,8 @@ def load(path: str = LIB_PATH):
     L.cem_n_env.argtypes = [C.c_int] * 4
     L.cem_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
     L.cem_batch_set_active.argtypes = [H, C.POINTER(C.c_int32)]
+    L.cem_base_path.argtypes = [H, C.c_float, C.c_float, C.c_float, C.c_float, C.POINTER(C.c_float), C.c_int,
+                                C.POINTER(C.c_int)]
     L.cem_multiplan_solve.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc), C.c_int,
                                       C.POINTER(cem_multiplan_params), C.POINTER(cem_result),
                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
@@ -360,6 +368,15 @@ def cem_sample_uniform(h, seed, problem, N, theta, stream=None):
 
 def cem_set_randomization(h, M, delta_mu, delta_mass, seed):
     _check(load().cem_set_randomization(h, int(M), float(delta_mu), float(delta_mass), int(seed)))
+
+
+def cem_base_path(h, start, goal):
+    """Waypoints (n, 2) of the A* path of the pick-place base, ending with the goal."""
+    xy = np.zeros(2 * 64, np.float32)
+    n = C.c_int(0)
+    _check(load().cem_base_path(h, float(start[0]), float(start[1]), float(goal[0]), float(goal[1]),
+                                xy.ctypes.data_as(C.POINTER(C.c_float)), 64, C.byref(n)))
+    return xy[:2 * min(n.value, 64)].reshape(-1, 2)
 
 
 def cem_n_env(n0, n1, j1, j):
@@ -836,6 +853,10 @@ class Scene:
                     mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
                     iters_done=r.iters_done, elapsed_ms=r.elapsed_ms, history=hist, k_eff=keff,
                     class_counts=counts, n_env=ns)
+
+    def base_path(self, start, goal):
+        """The A* waypoints the base would follow (A* controller scenes)."""
+        return cem_base_path(self.h, start, goal)
 
     def sample_uniform(self, seed, N, problem=0, stream=None):
         import torch

@@ -3,6 +3,7 @@
 // (Sec. III-B) with one iteration captured in a CUDA graph.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "plan.cuh"
 
 using namespace cem;
 
@@ -89,6 +91,126 @@ struct cem_ctx {
 
 namespace {
 
+// ---- base planner graph (A* moveTo controller), built once per scene in FP64
+// Footprint of body g: its slabs with a horizontal normal, every finite
+// bound moved out by r.
+struct HostFootprint {
+  int n;
+  double nx[CEM_MAX_SLABS], ny[CEM_MAX_SLABS], lo[CEM_MAX_SLABS], hi[CEM_MAX_SLABS];
+};
+
+bool host_footprint(const cem_geom& g, double r, HostFootprint& f) {
+  f.n = 0;
+  for (int i = 0; i < g.n_slabs; ++i) {
+    const cem_slab& sl = g.slab[i];
+    if (sl.n[2] != 0.0f) continue;
+    const double lo = sl.lo, hi = sl.hi;
+    f.nx[f.n] = sl.n[0];
+    f.ny[f.n] = sl.n[1];
+    f.lo[f.n] = std::fabs(lo) < 1e6 ? lo - r : lo;
+    f.hi[f.n] = std::fabs(hi) < 1e6 ? hi + r : hi;
+    ++f.n;
+  }
+  return f.n > 0;
+}
+
+bool host_inside(const HostFootprint& f, double x, double y) {
+  for (int i = 0; i < f.n; ++i) {
+    const double p = f.nx[i] * x + f.ny[i] * y;
+    if (!(p > f.lo[i] && p < f.hi[i])) return false;
+  }
+  return true;
+}
+
+// does the open segment a -> b cross the footprint's interior (clipping the
+// segment parameter against every slab)?
+bool host_crosses(const HostFootprint& f, double ax, double ay, double bx, double by) {
+  double t0 = 0.0, t1 = 1.0;
+  for (int i = 0; i < f.n; ++i) {
+    const double p0 = f.nx[i] * ax + f.ny[i] * ay, dp = f.nx[i] * (bx - ax) + f.ny[i] * (by - ay);
+    const double lo = f.lo[i] + 1e-9, hi = f.hi[i] - 1e-9;
+    if (std::fabs(dp) < 1e-15) {
+      if (p0 <= lo || p0 >= hi) return false;
+      continue;
+    }
+    const double ta = (lo - p0) / dp, tb = (hi - p0) / dp;
+    t0 = std::max(t0, std::min(ta, tb));
+    t1 = std::min(t1, std::max(ta, tb));
+    if (t0 >= t1) return false;
+  }
+  return t0 < t1;
+}
+
+// corners of the grown footprints (pushed 1 mm out, outside every grown
+// footprint) and their mutual visibility; -1 if there are more than
+// CEM_MAX_CORNERS
+int build_base_graph(const cem_scene_desc& s, DevScene& d) {
+  HostFootprint fp[CEM_MAX_GEOMS];
+  int nf = 0;
+  for (int g = 0; g < s.n_geoms; ++g)
+    if (s.geom[g].collide_base && host_footprint(s.geom[g], s.base_inflate, fp[nf])) ++nf;
+  std::vector<double> cx, cy;
+  for (int k = 0; k < nf; ++k) {
+    const HostFootprint& f = fp[k];
+    for (int i = 0; i < f.n; ++i)
+      for (int j = i + 1; j < f.n; ++j)
+        for (int ui = 0; ui < 2; ++ui)
+          for (int uj = 0; uj < 2; ++uj) {
+            const double bi = ui ? f.hi[i] : f.lo[i], bj = uj ? f.hi[j] : f.lo[j];
+            if (std::fabs(bi) >= 1e6 || std::fabs(bj) >= 1e6) continue;
+            const double det = f.nx[i] * f.ny[j] - f.ny[i] * f.nx[j];
+            if (std::fabs(det) < 1e-12) continue;
+            double x = (bi * f.ny[j] - bj * f.ny[i]) / det, y = (f.nx[i] * bj - f.nx[j] * bi) / det;
+            bool on = true;
+            for (int m = 0; m < f.n && on; ++m)
+              if (m != i && m != j) {
+                const double p = f.nx[m] * x + f.ny[m] * y;
+                on = p >= f.lo[m] - 1e-9 && p <= f.hi[m] + 1e-9;
+              }
+            if (!on) continue;
+            const double ox = (ui ? f.nx[i] : -f.nx[i]) + (uj ? f.nx[j] : -f.nx[j]);
+            const double oy = (ui ? f.ny[i] : -f.ny[i]) + (uj ? f.ny[j] : -f.ny[j]);
+            const double len = std::sqrt(ox * ox + oy * oy);
+            x += 1e-3 * ox / len;
+            y += 1e-3 * oy / len;
+            bool clear = true;
+            for (int q = 0; q < nf && clear; ++q) clear = !host_inside(fp[q], x, y);
+            if (!clear) continue;
+            cx.push_back(x);
+            cy.push_back(y);
+          }
+  }
+  if ((int)cx.size() > CEM_MAX_CORNERS) return -1;
+  d.n_corners = (int)cx.size();
+  for (int a = 0; a < d.n_corners; ++a) {
+    d.corner[a][0] = (float)cx[a];
+    d.corner[a][1] = (float)cy[a];
+    d.corner_vis[a] = 0;
+  }
+  for (int a = 0; a < d.n_corners; ++a)
+    for (int b = a + 1; b < d.n_corners; ++b) {
+      bool vis = true;
+      for (int q = 0; q < nf && vis; ++q) vis = !host_crosses(fp[q], cx[a], cy[a], cx[b], cy[b]);
+      if (vis) {
+        d.corner_vis[a] |= 1ull << b;
+        d.corner_vis[b] |= 1ull << a;
+      }
+    }
+  return d.n_corners;
+}
+
+// the planner of the rollout, one query (for cem_base_path)
+__global__ void base_path_kernel(const DevScene* __restrict__ s, float sx, float sy, float gx, float gy, float* xy,
+                                 int* n) {
+  float wx[kMaxWaypoints], wy[kMaxWaypoints];
+  const int k = plan_base_path(*s, sx, sy, gx, gy, wx, wy);
+  for (int i = 0; i < k; ++i) {
+    xy[2 * i] = wx[i];
+    xy[2 * i + 1] = wy[i];
+  }
+  *n = k;
+}
+
 int validate(const cem_scene_desc* s, const cem_skeleton_desc* k) {
   if (!s || !k) return fail(CEM_ERR_INVALID_ARG, "scene and skeleton descriptors are required");
   if (s->kind < CEM_SCENE_QUADRATIC || s->kind > CEM_SCENE_PICKPLACE) return fail(CEM_ERR_INVALID_ARG, "unknown scene kind");
@@ -129,6 +251,15 @@ int validate(const cem_scene_desc* s, const cem_skeleton_desc* k) {
   if (s->kind == CEM_SCENE_PUSH && !(s->block_mass > 0.0f)) return fail(CEM_ERR_INVALID_ARG, "block mass must be positive");
   if (s->kind == CEM_SCENE_PICKPLACE && !(s->obj_mass > 0.0f && s->arm_l1 > 0.0f && s->arm_l2 > 0.0f))
     return fail(CEM_ERR_INVALID_ARG, "object mass and arm links must be positive");
+  if (s->base_controller != 0 && s->base_controller != 1) return fail(CEM_ERR_INVALID_ARG, "base_controller is 0 or 1");
+  if (s->base_controller == 1) {
+    if (s->kind != CEM_SCENE_PICKPLACE) return fail(CEM_ERR_INVALID_ARG, "the A* base controller is for pick-place");
+    if (!(s->base_inflate >= 0.0f) || !(s->wp_switch > 0.0f) || !(s->pid_ki >= 0.0f) || !(s->pid_irad >= 0.0f) ||
+        !(s->pid_imax >= 0.0f) || !std::isfinite(s->base_inflate + s->wp_switch + s->pid_ki + s->pid_irad + s->pid_imax))
+      return fail(CEM_ERR_INVALID_ARG, "A* controller: inflate, integral gain/radius/limit >= 0, switch radius > 0");
+    DevScene tmp;
+    if (build_base_graph(*s, tmp) < 0) return fail(CEM_ERR_UNSUPPORTED, "more than 48 planner corners");
+  }
   return CEM_OK;
 }
 
@@ -237,6 +368,15 @@ DevScene prepare(const cem_scene_desc& s, const cem_skeleton_desc& k) {
   }
   for (int i = 0; i < CEM_MAX_D; ++i) d.theta_star[i] = s.theta_star[i];
   for (int i = 0; i < k.D * k.D; ++i) d.A[i] = s.A[i];
+  if (s.kind == CEM_SCENE_PICKPLACE && s.base_controller == 1) {
+    d.base_ctrl = 1;
+    d.base_infl = s.base_inflate;
+    d.wp_switch = s.wp_switch;
+    d.pid_ki = s.pid_ki;
+    d.pid_irad = s.pid_irad;
+    d.pid_imax = s.pid_imax;
+    build_base_graph(s, d);
+  }
   return d;
 }
 
@@ -682,6 +822,32 @@ int cem_solve(cem_handle h, const cem_solve_params* p, cem_result* out) {
   }
   CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
   return cem::handle_read_result(h, p, &b, out);
+}
+
+int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* xy_h, int cap, int* n_out) {
+  g_err.clear();
+  if (!h || !n_out) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  if (!h->host.base_ctrl) return fail(CEM_ERR_UNSUPPORTED, "the scene has no A* base controller");
+  if (cap < 0 || (cap > 0 && !xy_h)) return fail(CEM_ERR_INVALID_ARG, "cap >= 0 and an output array");
+  float* buf = nullptr;
+  int* cnt = nullptr;
+  CEM_CUDA(cudaMalloc(&buf, sizeof(float) * 2 * kMaxWaypoints));
+  cudaError_t e = cudaMalloc(&cnt, sizeof(int));
+  if (e == cudaSuccess) {
+    base_path_kernel<<<1, 1, 0, h->stream>>>(h->scene_d, sx, sy, gx, gy, buf, cnt);
+    e = cudaGetLastError();
+  }
+  float out[2 * kMaxWaypoints];
+  int n = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&n, cnt, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf, sizeof(out), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(buf);
+  cudaFree(cnt);
+  if (e != cudaSuccess) return cuda_fail(e, "cem_base_path");
+  for (int i = 0; i < 2 * std::min(n, cap); ++i) xy_h[i] = out[i];
+  *n_out = n;
+  return CEM_OK;
 }
 
 int cem_n_env(int n0, int n1, int j1, int j) {

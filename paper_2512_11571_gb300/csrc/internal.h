@@ -48,6 +48,12 @@ struct DevScene {
   // quadratic
   float theta_star[CEM_MAX_D];
   float A[CEM_MAX_D * CEM_MAX_D];
+  // A* base controller (pick-place): grown-footprint corners and their
+  // mutual visibility (bit j of corner_vis[i]), built on the host
+  int32_t base_ctrl, n_corners;
+  float base_infl, wp_switch, pid_ki, pid_irad, pid_imax, pad3;
+  float corner[CEM_MAX_CORNERS][2];
+  uint64_t corner_vis[CEM_MAX_CORNERS];
 };
 
 // Best-ever sample and iteration counter of a device-resident CE loop.

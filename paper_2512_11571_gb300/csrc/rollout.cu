@@ -18,6 +18,7 @@
 // the FP32 pipe and by instruction latency, not by HBM.
 #include "internal.h"
 #include "philox.cuh"
+#include "plan.cuh"
 
 namespace cem {
 namespace {
@@ -731,6 +732,11 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
   // once per event instead of once per lane.
   constexpr float kSkin = 0.15f, kRebuild = 0.075f;
   const unsigned lanes = __activemask();
+  // A* base controller: waypoints of the current moveTo, integral state
+  const bool astar = s.base_ctrl != 0;
+  float wpx[kMaxWaypoints], wpy[kMaxWaypoints];
+  int nwp = 0, wi = 0;
+  float Ix = 0.f, Iy = 0.f;
   uint32_t bmask = 0, omask = 0;
   float brx = 1e30f, bry = 1e30f, orx = 1e30f, ory = 1e30f, orz = 1e30f;
   for (int step = 0; step < T; ++step) {
@@ -745,6 +751,11 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
         mkd = 2.0f * sqrtf(mkp);
         rx = s.act_ref[ai] ? mgx : s.act_nom[ai][0];
         ry = s.act_ref[ai] ? mgy : s.act_nom[ai][1];
+        if (astar) {  // plan from where the base is now
+          nwp = plan_base_path(s, bx, by, mgx, mgy, wpx, wpy);
+          wi = 0;
+          Ix = Iy = 0.f;
+        }
       } else if (kind == CEM_ACT_GRASP) {
         sincosf(theta_at(s, row, o), &saz, &caz);
         hgrip = theta_at(s, row, o + 1);
@@ -758,11 +769,32 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
       loaded = ai;
     }
     float tx = 0.f, ty = 0.f, tz = 0.f;
+    float fix = 0.f, fiy = 0.f;  // integral force per unit mass
     if (kind == CEM_ACT_MOVE) {
       gx = mgx;
       gy = mgy;
       kp = mkp;
       kd = mkd;
+      if (astar) {
+        // past every waypoint already within the switching radius
+        while (wi < nwp - 1 && sqrtf((bx - wpx[wi]) * (bx - wpx[wi]) + (by - wpy[wi]) * (by - wpy[wi])) < s.wp_switch)
+          ++wi;
+        if (wi < nwp - 1) {  // an intermediate waypoint: PD towards it
+          gx = wpx[wi];
+          gy = wpy[wi];
+          Ix = Iy = 0.f;
+        } else {  // the goal: PID, integrating the error near it
+          const float ex_ = mgx - bx, ey_ = mgy - by;
+          if (sqrtf(ex_ * ex_ + ey_ * ey_) < s.pid_irad) {
+            Ix = fminf(fmaxf(Ix + ex_ * dt, -s.pid_imax), s.pid_imax);
+            Iy = fminf(fmaxf(Iy + ey_ * dt, -s.pid_imax), s.pid_imax);
+          } else {
+            Ix = Iy = 0.f;
+          }
+          fix = s.pid_ki * kp * Ix;
+          fiy = s.pid_ki * kp * Iy;
+        }
+      }
     } else if (kind == CEM_ACT_GRASP) {
       tx = ox;
       ty = oy;
@@ -787,6 +819,10 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
     // base: PD + penalty contacts with the static footprints
     float fx = mb * (kp * (gx - bx) - kd * bvx);
     float fy = mb * (kp * (gy - by) - kd * bvy);
+    if (astar && kind == CEM_ACT_MOVE) {
+      fx += mb * fix;
+      fy += mb * fiy;
+    }
     if (__any_sync(lanes, fmaxf(fabsf(bx - brx), fabsf(by - bry)) >= kRebuild)) {
       bmask = near_list<true, G>(s, n_geoms, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, kSkin, grp);
       brx = bx;

@@ -18,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -64,6 +65,11 @@ struct GemmArgs {
   const float* bias;   // EPI_BIAS_GELU
   const float* zsave;  // EPI_GELU_BWD
   int ldz;
+  // EPI_F32 split-K: blockIdx.z takes rows [z kchunk, (z + 1) kchunk) of the
+  // reduction and writes its partial tile to part + z M N (row-major); the
+  // partials are then summed in z order (deterministic)
+  int kchunk;
+  float* part;
 };
 
 constexpr int BM = 128, BN = 128, BK = 32, PADK = 8, GT = 256;
@@ -91,7 +97,9 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(GemmArgs g) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
   const bf16 zero = __float2bfloat16_rn(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  const int kbeg = g.kchunk > 0 ? (int)blockIdx.z * g.kchunk : 0;
+  const int kend = g.kchunk > 0 ? min(g.K, kbeg + g.kchunk) : g.K;
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll 4
     for (int i = 0; i < BM * BK / GT; ++i) {
       const int e = tid + i * GT;
@@ -99,7 +107,7 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(GemmArgs g) {
       const int c = g.a_kmajor ? e % BK : e / BM;
       const int m = m0 + r, k = k0 + c;
       bf16 v = zero;
-      if (m < g.M && k < g.K) v = g.a_kmajor ? g.A[(size_t)m * g.lda + k] : g.A[(size_t)k * g.lda + m];
+      if (m < g.M && k < kend) v = g.a_kmajor ? g.A[(size_t)m * g.lda + k] : g.A[(size_t)k * g.lda + m];
       As[r][c] = v;
     }
 #pragma unroll 4
@@ -109,7 +117,7 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(GemmArgs g) {
       const int c = g.b_kmajor ? e % BK : e / BN;
       const int n = n0 + r, k = k0 + c;
       bf16 v = zero;
-      if (n < g.N && k < g.K) v = g.b_kmajor ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
+      if (n < g.N && k < kend) v = g.b_kmajor ? g.B[(size_t)n * g.ldb + k] : g.B[(size_t)k * g.ldb + n];
       Bs[r][c] = v;
     }
     __syncthreads();
@@ -148,7 +156,8 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(GemmArgs g) {
         if (m >= g.M || n >= g.N) continue;
         const float v = acc[mt][nt][q];
         if (EPI == EPI_F32) {
-          g.C[(size_t)m * g.ldc + n] = v;
+          if (g.part) g.part[((size_t)blockIdx.z * g.M + m) * g.N + n] = v;
+          else g.C[(size_t)m * g.ldc + n] = v;
         } else if (EPI == EPI_BIAS_GELU) {
           const float z = v + g.bias[n];
           if (g.C) g.C[(size_t)m * g.ldc + n] = z;
@@ -159,12 +168,41 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(GemmArgs g) {
       }
 }
 
+// C[m, n] = sum over z of part[z][m][n], in z order
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C, int ldc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M * N) return;
+  float acc = 0.0f;
+  for (int z = 0; z < S; ++z) acc += part[(size_t)z * M * N + i];
+  C[(size_t)(i / N) * ldc + i % N] = acc;
+}
+
 template <int EPI>
 cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  gemm_bf16_kernel<EPI><<<grid, GT, 0, st>>>(g);
+  const int S = (EPI == EPI_F32 && g.part && g.kchunk > 0) ? (g.K + g.kchunk - 1) / g.kchunk : 1;
+  GemmArgs h = g;
+  if (S == 1) {  // one chunk: write C directly
+    h.kchunk = 0;
+    h.part = nullptr;
+  }
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, S);
+  gemm_bf16_kernel<EPI><<<grid, GT, 0, st>>>(h);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || S == 1 || EPI != EPI_F32) return e;
+  splitk_sum_kernel<<<(g.M * g.N + 255) / 256, 256, 0, st>>>(g.part, S, g.M, g.N, g.C, g.ldc);
   return cudaGetLastError();
+}
+
+// split of a K-long reduction into at most kMaxSplit chunks of >= 256 rows
+// (a multiple of the K tile), so the weight-gradient GEMMs fill the GPU
+constexpr int kMaxSplit = 32;
+int split_chunk(int K) {
+  int S = (K + 255) / 256;
+  if (S > kMaxSplit) S = kMaxSplit;
+  if (S < 1) S = 1;
+  const int c = (K + S - 1) / S;
+  return (c + BK - 1) / BK * BK;
 }
 
 // -------------------------------------------------------------- small kernels
@@ -487,6 +525,7 @@ struct cem_surrogate_ctx {
   float* tb = nullptr;
   float* partial = nullptr;
   float* loss_d = nullptr;
+  float* splitk = nullptr;  // split-K partials of the weight gradients
   // screening workspace
   int cap_pool = 0;
   float* pool_theta = nullptr;
@@ -519,6 +558,8 @@ void sur_free_work(cem_surrogate_ctx* s) {
   cudaFree(s->tb);
   cudaFree(s->partial);
   cudaFree(s->loss_d);
+  cudaFree(s->splitk);
+  s->splitk = nullptr;
   s->xin = nullptr;
   s->dz_a = s->dz_b = nullptr;
   s->raw = s->dy = s->tb = s->partial = s->loss_d = nullptr;
@@ -546,6 +587,7 @@ int ensure_rows(cem_surrogate_ctx* s, int M) {
   A((void**)&s->tb, sizeof(float) * M);
   A((void**)&s->partial, sizeof(float) * ((M + 255) / 256 + 1));
   A((void**)&s->loss_d, sizeof(float));
+  A((void**)&s->splitk, sizeof(float) * (size_t)kMaxSplit * s->width * std::max(s->width, s->in_dim));
   if (e != cudaSuccess) {
     cudaGetLastError();
     sur_free_work(s);
@@ -649,6 +691,8 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
     g.b_kmajor = 0;
     g.C = s->g + s->w_off[l];
     g.ldc = K;
+    g.kchunk = split_chunk(M);
+    g.part = s->splitk;
     cudaError_t e = gemm<EPI_F32>(g, st);
     if (e != cudaSuccess) return e;
     colsum_kernel<<<(W + 127) / 128, 128, 0, st>>>(dz, nullptr, M, W, s->g + s->b_off[l]);
@@ -881,8 +925,11 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   if (!is_dev(x_d) || !is_dev(t_d)) return fail(CEM_ERR_INVALID_ARG, "x and t must be device pointers");
   // whole data set in BF16 once
   bf16* Xall = nullptr;
-  if (cudaMalloc(&Xall, sizeof(bf16) * (size_t)M * s->in_dim) != cudaSuccess) {
+  float* hist_d = nullptr;  // per-step losses stay on the device until the end (no per-step sync)
+  if (cudaMalloc(&Xall, sizeof(bf16) * (size_t)M * s->in_dim) != cudaSuccess ||
+      (loss_hist_h && steps > 0 && cudaMalloc(&hist_d, sizeof(float) * (size_t)steps) != cudaSuccess)) {
     cudaGetLastError();
+    cudaFree(Xall);
     return fail(CEM_ERR_NO_MEMORY, "training set does not fit");
   }
   const size_t n = (size_t)M * s->in_dim;
@@ -891,6 +938,7 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   int rc = ensure_rows(s, batch);
   if (rc != CEM_OK) {
     cudaFree(Xall);
+    cudaFree(hist_d);
     return rc;
   }
   const Segs segs = param_segments(s);
@@ -908,14 +956,16 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
     adamw_kernel<<<(s->total + 255) / 256, 256>>>(s->p, s->g, s->m1, s->m2, s->pb, s->total, segs, lr, b1, b2, eps,
                                                   weight_decay, c1, c2);
     e = cudaGetLastError();
-    if (loss_hist_h && e == cudaSuccess) {
-      float l = 0.0f;
-      e = cudaMemcpy(&l, s->loss_d, sizeof(float), cudaMemcpyDeviceToHost);
-      loss_hist_h[it] = l / batch;
-    }
+    if (hist_d && e == cudaSuccess)
+      e = cudaMemcpyAsync(hist_d + it, s->loss_d, sizeof(float), cudaMemcpyDeviceToDevice, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (hist_d && e == cudaSuccess) {
+    e = cudaMemcpy(loss_hist_h, hist_d, sizeof(float) * (size_t)steps, cudaMemcpyDeviceToHost);
+    for (int it = 0; it < steps; ++it) loss_hist_h[it] /= (float)batch;
+  }
   cudaFree(Xall);
+  cudaFree(hist_d);
   if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("cem_surrogate_train: ") + cudaGetErrorString(e));
   return CEM_OK;
 }

@@ -101,10 +101,10 @@ __device__ __forceinline__ void yaw_sincos(float psi, float* sn, float* cs) {
   __sincosf(w, sn, cs);
 }
 
-__device__ __forceinline__ bool sat_rect(const B2& A, float ahx, float ahy, const B2& B, float bhx, float bhy,
-                                         float& nx, float& ny, float& depth, float& qx, float& qy) {
-  float sa, ca, sb, cb;
-  yaw_sincos(A.psi, &sa, &ca);
+// (sa, ca): A's yaw sine and cosine, already at hand in the caller
+__device__ __forceinline__ bool sat_rect(const B2& A, float sa, float ca, float ahx, float ahy, const B2& B, float bhx,
+                                         float bhy, float& nx, float& ny, float& depth, float& qx, float& qy) {
+  float sb, cb;
   yaw_sincos(B.psi, &sb, &cb);
   const float c = ca * cb + sa * sb, s = ca * sb - sa * cb;
   const float ac = fabsf(c), as = fabsf(s);
@@ -246,7 +246,7 @@ __device__ __noinline__ void planar_rollout(const DevScene& s, const float* __re
       yaw_sincos(b.psi, &sbp, &cbp);
       if (fabsf(cdx * cbp + cdy * sbp) < reach_u && fabsf(cdy * cbp - cdx * sbp) < reach_w) {
         float dep, qx, qy;
-        hit = sat_rect(b, bhx, bhy, k, khx, khy, nx, ny, dep, qx, qy);
+        hit = sat_rect(b, sbp, cbp, bhx, bhy, k, khx, khy, nx, ny, dep, qx, qy);
         if (hit) {
           rax = qx - b.x;
           ray = qy - b.y;

@@ -73,18 +73,17 @@ __device__ __forceinline__ bool endpoint_sees(const DevScene& s, float px, float
   return true;
 }
 
-// waypoints (wx, wy) of the path from (sx, sy) to (gx, gy), ending with the
-// goal; returns their number
-static __device__ __noinline__ int plan_base_path(const DevScene& s, float sx, float sy, float gx, float gy, float* wx,
-                                           float* wy) {
+// A* from (sx, sy) to (gx, gy) given the corners each endpoint sees;
+// writes the waypoints (wx, wy), ending with the goal, returns their number
+static __device__ __noinline__ int astar_base_path(const DevScene& s, float sx, float sy, float gx, float gy,
+                                                   uint64_t sees_s, uint64_t sees_g, float* wx, float* wy) {
   const int C = s.n_corners, S = C, Gn = C + 1, V = C + 2;
-  uint64_t sees_s = 0, sees_g = 0;  // corners visible from the start / the goal
-  for (int i = 0; i < C; ++i) {
-    if (endpoint_sees(s, sx, sy, s.corner[i][0], s.corner[i][1])) sees_s |= 1ull << i;
-    if (endpoint_sees(s, gx, gy, s.corner[i][0], s.corner[i][1])) sees_g |= 1ull << i;
-  }
   const bool direct = endpoint_sees(s, sx, sy, gx, gy) && endpoint_sees(s, gx, gy, sx, sy);
-  float g[kMaxWaypoints];
+  float g[kMaxWaypoints], h[kMaxWaypoints];  // cost so far, straight-line distance to the goal
+  for (int i = 0; i < C; ++i)
+    h[i] = sqrtf((s.corner[i][0] - gx) * (s.corner[i][0] - gx) + (s.corner[i][1] - gy) * (s.corner[i][1] - gy));
+  h[S] = sqrtf((sx - gx) * (sx - gx) + (sy - gy) * (sy - gy));
+  h[Gn] = 0.0f;
   int8_t parent[kMaxWaypoints];
   for (int i = 0; i < V; ++i) {
     g[i] = INFINITY;
@@ -98,9 +97,7 @@ static __device__ __noinline__ int plan_base_path(const DevScene& s, float sx, f
     float fu = INFINITY;
     for (uint64_t m = open; m; m &= m - 1ull) {
       const int i = __ffsll((long long)m) - 1;
-      const float xi = i < C ? s.corner[i][0] : (i == S ? sx : gx);
-      const float yi = i < C ? s.corner[i][1] : (i == S ? sy : gy);
-      const float f = g[i] + sqrtf((xi - gx) * (xi - gx) + (yi - gy) * (yi - gy));
+      const float f = g[i] + h[i];
       if (f < fu) {
         fu = f;
         u = i;
@@ -144,6 +141,56 @@ static __device__ __noinline__ int plan_base_path(const DevScene& s, float sx, f
     wy[k] = v < C ? s.corner[v][1] : gy;
   }
   return n;
+}
+
+}  // namespace cem
+
+namespace cem {
+
+// is corner i visible from endpoint (px, py)?  One compiled copy, so the
+// solo and the warp-cooperative queries decide every edge identically.
+static __device__ __noinline__ bool sees_corner(const DevScene& s, float px, float py, int i) {
+  return endpoint_sees(s, px, py, s.corner[i][0], s.corner[i][1]);
+}
+
+// corners visible from (px, py), tested by one thread
+__device__ __forceinline__ uint64_t corners_seen(const DevScene& s, float px, float py) {
+  uint64_t m = 0;
+  for (int i = 0; i < s.n_corners; ++i)
+    if (sees_corner(s, px, py, i)) m |= 1ull << i;
+  return m;
+}
+
+// the corner masks of lane `owner`'s endpoints, computed by all `lanes`
+// (each active lane takes every nact-th corner) and OR-reduced
+__device__ __forceinline__ void corners_seen_warp(const DevScene& s, unsigned lanes, float sx, float sy, float gx,
+                                                  float gy, uint64_t& ms, uint64_t& mg) {
+  const int lane = threadIdx.x & 31;
+  const int rank = __popc(lanes & ((1u << lane) - 1u)), nact = __popc(lanes);
+  uint32_t s_lo = 0, s_hi = 0, g_lo = 0, g_hi = 0;
+  for (int i = rank; i < s.n_corners; i += nact) {
+    const uint32_t bit = 1u << (i & 31);
+    if (sees_corner(s, sx, sy, i)) {
+      if (i < 32) s_lo |= bit;
+      else s_hi |= bit;
+    }
+    if (sees_corner(s, gx, gy, i)) {
+      if (i < 32) g_lo |= bit;
+      else g_hi |= bit;
+    }
+  }
+  s_lo = __reduce_or_sync(lanes, s_lo);
+  s_hi = __reduce_or_sync(lanes, s_hi);
+  g_lo = __reduce_or_sync(lanes, g_lo);
+  g_hi = __reduce_or_sync(lanes, g_hi);
+  ms = (uint64_t)s_lo | ((uint64_t)s_hi << 32);
+  mg = (uint64_t)g_lo | ((uint64_t)g_hi << 32);
+}
+
+// the whole path query by one thread
+static __device__ __noinline__ int plan_base_path(const DevScene& s, float sx, float sy, float gx, float gy, float* wx,
+                                                  float* wy) {
+  return astar_base_path(s, sx, sy, gx, gy, corners_seen(s, sx, sy), corners_seen(s, gx, gy), wx, wy);
 }
 
 }  // namespace cem

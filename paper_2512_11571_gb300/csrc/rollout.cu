@@ -737,6 +737,7 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
   float wpx[kMaxWaypoints], wpy[kMaxWaypoints];
   int nwp = 0, wi = 0;
   float Ix = 0.f, Iy = 0.f;
+  bool need_plan = false;
   uint32_t bmask = 0, omask = 0;
   float brx = 1e30f, bry = 1e30f, orx = 1e30f, ory = 1e30f, orz = 1e30f;
   for (int step = 0; step < T; ++step) {
@@ -751,8 +752,8 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
         mkd = 2.0f * sqrtf(mkp);
         rx = s.act_ref[ai] ? mgx : s.act_nom[ai][0];
         ry = s.act_ref[ai] ? mgy : s.act_nom[ai][1];
-        if (astar) {  // plan from where the base is now
-          nwp = plan_base_path(s, bx, by, mgx, mgy, wpx, wpy);
+        if (astar) {  // plan from where the base is now, below, with the whole warp's help
+          need_plan = true;
           wi = 0;
           Ix = Iy = 0.f;
         }
@@ -767,6 +768,23 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
         ptz = s.act_nom[ai][2] + theta_at(s, row, o + 2);
       }
       loaded = ai;
+    }
+    if (astar) {
+      // every lane that starts a moveTo this step gets its path in turn: all
+      // lanes split its corner-visibility tests, then it runs A* on the masks
+      // (the lanes of a lane group take their turns one by one, redundantly,
+      // so every group width runs this same code)
+      unsigned need = __ballot_sync(lanes, need_plan);
+      while (need) {
+        const int owner = __ffs(need) - 1;
+        need &= need - 1u;
+        const float sx = __shfl_sync(lanes, bx, owner), sy = __shfl_sync(lanes, by, owner);
+        const float qx = __shfl_sync(lanes, mgx, owner), qy = __shfl_sync(lanes, mgy, owner);
+        uint64_t ms, mg;
+        corners_seen_warp(s, lanes, sx, sy, qx, qy, ms, mg);
+        if ((int)(threadIdx.x & 31) == owner) nwp = astar_base_path(s, sx, sy, qx, qy, ms, mg, wpx, wpy);
+      }
+      need_plan = false;
     }
     float tx = 0.f, ty = 0.f, tz = 0.f;
     float fix = 0.f, fiy = 0.f;  // integral force per unit mass

@@ -329,6 +329,12 @@ int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm)
 int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float* best_ms_out);
 /* Simulated steps of one batch iteration: sum over problems of N * T. */
 long long cem_batch_steps_per_iteration(cem_batch_handle h);
+/* Domain randomisation of every problem of the batch, as
+ * cem_set_randomization for a single problem (environments of each problem's
+ * own iteration and Philox problem id, under `seed`): a batched problem
+ * equals cem_solve of that problem with the same randomisation.  The
+ * randomised samples take one lane per environment (lanes per rollout 1). */
+int cem_batch_set_randomization(cem_batch_handle h, int M, float delta_mu, float delta_mass, uint64_t seed);
 /* Which problems take part in the next iterations (active_h[n_problems],
  * non-zero = active).  An inactive problem is not sampled, rolled out or
  * refit: its distribution, best sample and iteration count stay as they
@@ -453,8 +459,9 @@ int cem_set_launch(cem_handle h, int block_threads);
  * the worst one (feasible only if feasible everywhere).  The M environments
  * of a sample run on M adjacent lanes (one lane each, whatever the lanes per
  * rollout setting) and are combined by warp shuffles.  M = 1 with both
- * spreads 0 switches it off.  Spreads in [0, 1).  Not applied to batches,
- * traces, the autotuner or cem_solve_static. */
+ * spreads 0 switches it off.  Spreads in [0, 1).  Batches take it from
+ * cem_batch_set_randomization; traces, the autotuner and cem_solve_static
+ * run without it. */
 int cem_set_randomization(cem_handle h, int M, float delta_mu, float delta_mass, uint64_t seed);
 /* Lanes per rollout for pick-and-place scenes: 1, 8 or 32 (other scene
  * kinds always take one lane; the trace always one).  A group of G lanes

@@ -35,6 +35,7 @@ EXPORTS = [
     "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
     "cem_set_randomization",
     "cem_batch_set_active", "cem_multiplan_solve", "cem_base_path",
+    "cem_batch_set_randomization",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -240,6 +241,7 @@ def load(path: str = LIB_PATH):
     L.cem_n_env.argtypes = [C.c_int] * 4
     L.cem_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
     L.cem_batch_set_active.argtypes = [H, C.POINTER(C.c_int32)]
+    L.cem_batch_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
     L.cem_base_path.argtypes = [H, C.c_float, C.c_float, C.c_float, C.c_float, C.POINTER(C.c_float), C.c_int,
                                 C.POINTER(C.c_int)]
     L.cem_multiplan_solve.argtypes = [C.POINTER(cem_scene_desc), C.POINTER(cem_skeleton_desc), C.c_int,
@@ -440,6 +442,10 @@ def cem_batch_create(problems):
     return h
 
 
+def cem_batch_set_randomization(h, M, delta_mu, delta_mass, seed):
+    _check(load().cem_batch_set_randomization(h, int(M), float(delta_mu), float(delta_mass), int(seed)))
+
+
 def cem_batch_set_active(h, active):
     a = np.ascontiguousarray(np.asarray(active, np.int32))
     _check(load().cem_batch_set_active(h, a.ctypes.data_as(C.POINTER(C.c_int32))))
@@ -550,6 +556,10 @@ class Batch:
 
     def set_threads_per_rollout(self, tpr):
         cem_batch_set_threads_per_rollout(self.h, tpr)
+
+    def set_randomization(self, M=1, delta_mu=0.0, delta_mass=0.0, seed=0):
+        """Domain randomisation of every problem (off: M=1, 0, 0)."""
+        cem_batch_set_randomization(self.h, M, delta_mu, delta_mass, seed)
 
     def set_active(self, active):
         """Which problems take part in the next iterations (reset: all)."""

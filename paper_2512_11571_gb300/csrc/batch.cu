@@ -56,6 +56,8 @@ struct cem_batch_ctx {
   int tpr = 1;                     // lanes per pick-and-place rollout (1, 8 or 32)
   std::vector<int> order;          // problems by descending work (the queue order)
   bool has_pickplace = false;
+  bool dr_on = false;  // domain randomisation of every problem's rollouts
+  DrArgs dr{};
   cudaGraphExec_t graph = nullptr;
   long long steps_per_iter = 0;
 };
@@ -110,7 +112,8 @@ cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st) {
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
-                                      h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, st);
+                                      h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, h->track_d,
+                                      h->dr_on ? &h->dr : nullptr, st);
   if (e != cudaSuccess) return e;
   return launch_refit_batch(h->args_d, h->P, h->maxK, h->maxD, st);
 }
@@ -396,7 +399,8 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
           if (e == cudaSuccess) e = cudaEventRecord(a, 0);
           if (e == cudaSuccess)
             e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d,
-                                                h->theta_d, h->J_d, h->cls_d, grid_size(h), w, t, 0);
+                                                h->theta_d, h->J_d, h->cls_d, grid_size(h), w, t, h->track_d,
+                                                h->dr_on ? &h->dr : nullptr, 0);
           if (e == cudaSuccess) e = cudaEventRecord(b, 0);
           if (e == cudaSuccess) e = cudaEventSynchronize(b);
           float ms = 0.0f;
@@ -433,6 +437,24 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
 }
 
 long long cem_batch_steps_per_iteration(cem_batch_handle h) { return h ? h->steps_per_iter : 0; }
+
+int cem_batch_set_randomization(cem_batch_handle h, int M, float delta_mu, float delta_mass, uint64_t seed) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (M < 1 || M > 32 || (M & (M - 1))) return fail(CEM_ERR_INVALID_ARG, "M must be 1, 2, 4, 8, 16 or 32");
+  if (!(delta_mu >= 0.0f && delta_mu < 1.0f) || !(delta_mass >= 0.0f && delta_mass < 1.0f))
+    return fail(CEM_ERR_INVALID_ARG, "spreads must lie in [0, 1)");
+  h->dr_on = !(M == 1 && delta_mu == 0.0f && delta_mass == 0.0f);
+  h->dr = DrArgs{};
+  h->dr.M = M;
+  h->dr.dmu = delta_mu;
+  h->dr.dm = delta_mass;
+  h->dr.seed = seed;
+  if (h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  return CEM_OK;
+}
 
 int cem_batch_set_active(cem_batch_handle h, const int32_t* active_h) {
   if (!h || !active_h) return fail(CEM_ERR_INVALID_ARG, "null argument");

@@ -145,7 +145,7 @@ cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
-                                            int tpr, cudaStream_t st);
+                                            int tpr, const Track* tracks, const DrArgs* dr, cudaStream_t st);
 int rollout_batch_max_ctas_per_sm(int warps, int tpr);
 
 // host helpers shared by the C entry points (capi.cu)

@@ -1086,7 +1086,8 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
                                                                  const BatchItem* __restrict__ items, int n_items,
                                                                  int* __restrict__ counter,
                                                                  const float* __restrict__ theta,
-                                                                 float* __restrict__ J, uint8_t* __restrict__ cls) {
+                                                                 float* __restrict__ J, uint8_t* __restrict__ cls,
+                                                                 const Track* __restrict__ tracks, const DrArgs dr) {
   __shared__ DevScene sc[kMaxBatchWarps];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DevScene& s = sc[w];
@@ -1105,7 +1106,41 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
       cur = item.problem;
     }
     const BatchProblem pb = probs[item.problem];
-    if (G > 1 && s.kind == CEM_SCENE_PICKPLACE) {
+    if (dr.M > 0 && s.kind != CEM_SCENE_QUADRATIC) {
+      // domain randomisation: the item's 32 samples in M passes, M lanes per
+      // sample (one environment each, of the problem's current iteration),
+      // combined as in the single-problem randomised kernel
+      const int M = dr.M, per = 32 / M, m = lane & (M - 1);
+      const uint32_t itn = tracks[item.problem].iter;
+      const unsigned gmask = M == 32 ? 0xffffffffu : (((1u << M) - 1u) << (lane & ~(M - 1)));
+      for (int sub = 0; sub < M; ++sub) {
+        const int n = item.first + sub * per + lane / M;
+        if (n < pb.N) {
+          uint32_t r[4];
+          philox4x32_10((uint32_t)m, 256u, itn, pb.problem, (uint32_t)dr.seed, (uint32_t)(dr.seed >> 32), r);
+          const float smu = fmaf(dr.dmu, fmaf(2.0f, u01(r[0]), -1.0f), 1.0f);
+          const float sm = fmaf(dr.dm, fmaf(2.0f, u01(r[1]), -1.0f), 1.0f);
+          const float* row = theta + pb.theta_off + (size_t)n * pb.D;
+          float Jn;
+          int c;
+          switch (s.kind) {
+            case CEM_SCENE_REACH: planar_rollout<false, false>(s, row, s.T, smu, sm, Jn, c, nullptr); break;
+            case CEM_SCENE_PUSH: planar_rollout<true, false>(s, row, s.T, smu, sm, Jn, c, nullptr); break;
+            default: pickplace_rollout<1, false>(s, row, s.T, smu, sm, Jn, c, nullptr); break;
+          }
+          for (int o = 1; o < M; o <<= 1) {
+            Jn += __shfl_xor_sync(gmask, Jn, o);
+            c = max(c, __shfl_xor_sync(gmask, c, o));
+          }
+          if (m == 0) {
+            const float mean = Jn * (1.0f / (float)M);
+            J[pb.sample_off + n] = mean;
+            cls[pb.sample_off + n] = (uint8_t)(isfinite(mean) ? c : 3);
+          }
+        }
+        __syncwarp();
+      }
+    } else if (G > 1 && s.kind == CEM_SCENE_PICKPLACE) {
       // G lanes per rollout: the 32-sample item in G passes of 32 / G
       for (int sub = 0; sub < G; ++sub) {
         const int n = item.first + sub * (32 / G) + lane / G;
@@ -1159,18 +1194,23 @@ int rollout_batch_max_ctas_per_sm(int warps, int tpr) {
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
-                                            int tpr, cudaStream_t st) {
+                                            int tpr, const Track* tracks, const DrArgs* dr_in, cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
   if (warps < 1 || warps > kMaxBatchWarps || grid < 1) return cudaErrorInvalidValue;
+  DrArgs dr{};  // M = 0: off
+  if (dr_in) {
+    if (dr_in->M < 1 || dr_in->M > 32 || (dr_in->M & (dr_in->M - 1)) || !tracks) return cudaErrorInvalidValue;
+    dr = *dr_in;
+  }
   if (tpr == 8)
     rollout_persistent_kernel<8><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                             J, cls);
+                                                             J, cls, tracks, dr);
   else if (tpr == 32)
     rollout_persistent_kernel<32><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                              J, cls);
+                                                              J, cls, tracks, dr);
   else if (tpr == 1)
     rollout_persistent_kernel<1><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                             J, cls);
+                                                             J, cls, tracks, dr);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -105,3 +105,28 @@ def test_randomisation_validation(P):
         for M, dmu, dm in ((3, 0.1, 0.1), (64, 0.1, 0.1), (0, 0.0, 0.0), (4, 1.0, 0.0), (4, 0.0, -0.1)):
             with pytest.raises(P.CemError):
                 S.set_randomization(M, dmu, dm)
+
+
+def test_batch_with_randomisation_equals_single_solves(P):
+    probs = []
+    sc, sk = workload.reach_scene(0)
+    probs.append(dict(scene=sc, skel=sk, N=200, K=20, seed=11))
+    sc, sk = workload.push_scene(1, T=500)
+    probs.append(dict(scene=sc, skel=sk, N=333, K=30, seed=12))
+    sc, sk = workload.pickplace_scene(2, T=600)
+    probs.append(dict(scene=sc, skel=sk, N=160, K=16, seed=13))
+    sc, sk = workload.quadratic_scene(3, D=6)  # no dynamics: nothing to randomise
+    probs.append(dict(scene=sc, skel=sk, N=256, K=32, seed=14))
+    for i, p in enumerate(probs):
+        p["problem"] = 300 + i
+    M, dmu, dm, seed = 4, 0.3, 0.3, 99
+    with P.Batch(probs) as B:
+        B.set_randomization(M, dmu, dm, seed)
+        B.iterate(3, use_graph=True)
+        got = B.read()
+    for pr, g in zip(probs, got):
+        with P.Scene(pr["scene"], pr["skel"]) as S:
+            S.set_randomization(M, dmu, dm, seed)
+            r = S.solve(pr["seed"], pr["N"], pr["K"], 3, problem=pr["problem"], use_graph=False)
+        assert g["best_J"] == r["best_J"] and g["best_cls"] == r["best_cls"]
+        assert np.array_equal(g["mean"], r["mean"]) and np.array_equal(g["cov"], r["cov"])

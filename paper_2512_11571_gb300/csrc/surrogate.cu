@@ -244,14 +244,45 @@ __global__ void loss_kernel(const float* __restrict__ raw, const float* __restri
   if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
 }
 
-// out[j] (+)= sum_m w[m] * X[m][j] in a fixed order (one thread per column)
-__global__ void colsum_kernel(const bf16* __restrict__ X, const float* __restrict__ w, int M, int N,
-                              float* __restrict__ out) {
+// Column sums in two deterministic stages: block (x, z) sums rows
+// [256 z, 256 z + 256) of 32 columns (8 row threads per column, rows in a
+// fixed interleave, then the 8 partials in order) into part[z][j]; a second
+// pass adds part[0..S)[j] in order.
+__global__ void __launch_bounds__(256) colsum_part_kernel(const bf16* __restrict__ X, const float* __restrict__ w,
+                                                          int M, int N, float* __restrict__ part) {
+  __shared__ float red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + tx, m0 = blockIdx.y * 256;
+  float acc = 0.0f;
+  if (j < N)
+    for (int r = ty; r < 256; r += 8) {
+      const int m = m0 + r;
+      if (m < M) acc = fmaf(w ? w[m] : 1.0f, __bfloat162float(X[(size_t)m * N + j]), acc);
+    }
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && j < N) {
+    float t = 0.0f;
+    for (int q = 0; q < 8; ++q) t += red[q][tx];
+    part[(size_t)blockIdx.y * N + j] = t;
+  }
+}
+
+__global__ void colsum_finish_kernel(const float* __restrict__ part, int S, int N, float* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  float s = 0.0f;
-  for (int m = 0; m < M; ++m) s = fmaf(w ? w[m] : 1.0f, __bfloat162float(X[(size_t)m * N + j]), s);
-  out[j] = s;
+  float t = 0.0f;
+  for (int z = 0; z < S; ++z) t += part[(size_t)z * N + j];
+  out[j] = t;
+}
+
+// out[j] = sum_m w[m] X[m][j] (w = 1 if null) with the two kernels above;
+// `part` holds ceil(M / 256) x N floats
+cudaError_t colsum(const bf16* X, const float* w, int M, int N, float* out, float* part, cudaStream_t st) {
+  const int S = (M + 255) / 256;
+  colsum_part_kernel<<<dim3((N + 31) / 32, S), 256, 0, st>>>(X, w, M, N, part);
+  colsum_finish_kernel<<<(N + 127) / 128, 128, 0, st>>>(part, S, N, out);
+  return cudaGetLastError();
 }
 
 // dz[m][j] = dy[m] * w[j] * gelu'(z[m][j]) (the output layer's input gradient)
@@ -525,7 +556,8 @@ struct cem_surrogate_ctx {
   float* tb = nullptr;
   float* partial = nullptr;
   float* loss_d = nullptr;
-  float* splitk = nullptr;  // split-K partials of the weight gradients
+  float* splitk = nullptr;   // split-K partials of the weight gradients
+  float* colpart = nullptr;  // row-chunk partials of the bias gradients
   // screening workspace
   int cap_pool = 0;
   float* pool_theta = nullptr;
@@ -559,7 +591,9 @@ void sur_free_work(cem_surrogate_ctx* s) {
   cudaFree(s->partial);
   cudaFree(s->loss_d);
   cudaFree(s->splitk);
+  cudaFree(s->colpart);
   s->splitk = nullptr;
+  s->colpart = nullptr;
   s->xin = nullptr;
   s->dz_a = s->dz_b = nullptr;
   s->raw = s->dy = s->tb = s->partial = s->loss_d = nullptr;
@@ -588,6 +622,7 @@ int ensure_rows(cem_surrogate_ctx* s, int M) {
   A((void**)&s->partial, sizeof(float) * ((M + 255) / 256 + 1));
   A((void**)&s->loss_d, sizeof(float));
   A((void**)&s->splitk, sizeof(float) * (size_t)kMaxSplit * s->width * std::max(s->width, s->in_dim));
+  A((void**)&s->colpart, sizeof(float) * (size_t)((M + 255) / 256) * s->width);
   if (e != cudaSuccess) {
     cudaGetLastError();
     sur_free_work(s);
@@ -667,7 +702,8 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
   loss_kernel<<<blocks, 256, 0, st>>>(s->raw, s->tb, s->norm, M, s->dy, s->partial);
   finish_sum_kernel<<<1, 256, 0, st>>>(s->partial, blocks, s->loss_d);
   // output layer: dW = dy . a_{L-1}, db = sum dy
-  colsum_kernel<<<(W + 127) / 128, 128, 0, st>>>(s->act[L - 1], s->dy, M, W, s->g + s->w_off[L]);
+  cudaError_t ce = colsum(s->act[L - 1], s->dy, M, W, s->g + s->w_off[L], s->colpart, st);
+  if (ce != cudaSuccess) return ce;
   finish_sum_kernel<<<1, 256, 0, st>>>(s->dy, M, s->g + s->b_off[L]);
   // dz of the last hidden layer
   const size_t n = (size_t)M * W;
@@ -695,7 +731,8 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
     g.part = s->splitk;
     cudaError_t e = gemm<EPI_F32>(g, st);
     if (e != cudaSuccess) return e;
-    colsum_kernel<<<(W + 127) / 128, 128, 0, st>>>(dz, nullptr, M, W, s->g + s->b_off[l]);
+    e = colsum(dz, nullptr, M, W, s->g + s->b_off[l], s->colpart, st);
+    if (e != cudaSuccess) return e;
     if (l > 0) {  // dz_{l-1} = (dz W_l) * gelu'(z_{l-1})
       GemmArgs h;
       std::memset(&h, 0, sizeof(h));

@@ -43,7 +43,7 @@ constexpr int kMaxIters = 4096;
 constexpr int kMaxDevices = 64;
 
 // the scratch memory of cem_solve_static (see the limits above)
-__device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // byte offsets of the regions inside g_scratch
 struct Layout {

@@ -374,6 +374,7 @@ def run_gb300(args):
 
     # CE time-to-cost: surrogate-screened vs plain (pick-place)
     ttc = time_to_cost(args.seed) if rank == 0 and not args.skip_surrogate else None
+    sur = surrogate_roofline(P, args.seed) if rank == 0 and not args.skip_surrogate else None
 
     # end to end through the public API with host buffers: cem_solve, one
     # iteration per step, distribution in from pinned host memory and the
@@ -423,6 +424,7 @@ def run_gb300(args):
                     "d2h_bytes_per_step": d2h},
             "batched_64": batch,
             "time_to_cost": ttc,
+            "roofline_surrogate": sur,
             "gpu_launches": 3 * args.steps,
             "gpu_launches_outside_timed_region": 5 + 3 * (args.steps + 1),
             "clocks": clocks,
@@ -476,6 +478,37 @@ def run_rollout_only(args):
     print(json.dumps({"rollout_only": cm["name"], "N": N, "T": T, "D": D, "block": args.block, "tpr": args.tpr, "controller": args.controller if cfg == 2 else None, "ms": ms,
                       "sim_steps_per_s": N * T / (ms / 1e3), "achieved_tflops": tf, "frac": tf / peak,
                       "classes": np.bincount(cls.cpu().numpy(), minlength=4).tolist()}), flush=True)
+
+
+def surrogate_roofline(P, seed, M=65536, reps=20):
+    """The fused tcgen05 surrogate forward (48 -> 4 x 256 GELU -> 1, BF16
+    operands, FP32 accumulation) on M rows: one untimed call, then `reps`
+    calls between CUDA events on the launching stream.  Dense BF16
+    contraction, so the roofline is the measured BF16 tensor peak."""
+    import torch
+
+    x = torch.rand((M, 48), device="cuda", generator=torch.Generator("cuda").manual_seed(seed)) * 2 - 1
+    flops = 2.0 * M * (48 * 256 + 3 * 256 * 256 + 256)
+    peaks, src = measured_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    with P.Surrogate(256, 4, seed=seed) as S:
+        S.set_forward_path(2)
+        y = S.forward(x)
+        st = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            P.cem_surrogate_forward(S.h, x, y, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if S.status() != 0:
+            raise SystemExit("surrogate forward: a bounded pipeline wait expired")
+    ms = e0.elapsed_time(e1) / reps
+    tf = flops / (ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "mlp_forward_tc_kernel", "rows": M, "ms": ms, "achieved": tf,
+            "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "peak_basis": f"bf16_tflops ({src}, burst)", "launches": reps}
 
 
 def run_mlp_only(args):

@@ -11,8 +11,12 @@
 // the tiled GEMM path: BF16 inputs, weights and activations, FP32
 // accumulation, FP32 bias and GELU.  The GELU's erf is the rational
 // approximation 7.1.28 of Abramowitz & Stegun (absolute error <= 3e-7, far
-// below the BF16 rounding of the activation), which costs about half the
-// instructions of the library erff; the biases are staged in shared memory.
+// below the BF16 rounding of the activation), evaluated on pairs of
+// activations with the packed FP32x2 instructions (fma/mul/add.rn.f32x2:
+// two IEEE operations per instruction, half the issue slots of scalar
+// code); each warp double-buffers its TMEM loads so the next 32 columns
+// are in flight while the current ones are processed; biases and output
+// weights are staged in shared memory.
 //
 // Operands use the canonical K-major layout without swizzling: 8-row x
 // 16-byte core matrices stored contiguously (128 B), core matrices adjacent
@@ -147,9 +151,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// issue a load of 32 consecutive FP32 columns of this thread's TMEM lane;
+// the registers hold the values only after tmem_wait32 on the same array
+__device__ __forceinline__ void tmem_issue32(uint32_t taddr, uint32_t* r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
       "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -158,30 +162,80 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
         "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16 for x >= 0, odd in x
-// (Abramowitz & Stegun, Handbook of Mathematical Functions, 7.1.28)
-__device__ __forceinline__ float erf_as(float x) {
-  const float ax = fabsf(x);
-  float p = fmaf(ax, 4.30638e-5f, 2.765672e-4f);
-  p = fmaf(ax, p, 1.520143e-4f);
-  p = fmaf(ax, p, 9.2705272e-3f);
-  p = fmaf(ax, p, 4.22820123e-2f);
-  p = fmaf(ax, p, 7.05230784e-2f);
-  p = fmaf(ax, p, 1.0f);
-  float q = p * p;  // p^16 by four squarings; overflow to inf gives erf = 1
-  q = q * q;
-  q = q * q;
-  q = q * q;
-  return copysignf(1.0f - __fdividef(1.0f, q), x);
+// wait for this thread's TMEM loads; the registers are operands of the wait,
+// so the compiler reads none of them before it
+__device__ __forceinline__ void tmem_wait32(uint32_t* r) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+        "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+        "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+      :
+      : "memory");
 }
 
-// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2
-__device__ __forceinline__ float gelu(float z) { return z * fmaf(0.5f, erf_as(z * 0.70710678118654752f), 0.5f); }
+// a pair of FP32 values in one 64-bit register (low, high)
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 fmul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f32x2 fadd2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// GELU(z) = z Phi(z) of a pair.  With a = |z| and E = erf(a / sqrt 2) =
+// 1 - (1 + p(a))^-16 (Abramowitz & Stegun 7.1.28, its coefficients a_i
+// scaled by 2^(-i/2) so the polynomial takes a directly), z Phi(z) =
+// (z + a E) / 2 for either sign of z, i.e. (z + a) / 2 - (a / 2) (1 + p(a))^-16.
+// Overflow of the 16th power to inf gives the exact limit relu(z).
+__device__ __forceinline__ f32x2 gelu2(f32x2 z) {
+  const f32x2 K1 = pk2(4.986734688e-02f, 4.986734688e-02f), K2 = pk2(2.114100568e-02f, 2.114100568e-02f);
+  const f32x2 K3 = pk2(3.277626354e-03f, 3.277626354e-03f), K4 = pk2(3.800357445e-05f, 3.800357445e-05f);
+  const f32x2 K5 = pk2(4.889063712e-05f, 4.889063712e-05f), K6 = pk2(5.382974905e-06f, 5.382974905e-06f);
+  const f32x2 ONE = pk2(1.0f, 1.0f), HALF = pk2(0.5f, 0.5f);
+  const f32x2 a = z & 0x7fffffff7fffffffull;  // |z| of both halves
+  f32x2 p = ffma2(a, K6, K5);
+  p = ffma2(a, p, K4);
+  p = ffma2(a, p, K3);
+  p = ffma2(a, p, K2);
+  p = ffma2(a, p, K1);
+  p = ffma2(a, p, ONE);
+  f32x2 q = fmul2(p, p);  // p^16 by four squarings
+  q = fmul2(q, q);
+  q = fmul2(q, q);
+  q = fmul2(q, q);
+  float q0, q1;
+  upk2(q, q0, q1);
+  const f32x2 nr = pk2(-rcp_approx(q0), -rcp_approx(q1));
+  const f32x2 ha = fmul2(a, HALF);
+  return ffma2(ha, nr, ffma2(z, HALF, ha));
+}
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
@@ -192,6 +246,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ volatile int s_fail;
   __shared__ __align__(16) float sbias[DEPTH * WIDTH];
+  __shared__ __align__(16) float swout[WIDTH];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * TM;
   const uint32_t sA = smem_u32(sm + SM_A), sW = smem_u32(sm + SM_W);
@@ -217,6 +272,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
 #pragma unroll
   for (int l = 0; l < DEPTH; ++l)
     for (int i = tid; i < WIDTH; i += THREADS) sbias[l * WIDTH + i] = a.bias[l][i];
+  for (int i = tid; i < WIDTH; i += THREADS) swout[i] = __bfloat162float(w_out[i]);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -276,11 +332,25 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
     __syncwarp();  // tcgen05.ld is warp-collective: reconverge after thread 0's copy issue
     // epilogue: TMEM -> bias + GELU -> BF16 activations (or the output dot)
     const float* bl = sbias + l * WIDTH;
-    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+    // this warp's 128 columns in 4 steps of 32, the next step's TMEM load
+    // in flight while the current step is processed
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
+    uint32_t ra[32], rb[32];
+    tmem_issue32(tbase, ra);
+    tmem_wait32(ra);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + bl[c0 + j]);
+    for (int cc = 0; cc < 4; ++cc) {
+      uint32_t* cur = (cc & 1) ? rb : ra;
+      uint32_t* nxt = (cc & 1) ? ra : rb;
+      if (cc + 1 < 4) tmem_issue32(tbase + 32u * (uint32_t)(cc + 1), nxt);
+      const int c0 = half * 128 + 32 * cc;
+      float v[32];
+#pragma unroll
+      for (int j = 0; j < 32; j += 2) {
+        const float2 b2 = *reinterpret_cast<const float2*>(bl + c0 + j);
+        const f32x2 g = gelu2(fadd2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])), pk2(b2.x, b2.y)));
+        upk2(g, v[j], v[j + 1]);
+      }
       if (l + 1 < DEPTH) {  // packing rounds to BF16 once
 #pragma unroll
         for (int kb = 0; kb < 4; ++kb) {
@@ -291,9 +361,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), __bfloat162float(w_out[c0 + j]), dot);
+        for (int j = 0; j < 32; ++j) dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), swout[c0 + j], dot);
       }
+      if (cc + 1 < 4) tmem_wait32(nxt);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -4,7 +4,11 @@ published absolute error bound of 3e-7.  Pinned here against the exact erf
 (scipy): the coefficients in FP64 must meet the published bound, and the
 kernel's FP32 operation sequence (fused multiply-adds, four squarings, a
 reciprocal) must stay within that bound plus its FP32 evaluation error,
-far below the 2^-9 relative rounding of the BF16 activation it feeds."""
+far below the 2^-9 relative rounding of the BF16 activation it feeds.
+The kernel evaluates GELU on pairs in the rearranged form
+z Phi(z) = (z + |z|) / 2 - (|z| / 2) (1 + p(|z|))^-16, with the coefficients
+scaled by 2^(-i/2) so the polynomial takes |z| instead of |z| / sqrt 2;
+that FP32 sequence is pinned against the exact GELU as well."""
 import numpy as np
 from scipy.special import erf
 
@@ -56,3 +60,39 @@ def test_fp32_sequence_and_gelu():
     exact = z * 0.5 * (1.0 + erf(x))
     assert np.max(np.abs(gelu - exact) / np.maximum(np.abs(z), 1.0)) <= 2.0e-6
     assert np.all(np.abs(e) <= 1.0) and e[-1] == 1.0 and e[0] == -1.0
+
+
+def gelu_packed_f32(z):
+    """The kernel's pair sequence, one lane: scaled coefficients rounded to
+    FP32 once, Horner by fused multiply-adds, four squarings, reciprocal,
+    two fused multiply-adds."""
+    z = f32(z)
+    a = np.abs(z)
+    K = [f32(c * 2.0 ** (-(i + 1) / 2)) for i, c in enumerate(A)]
+    p = fma32(a, K[5], K[4])
+    for c in (K[3], K[2], K[1], K[0], 1.0):
+        p = fma32(a, p, c)
+    q = f32(p * p)
+    for _ in range(3):
+        q = f32(q * q)
+    with np.errstate(over="ignore", divide="ignore"):
+        r = f32(np.where(np.isinf(q), 0.0, 1.0 / q))
+    ha = f32(0.5 * a)
+    return fma32(ha, -r, fma32(z, 0.5, ha))
+
+
+def test_packed_gelu_sequence():
+    # the rearrangement is exact algebra: (z + |z| E) / 2 = z (1 + erf(z / sqrt 2)) / 2
+    z = np.linspace(-16.0, 16.0, 320001)
+    exact = z * 0.5 * (1.0 + erf(z / np.sqrt(2.0)))
+    with np.errstate(over="ignore"):
+        g = gelu_packed_f32(z)
+    assert np.max(np.abs(g - exact) / np.maximum(np.abs(z), 1.0)) <= 2.0e-6
+    # limits: relu for large |z| (the 16th power overflows to inf), 0 at 0
+    assert gelu_packed_f32(np.array([0.0]))[0] == 0.0
+    with np.errstate(over="ignore"):
+        big = gelu_packed_f32(np.array([-30.0, 30.0]))
+    assert big[0] == 0.0 and big[1] == 30.0
+    # a dropped scale on the coefficients (unscaled a_i acting on |z|) is caught
+    wrong = np.sign(z) * (1.0 - (1.0 + sum(c * np.abs(z) ** (i + 1) for i, c in enumerate(A))) ** -16.0)
+    assert np.max(np.abs(z * 0.5 * (1.0 + wrong) - exact)) > 1e-2

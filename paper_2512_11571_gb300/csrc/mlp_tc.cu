@@ -1,30 +1,41 @@
 // Fused surrogate forward on the 5th-generation tensor cores (tcgen05).
 //
-// One CTA scores 128 candidates through the whole MLP (48 -> 4 x 256 GELU ->
-// 1): the activation tile stays in shared memory between layers, each
-// layer's weights arrive by bulk TMA copies (cp.async.bulk) from a pre-packed
-// global image, one thread issues the tcgen05.mma sequence (M = 128,
-// N = 256, K = 16, BF16 x BF16 -> FP32) into a 256-column TMEM accumulator,
-// and 8 warps drain TMEM with tcgen05.ld, add the bias, apply GELU and write
-// BF16 activations back as the next layer's A operand.  The output layer is a
-// dot product fused into the last epilogue.  Rounding points are those of
-// the tiled GEMM path: BF16 inputs, weights and activations, FP32
-// accumulation, FP32 bias and GELU.  The GELU's erf is the rational
-// approximation 7.1.28 of Abramowitz & Stegun (absolute error <= 3e-7, far
-// below the BF16 rounding of the activation), evaluated on pairs of
-// activations with the packed FP32x2 instructions (fma/mul/add.rn.f32x2:
-// two IEEE operations per instruction, half the issue slots of scalar
-// code); each warp double-buffers its TMEM loads so the next 32 columns
-// are in flight while the current ones are processed; biases and output
-// weights are staged in shared memory.
+// Scores candidates through the whole MLP (48 -> 4 x 256 GELU -> 1) in one
+// persistent launch: one CTA per SM walks over 128-row tiles.  Per CTA, one
+// warp issues the weight copies (cp.async.bulk) and the tcgen05.mma sequence
+// (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32); 16 epilogue warps drain
+// the accumulator with tcgen05.ld, add the bias, apply GELU and write BF16
+// activations back into shared memory as the next layer's A operand.
+//
+// Pipeline.  Two 256-column FP32 accumulators in TMEM serve alternate
+// layers, so the next layer's MMAs run while the epilogue still reads the
+// current one: the epilogue works in two steps of 32 columns per warp, and
+// as soon as every warp has written step c (K-slices c, c + 2, c + 4, c + 6
+// of the next layer's A) the MMA warp issues those slices' MMAs.  Hidden
+// weights stream through shared memory in 16 KB K-slices: slice j of the
+// next layer (or of layer 1 of the next tile) is copied in as soon as the
+// MMAs reading slice j of the current layer have finished.  W0 [256 x 48]
+// stays resident.  The last layer's epilogue writes no activations, so it
+// stages the next tile's input features into the A buffer and the MMA warp
+// starts that tile's first layer while the output dot product is finished.
+//
+// Arithmetic.  Rounding points are those of the tiled GEMM path: BF16
+// inputs, weights and activations, FP32 accumulation, FP32 bias and GELU.
+// The GELU's erf is the rational approximation 7.1.28 of Abramowitz &
+// Stegun (absolute error <= 3e-7, far below the BF16 rounding of the
+// activation), evaluated on pairs of activations with the packed FP32x2
+// instructions (fma/mul/add.rn.f32x2: two IEEE operations per
+// instruction); TMEM loads are double-buffered; biases and output weights
+// are staged in shared memory.  The K-slices of a layer accumulate in the
+// order the epilogue releases them (0, 2, 4, 6, 1, 3, 5, 7).
 //
 // Operands use the canonical K-major layout without swizzling: 8-row x
 // 16-byte core matrices stored contiguously (128 B), core matrices adjacent
 // along K 128 B apart (leading byte offset), adjacent along M/N K/8 * 128 B
 // apart (stride byte offset).  Every wait on an mbarrier is bounded: on
-// expiry the CTA records an error code, writes NaN scores for its rows,
+// expiry the CTA records an error code, writes NaN scores for all its rows,
 // waits (bounded) for its own copies and MMAs in flight, frees its TMEM and
-// returns.
+// returns; a flag in shared memory ends the other warps' waits at once.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -41,7 +52,12 @@ constexpr int TM = 128;       // rows per CTA (MMA M)
 constexpr int WIDTH = 256;    // hidden width (MMA N)
 constexpr int IN = 48;        // input features
 constexpr int DEPTH = 4;      // hidden layers
-constexpr int THREADS = 256;  // 8 warps
+constexpr int KC = 32;        // K per streamed weight slice
+constexpr int NCH = WIDTH / KC;  // slices per hidden layer
+constexpr int NSTEP = 2;         // epilogue steps per layer (32 columns per warp each)
+constexpr int EWARPS = 16;       // epilogue warps: 4 TMEM lane quadrants x 4 column quarters
+constexpr int ETHREADS = EWARPS * 32;
+constexpr int THREADS = ETHREADS + 32;  // + the MMA warp
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // give up on a pipeline wait after 1 s
 constexpr uint32_t kChunk = 16384;  // bytes per bulk copy
 
@@ -56,22 +72,27 @@ __host__ __device__ __forceinline__ uint32_t canon_off(int r, int k, int K) {
          (uint32_t)(k & 7) * 2u;
 }
 
-// packed weight image: W0 [256 x 48], W1..W3 [256 x 256], each canonical
+// packed weight image: W0 [256 x 48] canonical; W1..W3 [256 x 256] each as
+// 8 contiguous K-slices [256 x 32], every slice canonical with K = 32
 __host__ __device__ constexpr uint32_t w_offset(int l) {
   return l == 0 ? 0u : operand_bytes(WIDTH, IN) + (uint32_t)(l - 1) * operand_bytes(WIDTH, WIDTH);
 }
 constexpr uint32_t kPackBytes = operand_bytes(WIDTH, IN) + 3u * operand_bytes(WIDTH, WIDTH);
+constexpr uint32_t kSliceBytes = operand_bytes(WIDTH, KC);
 
 // shared memory plan (bytes)
 constexpr uint32_t SM_A = 0;                                     // activations [128 x 256]
-constexpr uint32_t SM_W = SM_A + operand_bytes(TM, WIDTH);        // weights [256 x 256]
-constexpr uint32_t SM_PART = SM_W + operand_bytes(WIDTH, WIDTH);  // 128 partial dot products
-constexpr uint32_t SM_BAR = SM_PART + TM * 4;                     // 2 mbarriers
-constexpr uint32_t SM_TMEM = SM_BAR + 16;                         // TMEM base from tcgen05.alloc
+constexpr uint32_t SM_W = SM_A + operand_bytes(TM, WIDTH);        // hidden weights, 8 slices
+constexpr uint32_t SM_W0 = SM_W + operand_bytes(WIDTH, WIDTH);    // W0 [256 x 48]
+constexpr uint32_t SM_PART = SM_W0 + operand_bytes(WIDTH, IN);    // 3 x 128 partial dot products
+constexpr uint32_t SM_BAR = SM_PART + 3 * TM * 4;
+// mbarriers: W0 copy, slice copies [8], slices free [8], activation steps
+// [2], accumulator ready, drain, next input staged
+constexpr int NBAR = 1 + 2 * NCH + NSTEP + 3;
+constexpr uint32_t SM_TMEM = SM_BAR + NBAR * 8;                   // TMEM base from tcgen05.alloc
 constexpr uint32_t SM_TOTAL = SM_TMEM + 16;
-static_assert(SM_TOTAL <= 227 * 1024, "shared memory plan exceeds 227 KB");
-static_assert(operand_bytes(WIDTH, IN) % 16 == 0 && operand_bytes(WIDTH, WIDTH) % 16 == 0,
-              "bulk copies move whole 16-byte units");
+static_assert(SM_TOTAL + (DEPTH + 1) * WIDTH * 4 + 64 <= 227 * 1024, "shared memory plan exceeds 227 KB");
+static_assert(operand_bytes(WIDTH, IN) % 16 == 0 && kSliceBytes % 16 == 0, "bulk copies move whole 16-byte units");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -135,6 +156,36 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const uint8_t* src, uint
         "l"(src + o), "r"(n), "r"(bar)
         : "memory");
   }
+}
+
+// mbar_wait that also gives up as soon as *fail is set by another thread
+__device__ __forceinline__ bool mbar_wait_or(uint32_t bar, uint32_t phase, volatile int* fail) {
+  uint64_t t0 = 0;
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (*fail) return false;
+    const uint64_t t = global_ns();
+    if (t0 == 0) t0 = t;
+    else if (t - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// one thread: one bulk copy of `bytes` (a multiple of 16, at most kChunk)
+__device__ __forceinline__ void copy_async(uint32_t dst, const uint8_t* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -248,9 +299,11 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
   __shared__ __align__(16) float sbias[DEPTH * WIDTH];
   __shared__ __align__(16) float swout[WIDTH];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int row0 = blockIdx.x * TM;
-  const uint32_t sA = smem_u32(sm + SM_A), sW = smem_u32(sm + SM_W);
-  const uint32_t bar_w = smem_u32(sm + SM_BAR), bar_mma = bar_w + 8;
+  const uint32_t sA = smem_u32(sm + SM_A), sW = smem_u32(sm + SM_W), sW0 = smem_u32(sm + SM_W0);
+  const uint32_t wbar0 = smem_u32(sm + SM_BAR);
+  const uint32_t wbar = wbar0 + 8, wfree = wbar + 8 * NCH, abar = wfree + 8 * NCH;
+  const uint32_t bar_mma = abar + 8 * NSTEP, bar_drain = bar_mma + 8, xbar = bar_drain + 8;
+  const int ntiles = (a.M + TM - 1) / TM;
   float* part = reinterpret_cast<float*>(sm + SM_PART);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_TMEM);
   const uint8_t* wpack = static_cast<const uint8_t*>(a.wpack);
@@ -259,146 +312,266 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
 
   if (tid == 0) {
     s_fail = 0;
-    mbar_init(bar_w, 1);
+    mbar_init(wbar0, 1);
+    for (int j = 0; j < NCH; ++j) {
+      mbar_init(wbar + 8 * j, 1);
+      mbar_init(wfree + 8 * j, 1);
+    }
+    for (int c = 0; c < NSTEP; ++c) mbar_init(abar + 8 * c, EWARPS);
     mbar_init(bar_mma, 1);
+    mbar_init(bar_drain, 1);
+    mbar_init(xbar, EWARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  if (warp == 0) {  // 256 TMEM columns: one FP32 accumulator row per lane
+  if (warp == 0) {  // two 256-column FP32 accumulators, used by alternate layers
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(WIDTH));
+                 "r"(2 * WIDTH));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
 #pragma unroll
   for (int l = 0; l < DEPTH; ++l)
     for (int i = tid; i < WIDTH; i += THREADS) sbias[l * WIDTH + i] = a.bias[l][i];
   for (int i = tid; i < WIDTH; i += THREADS) swout[i] = __bfloat162float(w_out[i]);
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = *tmem_slot;
-
-  // (the failure-detection test leaves the barrier without its arrival, so
-  // nothing completes it and the first wait runs out with nothing in flight)
-  if (tid == 0 && !a.expire_test) bulk_load(sW, wpack + w_offset(0), operand_bytes(WIDTH, IN), bar_w);
-  // input tile: 128 rows of 48 BF16 features, 16-byte pieces into the
-  // canonical layout; rows past M are zero
   for (int i = tid; i < TM * (IN / 8); i += THREADS) {
-    const int r = i / (IN / 8), kb = i % (IN / 8);
-    const int m = row0 + r;
+    const int r = i % TM, kb = i / TM;  // consecutive threads: consecutive rows, conflict-free stores
+    const int m = (int)blockIdx.x * TM + r;
     uint4 q = make_uint4(0u, 0u, 0u, 0u);
     if (m < a.M) q = *reinterpret_cast<const uint4*>(x + (size_t)m * IN + kb * 8);
     *reinterpret_cast<uint4*>(sm + SM_A + canon_off(r, kb * 8, IN)) = q;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
 
-  const uint32_t idesc = make_idesc(TM, WIDTH);
-  const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad.., columns 128 half..
-  const int r_local = quad * 32 + lane;
-  uint32_t ph_w = 0, ph_mma = 0;
-  int pending_w = 1, pending_mma = 0;  // copies / MMAs in flight
-  float dot = 0.0f;
-  for (int l = 0; l < DEPTH; ++l) {
-    const int K = l == 0 ? IN : WIDTH;
-    if (!mbar_wait(bar_w, ph_w)) s_fail = 1;
-    __syncthreads();
-    if (s_fail) break;
-    ph_w ^= 1;
-    pending_w = 0;
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sbo = (uint32_t)(K >> 3) * 128u;
-      for (int k0 = 0; k0 < K; k0 += 16) {
-        const uint64_t ad = make_desc(sA + (uint32_t)(k0 >> 3) * 128u, 128u, sbo);
-        const uint64_t bd = make_desc(sW + (uint32_t)(k0 >> 3) * 128u, 128u, sbo);
-        mma_bf16(tmem, ad, bd, idesc, k0 > 0 ? 1u : 0u);
+  if (warp == EWARPS) {
+    // ---- MMA warp: one lane issues the weight copies and the MMAs ----
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(TM, WIDTH);
+      int fail = 0;
+      uint32_t pend_w = 0;  // bit j < NCH: slice j copy not yet waited for; bit NCH: W0
+      uint32_t pph = 0;     // bit j: the parity that copy completes
+      bool pend_mma = false;
+      // (the failure-detection test leaves W0's barrier without its arrival)
+      if (!a.expire_test) {
+        bulk_load(sW0, wpack + w_offset(0), operand_bytes(WIDTH, IN), wbar0);
+        pend_w |= 1u << NCH;
       }
-      mma_commit(bar_mma);
-    }
-    pending_mma = 1;
-    if (!mbar_wait(bar_mma, ph_mma)) s_fail = 2;
-    __syncthreads();
-    if (s_fail) break;
-    ph_mma ^= 1;
-    pending_mma = 0;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // the MMAs have finished reading A and W: fetch the next weights now,
-    // overlapping the epilogue
-    if (l + 1 < DEPTH) {
-      if (tid == 0) bulk_load(sW, wpack + w_offset(l + 1), operand_bytes(WIDTH, WIDTH), bar_w);
-      pending_w = 1;
-    }
-    __syncwarp();  // tcgen05.ld is warp-collective: reconverge after thread 0's copy issue
-    // epilogue: TMEM -> bias + GELU -> BF16 activations (or the output dot)
-    const float* bl = sbias + l * WIDTH;
-    // this warp's 128 columns in 4 steps of 32, the next step's TMEM load
-    // in flight while the current step is processed
-    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * 128);
-    uint32_t ra[32], rb[32];
-    tmem_issue32(tbase, ra);
-    tmem_wait32(ra);
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      uint32_t* cur = (cc & 1) ? rb : ra;
-      uint32_t* nxt = (cc & 1) ? ra : rb;
-      if (cc + 1 < 4) tmem_issue32(tbase + 32u * (uint32_t)(cc + 1), nxt);
-      const int c0 = half * 128 + 32 * cc;
-      float v[32];
-#pragma unroll
-      for (int j = 0; j < 32; j += 2) {
-        const float2 b2 = *reinterpret_cast<const float2*>(bl + c0 + j);
-        const f32x2 g = gelu2(fadd2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])), pk2(b2.x, b2.y)));
-        upk2(g, v[j], v[j + 1]);
-      }
-      if (l + 1 < DEPTH) {  // packing rounds to BF16 once
-#pragma unroll
-        for (int kb = 0; kb < 4; ++kb) {
-          const uint4 q =
-              make_uint4(pack_bf16x2(v[8 * kb], v[8 * kb + 1]), pack_bf16x2(v[8 * kb + 2], v[8 * kb + 3]),
-                         pack_bf16x2(v[8 * kb + 4], v[8 * kb + 5]), pack_bf16x2(v[8 * kb + 6], v[8 * kb + 7]));
-          *reinterpret_cast<uint4*>(sm + SM_A + canon_off(r_local, c0 + 8 * kb, WIDTH)) = q;
+      for (int j = 0; j < NCH; ++j)
+        copy_async(sW + j * kSliceBytes, wpack + w_offset(1) + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
+      pend_w |= (1u << NCH) - 1u;
+      if (!mbar_wait_or(wbar0, 0, &s_fail)) fail = 1;
+      else pend_w &= ~(1u << NCH);
+      const uint32_t sbo0 = (uint32_t)(IN >> 3) * 128u;
+      for (int t = blockIdx.x, it = 0; t < ntiles && !fail; t += gridDim.x, ++it) {
+        const bool has_next = t + (int)gridDim.x < ntiles;
+        // layer 0: K = 48 from this tile's input (written by the epilogue warps after the first tile)
+        if (it > 0 && !mbar_wait_or(xbar, (uint32_t)(it - 1) & 1u, &s_fail)) {
+          fail = 5;
+          break;
         }
-      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int k0 = 0; k0 < IN; k0 += 16)
+          mma_bf16(tmem, make_desc(sA + (uint32_t)(k0 >> 3) * 128u, 128u, sbo0),
+                   make_desc(sW0 + (uint32_t)(k0 >> 3) * 128u, 128u, sbo0), idesc, k0 > 0 ? 1u : 0u);
+        mma_commit(bar_mma);
+        pend_mma = true;
+        for (int l = 1; l < DEPTH && !fail; ++l) {
+          const uint32_t ph = (uint32_t)(it + l - 1) & 1u;  // this layer's slices and activations
+          const uint32_t nph = (uint32_t)(it + l) & 1u;     // the refill's completion
+          const uint32_t dcol = (uint32_t)(l & 1) * WIDTH;
+          const bool refill = l + 1 < DEPTH || has_next;
+          const uint8_t* nsrc = wpack + w_offset(l + 1 < DEPTH ? l + 1 : 1);
+          for (int cc = 0; cc < NSTEP && !fail; ++cc) {
+            if (!mbar_wait_or(abar + 8 * cc, ph, &s_fail)) {
+              fail = 3;
+              break;
+            }
+            for (int h = 0; h < 4; ++h) {
+              const int j = NSTEP * h + cc;  // the slice step cc of column quarter h wrote
+              if (!mbar_wait_or(wbar + 8 * j, ph, &s_fail)) {
+                fail = 3;
+                break;
+              }
+              pend_w &= ~(1u << j);
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dot = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), swout[c0 + j], dot);
+              for (int kk = 0; kk < KC; kk += 16) {
+                const uint64_t ad =
+                    make_desc(sA + (uint32_t)((j * KC + kk) >> 3) * 128u, 128u, (uint32_t)(WIDTH >> 3) * 128u);
+                const uint64_t bd =
+                    make_desc(sW + j * kSliceBytes + (uint32_t)(kk >> 3) * 128u, 128u, (uint32_t)(KC >> 3) * 128u);
+                mma_bf16(tmem + dcol, ad, bd, idesc, (cc | h | kk) ? 1u : 0u);
+              }
+              if (refill) mma_commit(wfree + 8 * j);
+            }
+            if (fail) break;
+            if (cc == NSTEP - 1) mma_commit(bar_mma);
+            // the previous step's slices are free: refill them with the next layer's
+            for (int h = 0; refill && cc >= 1 && h < 4 && !fail; ++h) {
+              const int j = NSTEP * h + cc - 1;
+              if (!mbar_wait_or(wfree + 8 * j, ph, &s_fail)) {
+                fail = 4;
+              } else {
+                copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
+                pend_w |= 1u << j;
+                pph = (pph & ~(1u << j)) | (nph << j);
+              }
+            }
+          }
+          for (int h = 0; refill && h < 4 && !fail; ++h) {
+            const int j = NSTEP * h + NSTEP - 1;
+            if (!mbar_wait_or(wfree + 8 * j, ph, &s_fail)) {
+              fail = 4;
+            } else {
+              copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
+              pend_w |= 1u << j;
+              pph = (pph & ~(1u << j)) | (nph << j);
+            }
+          }
+        }
       }
-      if (cc + 1 < 4) tmem_wait32(nxt);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-  }
-  const int fail = s_fail;
-  if (!fail) {
-    if (half == 1) part[r_local] = dot;
-    __syncthreads();
-    if (half == 0) {
-      const int m = row0 + r_local;
-      if (m < a.M) a.y[m] = a.norm[0] + a.norm[1] * ((dot + part[r_local]) + a.b_out[0]);
+      if (fail) {
+        s_fail = fail;
+        // drain (bounded): every MMA issued and every copy not yet waited for
+        if (pend_mma) {
+          mma_commit(bar_drain);
+          mbar_wait(bar_drain, 0);
+        }
+        for (int j = 0; j <= NCH; ++j)
+          if (pend_w & (1u << j)) mbar_wait(j == NCH ? wbar0 : wbar + 8 * j, (pph >> j) & 1u);
+      }
     }
   } else {
-    // drain what this CTA still has in flight (bounded), report, poison rows
-    if (pending_mma) mbar_wait(bar_mma, ph_mma);
-    if (pending_w) mbar_wait(bar_w, ph_w);
-    if (tid == 0) atomicExch(a.status, fail);
-    if (tid < TM && row0 + tid < a.M) a.y[row0 + tid] = __int_as_float(0x7fc00000);
+    // ---- epilogue warps: TMEM -> bias + GELU -> BF16 activations, step by step ----
+    const int quad = warp & 3, qtr = warp >> 2;  // TMEM lane quadrant, column quarter
+    const int r_local = quad * 32 + lane;
+    const int tid_e = tid;  // 0 .. ETHREADS - 1
+    bool stop = false;  // the same value in every epilogue thread (barrier reduction)
+    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+      const bool has_next = t + (int)gridDim.x < ntiles;
+      float dq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      int l = 0;
+      for (; l < DEPTH; ++l) {
+        if (!mbar_wait_or(bar_mma, (uint32_t)l & 1u, &s_fail)) {
+          if (!s_fail) s_fail = 2;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the last layer leaves A free: fetch the next tile's input now, store it after the first step
+        uint4 xin[2];
+        const bool fetch = l + 1 == DEPTH && has_next;
+        if (fetch) {
+          const int tn = t + (int)gridDim.x;
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int i = tid_e + u * ETHREADS;
+            const int m = tn * TM + i % TM;
+            xin[u] = m < a.M && i < TM * (IN / 8) ? *reinterpret_cast<const uint4*>(x + (size_t)m * IN + (i / TM) * 8)
+                             : make_uint4(0u, 0u, 0u, 0u);
+          }
+        }
+        const float* bl = sbias + l * WIDTH;
+        const uint32_t tbase =
+            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(l & 1) * WIDTH + (uint32_t)(qtr * 64);
+        uint32_t ra[32], rb[32];
+        tmem_issue32(tbase, ra);
+        tmem_wait32(ra);
+#pragma unroll
+        for (int cc = 0; cc < NSTEP; ++cc) {
+          uint32_t* cur = (cc & 1) ? rb : ra;
+          uint32_t* nxt = (cc & 1) ? ra : rb;
+          if (cc + 1 < NSTEP) tmem_issue32(tbase + 32u * (uint32_t)(cc + 1), nxt);
+          const int c0 = qtr * 64 + 32 * cc;
+          float v[32];
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            const float2 b2 = *reinterpret_cast<const float2*>(bl + c0 + j);
+            const f32x2 g =
+                gelu2(fadd2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])), pk2(b2.x, b2.y)));
+            upk2(g, v[j], v[j + 1]);
+          }
+          if (l + 1 < DEPTH) {
+#pragma unroll
+            for (int kb = 0; kb < 4; ++kb) {
+              const uint4 q =
+                  make_uint4(pack_bf16x2(v[8 * kb], v[8 * kb + 1]), pack_bf16x2(v[8 * kb + 2], v[8 * kb + 3]),
+                             pack_bf16x2(v[8 * kb + 4], v[8 * kb + 5]), pack_bf16x2(v[8 * kb + 6], v[8 * kb + 7]));
+              *reinterpret_cast<uint4*>(sm + SM_A + canon_off(r_local, c0 + 8 * kb, WIDTH)) = q;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(abar + 8 * cc);
+            __syncwarp();
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+              dq[0] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), swout[c0 + j], dq[0]);
+              dq[1] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j + 1])), swout[c0 + j + 1], dq[1]);
+              dq[2] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j + 2])), swout[c0 + j + 2], dq[2]);
+              dq[3] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j + 3])), swout[c0 + j + 3], dq[3]);
+            }
+            if (cc == 0 && fetch) {
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const int i = tid_e + u * ETHREADS;
+                if (i < TM * (IN / 8))
+                  *reinterpret_cast<uint4*>(sm + SM_A + canon_off(i % TM, (i / TM) * 8, IN)) = xin[u];
+              }
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) bar_arrive(xbar);
+              __syncwarp();
+            }
+          }
+          if (cc + 1 < NSTEP) tmem_wait32(nxt);
+        }
+        // this layer's TMEM reads precede the arrivals that let a later layer overwrite them
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      }
+      const float dot = (dq[0] + dq[1]) + (dq[2] + dq[3]);
+      if (qtr > 0) part[(qtr - 1) * TM + r_local] = dot;
+      asm volatile("bar.sync 1, %0;" ::"n"(ETHREADS));
+      if (qtr == 0 && l == DEPTH) {
+        const int m = t * TM + r_local;
+        const float sum = (dot + part[r_local]) + (part[TM + r_local] + part[2 * TM + r_local]);
+        if (m < a.M) a.y[m] = a.norm[0] + a.norm[1] * (sum + a.b_out[0]);
+      }
+      // part is rewritten by the next tile; all epilogue threads leave together
+      int anyfail;
+      asm volatile(
+          "{\n .reg .pred q, p;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+          : "=r"(anyfail)
+          : "r"((int)s_fail), "n"(ETHREADS)
+          : "memory");
+      stop = anyfail != 0;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(WIDTH));
+  if (s_fail) {
+    if (tid == 0) atomicExch(a.status, s_fail);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+      if (tid < TM && t * TM + tid < a.M) a.y[t * TM + tid] = __int_as_float(0x7fc00000);
+  }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * WIDTH));
 }
 
 // W0..W3 (BF16, out x in row-major, at element offsets off.w[l] of the flat
-// BF16 parameter vector) -> the canonical packed image
+// BF16 parameter vector) -> the packed image (W0 canonical, hidden layers in
+// canonical K-slices)
 __global__ void pack_weights_kernel(const bf16* __restrict__ pb, MlpTcOffsets off, uint8_t* __restrict__ out) {
   const int l = blockIdx.y;
   const int K = l == 0 ? IN : WIDTH;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= WIDTH * K) return;
   const int n = i / K, k = i % K;
-  *reinterpret_cast<bf16*>(out + w_offset(l) + canon_off(n, k, K)) = pb[off.w[l] + i];
+  const uint32_t o = l == 0 ? canon_off(n, k, K) : (uint32_t)(k / KC) * kSliceBytes + canon_off(n, k % KC, KC);
+  *reinterpret_cast<bf16*>(out + w_offset(l) + o) = pb[off.w[l] + i];
 }
 
 }  // namespace
@@ -415,14 +588,22 @@ cudaError_t mlp_tc_pack(const void* pb, const MlpTcOffsets& off, void* pack, cud
 
 cudaError_t mlp_tc_forward(const MlpTcArgs& a, cudaStream_t st) {
   if (a.M <= 0) return cudaSuccess;
-  static bool configured = false;
-  if (!configured) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL);
+  constexpr int kMaxDevices = 64;
+  static int sms[kMaxDevices] = {0};  // per device: SM count once its kernel attribute is set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (sms[dev] == 0) {
+    e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL);
     if (e != cudaSuccess) return e;
-    configured = true;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    sms[dev] = n > 0 ? n : 1;
   }
-  mlp_forward_tc_kernel<<<(a.M + TM - 1) / TM, THREADS, SM_TOTAL, st>>>(a);
+  const int ntiles = (a.M + TM - 1) / TM;
+  mlp_forward_tc_kernel<<<ntiles < sms[dev] ? ntiles : sms[dev], THREADS, SM_TOTAL, st>>>(a);
   return cudaGetLastError();
 }
 

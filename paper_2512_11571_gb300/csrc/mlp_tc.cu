@@ -72,8 +72,9 @@ __host__ __device__ __forceinline__ uint32_t canon_off(int r, int k, int K) {
          (uint32_t)(k & 7) * 2u;
 }
 
-// packed weight image: W0 [256 x 48] canonical; W1..W3 [256 x 256] each as
-// 8 contiguous K-slices [256 x 32], every slice canonical with K = 32
+// packed weight image: W0 [256 x 48] canonical; W1..W3 [256 x 256], scaled
+// by 1/2 (see gelu2), each as 8 contiguous K-slices [256 x 32], every slice
+// canonical with K = 32
 __host__ __device__ constexpr uint32_t w_offset(int l) {
   return l == 0 ? 0u : operand_bytes(WIDTH, IN) + (uint32_t)(l - 1) * operand_bytes(WIDTH, WIDTH);
 }
@@ -86,8 +87,8 @@ constexpr uint32_t SM_W = SM_A + operand_bytes(TM, WIDTH);        // hidden weig
 constexpr uint32_t SM_W0 = SM_W + operand_bytes(WIDTH, WIDTH);    // W0 [256 x 48]
 constexpr uint32_t SM_PART = SM_W0 + operand_bytes(WIDTH, IN);    // 3 x 128 partial dot products
 constexpr uint32_t SM_BAR = SM_PART + 3 * TM * 4;
-// mbarriers: W0 copy, slice copies [8], slices free [8], activation steps
-// [2], accumulator ready, drain, next input staged
+// mbarriers: W0 copy, slice copies [8], a step's slices free [2 of 8 used],
+// activation steps [2], accumulator ready, drain, next input staged
 constexpr int NBAR = 1 + 2 * NCH + NSTEP + 3;
 constexpr uint32_t SM_TMEM = SM_BAR + NBAR * 8;                   // TMEM base from tcgen05.alloc
 constexpr uint32_t SM_TOTAL = SM_TMEM + 16;
@@ -260,16 +261,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
-// GELU(z) = z Phi(z) of a pair.  With a = |z| and E = erf(a / sqrt 2) =
+// 2 GELU(z) = 2 z Phi(z) of a pair.  With a = |z| and E = erf(a / sqrt 2) =
 // 1 - (1 + p(a))^-16 (Abramowitz & Stegun 7.1.28, its coefficients a_i
-// scaled by 2^(-i/2) so the polynomial takes a directly), z Phi(z) =
-// (z + a E) / 2 for either sign of z, i.e. (z + a) / 2 - (a / 2) (1 + p(a))^-16.
-// Overflow of the 16th power to inf gives the exact limit relu(z).
+// scaled by 2^(-i/2) so the polynomial takes a directly), 2 z Phi(z) =
+// z + a E for either sign of z, i.e. (z + a) - a (1 + p(a))^-16.  The factor
+// 1/2 of GELU lives in the packed weights of the next layer (and in the
+// output weights): scaling by a power of two is exact in BF16 and FP32, so
+// every product the tensor core forms is unchanged.  Overflow of the 16th
+// power to inf gives the exact limit 2 relu(z).
 __device__ __forceinline__ f32x2 gelu2(f32x2 z) {
   const f32x2 K1 = pk2(4.986734688e-02f, 4.986734688e-02f), K2 = pk2(2.114100568e-02f, 2.114100568e-02f);
   const f32x2 K3 = pk2(3.277626354e-03f, 3.277626354e-03f), K4 = pk2(3.800357445e-05f, 3.800357445e-05f);
   const f32x2 K5 = pk2(4.889063712e-05f, 4.889063712e-05f), K6 = pk2(5.382974905e-06f, 5.382974905e-06f);
-  const f32x2 ONE = pk2(1.0f, 1.0f), HALF = pk2(0.5f, 0.5f);
+  const f32x2 ONE = pk2(1.0f, 1.0f);
   const f32x2 a = z & 0x7fffffff7fffffffull;  // |z| of both halves
   f32x2 p = ffma2(a, K6, K5);
   p = ffma2(a, p, K4);
@@ -284,8 +288,7 @@ __device__ __forceinline__ f32x2 gelu2(f32x2 z) {
   float q0, q1;
   upk2(q, q0, q1);
   const f32x2 nr = pk2(-rcp_approx(q0), -rcp_approx(q1));
-  const f32x2 ha = fmul2(a, HALF);
-  return ffma2(ha, nr, ffma2(z, HALF, ha));
+  return ffma2(a, nr, fadd2(z, a));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
 #pragma unroll
   for (int l = 0; l < DEPTH; ++l)
     for (int i = tid; i < WIDTH; i += THREADS) sbias[l * WIDTH + i] = a.bias[l][i];
-  for (int i = tid; i < WIDTH; i += THREADS) swout[i] = __bfloat162float(w_out[i]);
+  for (int i = tid; i < WIDTH; i += THREADS) swout[i] = 0.5f * __bfloat162float(w_out[i]);  // see gelu2
   for (int i = tid; i < TM * (IN / 8); i += THREADS) {
     const int r = i % TM, kb = i / TM;  // consecutive threads: consecutive rows, conflict-free stores
     const int m = (int)blockIdx.x * TM + r;
@@ -385,18 +388,20 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
           const bool refill = l + 1 < DEPTH || has_next;
           const uint8_t* nsrc = wpack + w_offset(l + 1 < DEPTH ? l + 1 : 1);
           for (int cc = 0; cc < NSTEP && !fail; ++cc) {
-            if (!mbar_wait_or(abar + 8 * cc, ph, &s_fail)) {
+            // this step's slices first (their copies finished long before), then the activations
+            for (int h = 0; h < 4 && !fail; ++h) {
+              const int j = NSTEP * h + cc;
+              if (!mbar_wait_or(wbar + 8 * j, ph, &s_fail)) fail = 3;
+              else pend_w &= ~(1u << j);
+            }
+            if (fail || !mbar_wait_or(abar + 8 * cc, ph, &s_fail)) {
               fail = 3;
               break;
             }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
             for (int h = 0; h < 4; ++h) {
               const int j = NSTEP * h + cc;  // the slice step cc of column quarter h wrote
-              if (!mbar_wait_or(wbar + 8 * j, ph, &s_fail)) {
-                fail = 3;
-                break;
-              }
-              pend_w &= ~(1u << j);
-              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
               for (int kk = 0; kk < KC; kk += 16) {
                 const uint64_t ad =
@@ -405,30 +410,33 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
                     make_desc(sW + j * kSliceBytes + (uint32_t)(kk >> 3) * 128u, 128u, (uint32_t)(KC >> 3) * 128u);
                 mma_bf16(tmem + dcol, ad, bd, idesc, (cc | h | kk) ? 1u : 0u);
               }
-              if (refill) mma_commit(wfree + 8 * j);
             }
-            if (fail) break;
+            if (refill) mma_commit(wfree + 8 * cc);
             if (cc == NSTEP - 1) mma_commit(bar_mma);
             // the previous step's slices are free: refill them with the next layer's
-            for (int h = 0; refill && cc >= 1 && h < 4 && !fail; ++h) {
-              const int j = NSTEP * h + cc - 1;
-              if (!mbar_wait_or(wfree + 8 * j, ph, &s_fail)) {
+            if (refill && cc >= 1) {
+              if (!mbar_wait_or(wfree + 8 * (cc - 1), ph, &s_fail)) {
                 fail = 4;
               } else {
+                for (int h = 0; h < 4; ++h) {
+                  const int j = NSTEP * h + cc - 1;
+                  copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
+                  pend_w |= 1u << j;
+                  pph = (pph & ~(1u << j)) | (nph << j);
+                }
+              }
+            }
+          }
+          if (refill && !fail) {
+            if (!mbar_wait_or(wfree + 8 * (NSTEP - 1), ph, &s_fail)) {
+              fail = 4;
+            } else {
+              for (int h = 0; h < 4; ++h) {
+                const int j = NSTEP * h + NSTEP - 1;
                 copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
                 pend_w |= 1u << j;
                 pph = (pph & ~(1u << j)) | (nph << j);
               }
-            }
-          }
-          for (int h = 0; refill && h < 4 && !fail; ++h) {
-            const int j = NSTEP * h + NSTEP - 1;
-            if (!mbar_wait_or(wfree + 8 * j, ph, &s_fail)) {
-              fail = 4;
-            } else {
-              copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
-              pend_w |= 1u << j;
-              pph = (pph & ~(1u << j)) | (nph << j);
             }
           }
         }
@@ -562,8 +570,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
 }
 
 // W0..W3 (BF16, out x in row-major, at element offsets off.w[l] of the flat
-// BF16 parameter vector) -> the packed image (W0 canonical, hidden layers in
-// canonical K-slices)
+// BF16 parameter vector) -> the packed image (W0 canonical, W1..W3 halved and
+// in canonical K-slices)
 __global__ void pack_weights_kernel(const bf16* __restrict__ pb, MlpTcOffsets off, uint8_t* __restrict__ out) {
   const int l = blockIdx.y;
   const int K = l == 0 ? IN : WIDTH;
@@ -571,7 +579,9 @@ __global__ void pack_weights_kernel(const bf16* __restrict__ pb, MlpTcOffsets of
   if (i >= WIDTH * K) return;
   const int n = i / K, k = i % K;
   const uint32_t o = l == 0 ? canon_off(n, k, K) : (uint32_t)(k / KC) * kSliceBytes + canon_off(n, k % KC, KC);
-  *reinterpret_cast<bf16*>(out + w_offset(l) + o) = pb[off.w[l] + i];
+  // layers fed by a GELU output take the factor 1/2 of GELU (exact: a power of two)
+  *reinterpret_cast<bf16*>(out + w_offset(l) + o) =
+      l == 0 ? pb[off.w[l] + i] : __float2bfloat16_rn(0.5f * __bfloat162float(pb[off.w[l] + i]));
 }
 
 }  // namespace

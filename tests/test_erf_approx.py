@@ -5,10 +5,11 @@ published absolute error bound of 3e-7.  Pinned here against the exact erf
 kernel's FP32 operation sequence (fused multiply-adds, four squarings, a
 reciprocal) must stay within that bound plus its FP32 evaluation error,
 far below the 2^-9 relative rounding of the BF16 activation it feeds.
-The kernel evaluates GELU on pairs in the rearranged form
-z Phi(z) = (z + |z|) / 2 - (|z| / 2) (1 + p(|z|))^-16, with the coefficients
-scaled by 2^(-i/2) so the polynomial takes |z| instead of |z| / sqrt 2;
-that FP32 sequence is pinned against the exact GELU as well."""
+The kernel evaluates twice GELU on pairs in the rearranged form
+2 z Phi(z) = (z + |z|) - |z| (1 + p(|z|))^-16, with the coefficients scaled
+by 2^(-i/2) so the polynomial takes |z| instead of |z| / sqrt 2 (the factor
+1/2 sits, exactly, in the next layer's weights); that FP32 sequence is
+pinned against the exact GELU as well."""
 import numpy as np
 from scipy.special import erf
 
@@ -65,7 +66,7 @@ def test_fp32_sequence_and_gelu():
 def gelu_packed_f32(z):
     """The kernel's pair sequence, one lane: scaled coefficients rounded to
     FP32 once, Horner by fused multiply-adds, four squarings, reciprocal,
-    two fused multiply-adds."""
+    one add and one fused multiply-add giving 2 GELU(z); halved here (exact)."""
     z = f32(z)
     a = np.abs(z)
     K = [f32(c * 2.0 ** (-(i + 1) / 2)) for i, c in enumerate(A)]
@@ -77,8 +78,7 @@ def gelu_packed_f32(z):
         q = f32(q * q)
     with np.errstate(over="ignore", divide="ignore"):
         r = f32(np.where(np.isinf(q), 0.0, 1.0 / q))
-    ha = f32(0.5 * a)
-    return fma32(ha, -r, fma32(z, 0.5, ha))
+    return 0.5 * fma32(a, -r, f32(z + a))
 
 
 def test_packed_gelu_sequence():

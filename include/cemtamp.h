@@ -397,7 +397,7 @@ int cem_surrogate_get_params(cem_surrogate_handle s, float* params_h, float* nor
 int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float* y_d, void* stream);
 /* Forward path for inference: 0 automatic (tcgen05 where the shape allows),
  * 1 the tiled mma.sync GEMM, 2 tcgen05 (CEM_ERR_UNSUPPORTED unless width 256
- * and depth 4).  Training always uses the tiled GEMM. */
+ * and depth 4).  Training follows cem_surrogate_set_gemm_path. */
 int cem_surrogate_set_forward_path(cem_surrogate_handle s, int path);
 /* Failure-detection test hook: while on != 0, tcgen05 forwards leave their
  * first weight-copy barrier without its arrival, so every CTA's first
@@ -407,6 +407,17 @@ int cem_surrogate_set_forward_path(cem_surrogate_handle s, int path);
 int cem_surrogate_test_expire_wait(cem_surrogate_handle s, int on);
 /* The path inference takes now: 1 tiled GEMM, 2 tcgen05; -1 for NULL. */
 int cem_surrogate_forward_path(cem_surrogate_handle s);
+/* Dense layers of training (cem_surrogate_gradient, cem_surrogate_train)
+ * and of the layer-by-layer inference forward: 0 automatic or 2 = the
+ * tcgen05 GEMM (M = 128 x N <= 128 tiles, both operand majors read straight
+ * by the tensor core, fused bias + GELU / GELU' / split-K epilogues; a layer
+ * whose shape it does not take runs on the tiled kernel), 1 = the tiled
+ * mma.sync GEMM.  Same products, FP32 accumulation order differs.  Errors:
+ * CEM_ERR_INVALID_ARG for another value.  A tcgen05 GEMM whose bounded wait
+ * expires sets status 1 / 2 (read by cem_surrogate_status). */
+int cem_surrogate_set_gemm_path(cem_surrogate_handle s, int path);
+/* The path training GEMMs take now: 1 tiled, 2 tcgen05; -1 for NULL. */
+int cem_surrogate_gemm_path(cem_surrogate_handle s);
 /* Synchronises, writes and clears the tcgen05 forward's status word: 0, or
  * 1 / 2 if a wait for the weight copy / the MMAs expired.  A non-zero code
  * also makes cem_solve_screened return CEM_ERR_TIMEOUT. */

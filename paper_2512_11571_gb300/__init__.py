@@ -40,6 +40,7 @@ EXPORTS = [
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
     "cem_surrogate_set_forward_path", "cem_surrogate_forward_path", "cem_surrogate_status",
+    "cem_surrogate_set_gemm_path", "cem_surrogate_gemm_path",
     "cem_last_error", "cem_version",
 ]
 
@@ -273,6 +274,8 @@ def load(path: str = LIB_PATH):
     L.cem_surrogate_forward.argtypes = [H, vp, C.c_int, vp, vp]
     L.cem_surrogate_set_forward_path.argtypes = [H, C.c_int]
     L.cem_surrogate_forward_path.argtypes = [H]
+    L.cem_surrogate_set_gemm_path.argtypes = [H, C.c_int]
+    L.cem_surrogate_gemm_path.argtypes = [H]
     L.cem_surrogate_test_expire_wait.argtypes = [H, C.c_int]
     L.cem_surrogate_status.argtypes = [H, C.POINTER(C.c_int)]
     L.cem_surrogate_gradient.argtypes = [H, vp, vp, C.c_int, fptr, fptr]
@@ -627,6 +630,14 @@ def cem_surrogate_forward_path(s):
     return int(load().cem_surrogate_forward_path(s))
 
 
+def cem_surrogate_set_gemm_path(s, path):
+    _check(load().cem_surrogate_set_gemm_path(s, int(path)))
+
+
+def cem_surrogate_gemm_path(s):
+    return int(load().cem_surrogate_gemm_path(s))
+
+
 def cem_surrogate_status(s):
     code = C.c_int(0)
     _check(load().cem_surrogate_status(s, C.byref(code)))
@@ -711,6 +722,14 @@ class Surrogate:
     @property
     def forward_path(self):
         return cem_surrogate_forward_path(self.h)
+
+    def set_gemm_path(self, path):
+        """Training GEMMs: 0 automatic, 1 tiled mma.sync, 2 tcgen05."""
+        cem_surrogate_set_gemm_path(self.h, path)
+
+    @property
+    def gemm_path(self):
+        return cem_surrogate_gemm_path(self.h)
 
     def test_expire_wait(self, on):
         """Failure-detection hook: make the tcgen05 forward's first wait run out."""

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcemtamp.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["capi.cu", "sample.cu", "rollout.cu", "refit.cu", "batch.cu", "surrogate.cu", "mlp_tc.cu", "solve_static.cu"]
+SOURCES = ["capi.cu", "sample.cu", "rollout.cu", "refit.cu", "batch.cu", "surrogate.cu", "mlp_tc.cu", "gemm_tc.cu", "solve_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
 

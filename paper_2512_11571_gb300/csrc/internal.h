@@ -1,6 +1,7 @@
 // Internal declarations of the cemtamp CUDA library (device scene layout,
 // kernel launchers, error helpers).  Not part of the public ABI.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -203,5 +204,41 @@ bool mlp_tc_supported(int in_dim, int width, int depth);
 size_t mlp_tc_pack_bytes();
 cudaError_t mlp_tc_pack(const void* pb, const MlpTcOffsets& off, void* pack, cudaStream_t st);
 cudaError_t mlp_tc_forward(const MlpTcArgs& a, cudaStream_t st);
+
+// ---- dense layers of the surrogate (csrc/surrogate.cu tiled path,
+// csrc/gemm_tc.cu tcgen05 path)
+// C[M x N] = op(A)[M x K] * op(B)[K x N], BF16 operands, FP32 accumulation,
+// op(A)(m, k) = a_kmajor ? A[m * lda + k] : A[k * lda + m],
+// op(B)(k, n) = b_kmajor ? B[n * ldb + k] : B[k * ldb + n], and a fused
+// epilogue: EPI_F32 stores C (or split-K partials), EPI_BIAS_GELU stores
+// z = C + bias (FP32, optional) and GELU(z) (BF16), EPI_GELU_BWD stores
+// C * GELU'(zsave) (BF16).
+enum { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_GELU_BWD = 2 };
+
+struct GemmArgs {
+  int M, N, K;
+  const __nv_bfloat16* A;
+  int lda, a_kmajor;
+  const __nv_bfloat16* B;
+  int ldb, b_kmajor;
+  float* C;  // EPI_F32: output; EPI_BIAS_GELU: pre-activation z (may be null)
+  int ldc;
+  __nv_bfloat16* Cb;  // EPI_BIAS_GELU: activation; EPI_GELU_BWD: dz
+  int ldcb;
+  const float* bias;   // EPI_BIAS_GELU
+  const float* zsave;  // EPI_GELU_BWD
+  int ldz;
+  // EPI_F32 split-K: blockIdx.z takes rows [z kchunk, (z + 1) kchunk) of the
+  // reduction and writes its partial tile to part + z M N (row-major); the
+  // partials are then summed in z order (deterministic)
+  int kchunk;
+  float* part;
+};
+// tcgen05 path: shapes it takes (operand rows and leading dimensions in
+// whole 16-byte units, N a multiple of 16, 16-byte aligned bases)
+bool gemm_tc_supported(const GemmArgs& g);
+// the same product and epilogue on the 5th-generation tensor cores; a
+// pipeline wait that runs out sets *status (device int) non-zero
+cudaError_t gemm_tc(int epi, const GemmArgs& g, int* status, cudaStream_t st);
 
 }  // namespace cem

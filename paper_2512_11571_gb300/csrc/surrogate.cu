@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "gelu.cuh"
 #include "internal.h"
 
 using namespace cem;
@@ -40,38 +41,11 @@ int fail(int code, const std::string& m) { return set_last_error(code, m); }
     if (e_ != cudaSuccess) return fail(CEM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));  \
   } while (0)
 
-// ---------------------------------------------------------------- math
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
 
 // ---------------------------------------------------------------- GEMM
 // C[M x N] = op(A)[M x K] * op(B)[K x N] on BF16 tensor cores, FP32 accumulate.
 // op(A)(m, k) = a_kmajor ? A[m * lda + k] : A[k * lda + m]
 // op(B)(k, n) = b_kmajor ? B[n * ldb + k] : B[k * ldb + n]
-enum { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_GELU_BWD = 2 };
-
-struct GemmArgs {
-  int M, N, K;
-  const bf16* A;
-  int lda, a_kmajor;
-  const bf16* B;
-  int ldb, b_kmajor;
-  float* C;  // EPI_F32: output; EPI_BIAS_GELU: pre-activation z (may be null)
-  int ldc;
-  bf16* Cb;  // EPI_BIAS_GELU: activation; EPI_GELU_BWD: dz
-  int ldcb;
-  const float* bias;   // EPI_BIAS_GELU
-  const float* zsave;  // EPI_GELU_BWD
-  int ldz;
-  // EPI_F32 split-K: blockIdx.z takes rows [z kchunk, (z + 1) kchunk) of the
-  // reduction and writes its partial tile to part + z M N (row-major); the
-  // partials are then summed in z order (deterministic)
-  int kchunk;
-  float* part;
-};
-
 constexpr int BM = 128, BN = 128, BK = 32, PADK = 8, GT = 256;
 
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
@@ -177,8 +151,11 @@ __global__ void splitk_sum_kernel(const float* __restrict__ part, int S, int M, 
   C[(size_t)(i / N) * ldc + i % N] = acc;
 }
 
+// tc: run the product on tcgen05 (csrc/gemm_tc.cu) when its shape allows,
+// else on the tiled mma.sync kernel above; status: the tcgen05 path's
+// expired-wait flag
 template <int EPI>
-cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
+cudaError_t gemm(const GemmArgs& g, bool tc, int* status, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   const int S = (EPI == EPI_F32 && g.part && g.kchunk > 0) ? (g.K + g.kchunk - 1) / g.kchunk : 1;
   GemmArgs h = g;
@@ -186,9 +163,14 @@ cudaError_t gemm(const GemmArgs& g, cudaStream_t st) {
     h.kchunk = 0;
     h.part = nullptr;
   }
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, S);
-  gemm_bf16_kernel<EPI><<<grid, GT, 0, st>>>(h);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  if (tc && gemm_tc_supported(h)) {
+    e = gemm_tc(EPI, h, status, st);
+  } else {
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, S);
+    gemm_bf16_kernel<EPI><<<grid, GT, 0, st>>>(h);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || S == 1 || EPI != EPI_F32) return e;
   splitk_sum_kernel<<<(g.M * g.N + 255) / 256, 256, 0, st>>>(g.part, S, g.M, g.N, g.C, g.ldc);
   return cudaGetLastError();
@@ -571,7 +553,8 @@ struct cem_surrogate_ctx {
   void* tc_pack = nullptr;
   int* tc_status = nullptr;
   bool tc_pack_valid = false;
-  int fwd_path = 0;  // 0 automatic, 1 tiled GEMM, 2 tcgen05
+  int fwd_path = 0;   // 0 automatic, 1 tiled GEMM, 2 tcgen05
+  int gemm_path = 0;  // training GEMMs: 0 automatic (tcgen05 where the shape allows), 1 tiled mma.sync
   int expire_test = 0;
 };
 
@@ -633,7 +616,8 @@ int ensure_rows(cem_surrogate_ctx* s, int M) {
 }
 
 // forward of M rows already in s->xin (BF16); keeps activations for backward
-cudaError_t forward_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st) {
+// tc: the dense layers on the tcgen05 GEMM (else the tiled mma.sync kernel)
+cudaError_t forward_rows(cem_surrogate_ctx* s, int M, float* y, bool tc, cudaStream_t st) {
   const bf16* a = s->xin;
   int K = s->in_dim;
   for (int l = 0; l < s->depth; ++l) {
@@ -653,7 +637,7 @@ cudaError_t forward_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st)
     g.Cb = s->act[l];
     g.ldcb = s->width;
     g.bias = s->p + s->b_off[l];
-    cudaError_t e = gemm<EPI_BIAS_GELU>(g, st);
+    cudaError_t e = gemm<EPI_BIAS_GELU>(g, tc, s->tc_status, st);
     if (e != cudaSuccess) return e;
     a = s->act[l];
     K = s->width;
@@ -665,6 +649,8 @@ cudaError_t forward_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st)
   return cudaGetLastError();
 }
 
+bool use_tc_gemm(const cem_surrogate_ctx* s) { return s->gemm_path != 1; }
+
 bool use_tc(const cem_surrogate_ctx* s) {
   return s->fwd_path != 1 && mlp_tc_supported(s->in_dim, s->width, s->depth);
 }
@@ -672,7 +658,7 @@ bool use_tc(const cem_surrogate_ctx* s) {
 // scores of M rows already in s->xin, no activations kept: the fused tcgen05
 // kernel where the shape allows, else the tiled GEMM forward
 cudaError_t infer_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st) {
-  if (!use_tc(s)) return forward_rows(s, M, y, st);
+  if (!use_tc(s)) return forward_rows(s, M, y, s->fwd_path != 1 && use_tc_gemm(s), st);
   if (!s->tc_pack_valid) {
     MlpTcOffsets off;
     for (int l = 0; l < 4; ++l) off.w[l] = s->w_off[l];
@@ -729,7 +715,7 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
     g.ldc = K;
     g.kchunk = split_chunk(M);
     g.part = s->splitk;
-    cudaError_t e = gemm<EPI_F32>(g, st);
+    cudaError_t e = gemm<EPI_F32>(g, use_tc_gemm(s), s->tc_status, st);
     if (e != cudaSuccess) return e;
     e = colsum(dz, nullptr, M, W, s->g + s->b_off[l], s->colpart, st);
     if (e != cudaSuccess) return e;
@@ -749,7 +735,7 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
       h.ldcb = K;
       h.zsave = s->pre[l - 1];
       h.ldz = W;
-      e = gemm<EPI_GELU_BWD>(h, st);
+      e = gemm<EPI_GELU_BWD>(h, use_tc_gemm(s), s->tc_status, st);
       if (e != cudaSuccess) return e;
       bf16* t = dz;
       dz = dz_next;
@@ -926,6 +912,15 @@ int cem_surrogate_test_expire_wait(cem_surrogate_handle s, int on) {
 
 int cem_surrogate_forward_path(cem_surrogate_handle s) { return s ? (use_tc(s) ? 2 : 1) : -1; }
 
+int cem_surrogate_set_gemm_path(cem_surrogate_handle s, int path) {
+  if (!s) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (path < 0 || path > 2) return fail(CEM_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+  s->gemm_path = path;
+  return CEM_OK;
+}
+
+int cem_surrogate_gemm_path(cem_surrogate_handle s) { return s ? (use_tc_gemm(s) ? 2 : 1) : -1; }
+
 int cem_surrogate_status(cem_surrogate_handle s, int* status_h) {
   if (!s || !status_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
   SUR_CUDA(cudaDeviceSynchronize());
@@ -942,7 +937,7 @@ int cem_surrogate_gradient(cem_surrogate_handle s, const float* x_d, const float
   int rc = load_features(s, x_d, M, 0);
   if (rc != CEM_OK) return rc;
   SUR_CUDA(cudaMemcpy(s->tb, t_d, sizeof(float) * M, cudaMemcpyDeviceToDevice));
-  SUR_CUDA(forward_rows(s, M, nullptr, 0));
+  SUR_CUDA(forward_rows(s, M, nullptr, use_tc_gemm(s), 0));
   SUR_CUDA(backward_rows(s, M, 0));
   SUR_CUDA(cudaDeviceSynchronize());
   SUR_CUDA(cudaMemcpy(grad_h, s->g, sizeof(float) * s->total, cudaMemcpyDeviceToHost));
@@ -985,7 +980,7 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   for (int it = 0; it < steps && e == cudaSuccess; ++it) {
     gather_batch_kernel<<<(batch + 255) / 256, 256>>>(Xall, t_d, M, s->in_dim, batch, seed, (uint32_t)it, s->xin,
                                                        s->tb);
-    e = forward_rows(s, batch, nullptr, 0);
+    e = forward_rows(s, batch, nullptr, use_tc_gemm(s), 0);
     if (e == cudaSuccess) e = backward_rows(s, batch, 0);
     if (e != cudaSuccess) break;
     ++s->adam_step;

@@ -409,7 +409,7 @@ int cem_surrogate_test_expire_wait(cem_surrogate_handle s, int on);
 int cem_surrogate_forward_path(cem_surrogate_handle s);
 /* Dense layers of training (cem_surrogate_gradient, cem_surrogate_train)
  * and of the layer-by-layer inference forward: 0 automatic or 2 = the
- * tcgen05 GEMM (M = 128 x N <= 128 tiles, both operand majors read straight
+ * tcgen05 GEMM (128 x 64 tiles, both operand majors read straight
  * by the tensor core, fused bias + GELU / GELU' / split-K epilogues; a layer
  * whose shape it does not take runs on the tiled kernel), 1 = the tiled
  * mma.sync GEMM.  Same products, FP32 accumulation order differs.  Errors:

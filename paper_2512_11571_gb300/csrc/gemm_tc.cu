@@ -3,14 +3,16 @@
 // path (FP32 / split-K partials, bias + GELU keeping the pre-activation,
 // GELU' for the backward pass).
 //
-// One CTA computes a 128 x TN tile of C (TN <= 128, a multiple of 16) over
-// its K range.  Four warps stage K-slices of 32 into a ring of shared-memory
+// One CTA computes a 128 x TN tile of C (TN <= 64, a multiple of 16) over
+// its K range.  Eight warps stage K-slices of 32 into a ring of shared-memory
 // buffers with cp.async (16-byte pieces, zero fill outside the operands);
 // one thread issues two tcgen05.mma (M = 128, N = TN, K = 16, BF16 x BF16 ->
 // FP32) per slice into a TMEM accumulator and commits each slice to the
-// mbarrier that frees its buffer; after the last slice the four warps drain
-// their TMEM lane quadrant (one row of C per thread) with tcgen05.ld and run
-// the epilogue.
+// mbarrier that frees its buffer; after the last slice each warp drains 32
+// columns of its TMEM lane quadrant (one row of C per thread) with
+// tcgen05.ld and runs the epilogue.  The small tiles give the batch-sized
+// training GEMMs (4096 x 256 x 256) 128 CTAs, so the epilogue math (GELU,
+// GELU') spreads over most SMs.
 //
 // Both operand majors go straight to the tensor core.  A slice of an operand
 // with R rows (M or N) is stored as core matrices of 8 x 16 bytes,
@@ -39,20 +41,20 @@ namespace {
 typedef __nv_bfloat16 bf16;
 
 constexpr int TM = 128;      // rows of C per CTA (MMA M)
-constexpr int TN_MAX = 128;  // columns of C per CTA (MMA N)
+constexpr int TN_MAX = 64;   // columns of C per CTA (MMA N)
 constexpr int KS = 32;       // K per pipeline slice (two K = 16 MMAs)
 constexpr int STAGES = 6;
-constexpr int THREADS = 128;  // one TMEM lane quadrant per warp in the epilogue
+constexpr int THREADS = 256;  // epilogue: warp w drains lane quadrant w % 4, columns 32 (w / 4) ..
 constexpr uint32_t A_BYTES = TM * KS * 2;
 constexpr uint32_t B_BYTES = TN_MAX * KS * 2;
 constexpr uint32_t STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t SM_BAR = STAGES * STAGE_BYTES;        // one mbarrier per stage
 constexpr uint32_t SM_TMEM = SM_BAR + STAGES * 8;         // TMEM base from tcgen05.alloc
 constexpr uint32_t SM_TOTAL = SM_TMEM + 16;
-constexpr uint32_t TMEM_COLS = 128;
+constexpr uint32_t TMEM_COLS = 64;
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 static_assert(TMEM_COLS >= TN_MAX, "accumulator columns");
-static_assert(2 * SM_TOTAL <= 227 * 1024, "two CTAs per SM");
+static_assert(3 * SM_TOTAL <= 227 * 1024, "three CTAs per SM");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -227,10 +229,12 @@ __global__ void __launch_bounds__(THREADS) gemm_tc_kernel(const GemmArgs g, int*
   if (fail) {
     if (tid == 0) atomicExch(status, fail);
   } else {
-    const int m = m0 + warp * 32 + lane;
-    for (int c = 0; c < tn; c += 16) {
+    const int quad = warp & 3, cbeg = (warp >> 2) * 32;
+    const int m = m0 + quad * 32 + lane;
+    const int cend = cbeg + 32 < tn ? cbeg + 32 : tn;
+    for (int c = cbeg; c < cend; c += 16) {
       float v[16];
-      if (nk > 0) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      if (nk > 0) tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c, v);
       else
 #pragma unroll
         for (int i = 0; i < 16; ++i) v[i] = 0.0f;

@@ -227,17 +227,20 @@ __global__ void loss_kernel(const float* __restrict__ raw, const float* __restri
 }
 
 // Column sums in two deterministic stages: block (x, z) sums rows
-// [256 z, 256 z + 256) of 32 columns (8 row threads per column, rows in a
-// fixed interleave, then the 8 partials in order) into part[z][j]; a second
-// pass adds part[0..S)[j] in order.
+// [64 z, 64 z + 64) of 32 columns (8 row threads per column, rows in a fixed
+// interleave, then the 8 partials in order) into part[z][j]; a second pass
+// adds part[0..S)[j] in order.
+constexpr int kColRows = 64;  // rows per first-stage block
+
 __global__ void __launch_bounds__(256) colsum_part_kernel(const bf16* __restrict__ X, const float* __restrict__ w,
                                                           int M, int N, float* __restrict__ part) {
   __shared__ float red[8][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int j = blockIdx.x * 32 + tx, m0 = blockIdx.y * 256;
+  const int j = blockIdx.x * 32 + tx, m0 = blockIdx.y * kColRows;
   float acc = 0.0f;
   if (j < N)
-    for (int r = ty; r < 256; r += 8) {
+#pragma unroll
+    for (int r = ty; r < kColRows; r += 8) {
       const int m = m0 + r;
       if (m < M) acc = fmaf(w ? w[m] : 1.0f, __bfloat162float(X[(size_t)m * N + j]), acc);
     }
@@ -259,9 +262,9 @@ __global__ void colsum_finish_kernel(const float* __restrict__ part, int S, int 
 }
 
 // out[j] = sum_m w[m] X[m][j] (w = 1 if null) with the two kernels above;
-// `part` holds ceil(M / 256) x N floats
+// `part` holds ceil(M / kColRows) x N floats
 cudaError_t colsum(const bf16* X, const float* w, int M, int N, float* out, float* part, cudaStream_t st) {
-  const int S = (M + 255) / 256;
+  const int S = (M + kColRows - 1) / kColRows;
   colsum_part_kernel<<<dim3((N + 31) / 32, S), 256, 0, st>>>(X, w, M, N, part);
   colsum_finish_kernel<<<(N + 127) / 128, 128, 0, st>>>(part, S, N, out);
   return cudaGetLastError();
@@ -605,7 +608,7 @@ int ensure_rows(cem_surrogate_ctx* s, int M) {
   A((void**)&s->partial, sizeof(float) * ((M + 255) / 256 + 1));
   A((void**)&s->loss_d, sizeof(float));
   A((void**)&s->splitk, sizeof(float) * (size_t)kMaxSplit * s->width * std::max(s->width, s->in_dim));
-  A((void**)&s->colpart, sizeof(float) * (size_t)((M + 255) / 256) * s->width);
+  A((void**)&s->colpart, sizeof(float) * (size_t)((M + kColRows - 1) / kColRows) * s->width);
   if (e != cudaSuccess) {
     cudaGetLastError();
     sur_free_work(s);

@@ -78,6 +78,8 @@ def parse():
                          "every plan to the end vs successive halving")
     ap.add_argument("--mlp-only", type=int, default=0,
                     help="time only the surrogate forward on this many rows (profiling driver)")
+    ap.add_argument("--train-only", type=int, default=0,
+                    help="time this many surrogate training steps (batch 4096) on each GEMM path (profiling driver)")
     return ap.parse_args()
 
 
@@ -511,6 +513,39 @@ def surrogate_roofline(P, seed, M=65536, reps=20):
             "peak_basis": f"bf16_tflops ({src}, burst)", "launches": reps}
 
 
+def run_train_only(args):
+    """Times --train-only AdamW steps of the surrogate (48 -> 4 x 256 -> 1,
+    batch 4096 drawn from 65,536 stored rows) with the dense layers on the
+    tiled mma.sync GEMM and on the tcgen05 GEMM: 5 untimed steps, then the
+    timed ones (each cem_surrogate_train call ends with a device sync)."""
+    import numpy as np
+    import torch
+
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    rng = np.random.default_rng(args.seed)
+    x = torch.tensor(rng.uniform(-1, 1, (65536, 48)).astype(np.float32), device="cuda")
+    t = torch.tensor(rng.uniform(0, 1, 65536).astype(np.float32), device="cuda")
+    B = 4096
+    # forward: 4 layers; backward: weight gradients of 4 layers, input gradients of 3
+    gemm_flops = 2.0 * B * ((48 * 256 + 3 * 256 * 256) * 2 + 3 * 256 * 256)
+    out = {"train_only": args.train_only, "batch": B, "gemm_gflop_per_step": gemm_flops / 1e9}
+    for path, name in ((1, "tiled_mma_sync"), (2, "tcgen05")):
+        with P.Surrogate(256, 4, seed=args.seed) as S:
+            S.set_gemm_path(path)
+            S.train(x, t, batch=B, steps=5, seed=1)
+            t0 = time.perf_counter()
+            S.train(x, t, batch=B, steps=args.train_only, seed=1)
+            ms = (time.perf_counter() - t0) / args.train_only * 1e3
+            if S.status() != 0:
+                raise SystemExit("surrogate training: a bounded pipeline wait expired")
+        out[name] = {"ms_per_step": ms}
+    print(json.dumps(out), flush=True)
+
+
 def run_mlp_only(args):
     """Times the surrogate's BF16 tensor-core forward (4 x 256-wide layers) on
     --mlp-only rows through both paths (the tiled mma.sync GEMM and the fused
@@ -662,6 +697,9 @@ def main():
         return
     if args.paper_ce:
         run_paper_ce(args)
+        return
+    if args.train_only:
+        run_train_only(args)
         return
     if args.mlp_only:
         run_mlp_only(args)

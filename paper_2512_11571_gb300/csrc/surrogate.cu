@@ -229,7 +229,8 @@ __global__ void loss_kernel(const float* __restrict__ raw, const float* __restri
 // Column sums in two deterministic stages: block (x, z) sums rows
 // [64 z, 64 z + 64) of 32 columns (8 row threads per column, rows in a fixed
 // interleave, then the 8 partials in order) into part[z][j]; a second pass
-// adds part[0..S)[j] in order.
+// adds part[0..S)[j] the same way (8 interleaved runs, then their sums in
+// order).
 constexpr int kColRows = 64;  // rows per first-stage block
 
 __global__ void __launch_bounds__(256) colsum_part_kernel(const bf16* __restrict__ X, const float* __restrict__ w,
@@ -253,12 +254,23 @@ __global__ void __launch_bounds__(256) colsum_part_kernel(const bf16* __restrict
   }
 }
 
-__global__ void colsum_finish_kernel(const float* __restrict__ part, int S, int N, float* __restrict__ out) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= N) return;
+// second stage: 8 row threads per column add partials z = ty, ty + 8, ...
+// in order, then the 8 sums are added in order
+__global__ void __launch_bounds__(256) colsum_finish_kernel(const float* __restrict__ part, int S, int N,
+                                                            float* __restrict__ out) {
+  __shared__ float red[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int j = blockIdx.x * 32 + tx;
   float t = 0.0f;
-  for (int z = 0; z < S; ++z) t += part[(size_t)z * N + j];
-  out[j] = t;
+  if (j < N)
+    for (int z = ty; z < S; z += 8) t += part[(size_t)z * N + j];
+  red[ty][tx] = t;
+  __syncthreads();
+  if (ty == 0 && j < N) {
+    float u = 0.0f;
+    for (int q = 0; q < 8; ++q) u += red[q][tx];
+    out[j] = u;
+  }
 }
 
 // out[j] = sum_m w[m] X[m][j] (w = 1 if null) with the two kernels above;
@@ -266,7 +278,7 @@ __global__ void colsum_finish_kernel(const float* __restrict__ part, int S, int 
 cudaError_t colsum(const bf16* X, const float* w, int M, int N, float* out, float* part, cudaStream_t st) {
   const int S = (M + kColRows - 1) / kColRows;
   colsum_part_kernel<<<dim3((N + 31) / 32, S), 256, 0, st>>>(X, w, M, N, part);
-  colsum_finish_kernel<<<(N + 127) / 128, 128, 0, st>>>(part, S, N, out);
+  colsum_finish_kernel<<<(N + 31) / 32, 256, 0, st>>>(part, S, N, out);
   return cudaGetLastError();
 }
 
@@ -331,11 +343,22 @@ struct Segs {
 };
 
 // AdamW on the FP32 master parameters, then refresh their BF16 copies
+// adam_t_d: AdamW steps taken before this one (device counter, see step_end_kernel)
+// end of a training step: record the batch loss, advance both counters
+__global__ void step_end_kernel(int* __restrict__ step_d, long long* __restrict__ adam_t_d,
+                                const float* __restrict__ loss_d, float* __restrict__ hist_d) {
+  if (hist_d) hist_d[*step_d] = *loss_d;
+  *step_d += 1;
+  *adam_t_d += 1;
+}
+
 __global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ grad, float* __restrict__ m1,
                              float* __restrict__ m2, bf16* __restrict__ pb, int total, Segs segs, float lr, float b1,
-                             float b2, float eps, float wd, float c1, float c2) {
+                             float b2, float eps, float wd, const long long* __restrict__ adam_t_d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= total) return;
+  const float tstep = (float)(*adam_t_d + 1);
+  const float c1 = 1.0f - powf(b1, tstep), c2 = 1.0f - powf(b2, tstep);
   int decay = 0;
   for (int s = 0; s < segs.n; ++s)
     if (i >= segs.off[s] && i < segs.off[s] + segs.len[s]) decay = segs.decay[s];
@@ -376,11 +399,14 @@ __global__ void features_kernel(const float* __restrict__ theta, int N, int D, c
 }
 
 // minibatch of B rows drawn with replacement (Philox on (step, i)); gathers x and t
+// step: the training call's step counter on the device (so one captured
+// step replays with a new batch each time)
 __global__ void gather_batch_kernel(const bf16* __restrict__ X, const float* __restrict__ t, int M, int in_dim,
-                                    int B, uint64_t seed, uint32_t step, bf16* __restrict__ xb,
+                                    int B, uint64_t seed, const int* __restrict__ step_d, bf16* __restrict__ xb,
                                     float* __restrict__ tb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= B) return;
+  const uint32_t step = (uint32_t)*step_d;
   // one Philox block per row: the first word picks the row
   uint32_t c0 = (uint32_t)i, c1 = step, c2 = 0x5AFEu, c3 = 0u, k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
   for (int r = 0; r < 10; ++r) {
@@ -555,6 +581,8 @@ struct cem_surrogate_ctx {
   // change), status word of its bounded waits, path selection
   void* tc_pack = nullptr;
   int* tc_status = nullptr;
+  int* step_d = nullptr;         // training: step of the current cem_surrogate_train call
+  long long* adam_t_d = nullptr;  // training: AdamW steps taken (mirrors adam_step)
   bool tc_pack_valid = false;
   int fwd_path = 0;   // 0 automatic, 1 tiled GEMM, 2 tcgen05
   int gemm_path = 0;  // training GEMMs: 0 automatic (tcgen05 where the shape allows), 1 tiled mma.sync
@@ -835,6 +863,8 @@ int cem_surrogate_create(int in_dim, int width, int depth, uint64_t seed, cem_su
   A((void**)&s->scene16, sizeof(float) * 16);
   if (mlp_tc_supported(in_dim, width, depth)) A(&s->tc_pack, mlp_tc_pack_bytes());
   A((void**)&s->tc_status, sizeof(int));
+  A((void**)&s->step_d, sizeof(int));
+  A((void**)&s->adam_t_d, sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(s->tc_status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(s->p, init.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(s->m1, 0, sizeof(float) * o);
@@ -858,7 +888,8 @@ int cem_surrogate_destroy(cem_surrogate_handle s) {
   cudaDeviceSynchronize();
   sur_free_work(s);
   void* ptrs[] = {s->p, s->pb, s->g, s->m1, s->m2, s->norm, s->lohi, s->scene16,
-                  s->pool_theta, s->pool_x, s->pool_score, s->keep_idx, s->tc_pack, s->tc_status};
+                  s->pool_theta, s->pool_x, s->pool_score, s->keep_idx, s->tc_pack, s->tc_status,
+                  s->step_d, s->adam_t_d};
   for (void* p : ptrs) cudaFree(p);
   delete s;
   return CEM_OK;
@@ -961,17 +992,26 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   // whole data set in BF16 once
   bf16* Xall = nullptr;
   float* hist_d = nullptr;  // per-step losses stay on the device until the end (no per-step sync)
+  cudaStream_t st = nullptr;
   if (cudaMalloc(&Xall, sizeof(bf16) * (size_t)M * s->in_dim) != cudaSuccess ||
       (loss_hist_h && steps > 0 && cudaMalloc(&hist_d, sizeof(float) * (size_t)steps) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(Xall);
     return fail(CEM_ERR_NO_MEMORY, "training set does not fit");
   }
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(Xall);
+    cudaFree(hist_d);
+    return fail(CEM_ERR_CUDA, "cem_surrogate_train: stream creation failed");
+  }
+  cudaDeviceSynchronize();  // earlier work on other streams (parameters, data) is complete
   const size_t n = (size_t)M * s->in_dim;
-  to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256>>>(x_d, n, Xall);
-  if (normalize) target_stats_kernel<<<1, 256>>>(t_d, M, s->norm);
+  to_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x_d, n, Xall);
+  if (normalize) target_stats_kernel<<<1, 256, 0, st>>>(t_d, M, s->norm);
   int rc = ensure_rows(s, batch);
   if (rc != CEM_OK) {
+    cudaStreamDestroy(st);
     cudaFree(Xall);
     cudaFree(hist_d);
     return rc;
@@ -979,26 +1019,50 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   const Segs segs = param_segments(s);
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   s->tc_pack_valid = false;  // the BF16 weights change below
-  cudaError_t e = cudaGetLastError();
-  for (int it = 0; it < steps && e == cudaSuccess; ++it) {
-    gather_batch_kernel<<<(batch + 255) / 256, 256>>>(Xall, t_d, M, s->in_dim, batch, seed, (uint32_t)it, s->xin,
-                                                       s->tb);
-    e = forward_rows(s, batch, nullptr, use_tc_gemm(s), 0);
-    if (e == cudaSuccess) e = backward_rows(s, batch, 0);
-    if (e != cudaSuccess) break;
-    ++s->adam_step;
-    const float c1 = 1.0f - std::pow(b1, (float)s->adam_step), c2 = 1.0f - std::pow(b2, (float)s->adam_step);
-    adamw_kernel<<<(s->total + 255) / 256, 256>>>(s->p, s->g, s->m1, s->m2, s->pb, s->total, segs, lr, b1, b2, eps,
-                                                  weight_decay, c1, c2);
-    e = cudaGetLastError();
-    if (hist_d && e == cudaSuccess)
-      e = cudaMemcpyAsync(hist_d + it, s->loss_d, sizeof(float), cudaMemcpyDeviceToDevice, 0);
+  cudaError_t e = cudaMemsetAsync(s->step_d, 0, sizeof(int), st);
+  const long long t0 = s->adam_step;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(s->adam_t_d, &t0, sizeof(t0), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // t0 is read before this function returns
+  // one step: batch -> forward -> backward -> AdamW -> counters; everything
+  // that varies between steps is read from the device
+  auto enqueue_step = [&]() -> cudaError_t {
+    gather_batch_kernel<<<(batch + 255) / 256, 256, 0, st>>>(Xall, t_d, M, s->in_dim, batch, seed, s->step_d,
+                                                              s->xin, s->tb);
+    cudaError_t r = forward_rows(s, batch, nullptr, use_tc_gemm(s), st);
+    if (r == cudaSuccess) r = backward_rows(s, batch, st);
+    if (r != cudaSuccess) return r;
+    adamw_kernel<<<(s->total + 255) / 256, 256, 0, st>>>(s->p, s->g, s->m1, s->m2, s->pb, s->total, segs, lr, b1, b2,
+                                                         eps, weight_decay, s->adam_t_d);
+    step_end_kernel<<<1, 1, 0, st>>>(s->step_d, s->adam_t_d, s->loss_d, hist_d);
+    return cudaGetLastError();
+  };
+  // the first step runs directly (it also sets up the kernels), the others
+  // replay that step captured as one CUDA graph; direct launches if capture fails
+  int done = 0;
+  if (e == cudaSuccess && steps > 0) {
+    e = enqueue_step();
+    done = 1;
   }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && steps > 1) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t ce = enqueue_step();
+      const cudaError_t ee = cudaStreamEndCapture(st, &graph);
+      if (ce != cudaSuccess || ee != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+    }
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    for (; done < steps && e == cudaSuccess; ++done) e = exec ? cudaGraphLaunch(exec, st) : enqueue_step();
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) s->adam_step += steps;
   if (hist_d && e == cudaSuccess) {
     e = cudaMemcpy(loss_hist_h, hist_d, sizeof(float) * (size_t)steps, cudaMemcpyDeviceToHost);
     for (int it = 0; it < steps; ++it) loss_hist_h[it] /= (float)batch;
   }
+  cudaStreamDestroy(st);
   cudaFree(Xall);
   cudaFree(hist_d);
   if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("cem_surrogate_train: ") + cudaGetErrorString(e));

@@ -107,10 +107,17 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid) 
                : "memory");
 }
 
+// 16 bytes into shared memory from registers
+__device__ __forceinline__ void st16(uint32_t dst, uint4 v) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+               : "memory");
+}
+
 // one K-slice [k0, k0 + KS) of an operand with `rows` rows starting at r0
-// (extent nrows) into its core-matrix layout at dst
+// (extent nrows) into its core-matrix layout at dst; ones_at > 0 (MN-major
+// only): rows from ones_at on are not read, row ones_at is 1 and the rest 0
 __device__ __forceinline__ void stage_operand(uint32_t dst, const bf16* X, int ld, int kmajor, int r0, int rows,
-                                              int nrows, int k0, int kend, int tid) {
+                                              int nrows, int k0, int kend, int tid, int ones_at = 0) {
   // consecutive threads fill consecutive 16-byte rows of a core matrix
   // (conflict-free shared-memory stores)
   for (int i = tid; i < rows * (KS / 8); i += THREADS) {
@@ -122,8 +129,13 @@ __device__ __forceinline__ void stage_operand(uint32_t dst, const bf16* X, int l
     } else {  // piece (k, g): rows r0 + 8 g .. + 7 at k
       const int k = i % KS, g = i / KS;
       const int gk = k0 + k, gr = r0 + g * 8;
+      const uint32_t d = dst + (uint32_t)((g * 4 + (k >> 3)) * 128 + (k & 7) * 16);
+      if (ones_at > 0 && gr >= ones_at) {  // BF16 1.0 in the first element of row ones_at
+        st16(d, make_uint4(gr == ones_at && gk < kend ? 0x3F80u : 0u, 0u, 0u, 0u));
+        continue;
+      }
       const bool ok = gk < kend && gr < nrows;
-      cp16(dst + (uint32_t)((g * 4 + (k >> 3)) * 128 + (k & 7) * 16), ok ? X + (size_t)gk * ld + gr : X, ok);
+      cp16(d, ok ? X + (size_t)gk * ld + gr : X, ok);
     }
   }
 }
@@ -180,7 +192,7 @@ __global__ void __launch_bounds__(THREADS) gemm_tc_kernel(const GemmArgs g, int*
     const uint32_t sa = base + (uint32_t)(kc % STAGES) * STAGE_BYTES, sb = sa + A_BYTES;
     const int k0 = kbeg + kc * KS;
     stage_operand(sa, g.A, g.lda, g.a_kmajor, m0, TM, g.M, k0, kend, tid);
-    stage_operand(sb, g.B, g.ldb, g.b_kmajor, n0, tn, g.N, k0, kend, tid);
+    stage_operand(sb, g.B, g.ldb, g.b_kmajor, n0, tn, g.N, k0, kend, tid, g.n_real);
   };
 
   for (int s = 0; s < STAGES - 1; ++s) {
@@ -241,6 +253,10 @@ __global__ void __launch_bounds__(THREADS) gemm_tc_kernel(const GemmArgs g, int*
       if (m >= g.M) continue;
       const int n = n0 + c;
       if (EPI == EPI_F32) {
+        if (!g.part && g.n_real > 0 && n >= g.n_real) {  // the ones column: a row sum
+          if (n == g.n_real) g.cbias[m] = v[0];
+          continue;
+        }
         float* dst = g.part ? g.part + ((size_t)blockIdx.z * g.M + m) * g.N + n : g.C + (size_t)m * g.ldc + n;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -295,6 +311,7 @@ bool gemm_tc_supported(const GemmArgs& g) {
   if (g.C && (g.ldc % 4 != 0 || !aligned16(g.C))) return false;
   if (g.Cb && (g.ldcb % 8 != 0 || !aligned16(g.Cb))) return false;
   if (g.part && !aligned16(g.part)) return false;
+  if (g.n_real > 0 && (g.b_kmajor || g.n_real % 16 != 0 || g.N != g.n_real + 16 || !g.cbias)) return false;
   return true;
 }
 

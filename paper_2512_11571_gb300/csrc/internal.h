@@ -233,6 +233,12 @@ struct GemmArgs {
   // partials are then summed in z order (deterministic)
   int kchunk;
   float* part;
+  // EPI_F32, tcgen05 path only: n_real > 0 appends a row of ones to op(B)
+  // (MN-major B with n_real real rows, N = n_real + 16), so column n_real of
+  // C is the row sum of op(A) (a bias gradient); it goes to cbias[m], the
+  // columns < n_real to C
+  int n_real;
+  float* cbias;
 };
 // tcgen05 path: shapes it takes (operand rows and leading dimensions in
 // whole 16-byte units, N a multiple of 16, 16-byte aligned bases)

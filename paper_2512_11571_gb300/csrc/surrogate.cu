@@ -142,13 +142,18 @@ __global__ void __launch_bounds__(GT) gemm_bf16_kernel(GemmArgs g) {
       }
 }
 
-// C[m, n] = sum over z of part[z][m][n], in z order
-__global__ void splitk_sum_kernel(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C, int ldc) {
+// C[m, n] = sum over z of part[z][m][n], in z order; with n_real > 0 the
+// columns >= n_real are the appended ones column (n_real -> cbias[m]) and padding
+__global__ void splitk_sum_kernel(const float* __restrict__ part, int S, int M, int N, float* __restrict__ C, int ldc,
+                                  int n_real, float* __restrict__ cbias) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= M * N) return;
+  const int m = i / N, n = i % N;
+  if (n_real > 0 && n > n_real) return;
   float acc = 0.0f;
   for (int z = 0; z < S; ++z) acc += part[(size_t)z * M * N + i];
-  C[(size_t)(i / N) * ldc + i % N] = acc;
+  if (n_real > 0 && n == n_real) cbias[m] = acc;
+  else C[(size_t)m * ldc + n] = acc;
 }
 
 // tc: run the product on tcgen05 (csrc/gemm_tc.cu) when its shape allows,
@@ -166,13 +171,15 @@ cudaError_t gemm(const GemmArgs& g, bool tc, int* status, cudaStream_t st) {
   cudaError_t e;
   if (tc && gemm_tc_supported(h)) {
     e = gemm_tc(EPI, h, status, st);
+  } else if (g.n_real > 0) {
+    return cudaErrorInvalidValue;  // the ones column exists on the tcgen05 path only
   } else {
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, S);
     gemm_bf16_kernel<EPI><<<grid, GT, 0, st>>>(h);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess || S == 1 || EPI != EPI_F32) return e;
-  splitk_sum_kernel<<<(g.M * g.N + 255) / 256, 256, 0, st>>>(g.part, S, g.M, g.N, g.C, g.ldc);
+  splitk_sum_kernel<<<(g.M * g.N + 255) / 256, 256, 0, st>>>(g.part, S, g.M, g.N, g.C, g.ldc, g.n_real, g.cbias);
   return cudaGetLastError();
 }
 
@@ -635,7 +642,7 @@ int ensure_rows(cem_surrogate_ctx* s, int M) {
   A((void**)&s->tb, sizeof(float) * M);
   A((void**)&s->partial, sizeof(float) * ((M + 255) / 256 + 1));
   A((void**)&s->loss_d, sizeof(float));
-  A((void**)&s->splitk, sizeof(float) * (size_t)kMaxSplit * s->width * std::max(s->width, s->in_dim));
+  A((void**)&s->splitk, sizeof(float) * (size_t)kMaxSplit * s->width * (std::max(s->width, s->in_dim) + 16));
   A((void**)&s->colpart, sizeof(float) * (size_t)((M + kColRows - 1) / kColRows) * s->width);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -746,9 +753,19 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
     g.ldc = K;
     g.kchunk = split_chunk(M);
     g.part = s->splitk;
-    cudaError_t e = gemm<EPI_F32>(g, use_tc_gemm(s), s->tc_status, st);
-    if (e != cudaSuccess) return e;
-    e = colsum(dz, nullptr, M, W, s->g + s->b_off[l], s->colpart, st);
+    // on tcgen05 the bias gradient db_l = sum over rows of dz rides along as
+    // one more column (a row of ones appended to a_in^T); else a column sum
+    GemmArgs ga = g;
+    ga.N = K + 16;
+    ga.n_real = K;
+    ga.cbias = s->g + s->b_off[l];
+    cudaError_t e;
+    if (use_tc_gemm(s) && gemm_tc_supported(ga)) {
+      e = gemm<EPI_F32>(ga, true, s->tc_status, st);
+    } else {
+      e = gemm<EPI_F32>(g, use_tc_gemm(s), s->tc_status, st);
+      if (e == cudaSuccess) e = colsum(dz, nullptr, M, W, s->g + s->b_off[l], s->colpart, st);
+    }
     if (e != cudaSuccess) return e;
     if (l > 0) {  // dz_{l-1} = (dz W_l) * gelu'(z_{l-1})
       GemmArgs h;

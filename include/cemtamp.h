@@ -453,6 +453,26 @@ int cem_surrogate_screen(cem_handle h, cem_surrogate_handle s, const float* mean
  * costs only (elites never come from the surrogate).  Synchronous. */
 int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
                        int n_pool, int n_explore, cem_result* out);
+/* Online fine-tuning of the surrogate during a screened run (not in the
+ * paper, which has no surrogate): the features and score targets of every
+ * simulated sample go into a device ring of `capacity` rows (a multiple of
+ * p->N, at most 2^22; the most recent samples win), and after every `every`
+ * iterations (0 = never, not after the last) the surrogate takes `steps`
+ * AdamW steps of `batch` rows drawn from the filled part of the ring, with
+ * the target normalisation of its earlier training kept.  seed + iteration
+ * draws the batches. */
+typedef struct {
+  int32_t every, steps, batch, capacity;
+  float lr, weight_decay;
+  uint64_t seed;
+} cem_finetune_params;
+/* cem_solve_screened with the fine-tuning above; the surrogate's weights
+ * change.  With every = 0 the result equals cem_solve_screened's.  Errors:
+ * CEM_ERR_INVALID_ARG for bad fine-tune parameters, CEM_ERR_NO_MEMORY if the
+ * ring does not fit, CEM_ERR_UNSUPPORTED unless the surrogate takes the 48
+ * standard features.  Synchronous. */
+int cem_solve_screened_ft(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
+                          int n_pool, int n_explore, const cem_finetune_params* ft, cem_result* out);
 
 /* Threads per block of the rollout kernel: 0 (automatic), 8, 16 or a
  * multiple of 32 up to 256. */

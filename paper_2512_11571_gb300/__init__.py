@@ -39,6 +39,7 @@ EXPORTS = [
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
+    "cem_solve_screened_ft",
     "cem_surrogate_set_forward_path", "cem_surrogate_forward_path", "cem_surrogate_status",
     "cem_surrogate_set_gemm_path", "cem_surrogate_gemm_path",
     "cem_last_error", "cem_version",
@@ -128,6 +129,11 @@ class cem_problem_params(C.Structure):
 class cem_multiplan_params(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("N", C.c_int32), ("K", C.c_int32), ("iters", C.c_int32),
                 ("cov_mode", C.c_int32), ("halving_iters", C.c_int32), ("keep", C.c_int32)]
+
+
+class cem_finetune_params(C.Structure):
+    _fields_ = [("every", C.c_int32), ("steps", C.c_int32), ("batch", C.c_int32), ("capacity", C.c_int32),
+                ("lr", C.c_float), ("weight_decay", C.c_float), ("seed", C.c_uint64)]
 
 
 class cem_result(C.Structure):
@@ -287,6 +293,8 @@ def load(path: str = LIB_PATH):
                                        vp, vp, vp]
     L.cem_solve_screened.argtypes = [H, H, fptr, C.POINTER(cem_solve_params), C.c_int, C.c_int,
                                      C.POINTER(cem_result)]
+    L.cem_solve_screened_ft.argtypes = [H, H, fptr, C.POINTER(cem_solve_params), C.c_int, C.c_int,
+                                        C.POINTER(cem_finetune_params), C.POINTER(cem_result)]
     L.cem_autotune.argtypes = [H, C.c_int, C.c_char_p, C.POINTER(C.c_int)]
     L.cem_last_error.restype = C.c_char_p
     L.cem_version.restype = C.c_char_p
@@ -685,6 +693,13 @@ def cem_solve_screened(h, s, scene16, params: cem_solve_params, n_pool, n_explor
     return out
 
 
+def cem_solve_screened_ft(h, s, scene16, params: cem_solve_params, n_pool, n_explore, ft: cem_finetune_params):
+    sc_, psc = _f32(scene16)
+    out = cem_result()
+    _check(load().cem_solve_screened_ft(h, s, psc, C.byref(params), n_pool, n_explore, C.byref(ft), C.byref(out)))
+    return out
+
+
 class Surrogate:
     """The cost surrogate MLP (one library handle)."""
 
@@ -911,14 +926,23 @@ class Scene:
         return cem_get_launch(self.h, N)
 
     def solve_screened(self, surrogate, scene16, seed, N, K, iters, n_pool, n_explore=0, cov_mode="full",
-                       problem=0):
+                       problem=0, finetune=None):
+        """Screened CE loop; finetune = dict(every, steps, batch, capacity, lr,
+        weight_decay, seed) fine-tunes the surrogate on the run's own samples."""
         p = cem_solve_params()
         p.seed, p.N, p.K, p.iters, p.cov_mode, p.problem = seed, N, K, iters, COV[cov_mode], problem
         hist = np.zeros(iters, np.float32)
         keff = np.zeros(iters, np.int32)
         p.best_J_hist_h = hist.ctypes.data_as(C.POINTER(C.c_float))
         p.k_eff_hist_h = keff.ctypes.data_as(C.POINTER(C.c_int32))
-        r = cem_solve_screened(self.h, surrogate.h, scene16, p, n_pool, n_explore)
+        if finetune is None:
+            r = cem_solve_screened(self.h, surrogate.h, scene16, p, n_pool, n_explore)
+        else:
+            f = dict(every=5, steps=100, batch=4096, capacity=4 * N, lr=5e-4, weight_decay=1e-4, seed=0)
+            f.update(finetune)
+            ft = cem_finetune_params(int(f["every"]), int(f["steps"]), int(f["batch"]), int(f["capacity"]),
+                                     float(f["lr"]), float(f["weight_decay"]), int(f["seed"]))
+            r = cem_solve_screened_ft(self.h, surrogate.h, scene16, p, n_pool, n_explore, ft)
         D = self.D
         return dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                     mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),

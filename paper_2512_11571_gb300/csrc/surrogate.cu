@@ -1194,8 +1194,25 @@ int cem_surrogate_screen(cem_handle h, cem_surrogate_handle s, const float* mean
   return CEM_OK;
 }
 
-int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
-                       int n_pool, int n_explore, cem_result* out) {
+}  // extern "C"
+
+namespace {
+
+// the replay ring of cem_solve_screened_ft (features and targets of every
+// simulated sample of the run), freed on every way out
+struct Replay {
+  float* x = nullptr;
+  float* t = nullptr;
+  ~Replay() {
+    cudaFree(x);
+    cudaFree(t);
+  }
+};
+
+// the screened CE loop; ft (may be null): fine-tune the surrogate on the
+// run's own simulated samples every ft->every iterations
+int solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
+                   int n_pool, int n_explore, const cem_finetune_params* ft, cem_result* out) {
   set_last_error(CEM_OK, "");
   if (!h || !s || !scene16_h || !p || !out) return fail(CEM_ERR_INVALID_ARG, "null argument");
   if (p->N < 1 || n_pool < p->N || n_pool > CEM_MAX_N) return fail(CEM_ERR_UNSUPPORTED, "1 <= N <= n_pool <= 2^20");
@@ -1204,6 +1221,19 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
     return fail(CEM_ERR_UNSUPPORTED, "K in 1..4096, iters in 1..1e5");
   const cem_skeleton_desc& k = handle_skeleton(h);
   const int D = k.D, N = p->N;
+  Replay rb;
+  if (ft) {
+    if (ft->every < 0 || ft->steps < 0 || ft->batch < 1 || ft->batch > (1 << 20))
+      return fail(CEM_ERR_INVALID_ARG, "fine-tune: every >= 0, steps >= 0, batch in 1..2^20");
+    if (ft->capacity < N || ft->capacity % N != 0 || ft->capacity > (1 << 22))
+      return fail(CEM_ERR_INVALID_ARG, "fine-tune: capacity a multiple of N, at most 2^22");
+    if (s->in_dim != 48) return fail(CEM_ERR_UNSUPPORTED, "fine-tune needs the 48-feature surrogate input");
+    if (cudaMalloc(&rb.x, sizeof(float) * (size_t)ft->capacity * 48) != cudaSuccess ||
+        cudaMalloc(&rb.t, sizeof(float) * (size_t)ft->capacity) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(CEM_ERR_NO_MEMORY, "fine-tune replay buffer does not fit");
+    }
+  }
   int rc = ensure_pool(s, n_pool, N, D);
   if (rc != CEM_OK) return rc;
   SolveBuffers b;
@@ -1247,7 +1277,23 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
       dr.iter_ptr = &b.track->iter;
     }
     SUR_CUDA(launch_rollout(b.scene, b.kind, b.theta, N, b.J, b.cls, b.block, b.tpr, b.dr ? &dr : nullptr, st));
+    if (ft) {  // this iteration's simulated samples (features, score targets) into the ring
+      const int pos = (int)(((long long)j * N) % ft->capacity);
+      features_kernel<float><<<(N + 127) / 128, 128, 0, st>>>(b.theta, N, D, s->lohi, s->scene16, rb.x + (size_t)pos * 48);
+      score_target_kernel<<<(N + 255) / 256, 256, 0, st>>>(b.J, b.cls, N, rb.t + pos);
+      SUR_CUDA(cudaGetLastError());
+    }
     SUR_CUDA(launch_refit(a, st));
+    if (ft && ft->every > 0 && ft->steps > 0 && (j + 1) % ft->every == 0 && j + 1 < p->iters) {
+      // fine-tune on every sample simulated so far (the ring's filled part),
+      // keeping the target normalisation of the surrogate's training
+      const long long seen = (long long)(j + 1) * N;
+      const int filled = (int)(seen < ft->capacity ? seen : ft->capacity);
+      SUR_CUDA(cudaStreamSynchronize(st));
+      rc = cem_surrogate_train(s, rb.x, rb.t, filled, ft->batch < filled ? ft->batch : filled, ft->steps, ft->lr,
+                               ft->weight_decay, ft->seed + (uint64_t)j, 0, nullptr);
+      if (rc != CEM_OK) return rc;
+    }
   }
   SUR_CUDA(cudaEventRecord(b.ev1, st));
   rc = handle_read_result(h, p, &b, out);
@@ -1259,6 +1305,21 @@ int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene1
     return fail(CEM_ERR_TIMEOUT, "surrogate forward: a bounded wait on the tensor-core pipeline expired");
   }
   return CEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cem_solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
+                       int n_pool, int n_explore, cem_result* out) {
+  return solve_screened(h, s, scene16_h, p, n_pool, n_explore, nullptr, out);
+}
+
+int cem_solve_screened_ft(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
+                          int n_pool, int n_explore, const cem_finetune_params* ft, cem_result* out) {
+  if (!ft) return fail(CEM_ERR_INVALID_ARG, "null fine-tune parameters");
+  return solve_screened(h, s, scene16_h, p, n_pool, n_explore, ft, out);
 }
 
 }  // extern "C"

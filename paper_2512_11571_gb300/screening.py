@@ -64,18 +64,28 @@ def train_surrogate(X, t, width=256, depth=4, steps=3000, batch=8192, lr=1e-3, s
     return sur, hist
 
 
-def compare(sur, scene_seeds, N=16384, K=512, iters=25, n_pool=65536, n_explore=8192):
+def compare(sur, scene_seeds, N=16384, K=512, iters=25, n_pool=65536, n_explore=8192, finetune=None):
     """Plain CE and surrogate-screened CE (same rollouts per iteration) on
     held-out scenes: final best cost, loop time, and time to reach 1% of the
-    plain run's final cost."""
+    plain run's final cost.  finetune (a dict for Scene.solve_screened): also
+    a screened run whose surrogate fine-tunes on the run's own samples; every
+    screened run starts from the surrogate as given, which is restored at the
+    end."""
+    w0, n0 = sur.params()
     rows = []
     for s in scene_seeds:
         sc, sk, _ = workload.config(2, seed=s)
         f16 = workload.scene_features(sc)
+        c = None
         with Scene(sc, sk) as S:
             S.solve(s, N, K, 1)  # warm-up (allocation, graph)
             a = S.solve(s, N, K, iters)
+            sur.set_params(w0, n0)
             b = S.solve_screened(sur, f16, seed=s, N=N, K=K, iters=iters, n_pool=n_pool, n_explore=n_explore)
+            if finetune is not None:
+                sur.set_params(w0, n0)
+                c = S.solve_screened(sur, f16, seed=s, N=N, K=K, iters=iters, n_pool=n_pool, n_explore=n_explore,
+                                     finetune=dict(finetune, seed=s))
         target = 1.01 * a["best_J"]
 
         def ttc(r):
@@ -83,7 +93,11 @@ def compare(sur, scene_seeds, N=16384, K=512, iters=25, n_pool=65536, n_explore=
             ok = np.where(r["history"] <= target)[0]
             return float(t[ok[0]]) if len(ok) else None
 
-        rows.append(dict(scene=s, plain_J=float(a["best_J"]), plain_ms=a["elapsed_ms"], plain_cls=a["best_cls"],
-                         screened_J=float(b["best_J"]), screened_ms=b["elapsed_ms"], screened_cls=b["best_cls"],
-                         plain_ttc_ms=ttc(a), screened_ttc_ms=ttc(b)))
+        row = dict(scene=s, plain_J=float(a["best_J"]), plain_ms=a["elapsed_ms"], plain_cls=a["best_cls"],
+                   screened_J=float(b["best_J"]), screened_ms=b["elapsed_ms"], screened_cls=b["best_cls"],
+                   plain_ttc_ms=ttc(a), screened_ttc_ms=ttc(b))
+        if c is not None:  # loop time includes the fine-tuning steps
+            row.update(finetuned_J=float(c["best_J"]), finetuned_ms=c["elapsed_ms"], finetuned_cls=c["best_cls"])
+        rows.append(row)
+    sur.set_params(w0, n0)
     return rows

@@ -70,7 +70,7 @@ def _c_offsets(struct_name, fields, tmp_path):
 
 @pytest.mark.parametrize("name", ["cem_slab", "cem_geom", "cem_scene_desc", "cem_action_desc",
                                   "cem_skeleton_desc", "cem_solve_params", "cem_result", "cem_problem_params",
-                                  "cem_paper_params"])
+                                  "cem_paper_params", "cem_finetune_params"])
 def test_struct_layout_matches_header(pkg, name, tmp_path):
     cls = getattr(pkg, name)
     fields = [f[0] for f in cls._fields_]

@@ -185,9 +185,39 @@ def cpu_baseline(sc, sk, cm, seconds=10.0, max_reps=20):
         oracle.refit(th, idx, lo, hi)
         reps += 1
     el = time.perf_counter() - t0
+    # one thread: rollouts of a bounded slice of the same batch
+    n1 = min(N, 1024)
+    th = oracle.sample(1, 0, 0, n1, mean, chol)
+    t1 = time.perf_counter()
+    oracle.rollout(sc, sk, th, nthreads=1)
+    el1 = time.perf_counter() - t1
     return {"value": reps * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} full CE iterations (N={N}, T={T}) of the same workload, FP64, "
-                      f"{cores} threads, {el:.1f} s"}
+                      f"{cores} threads, {el:.1f} s",
+            "single_thread": {"value": n1 * T / el1, "unit": UNIT,
+                              "sample": f"rollouts of {n1} samples (T={T}), 1 thread, {el1:.2f} s"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
 
 
 def run_reference(args):

@@ -19,7 +19,7 @@ import numpy as np
 
 import workload
 
-from . import COV, Scene, Surrogate, cem_surrogate_targets
+from . import COV, Batch, Scene, Surrogate, cem_surrogate_targets
 
 
 def _dev(a):
@@ -28,9 +28,61 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
 
 
-def training_set(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surrogate=None):
+def training_set(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surrogate=None, streams=8):
     """(X [n_scenes*per_scene, 48], t) on the device from pick-place scenes
-    seed0 .. seed0 + n_scenes - 1."""
+    seed0 .. seed0 + n_scenes - 1.  The warm-up CE of all scenes runs as one
+    batch (one persistent rollout launch per iteration); the scenes' sample
+    rollouts then run on `streams` CUDA streams at once, so the GPU is full
+    although one scene's rollouts alone would leave most SMs idle."""
+    import torch
+
+    own = surrogate is None
+    sur = Surrogate(64, 1) if own else surrogate
+    specs = []
+    for s in range(n_scenes):
+        sc, sk, _ = workload.config(2, seed=seed0 + s)
+        specs.append((sc, sk, workload.scene_features(sc), np.array(sk["lo"]), np.array(sk["hi"])))
+    probs = [dict(scene=sc, skel=sk, N=4096, K=256, seed=s, problem=s) for s, (sc, sk, *_) in enumerate(specs)]
+    with Batch(probs) as B:
+        B.iterate(warm_iters)
+        warm = B.read()
+    scenes = [Scene(sc, sk) for sc, sk, *_ in specs]
+    X, T = [], []
+    try:
+        dists = []
+        for (sc, sk, f16, lo, hi), r in zip(specs, warm):
+            chol = np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo)))
+            dists.append([(_dev((lo + hi) / 2), _dev(np.diag((hi - lo) / 4))), (_dev(r["mean"]), _dev(chol))])
+        torch.cuda.synchronize()  # inputs in place before other streams read them
+        pool = [torch.cuda.Stream() for _ in range(streams)]
+        out = []
+        for s, S in enumerate(scenes):
+            with torch.cuda.stream(pool[s % streams]):
+                for j, (m, c) in enumerate(dists[s]):
+                    th = S.sample(m, c, 77 + s, j, per_scene // 2)
+                    J, cls = S.rollout(th)
+                    t = torch.empty_like(J)
+                    cem_surrogate_targets(J, cls, t)
+                    out.append((s, th, t))
+        torch.cuda.synchronize()
+        # features one scene after another (the surrogate context holds one scene's tables)
+        for s, th, t in out:
+            _, _, f16, lo, hi = specs[s]
+            X.append(sur.features(th, lo, hi, f16))
+            T.append(t)
+        x, tt = torch.cat(X), torch.cat(T)
+        torch.cuda.synchronize()
+    finally:
+        for S in scenes:
+            S.close()
+        if own:
+            sur.close()
+    return x, tt
+
+
+def training_set_serial(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surrogate=None):
+    """training_set one scene at a time (cem_solve for the warm-up CE, every
+    launch on the current stream): the reference for the batched version."""
     import torch
 
     own = surrogate is None

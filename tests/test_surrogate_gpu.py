@@ -141,3 +141,21 @@ def test_screened_solve_runs(P):
     with P.Scene(sc, sk, T=600) as Sc, P.Surrogate(64, 2, seed=4) as S:
         r = Sc.solve_screened(S, f16, seed=1, N=512, K=32, iters=3, n_pool=4096)
     assert r["iters_done"] == 3 and np.isfinite(r["best_J"]) and r["best_cls"] <= 2
+
+
+def test_batched_training_set_matches_serial(P):
+    """The batched generator (one batch for the warm-up CE, sample rollouts on
+    several streams) gives the serial generator's rows for the initial
+    distribution bit for bit; the warm-distribution rows come from the same
+    procedure under the batch's per-problem random streams."""
+    from paper_2512_11571_gb300 import screening
+
+    n, per = 3, 2048
+    Xb, tb = screening.training_set(n_scenes=n, per_scene=per, streams=2)
+    Xs, ts = screening.training_set_serial(n_scenes=n, per_scene=per)
+    Xb, tb, Xs, ts = (a.cpu().numpy() for a in (Xb, tb, Xs, ts))
+    assert Xb.shape == Xs.shape == (n * per, 48) and tb.shape == ts.shape == (n * per,)
+    assert np.all(np.isfinite(Xb)) and np.all(np.isfinite(tb))
+    for s in range(n):
+        rows = slice(s * per, s * per + per // 2)  # the initial-distribution half of scene s
+        assert np.array_equal(Xb[rows], Xs[rows]) and np.array_equal(tb[rows], ts[rows])

@@ -159,7 +159,7 @@ __device__ __forceinline__ bool sat_rect(const B2& A, float sa, float ca, float 
   }
   float lx, ly;
   if (ws > 0.0f) {
-    const float inv = 1.0f / ws;
+    const float inv = __fdividef(1.0f, ws);  // fast reciprocal (2 ulp; 0 < ws, far below 2^126)
     lx = mx * inv;
     ly = my * inv;
   } else {
@@ -281,7 +281,9 @@ __device__ __noinline__ void planar_rollout(const DevScene& s, const float* __re
         const float vt = vrx * tx + vry * ty;
         const float ca = cross2(rax, ray, tx, ty), cb = cross2(rbx, rby, tx, ty);
         const float inv_m = inv_mb + inv_mk + ca * ca * inv_Ib + cb * cb * inv_Ik;
-        const float jm = fminf(mu_dt * Fn, fabsf(vt) / inv_m);
+        // fast division (2 ulp; inv_m is an inverse mass sum of order 1..10):
+        // this chain sets the step latency of every warp with a block contact
+        const float jm = fminf(mu_dt * Fn, __fdividef(fabsf(vt), inv_m));
         const float jt = vt > 0.0f ? -jm : jm;
         const float jx = jt * tx, jy = jt * ty;
         k.vx += jx * inv_mk;
@@ -652,7 +654,7 @@ __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, fl
   const float r2 = dx * dx + dy * dy;
   float rr = sqrtf(r2);
   if (rr > 0.0f) {
-    const float inv = 1.0f / rr;
+    const float inv = __fdividef(1.0f, rr);  // fast reciprocal (2 ulp; 0 < rr, far below 2^126)
     cbeta = dx * inv;
     sbeta = dy * inv;
   } else {
@@ -706,6 +708,7 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
                                                float sm, float& J_out, int& cls_out, float* tr) {
   const Group<G> grp;
   const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps;
+  const float inv_dt = 1.0f / dt;  // the held object's velocity: a product, not three divisions per step
   const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap * smu, bcap2 = bcap * bcap;
   const ObjPhys op{s.obj_cap * smu, s.mo * sm, s.dt_mo / sm};
   const float kc = s.k_contact, cc = s.c_contact, akp = s.arm_kp, akd = s.arm_kd;
@@ -873,9 +876,9 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
       ox = nex + offx;
       oy = ney + offy;
       oz = nez + offz;
-      ovx = (nex - ex) / dt;
-      ovy = (ney - ey) / dt;
-      ovz = (nez - ez) / dt;
+      ovx = (nex - ex) * inv_dt;
+      ovy = (ney - ey) * inv_dt;
+      ovz = (nez - ez) * inv_dt;
     } else {
       if (orebuild) {
         omask = near_list<false, G>(s, n_geoms, ox, oy, oz, h, h, h, kSkin, grp);

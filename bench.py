@@ -426,8 +426,11 @@ def run_gb300(args):
         S.solve(args.seed, N, K, 1, init_mean=init_mean, init_cov=init_cov, start_iter=j)
     e2e_s = time.perf_counter() - t0
     e_units, e_secs = aggregate(N * T * args.steps, e2e_s, world)
-    h2d = 4 * D + 4 * D * D * 2 + 128 + 4  # mean, cov, chol, loop state, status
-    d2h = 128 + 4 * D + 4 * D * D + 4 + 4 + 4  # loop state, mean, cov, status, histories
+    # cem_solve moves its small state as one block each way (capi.cu: loop
+    # state 96 B, status, k_eff, mean / cov / chol at the 18-parameter
+    # maximum, each 16-byte aligned: 2800 B), plus the two 1-iteration histories
+    h2d = 2800
+    d2h = 2800 + 4 + 4
 
     if rank == 0:
         fps = flops_per_step(cm["name"])

@@ -81,6 +81,11 @@ struct cem_ctx {
   float* hist_J_d = nullptr;
   int32_t* hist_keff_d = nullptr;
   int32_t* hist_cnt_d = nullptr;
+  // the small solve state (track, status, k_eff, mean, cov, chol, histories)
+  // lives in one device block carved into the pointers above, mirrored by a
+  // pinned host block: a solve moves it in one copy each way
+  unsigned char* state_d = nullptr;
+  unsigned char* state_h = nullptr;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_N = -1, graph_K = -1, graph_cov = -1;
@@ -385,19 +390,44 @@ int default_block(const cem_ctx* h, int N) {
   return cem::default_rollout_block(N);
 }
 
+// byte offsets of the solve state block (iters: history capacity)
+struct StateLayout {
+  size_t track, status, keff, mean, cov, chol, hist_J, hist_keff, hist_cnt, end;
+};
+
+StateLayout state_layout(int iters) {
+  auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  StateLayout L;
+  size_t o = 0;
+  L.track = o;
+  o = up16(o + sizeof(Track));
+  L.status = o;
+  o = up16(o + sizeof(int32_t));
+  L.keff = o;
+  o = up16(o + sizeof(int32_t));
+  L.mean = o;
+  o = up16(o + sizeof(float) * CEM_MAX_D);
+  L.cov = o;
+  o = up16(o + sizeof(float) * CEM_MAX_D * CEM_MAX_D);
+  L.chol = o;
+  o = up16(o + sizeof(float) * CEM_MAX_D * CEM_MAX_D);
+  L.hist_J = o;
+  o = up16(o + sizeof(float) * (size_t)iters);
+  L.hist_keff = o;
+  o = up16(o + sizeof(int32_t) * (size_t)iters);
+  L.hist_cnt = o;
+  o = up16(o + sizeof(int32_t) * 4 * (size_t)iters);
+  L.end = o;
+  return L;
+}
+
 void free_work(cem_ctx* h) {
   cudaFree(h->theta_d);
   cudaFree(h->J_d);
   cudaFree(h->cls_d);
-  cudaFree(h->mean_d);
-  cudaFree(h->cov_d);
-  cudaFree(h->chol_d);
-  cudaFree(h->keff_d);
-  cudaFree(h->status_d);
-  cudaFree(h->track_d);
-  cudaFree(h->hist_J_d);
-  cudaFree(h->hist_keff_d);
-  cudaFree(h->hist_cnt_d);
+  cudaFree(h->state_d);
+  cudaFreeHost(h->state_h);
+  h->state_d = h->state_h = nullptr;
   h->theta_d = nullptr;
   h->J_d = nullptr;
   h->cls_d = nullptr;
@@ -419,20 +449,24 @@ int ensure_work(cem_ctx* h, int N, int iters) {
   }
   free_work(h);
   const int n = N > 0 ? N : 1, it = iters > 0 ? iters : 1;
+  const StateLayout L = state_layout(it);
   if (cudaMalloc(&h->theta_d, sizeof(float) * (size_t)n * D) != cudaSuccess ||
       cudaMalloc(&h->J_d, sizeof(float) * (size_t)n) != cudaSuccess ||
-      cudaMalloc(&h->cls_d, (size_t)n) != cudaSuccess || cudaMalloc(&h->mean_d, sizeof(float) * D) != cudaSuccess ||
-      cudaMalloc(&h->cov_d, sizeof(float) * D * D) != cudaSuccess ||
-      cudaMalloc(&h->chol_d, sizeof(float) * D * D) != cudaSuccess ||
-      cudaMalloc(&h->keff_d, sizeof(int32_t)) != cudaSuccess || cudaMalloc(&h->status_d, sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&h->track_d, sizeof(Track)) != cudaSuccess ||
-      cudaMalloc(&h->hist_J_d, sizeof(float) * it) != cudaSuccess ||
-      cudaMalloc(&h->hist_keff_d, sizeof(int32_t) * it) != cudaSuccess ||
-      cudaMalloc(&h->hist_cnt_d, sizeof(int32_t) * 4 * it) != cudaSuccess) {
+      cudaMalloc(&h->cls_d, (size_t)n) != cudaSuccess || cudaMalloc(&h->state_d, L.end) != cudaSuccess ||
+      cudaMallocHost(&h->state_h, L.end) != cudaSuccess) {
     cudaGetLastError();
     free_work(h);
-    return fail(CEM_ERR_NO_MEMORY, "cudaMalloc of the solve workspace failed");
+    return fail(CEM_ERR_NO_MEMORY, "allocation of the solve workspace failed");
   }
+  h->track_d = reinterpret_cast<Track*>(h->state_d + L.track);
+  h->status_d = reinterpret_cast<int32_t*>(h->state_d + L.status);
+  h->keff_d = reinterpret_cast<int32_t*>(h->state_d + L.keff);
+  h->mean_d = reinterpret_cast<float*>(h->state_d + L.mean);
+  h->cov_d = reinterpret_cast<float*>(h->state_d + L.cov);
+  h->chol_d = reinterpret_cast<float*>(h->state_d + L.chol);
+  h->hist_J_d = reinterpret_cast<float*>(h->state_d + L.hist_J);
+  h->hist_keff_d = reinterpret_cast<int32_t*>(h->state_d + L.hist_keff);
+  h->hist_cnt_d = reinterpret_cast<int32_t*>(h->state_d + L.hist_cnt);
   h->cap_N = n;
   h->cap_iters = it;
   return CEM_OK;
@@ -555,13 +589,16 @@ int handle_init_distribution(cem_handle h, const cem_solve_params* p, SolveBuffe
   tr.best_J = INFINITY;
   tr.hist_len = p->iters;
   const int32_t zero = 0;
-  CEM_CUDA(cudaMemcpyAsync(b->mean, mean.data(), sizeof(float) * D, cudaMemcpyHostToDevice, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(b->cov, cov.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(b->chol, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(b->track, &tr, sizeof(Track), cudaMemcpyHostToDevice, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(b->status, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, b->stream));
-  // the host vectors are consumed before they go out of scope
-  CEM_CUDA(cudaStreamSynchronize(b->stream));
+  // the pinned mirror takes the initial state; one copy moves it
+  const StateLayout L = state_layout(h->cap_iters);
+  unsigned char* m = h->state_h;
+  CEM_CUDA(cudaStreamSynchronize(b->stream));  // nothing of an earlier call still reads or fills the mirror
+  std::memcpy(m + L.track, &tr, sizeof(Track));
+  std::memcpy(m + L.status, &zero, sizeof(int32_t));
+  std::memcpy(m + L.mean, mean.data(), sizeof(float) * D);
+  std::memcpy(m + L.cov, cov.data(), sizeof(float) * D * D);
+  std::memcpy(m + L.chol, chol.data(), sizeof(float) * D * D);
+  CEM_CUDA(cudaMemcpyAsync(h->state_d, m, L.hist_J, cudaMemcpyHostToDevice, b->stream));
   return CEM_OK;
 }
 
@@ -569,20 +606,28 @@ int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b,
   const int D = h->skel.D;
   Track tr;
   int32_t status = 0;
-  CEM_CUDA(cudaMemcpyAsync(&tr, b->track, sizeof(Track), cudaMemcpyDeviceToHost, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(out->mean, b->mean, sizeof(float) * D, cudaMemcpyDeviceToHost, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(out->cov, b->cov, sizeof(float) * D * D, cudaMemcpyDeviceToHost, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(out->chol, b->chol, sizeof(float) * D * D, cudaMemcpyDeviceToHost, b->stream));
-  CEM_CUDA(cudaMemcpyAsync(&status, b->status, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
-  if (p->best_J_hist_h)
-    CEM_CUDA(cudaMemcpyAsync(p->best_J_hist_h, b->hist_J, sizeof(float) * p->iters, cudaMemcpyDeviceToHost, b->stream));
+  // the state block (and the histories asked for) into the pinned mirror,
+  // one copy per contiguous range, then one synchronisation
+  const StateLayout L = state_layout(h->cap_iters);
+  unsigned char* m = h->state_h;
+  const size_t n_j = p->best_J_hist_h ? sizeof(float) * (size_t)p->iters : 0;
+  CEM_CUDA(cudaMemcpyAsync(m, h->state_d, L.hist_J + n_j, cudaMemcpyDeviceToHost, b->stream));
   if (p->k_eff_hist_h)
-    CEM_CUDA(cudaMemcpyAsync(p->k_eff_hist_h, b->hist_keff, sizeof(int32_t) * p->iters, cudaMemcpyDeviceToHost,
-                             b->stream));
+    CEM_CUDA(cudaMemcpyAsync(m + L.hist_keff, h->state_d + L.hist_keff, sizeof(int32_t) * (size_t)p->iters,
+                             cudaMemcpyDeviceToHost, b->stream));
   if (p->class_count_hist_h)
-    CEM_CUDA(cudaMemcpyAsync(p->class_count_hist_h, b->hist_cnt, sizeof(int32_t) * 4 * p->iters,
+    CEM_CUDA(cudaMemcpyAsync(m + L.hist_cnt, h->state_d + L.hist_cnt, sizeof(int32_t) * 4 * (size_t)p->iters,
                              cudaMemcpyDeviceToHost, b->stream));
   CEM_CUDA(cudaStreamSynchronize(b->stream));
+  std::memcpy(&tr, m + L.track, sizeof(Track));
+  std::memcpy(&status, m + L.status, sizeof(int32_t));
+  std::memcpy(out->mean, m + L.mean, sizeof(float) * D);
+  std::memcpy(out->cov, m + L.cov, sizeof(float) * D * D);
+  std::memcpy(out->chol, m + L.chol, sizeof(float) * D * D);
+  if (p->best_J_hist_h) std::memcpy(p->best_J_hist_h, m + L.hist_J, n_j);
+  if (p->k_eff_hist_h) std::memcpy(p->k_eff_hist_h, m + L.hist_keff, sizeof(int32_t) * (size_t)p->iters);
+  if (p->class_count_hist_h)
+    std::memcpy(p->class_count_hist_h, m + L.hist_cnt, sizeof(int32_t) * 4 * (size_t)p->iters);
   float ms = 0.0f;
   CEM_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
   out->elapsed_ms = ms;

@@ -474,7 +474,7 @@ typedef struct {
 int cem_solve_screened_ft(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
                           int n_pool, int n_explore, const cem_finetune_params* ft, cem_result* out);
 
-/* Threads per block of the rollout kernel: 0 (automatic), 8, 16 or a
+/* Threads per block of the rollout kernel: 0 (automatic), 2, 4, 8, 16 or a
  * multiple of 32 up to 256. */
 int cem_set_launch(cem_handle h, int block_threads);
 /* Domain randomisation (Sec. IV-C: plans robust to bounded uncertainty in

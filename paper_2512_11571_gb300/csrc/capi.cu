@@ -387,7 +387,7 @@ DevScene prepare(const cem_scene_desc& s, const cem_skeleton_desc& k) {
 
 int default_block(const cem_ctx* h, int N) {
   if (h->block > 0) return h->block;
-  return cem::default_rollout_block(N);
+  return cem::default_rollout_block(N, h->host.kind, h->tpr);
 }
 
 // byte offsets of the solve state block (iters: history capacity)
@@ -643,7 +643,7 @@ int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b,
 int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k) { return validate(s, k); }
 DevScene prepare_scene(const cem_scene_desc& s, const cem_skeleton_desc& k) { return prepare(s, k); }
 int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
-int default_rollout_block(int N) {
+int default_rollout_block(int N, int kind, int tpr) {
   // spread small batches over every SM scheduler: CTAs of 16 threads (each
   // half-warp its own warp, 4 schedulers per SM) until the schedulers all
   // have work, larger CTAs after that (measured on the 4096-rollout push
@@ -653,6 +653,16 @@ int default_rollout_block(int N) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int b = 16;
   while (b < 256 && (N + 2 * b - 1) / (2 * b) >= 4 * sms) b *= 2;
+  if (kind == CEM_SCENE_PICKPLACE && tpr == 1) {
+    // pick-and-place lanes spend long stretches in different actions, so a
+    // warp pays for its lanes' different branches one after another: fewer
+    // lanes per warp, about 14 warps per SM (3.5 per scheduler), measured
+    // 6.7 ms against 7.5 ms at N = 4096 (2 lanes) and equal at N = 16384
+    const double target = (double)N / (14.0 * sms);
+    int s = 2;
+    while (s < 256 && s * 1.41 < target) s *= 2;
+    if (s < b) b = s;
+  }
   return b;
 }
 }  // namespace cem
@@ -702,7 +712,7 @@ int cem_scene_destroy(cem_handle h) {
 
 int cem_set_launch(cem_handle h, int block_threads) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
-  if (block_threads != 0 && block_threads != 8 && block_threads != 16 &&
+  if (block_threads != 0 && block_threads != 2 && block_threads != 4 && block_threads != 8 && block_threads != 16 &&
       (block_threads < 32 || block_threads > 256 || block_threads % 32))
     return fail(CEM_ERR_INVALID_ARG, "block size must be 0, 8, 16 or a multiple of 32 in 32..256");
   h->block = block_threads;
@@ -993,7 +1003,7 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
       if (bar != std::string::npos && line.substr(0, bar) == key) {
         int b = 0, t = 1;
         const int got = std::sscanf(line.c_str() + bar + 1, "%d|%d", &b, &t);
-        const bool ok_b = b == 16 || (b >= 32 && b <= 256 && b % 32 == 0);
+        const bool ok_b = b == 2 || b == 4 || b == 8 || b == 16 || (b >= 32 && b <= 256 && b % 32 == 0);
         const bool ok_t = t == 1 || (multi_lane && (t == 8 || t == 32) && b >= 32);
         if (got >= 1 && ok_b && ok_t) {
           h->block = b;
@@ -1022,19 +1032,21 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
   CEM_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * D * D, cudaMemcpyHostToDevice, h->stream));
   cudaError_t e = launch_sample(h->mean_d, h->chol_d, 12345, nullptr, 0, 0, N, D, h->theta_d, h->stream);
   if (e != cudaSuccess) return cuda_fail(e, "autotune sample");
-  // candidates: threads per CTA, and for pick-and-place also 8 or 32 lanes
-  // per rollout; a lane width whose first shape is over twice the best so
-  // far is dropped
-  const int blocks1[] = {16, 32, 64, 128, 256};
+  // candidates: threads per CTA (those that keep the CTAs within what the
+  // SMs hold at once), and for pick-and-place also 8 or 32 lanes per
+  // rollout; a lane width whose first shape is over twice the best so far
+  // is dropped
+  const int blocks1[] = {2, 4, 8, 16, 32, 64, 128, 256};
   const int blocksG[] = {32, 64, 128, 256};
   float best_ms = INFINITY;
   int best_b = 128, best_t = 1;
   for (int t : {1, 8, 32}) {
     if (t > 1 && !multi_lane) break;
     const int* bl = t == 1 ? blocks1 : blocksG;
-    const int nb = t == 1 ? 5 : 4;
+    const int nb = t == 1 ? 8 : 4;
     for (int i = 0; i < nb; ++i) {
       const int b = bl[i];
+      if (t == 1 && b < 16 && (long long)(N + b - 1) / b > 32LL * sms) continue;  // more CTAs than resident
       float tot = 0.0f;
       for (int rep = 0; rep < 3; ++rep) {
         CEM_CUDA(cudaEventRecord(h->ev0, h->stream));

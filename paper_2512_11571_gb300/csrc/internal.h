@@ -152,7 +152,8 @@ int rollout_batch_max_ctas_per_sm(int warps, int tpr);
 // host helpers shared by the C entry points (capi.cu)
 int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k);
 DevScene prepare_scene(const cem_scene_desc& s, const cem_skeleton_desc& k);
-int default_rollout_block(int N);
+// rollout threads per CTA when none is set (kind: CEM_SCENE_*, tpr: lanes per rollout)
+int default_rollout_block(int N, int kind = -1, int tpr = 1);
 // records the thread-local message returned by cem_last_error; returns code
 int set_last_error(int code, const std::string& msg);
 

@@ -217,7 +217,7 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   a.hist_keff = hist_keff_d;
   a.hist_cnt = hist_cnt_d;
   a.status = status_d;
-  const int block = default_rollout_block(p->N);
+  const int block = default_rollout_block(p->N, host.kind, 1);
   for (int j = 0; j < p->iters; ++j) {
     STATIC_CUDA(launch_sample(mean_d, chol_d, p->seed, &track_d->iter, 0, p->problem, p->N, D, theta_d, st));
     STATIC_CUDA(launch_rollout(scene_d, host.kind, theta_d, p->N, J_d, cls_d, block, 1, nullptr, st));

@@ -43,7 +43,7 @@ def test_lane_widths_are_bit_identical(P, seed, L, obstacle, N):
         chol = torch.tensor(np.diag((hi - lo) / 4), dtype=torch.float32, device="cuda")
         theta = S.sample(mean, chol, seed, 0, N)
         J1, c1 = rollouts(P, S, theta, 1, 64)
-        for tpr, block in ((8, 32), (8, 256), (32, 32), (32, 128)):
+        for tpr, block in ((1, 2), (1, 4), (1, 8), (1, 16), (8, 32), (8, 256), (32, 32), (32, 128)):
             J, c = rollouts(P, S, theta, tpr, block)
             assert np.array_equal(c, c1), (tpr, block)
             assert np.array_equal(J.view(np.uint32), J1.view(np.uint32)), (tpr, block)
@@ -121,3 +121,19 @@ def test_lane_width_validation(P):
                 S.set_threads_per_rollout(bad)
         S.set_threads_per_rollout(8)  # accepted; push rollouts keep one lane
         assert S.launch(4096)[1] == 1
+
+
+def test_default_launch_shapes(P):
+    """Pick-and-place with one lane per rollout takes few lanes per CTA when
+    N is small (lanes in different actions diverge), the other scenes keep
+    16-thread CTAs; an explicit block size wins."""
+    sc, sk, _ = workload.config(2, seed=0)
+    with P.Scene(sc, sk) as S:
+        assert S.launch(4096) == (2, 1)
+        assert S.launch(16384) == (8, 1)
+        assert S.launch(65536)[0] == 32
+        S.set_launch(64)
+        assert S.launch(4096) == (64, 1)
+    sc, sk, _ = workload.config(1, seed=0)
+    with P.Scene(sc, sk) as S:
+        assert S.launch(4096) == (16, 1)

@@ -646,13 +646,14 @@ int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
 int default_rollout_block(int N, int kind, int tpr) {
   // spread small batches over every SM scheduler: CTAs of 16 threads (each
   // half-warp its own warp, 4 schedulers per SM) until the schedulers all
-  // have work, larger CTAs after that (measured on the 4096-rollout push
-  // workload: 0.505 ms with 16 threads per CTA, 0.526 ms with 32 or 64)
+  // have work, larger CTAs after that, up to 128 threads (measured on the
+  // push workload: 0.505 ms with 16 threads per CTA at N = 4096, 0.526 ms
+  // with 32 or 64; at N = 196,608 128 threads are 4 % faster than 256)
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int b = 16;
-  while (b < 256 && (N + 2 * b - 1) / (2 * b) >= 4 * sms) b *= 2;
+  while (b < 128 && (N + 2 * b - 1) / (2 * b) >= 4 * sms) b *= 2;
   if (kind == CEM_SCENE_PICKPLACE && tpr == 1) {
     // pick-and-place lanes spend long stretches in different actions, so a
     // warp pays for its lanes' different branches one after another: fewer

@@ -974,11 +974,21 @@ __device__ __forceinline__ void stage_scene(const DevScene* __restrict__ g, DevS
   __syncthreads();
 }
 
+// Occupancy: the planar rollouts fit 80 registers without spilling, so three
+// 256-thread CTAs share an SM (12 % faster at N = 196,608 than two); the
+// pick-and-place rollout keeps 128 registers (two CTAs): given more it takes
+// ~150, and its small CTAs then no longer fit one wave at N = 16384
+template <int KIND>
+constexpr int rollout_min_ctas() {
+  return KIND == CEM_SCENE_PICKPLACE ? 2 : 3;
+}
+
 // One rollout per group of G lanes (G > 1 only for pick-and-place); the
 // group's first lane writes the result.
 template <int KIND, bool TRACE, int G>
-__global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict__ scene_g,
-                                                      const float* __restrict__ theta, int N, int steps,
+__global__ void __launch_bounds__(256, rollout_min_ctas<KIND>()) rollout_kernel(const DevScene* __restrict__ scene_g,
+                                                                                const float* __restrict__ theta, int N,
+                                                                                int steps,
                                                       float* __restrict__ J, uint8_t* __restrict__ cls,
                                                       float* __restrict__ trace) {
   __shared__ DevScene s;
@@ -1005,7 +1015,7 @@ __global__ void __launch_bounds__(256) rollout_kernel(const DevScene* __restrict
 // by shuffles: the mean cost (an xor-butterfly sum, identical in every lane)
 // and the worst class; the group's first lane writes.
 template <int KIND>
-__global__ void __launch_bounds__(256) rollout_dr_kernel(const DevScene* __restrict__ scene_g,
+__global__ void __launch_bounds__(256, rollout_min_ctas<KIND>()) rollout_dr_kernel(const DevScene* __restrict__ scene_g,
                                                          const float* __restrict__ theta, int N,
                                                          float* __restrict__ J, uint8_t* __restrict__ cls,
                                                          const DrArgs dr) {

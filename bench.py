@@ -36,7 +36,7 @@ SATURATED_N = 48 * 4096  # enough rollouts to give every SM scheduler several wa
 # DRAM bytes (read + write) of one rollout launch of this workload from the
 # ncu capture in profiles/rollout_push_N4096_T1000.md; reported only while the
 # kernel source still matches the one the counters were taken on
-ROLLOUT_TRAFFIC = {"rollout.cu sha256[:16]": "0c62a536cdf63ab3", "bytes": 126976}
+ROLLOUT_TRAFFIC = {"rollout.cu sha256[:16]": "6c45f86787854617", "bytes": 127232}
 
 
 def rollout_traffic():

@@ -428,9 +428,10 @@ def run_gb300(args):
     e_units, e_secs = aggregate(N * T * args.steps, e2e_s, world)
     # cem_solve moves its small state as one block each way (capi.cu: loop
     # state 96 B, status, k_eff, mean / cov / chol at the 18-parameter
-    # maximum, each 16-byte aligned: 2800 B), plus the two 1-iteration histories
+    # maximum, each 16-byte aligned: 2800 B), plus the 1-iteration histories
+    # the binding asks for (best cost, k_eff, class counts)
     h2d = 2800
-    d2h = 2800 + 4 + 4
+    d2h = 2800 + 4 + 4 + 16
 
     if rank == 0:
         fps = flops_per_step(cm["name"])

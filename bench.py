@@ -290,7 +290,9 @@ def batched_measurement(P, seed, rank, iters=3):
 
 def time_to_cost(seed):
     """CE time-to-cost, surrogate-screened vs plain, on the pick-place task:
-    a surrogate trained on 1,048,576 simulator rollouts (64 training scenes),
+    a surrogate trained on 2,097,152 simulator rollouts (64 training scenes,
+    8192 samples each from the initial distribution and after 4, 8 and 16 CE
+    iterations),
     then plain CE (N = 16384, K = 512, 25 iterations) and screened CE (pool
     65536, the same 16384 rollouts per iteration, 8192 of them unscreened)
     on three held-out scenes; a third run fine-tunes the surrogate on its own
@@ -301,7 +303,8 @@ def time_to_cost(seed):
     from paper_2512_11571_gb300 import screening
 
     t0 = _t.perf_counter()
-    X, t = screening.training_set(n_scenes=64, per_scene=16384)
+    X, t = screening.training_set(n_scenes=64, per_dist=8192)
+    n_rollouts = int(X.shape[0])
     t_data = _t.perf_counter() - t0
     t0 = _t.perf_counter()
     sur, hist = screening.train_surrogate(X, t, steps=3000)
@@ -310,7 +313,7 @@ def time_to_cost(seed):
     ft = dict(every=5, steps=100, batch=4096, capacity=65536, lr=5e-4, weight_decay=1e-4)
     rows = screening.compare(sur, [seed, seed + 1, seed + 2], finetune=ft)
     sur.close()
-    return {"training_rollouts": 64 * 16384, "data_s": t_data, "train_s": t_train,
+    return {"training_rollouts": n_rollouts, "data_s": t_data, "train_s": t_train,
             "train_loss_first_last": [float(hist[:10].mean()), float(hist[-10:].mean())], "scenes": rows,
             "mean_plain_J": float(np.mean([r["plain_J"] for r in rows])),
             "mean_screened_J": float(np.mean([r["screened_J"] for r in rows])),

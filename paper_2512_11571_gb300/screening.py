@@ -4,10 +4,10 @@ simulator, training, and the screened-vs-plain comparison.
 Sequencing only: every sample, rollout, feature, target, training step and
 screening step runs in libcemtamp's kernels; torch holds device memory.
 
-Training data: for each training scene, half of the samples come from the
-initial CE distribution and half from the distribution after a few plain CE
-iterations on that scene (the region CE visits next); target =
-log(1 + J + 10 * class).  Screening keeps CE's simulation budget and elite
+Training data: for each training scene, equal numbers of samples from the
+initial CE distribution and from the distributions after 4, 8 and 16 plain
+CE iterations on that scene (the regions CE visits later, where screening
+has to tell good candidates apart); target = log(1 + J + 10 * class).  Screening keeps CE's simulation budget and elite
 rule (elites from simulated costs only) and spends the surrogate on choosing
 which candidates of a larger pool get simulated, keeping an unscreened
 exploration share so that the elite set is not confined to the surrogate's
@@ -28,10 +28,12 @@ def _dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
 
 
-def training_set(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surrogate=None, streams=8):
-    """(X [n_scenes*per_scene, 48], t) on the device from pick-place scenes
-    seed0 .. seed0 + n_scenes - 1.  The warm-up CE of all scenes runs as one
-    batch (one persistent rollout launch per iteration); the scenes' sample
+def training_set(n_scenes=64, per_dist=8192, stages=(4, 8, 16), seed0=10 ** 6, surrogate=None, streams=8):
+    """(X [n_scenes * per_dist * (len(stages) + 1), 48], t) on the device from
+    pick-place scenes seed0 .. seed0 + n_scenes - 1: per scene, per_dist
+    samples from the initial distribution and from the CE distribution after
+    each stage's iteration count.  The CE of all scenes runs as one batch
+    (one persistent rollout launch per iteration); the scenes' sample
     rollouts then run on `streams` CUDA streams at once, so the GPU is full
     although one scene's rollouts alone would leave most SMs idle."""
     import torch
@@ -43,23 +45,26 @@ def training_set(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surr
         sc, sk, _ = workload.config(2, seed=seed0 + s)
         specs.append((sc, sk, workload.scene_features(sc), np.array(sk["lo"]), np.array(sk["hi"])))
     probs = [dict(scene=sc, skel=sk, N=4096, K=256, seed=s, problem=s) for s, (sc, sk, *_) in enumerate(specs)]
+    dists = [[(_dev((lo + hi) / 2), _dev(np.diag((hi - lo) / 4)))] for (_, _, _, lo, hi) in specs]
     with Batch(probs) as B:
-        B.iterate(warm_iters)
-        warm = B.read()
+        done = 0
+        for st in stages:
+            B.iterate(st - done)
+            done = st
+            for s, r in enumerate(B.read()):
+                lo = specs[s][3]
+                chol = np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo)))
+                dists[s].append((_dev(r["mean"]), _dev(chol)))
     scenes = [Scene(sc, sk) for sc, sk, *_ in specs]
     X, T = [], []
     try:
-        dists = []
-        for (sc, sk, f16, lo, hi), r in zip(specs, warm):
-            chol = np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo)))
-            dists.append([(_dev((lo + hi) / 2), _dev(np.diag((hi - lo) / 4))), (_dev(r["mean"]), _dev(chol))])
         torch.cuda.synchronize()  # inputs in place before other streams read them
         pool = [torch.cuda.Stream() for _ in range(streams)]
         out = []
         for s, S in enumerate(scenes):
             with torch.cuda.stream(pool[s % streams]):
                 for j, (m, c) in enumerate(dists[s]):
-                    th = S.sample(m, c, 77 + s, j, per_scene // 2)
+                    th = S.sample(m, c, 77 + s, j, per_dist)
                     J, cls = S.rollout(th)
                     t = torch.empty_like(J)
                     cem_surrogate_targets(J, cls, t)
@@ -80,8 +85,8 @@ def training_set(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surr
     return x, tt
 
 
-def training_set_serial(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=4, surrogate=None):
-    """training_set one scene at a time (cem_solve for the warm-up CE, every
+def training_set_serial(n_scenes=64, per_dist=8192, stages=(4, 8, 16), seed0=10 ** 6, surrogate=None):
+    """training_set one scene at a time (cem_solve for each scene's CE, every
     launch on the current stream): the reference for the batched version."""
     import torch
 
@@ -94,11 +99,12 @@ def training_set_serial(n_scenes=64, per_scene=16384, seed0=10 ** 6, warm_iters=
             f16 = workload.scene_features(sc)
             lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
             with Scene(sc, sk) as S:
-                r = S.solve(s, 4096, 256, warm_iters)
-                dists = [((lo + hi) / 2, np.diag((hi - lo) / 4)),
-                         (r["mean"], np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo))))]
+                dists = [((lo + hi) / 2, np.diag((hi - lo) / 4))]
+                for st in stages:
+                    r = S.solve(s, 4096, 256, st)
+                    dists.append((r["mean"], np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo)))))
                 for j, (m, c) in enumerate(dists):
-                    th = S.sample(_dev(m), _dev(c), 77 + s, j, per_scene // 2)
+                    th = S.sample(_dev(m), _dev(c), 77 + s, j, per_dist)
                     J, cls = S.rollout(th)
                     t = torch.empty_like(J)
                     cem_surrogate_targets(J, cls, t)

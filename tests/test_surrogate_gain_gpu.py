@@ -25,10 +25,13 @@ def P():
 def test_trained_surrogate_improves_screened_ce(P):
     from paper_2512_11571_gb300 import screening
 
-    X, t = screening.training_set(n_scenes=32, per_scene=16384)
-    assert X.shape == (32 * 16384, 48)
+    X, t = screening.training_set(n_scenes=32, per_dist=8192)
+    assert X.shape == (32 * 4 * 8192, 48)
     sur, hist = screening.train_surrogate(X, t, steps=2000)
-    assert hist[-50:].mean() < 0.25 * hist[:5].mean()
+    # the training set now includes late-stage CE samples, whose costs sit
+    # close together relative to the target normalisation: a larger share of
+    # the normalised loss is irreducible, so the bar is a two-thirds drop
+    assert hist[-50:].mean() < 0.35 * hist[:5].mean()
     scenes = list(range(6))
     trained = screening.compare(sur, scenes)
     untrained_net = P.Surrogate(256, 4, seed=99)

@@ -150,12 +150,13 @@ def test_batched_training_set_matches_serial(P):
     procedure under the batch's per-problem random streams."""
     from paper_2512_11571_gb300 import screening
 
-    n, per = 3, 2048
-    Xb, tb = screening.training_set(n_scenes=n, per_scene=per, streams=2)
-    Xs, ts = screening.training_set_serial(n_scenes=n, per_scene=per)
+    n, per, stages = 3, 1024, (2, 4)
+    Xb, tb = screening.training_set(n_scenes=n, per_dist=per, stages=stages, streams=2)
+    Xs, ts = screening.training_set_serial(n_scenes=n, per_dist=per, stages=stages)
     Xb, tb, Xs, ts = (a.cpu().numpy() for a in (Xb, tb, Xs, ts))
-    assert Xb.shape == Xs.shape == (n * per, 48) and tb.shape == ts.shape == (n * per,)
+    rows_per_scene = per * (len(stages) + 1)
+    assert Xb.shape == Xs.shape == (n * rows_per_scene, 48) and tb.shape == ts.shape == (n * rows_per_scene,)
     assert np.all(np.isfinite(Xb)) and np.all(np.isfinite(tb))
     for s in range(n):
-        rows = slice(s * per, s * per + per // 2)  # the initial-distribution half of scene s
+        rows = slice(s * rows_per_scene, s * rows_per_scene + per)  # the initial-distribution block of scene s
         assert np.array_equal(Xb[rows], Xs[rows]) and np.array_equal(tb[rows], ts[rows])

@@ -311,16 +311,65 @@ def _check(rc):
         raise CemError(rc, load().cem_last_error().decode())
 
 
-def _ptr(t):
+# The library takes plain device pointers and cannot see a buffer's size or
+# type, so the wrappers check both before the call: a short or mistyped
+# tensor would otherwise be read or written out of bounds on the device.
+# Parameters per sample of each live scene handle, input width of each
+# surrogate handle (sizes that the C calls take from the handle):
+_SCENE_D: dict[int, int] = {}
+_SUR_IN: dict[int, int] = {}
+FEATURES = 48  # cem_surrogate_features writes x[N][48]
+
+
+def _ptr(t, dtype=None, n=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor of `dtype` (a torch dtype
+    or a tuple of them) holding at least `n` elements."""
     import torch
 
     if t is None:
         return None
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("expected a CUDA tensor")
+        raise TypeError(f"{name}: expected a CUDA tensor")
     if not t.is_contiguous():
-        raise ValueError("tensor must be contiguous")
+        raise ValueError(f"{name}: tensor must be contiguous")
+    if dtype is not None and t.dtype not in (dtype if isinstance(dtype, tuple) else (dtype,)):
+        raise TypeError(f"{name}: expected dtype {dtype}, got {t.dtype}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{name}: needs at least {n} elements, has {t.numel()}")
     return C.c_void_p(t.data_ptr())
+
+
+def _f32t():
+    import torch
+
+    return torch.float32
+
+
+def _u8t():
+    import torch
+
+    return torch.uint8
+
+
+def _i32t():
+    import torch
+
+    return (torch.int32, getattr(torch, "uint32", torch.int32))
+
+
+def _dim(h):
+    """Parameters per sample of scene handle h (None if not created here)."""
+    return _SCENE_D.get(getattr(h, "value", h))
+
+
+def _mul(*a):
+    """Product of sizes, None if one is unknown."""
+    r = 1
+    for x in a:
+        if x is None:
+            return None
+        r *= int(x)
+    return r
 
 
 def _stream(stream):
@@ -335,32 +384,45 @@ def cem_scene_create(scene: dict, skel: dict, T: int | None = None):
     s, k = pack_scene(scene, skel, T)
     h = C.c_void_p()
     _check(load().cem_scene_create(C.byref(s), C.byref(k), C.byref(h)))
+    _SCENE_D[h.value] = len(skel["lo"])
     return h
 
 
 def cem_scene_destroy(h):
     _check(load().cem_scene_destroy(h))
+    _SCENE_D.pop(getattr(h, "value", h), None)
 
 
 def cem_sample(h, mean, chol, seed, it, problem, N, theta, stream=None):
-    _check(load().cem_sample(h, _ptr(mean), _ptr(chol), seed, it, problem, N, _ptr(theta), _stream(stream)))
+    D = _dim(h)
+    _check(load().cem_sample(h, _ptr(mean, _f32t(), D, "mean"), _ptr(chol, _f32t(), _mul(D, D), "chol"), seed, it,
+                             problem, N, _ptr(theta, _f32t(), _mul(N, D), "theta"), _stream(stream)))
 
 
 def cem_philox_words(h, seed, it, problem, N, words, stream=None):
-    _check(load().cem_philox_words(h, seed, it, problem, N, _ptr(words), _stream(stream)))
+    D = _dim(h)
+    nw = None if D is None else 4 * ((D + 3) // 4)
+    _check(load().cem_philox_words(h, seed, it, problem, N, _ptr(words, _i32t(), _mul(N, nw), "words"),
+                                   _stream(stream)))
 
 
 def cem_rollout_batch(h, theta, N, J, cls, stream=None):
-    _check(load().cem_rollout_batch(h, _ptr(theta), N, _ptr(J), _ptr(cls), _stream(stream)))
+    _check(load().cem_rollout_batch(h, _ptr(theta, _f32t(), _mul(N, _dim(h)), "theta"), N,
+                                    _ptr(J, _f32t(), N, "J"), _ptr(cls, _u8t(), N, "cls"), _stream(stream)))
 
 
 def cem_rollout_trace(h, theta, N, steps, states, stream=None):
-    _check(load().cem_rollout_trace(h, _ptr(theta), N, steps, _ptr(states), _stream(stream)))
+    _check(load().cem_rollout_trace(h, _ptr(theta, _f32t(), _mul(N, _dim(h)), "theta"), N, steps,
+                                    _ptr(states, _f32t(), _mul(N, steps, TRACE_W), "states"), _stream(stream)))
 
 
 def cem_refit(h, theta, J, cls, N, K, cov_mode, mean, cov, chol, elite_idx=None, k_eff=None, stream=None):
-    _check(load().cem_refit(h, _ptr(theta), _ptr(J), _ptr(cls), N, K, cov_mode, _ptr(mean), _ptr(cov),
-                            _ptr(chol), _ptr(elite_idx), _ptr(k_eff), _stream(stream)))
+    D = _dim(h)
+    f = _f32t()
+    _check(load().cem_refit(h, _ptr(theta, f, _mul(N, D), "theta"), _ptr(J, f, N, "J"), _ptr(cls, _u8t(), N, "cls"),
+                            N, K, cov_mode, _ptr(mean, f, D, "mean"), _ptr(cov, f, _mul(D, D), "cov"),
+                            _ptr(chol, f, _mul(D, D), "chol"), _ptr(elite_idx, _i32t(), K, "elite_idx"),
+                            _ptr(k_eff, _i32t(), 1, "k_eff"), _stream(stream)))
 
 
 def cem_solve(h, params: cem_solve_params):
@@ -376,7 +438,8 @@ def cem_solve_paper(h, params: cem_paper_params):
 
 
 def cem_sample_uniform(h, seed, problem, N, theta, stream=None):
-    _check(load().cem_sample_uniform(h, seed, problem, N, _ptr(theta), _stream(stream)))
+    _check(load().cem_sample_uniform(h, seed, problem, N, _ptr(theta, _f32t(), _mul(N, _dim(h)), "theta"),
+                                     _stream(stream)))
 
 
 def cem_set_randomization(h, M, delta_mu, delta_mass, seed):
@@ -588,19 +651,28 @@ class Batch:
         return cem_batch_steps_per_iteration(self.h)
 
 
-def _f32(a):
+def _f32(a, n=None, name="array"):
+    """FP32 host copy of `a` and its pointer; `n`: the element count the call reads."""
     a = np.ascontiguousarray(a, np.float32)
+    if n is not None and a.size != n:
+        raise ValueError(f"{name}: expected {n} elements, got {a.size}")
     return a, a.ctypes.data_as(C.POINTER(C.c_float))
 
 
 def cem_surrogate_create(in_dim=48, width=256, depth=4, seed=0):
     h = C.c_void_p()
     _check(load().cem_surrogate_create(in_dim, width, depth, seed, C.byref(h)))
+    _SUR_IN[h.value] = int(in_dim)
     return h
 
 
 def cem_surrogate_destroy(s):
     _check(load().cem_surrogate_destroy(s))
+    _SUR_IN.pop(getattr(s, "value", s), None)
+
+
+def _in_dim(s):
+    return _SUR_IN.get(getattr(s, "value", s))
 
 
 def cem_surrogate_num_params(s):
@@ -608,9 +680,9 @@ def cem_surrogate_num_params(s):
 
 
 def cem_surrogate_set_params(s, params, norm=None):
-    p, pp = _f32(params)
+    p, pp = _f32(params, cem_surrogate_num_params(s), "params")
     if norm is not None:
-        n, pn = _f32(norm)
+        n, pn = _f32(norm, 2, "norm")
     _check(load().cem_surrogate_set_params(s, pp, pn if norm is not None else None))
 
 
@@ -623,7 +695,9 @@ def cem_surrogate_get_params(s):
 
 
 def cem_surrogate_forward(s, x, y, stream=None):
-    _check(load().cem_surrogate_forward(s, _ptr(x), x.shape[0], _ptr(y), _stream(stream)))
+    M = x.shape[0]
+    _check(load().cem_surrogate_forward(s, _ptr(x, _f32t(), _mul(M, _in_dim(s)), "x"), M, _ptr(y, _f32t(), M, "y"),
+                                        _stream(stream)))
 
 
 def cem_surrogate_set_forward_path(s, path):
@@ -655,46 +729,55 @@ def cem_surrogate_status(s):
 def cem_surrogate_gradient(s, x, t):
     g = np.zeros(cem_surrogate_num_params(s), np.float32)
     loss = C.c_float()
-    _check(load().cem_surrogate_gradient(s, _ptr(x), _ptr(t), x.shape[0], g.ctypes.data_as(C.POINTER(C.c_float)),
-                                         C.byref(loss)))
+    M = x.shape[0]
+    _check(load().cem_surrogate_gradient(s, _ptr(x, _f32t(), _mul(M, _in_dim(s)), "x"), _ptr(t, _f32t(), M, "t"), M,
+                                         g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)))
     return g, loss.value
 
 
 def cem_surrogate_train(s, x, t, batch, steps, lr=1e-3, weight_decay=1e-4, seed=0, normalize=True):
     hist = np.zeros(max(steps, 1), np.float32)
-    _check(load().cem_surrogate_train(s, _ptr(x), _ptr(t), x.shape[0], batch, steps, lr, weight_decay, seed,
-                                      int(normalize), hist.ctypes.data_as(C.POINTER(C.c_float))))
+    M = x.shape[0]
+    _check(load().cem_surrogate_train(s, _ptr(x, _f32t(), _mul(M, _in_dim(s)), "x"), _ptr(t, _f32t(), M, "t"), M, batch,
+                                      steps, lr, weight_decay, seed, int(normalize),
+                                      hist.ctypes.data_as(C.POINTER(C.c_float))))
     return hist[:steps]
 
 
 def cem_surrogate_features(s, theta, lo, hi, scene16, x, stream=None):
-    lo_, plo = _f32(lo)
-    hi_, phi = _f32(hi)
-    sc_, psc = _f32(scene16)
-    _check(load().cem_surrogate_features(s, _ptr(theta), theta.shape[0], theta.shape[1], plo, phi, psc, _ptr(x),
-                                         _stream(stream)))
+    N, D = theta.shape[0], theta.shape[1]
+    lo_, plo = _f32(lo, D, "lo")
+    hi_, phi = _f32(hi, D, "hi")
+    sc_, psc = _f32(scene16, 16, "scene16")
+    _check(load().cem_surrogate_features(s, _ptr(theta, _f32t(), N * D, "theta"), N, D, plo, phi, psc,
+                                         _ptr(x, _f32t(), N * FEATURES, "x"), _stream(stream)))
 
 
 def cem_surrogate_targets(J, cls, t, stream=None):
-    _check(load().cem_surrogate_targets(_ptr(J), _ptr(cls), J.shape[0], _ptr(t), _stream(stream)))
+    N = J.shape[0]
+    _check(load().cem_surrogate_targets(_ptr(J, _f32t(), N, "J"), _ptr(cls, _u8t(), N, "cls"), N,
+                                        _ptr(t, _f32t(), N, "t"), _stream(stream)))
 
 
 def cem_surrogate_screen(h, s, mean, chol, seed, it, problem, n_pool, n_keep, scene16, theta_keep, keep_idx=None,
                          stream=None):
-    sc_, psc = _f32(scene16)
-    _check(load().cem_surrogate_screen(h, s, _ptr(mean), _ptr(chol), seed, it, problem, n_pool, n_keep, psc,
-                                       _ptr(theta_keep), _ptr(keep_idx), _stream(stream)))
+    sc_, psc = _f32(scene16, 16, "scene16")
+    D = _dim(h)
+    f = _f32t()
+    _check(load().cem_surrogate_screen(h, s, _ptr(mean, f, D, "mean"), _ptr(chol, f, _mul(D, D), "chol"), seed, it,
+                                       problem, n_pool, n_keep, psc, _ptr(theta_keep, f, _mul(n_keep, D), "theta_keep"),
+                                       _ptr(keep_idx, _i32t(), n_keep, "keep_idx"), _stream(stream)))
 
 
 def cem_solve_screened(h, s, scene16, params: cem_solve_params, n_pool, n_explore=0):
-    sc_, psc = _f32(scene16)
+    sc_, psc = _f32(scene16, 16, "scene16")
     out = cem_result()
     _check(load().cem_solve_screened(h, s, psc, C.byref(params), n_pool, n_explore, C.byref(out)))
     return out
 
 
 def cem_solve_screened_ft(h, s, scene16, params: cem_solve_params, n_pool, n_explore, ft: cem_finetune_params):
-    sc_, psc = _f32(scene16)
+    sc_, psc = _f32(scene16, 16, "scene16")
     out = cem_result()
     _check(load().cem_solve_screened_ft(h, s, psc, C.byref(params), n_pool, n_explore, C.byref(ft), C.byref(out)))
     return out

@@ -184,3 +184,20 @@ def test_batch_validation_names_the_problem(pkg):
     assert L.cem_batch_iterate(None, 1, 1, None) == -1
     assert L.cem_batch_set_threads_per_rollout(None, 8) == -1
     assert L.cem_batch_get_launch(None, None, None, None) == -1
+
+
+def test_binding_checks_buffers_before_the_call(pkg):
+    """The wrappers refuse host arrays of the wrong length and non-CUDA
+    tensors before anything reaches the library (sizes the C call cannot
+    see: it takes plain pointers)."""
+    np = pytest.importorskip("numpy")
+    torch = pytest.importorskip("torch")
+    th = torch.zeros(4, 3)
+    with pytest.raises(ValueError, match="lo"):
+        pkg.cem_surrogate_features(None, th, np.zeros(2), np.ones(3), np.zeros(16), None)
+    with pytest.raises(ValueError, match="scene16"):
+        pkg.cem_surrogate_features(None, th, np.zeros(3), np.ones(3), np.zeros(15), None)
+    with pytest.raises(TypeError, match="theta: expected a CUDA tensor"):
+        pkg.cem_rollout_batch(None, th, 4, torch.zeros(4), torch.zeros(4, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="scene16"):
+        pkg.cem_solve_screened(None, None, np.zeros(17), pkg.cem_solve_params(), 64)

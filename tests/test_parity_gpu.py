@@ -424,3 +424,33 @@ def test_autotune_and_cache(P, tmp_path):
         assert len(open(cache).read().strip().splitlines()) == 1
         r = S.solve(1, cm["N"], cm["K"], 2)
     assert np.isfinite(r["best_J"])
+
+
+def test_binding_rejects_short_or_mistyped_buffers(P):
+    """A buffer shorter than the call's sizes, or of another type, raises in
+    the wrapper; no kernel sees it."""
+    sc, sk, _ = workload.config(1)
+    with P.Scene(sc, sk) as S:
+        N, D = 64, S.D
+        th = torch.zeros((N, D), device="cuda")
+        J = torch.empty(N, device="cuda")
+        cls = torch.empty(N, dtype=torch.uint8, device="cuda")
+        mean, chol = torch.zeros(D, device="cuda"), torch.eye(D, device="cuda")
+        with pytest.raises(ValueError, match="theta"):
+            P.cem_rollout_batch(S.h, th[: N - 1], N, J, cls)
+        with pytest.raises(ValueError, match="J"):
+            P.cem_rollout_batch(S.h, th, N, J[: N - 1], cls)
+        with pytest.raises(TypeError, match="cls"):
+            P.cem_rollout_batch(S.h, th, N, J, cls.float())
+        with pytest.raises(ValueError, match="chol"):
+            P.cem_sample(S.h, mean, chol[:-1], 0, 0, 0, N, th)
+        with pytest.raises(TypeError, match="mean"):
+            P.cem_sample(S.h, mean.double(), chol, 0, 0, 0, N, th)
+        with pytest.raises(ValueError, match="elite_idx"):
+            P.cem_refit(S.h, th, J, cls, N, 8, 0, mean, chol @ chol.T, chol.clone(),
+                        torch.empty(4, dtype=torch.int32, device="cuda"))
+        # the same calls with the right buffers still run
+        P.cem_sample(S.h, mean, chol, 0, 0, 0, N, th)
+        P.cem_rollout_batch(S.h, th, N, J, cls)
+        torch.cuda.synchronize()
+        assert torch.isfinite(J).all()

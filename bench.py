@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--n", type=int, default=0,
                     help="samples for --rollout-only (0 = the workload's N) and per plan for --multiplan (0 = 4096)")
     ap.add_argument("--reps", type=int, default=3, help="timed launches for --rollout-only")
+    ap.add_argument("--refit-only", action="store_true",
+                    help="time only the select + refit kernel on the move-and-push and pick-place workloads, "
+                         "with their initial class mix and with every sample in class 0 (profiling driver)")
     ap.add_argument("--tpr", type=int, default=1,
                     help="lanes per pick-and-place rollout for --rollout-only (1, 8 or 32)")
     ap.add_argument("--controller", choices=["pd", "astar"], default="pd",
@@ -523,6 +526,55 @@ def run_rollout_only(args):
                       "classes": np.bincount(cls.cpu().numpy(), minlength=4).tolist()}), flush=True)
 
 
+def run_refit_only(args):
+    """Times cem_refit alone (20 launches between CUDA events, best of 5) on
+    the initial samples of the move-and-push and pick-place workloads: with
+    their own classes (few goal samples: K_eff < K, no radix select) and
+    with every sample in class 0 (the radix select of the K-th key runs).
+    Prints one JSON line with the times and a hash of the elite indices,
+    mean, covariance and factor of each case."""
+    import hashlib
+
+    import torch
+
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    out = {"refit_only": True}
+    for cfg in (1, 2):
+        sc, sk, cm = workload.config(cfg, seed=args.seed)
+        N, K = cm["N"], cm["K"]
+        lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
+        with P.Scene(sc, sk) as S:
+            m0 = torch.tensor((lo + hi) / 2, device="cuda")
+            c0 = torch.tensor(np.diag((hi - lo) / 4), device="cuda")
+            th = S.sample(m0, c0, args.seed, 0, N)
+            J, cls = S.rollout(th)
+            idx = torch.empty(K, dtype=torch.int32, device="cuda")
+            ke = torch.empty(1, dtype=torch.int32, device="cuda")
+            for name, cc in (("initial", cls), ("all_class0", torch.zeros_like(cls))):
+                mean, chol = m0.clone(), c0.clone()
+                cov = chol @ chol.T
+                P.cem_refit(S.h, th, J, cc, N, K, 0, mean, cov, chol, idx, ke)
+                torch.cuda.synchronize()
+                best = float("inf")
+                for _ in range(5):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(20):
+                        P.cem_refit(S.h, th, J, cc, N, K, 0, mean, cov, chol, idx, ke)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    best = min(best, e0.elapsed_time(e1) / 20 * 1e3)
+                k = int(ke.item())
+                blob = b"".join(t.cpu().numpy().tobytes() for t in (idx[:k], mean, cov, chol))
+                out[f"{cm['name']}/{name}"] = {"N": N, "K": K, "k_eff": k, "us": round(best, 2),
+                                               "hash": hashlib.sha256(blob).hexdigest()[:12]}
+    print(json.dumps(out), flush=True)
+
+
 def surrogate_roofline(P, seed, M=65536, reps=20):
     """The fused tcgen05 surrogate forward (48 -> 4 x 256 GELU -> 1, BF16
     operands, FP32 accumulation) on M rows: one untimed call, then `reps`
@@ -747,6 +799,9 @@ def main():
         return
     if args.rollout_only:
         run_rollout_only(args)
+        return
+    if args.refit_only:
+        run_refit_only(args)
         return
     if args.impl == "reference":
         run_reference(args)

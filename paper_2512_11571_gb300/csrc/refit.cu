@@ -15,7 +15,11 @@
 // radix select over 52-bit keys (32-bit order-preserving cost bits, 20-bit
 // index) with shared-memory histograms, then a bitonic sort of the K_eff
 // elites (<= 4096 keys in shared memory; elite rows are read through L2);
-// ties are impossible because the index is part of the key.  The
+// ties are impossible because the index is part of the key.  The keys of
+// the first KR * 1024 samples stay in registers across the passes; lanes of
+// a warp that fall into the same histogram bin add once (costs are close
+// together, so the high bits put most keys in one bin); one warp finds the
+// bin that holds the wanted rank (prefix sums over the lanes).  The
 // statistics are accumulated in FP64 by groups of four threads per output
 // with a fixed reduction order (run-to-run deterministic), and one warp
 // factorises the covariance.
@@ -26,6 +30,7 @@ namespace {
 
 constexpr int RT = 1024;
 constexpr int KEY_BITS = 52;
+constexpr int KR = 4;  // samples per thread whose keys stay in registers (N <= 4096 entirely)
 
 __device__ __forceinline__ uint32_t order_bits(float x) {
   const uint32_t u = __float_as_uint(x);
@@ -53,10 +58,13 @@ __device__ bool cholesky_warp(double* A, int D, int lane) {
     double d = A[j * D + j];
     const bool ok = d > 0.0;
     if (!__all_sync(0xffffffffu, ok)) return false;
-    const double ljj = sqrt(d);
+    // one reciprocal square root instead of a square root and a division
+    // per row (FP64 is slow on this part; the result is cast to FP32)
+    const double r = rsqrt(d);
+    const double ljj = d * r;
     __syncwarp();
     if (lane == j) A[j * D + j] = ljj;
-    if (lane > j && lane < D) A[lane * D + j] /= ljj;
+    if (lane > j && lane < D) A[lane * D + j] *= r;
     __syncwarp();
     if (lane > j && lane < D)
       for (int k = j + 1; k <= lane; ++k) A[lane * D + k] -= A[lane * D + j] * A[k * D + j];
@@ -70,6 +78,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
   __shared__ int cnt[4];
   __shared__ uint32_t hist[256];
   __shared__ int s_cstar, s_keff, s_rank, s_n, s_fail;
+  __shared__ double s_invk;
   __shared__ uint64_t s_prefix, s_mask;
   __shared__ double s_mean[CEM_MAX_D];
   __shared__ double s_cov[CEM_MAX_D * CEM_MAX_D];
@@ -78,7 +87,20 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
   if (tid < 4) cnt[tid] = 0;
   if (tid == 0) s_n = 0;
   __syncthreads();
-  for (int i = tid; i < N; i += RT) {
+  // keys and classes of samples tid + r * RT, r < KR (class 4: no sample)
+  uint64_t rkey[KR];
+  int rcls[KR];
+#pragma unroll
+  for (int r = 0; r < KR; ++r) {
+    const int i = r * RT + tid;
+    rcls[r] = 4;
+    rkey[r] = 0;
+    if (i < N) {
+      rcls[r] = classify(a.J, a.cls, i, rkey[r]);
+      atomicAdd(&cnt[rcls[r]], 1);
+    }
+  }
+  for (int i = KR * RT + tid; i < N; i += RT) {
     uint64_t key;
     atomicAdd(&cnt[classify(a.J, a.cls, i, key)], 1);
   }
@@ -87,6 +109,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
     const int cs = cnt[0] > 0 ? 0 : cnt[1] > 0 ? 1 : cnt[2] > 0 ? 2 : -1;
     s_cstar = cs;
     s_keff = cs < 0 ? 0 : min(a.K, cnt[cs]);
+    s_invk = s_keff > 0 ? 1.0 / (double)s_keff : 0.0;
     s_rank = s_keff;
     s_prefix = 0;
     s_mask = 0;
@@ -103,22 +126,54 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
         for (int d = tid; d < 256; d += RT) hist[d] = 0;
         __syncthreads();
         const uint64_t prefix = s_prefix, mask = s_mask;
-        for (int i = tid; i < N; i += RT) {
-          uint64_t key;
-          if (classify(a.J, a.cls, i, key) == cstar && (key & mask) == prefix)
-            atomicAdd(&hist[(key >> shift) & ((1u << width) - 1)], 1u);
+        const uint32_t bmask = (1u << width) - 1;
+        // the lanes of a warp with the same bin add once (every lane takes
+        // part: the loop bounds are the same for the whole CTA)
+        auto count = [&](int c, uint64_t key) {
+          const int bin = (c == cstar && (key & mask) == prefix) ? (int)((key >> shift) & bmask) : -1;
+          const unsigned same = __match_any_sync(0xffffffffu, bin);
+          if (bin >= 0 && (tid & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(same));
+        };
+#pragma unroll
+        for (int r = 0; r < KR; ++r)
+          if (r * RT < N) count(rcls[r], rkey[r]);
+        for (int base = KR * RT; base < N; base += RT) {
+          uint64_t key = 0;
+          const int c = base + tid < N ? classify(a.J, a.cls, base + tid, key) : 4;
+          count(c, key);
         }
         __syncthreads();
-        if (tid == 0) {
-          uint32_t cum = 0;
-          int d = 0;
-          for (; d < (1 << width); ++d) {
-            if (cum + hist[d] >= (uint32_t)s_rank) break;
-            cum += hist[d];
+        if (tid < 32) {
+          // lane l sums bins [l * per, (l + 1) * per); the lane whose range
+          // holds the rank-th key walks its bins to the one that holds it
+          const int nb = 1 << width, per = (nb + 31) / 32;
+          uint32_t loc[8], sum = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int d = tid * per + q;
+            loc[q] = (q < per && d < nb) ? hist[d] : 0u;
+            sum += loc[q];
           }
-          s_rank -= (int)cum;
-          s_prefix |= (uint64_t)d << shift;
-          s_mask |= (uint64_t)((1u << width) - 1) << shift;
+          uint32_t incl = sum;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (tid >= o) incl += t;
+          }
+          const uint32_t rank = (uint32_t)s_rank, excl = incl - sum;
+          if (excl < rank && rank <= incl) {
+            uint32_t cum = excl;
+            int d = tid * per;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              if (q >= per || cum + loc[q] >= rank) break;
+              cum += loc[q];
+              ++d;
+            }
+            s_rank = (int)(rank - cum);
+            s_prefix |= (uint64_t)d << shift;
+            s_mask |= (uint64_t)bmask << shift;
+          }
         }
         __syncthreads();
       }
@@ -130,7 +185,13 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
     uint64_t* keys = reinterpret_cast<uint64_t*>(dyn);
     for (int i = tid; i < P; i += RT) keys[i] = ~0ull;
     __syncthreads();
-    for (int i = tid; i < N; i += RT) {
+#pragma unroll
+    for (int r = 0; r < KR; ++r)
+      if (rcls[r] == cstar && rkey[r] <= kth) {
+        const int pos = atomicAdd(&s_n, 1);
+        if (pos < P) keys[pos] = rkey[r];
+      }
+    for (int i = KR * RT + tid; i < N; i += RT) {
       uint64_t key;
       if (classify(a.J, a.cls, i, key) == cstar && key <= kth) {
         const int pos = atomicAdd(&s_n, 1);
@@ -173,7 +234,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
         for (int e = part; e < keff; e += 4) v += (double)eth(e, grp);
       v += __shfl_down_sync(0xffffffffu, v, 2);
       v += __shfl_down_sync(0xffffffffu, v, 1);
-      if (grp < D && part == 0) s_mean[grp] = v / keff;
+      if (grp < D && part == 0) s_mean[grp] = v * s_invk;
       __syncthreads();
       const int npair = D * (D + 1) / 2;
       int pi = 0, pj = 0;
@@ -194,7 +255,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
       v += __shfl_down_sync(0xffffffffu, v, 2);
       v += __shfl_down_sync(0xffffffffu, v, 1);
       if (grp < npair && part == 0) {
-        double c = v / keff;
+        double c = v * s_invk;
         if (pi == pj) {
           const double w = 1e-4 * ((double)a.hi[pi] - (double)a.lo[pi]);
           c += w * w;

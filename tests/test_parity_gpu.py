@@ -293,7 +293,7 @@ def refit_case(P, orc, J, cls, theta, K, lo, hi, diag=False):
     return k
 
 
-@pytest.mark.parametrize("N,K,D", [(64, 8, 3), (1000, 50, 6), (4096, 200, 6), (16384, 512, 14),
+@pytest.mark.parametrize("N,K,D", [(64, 8, 3), (1000, 50, 6), (4096, 200, 6), (5003, 300, 7), (16384, 512, 14),
                                    (65536, 1024, 18), (100, 300, 5)])
 def test_select_refit_matches_oracle(P, orc, N, K, D):
     rng = np.random.default_rng(N + K)

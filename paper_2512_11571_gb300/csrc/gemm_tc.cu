@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "gelu.cuh"
@@ -318,12 +319,12 @@ bool gemm_tc_supported(const GemmArgs& g) {
 cudaError_t gemm_tc(int epi, const GemmArgs& g, int* status, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   constexpr int kMaxDevices = 64;
-  static bool configured[kMaxDevices][3] = {};
+  static std::atomic<bool> configured[kMaxDevices][3];  // host threads may race here; the set-up is idempotent
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices || epi < 0 || epi > 2) return cudaErrorInvalidValue;
-  if (!configured[dev][epi]) {
+  if (!configured[dev][epi].load(std::memory_order_acquire)) {
     e = epi == EPI_F32 ? cudaFuncSetAttribute(gemm_tc_kernel<EPI_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               (int)SM_TOTAL)
         : epi == EPI_BIAS_GELU
@@ -332,7 +333,7 @@ cudaError_t gemm_tc(int epi, const GemmArgs& g, int* status, cudaStream_t st) {
             : cudaFuncSetAttribute(gemm_tc_kernel<EPI_GELU_BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)SM_TOTAL);
     if (e != cudaSuccess) return e;
-    configured[dev][epi] = true;
+    configured[dev][epi].store(true, std::memory_order_release);
   }
   const int S = (epi == EPI_F32 && g.part && g.kchunk > 0) ? (g.K + g.kchunk - 1) / g.kchunk : 1;
   GemmArgs h = g;

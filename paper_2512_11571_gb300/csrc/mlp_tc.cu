@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "internal.h"
@@ -599,21 +600,25 @@ cudaError_t mlp_tc_pack(const void* pb, const MlpTcOffsets& off, void* pack, cud
 cudaError_t mlp_tc_forward(const MlpTcArgs& a, cudaStream_t st) {
   if (a.M <= 0) return cudaSuccess;
   constexpr int kMaxDevices = 64;
-  static int sms[kMaxDevices] = {0};  // per device: SM count once its kernel attribute is set
+  // per device: SM count once its kernel attribute is set (host threads
+  // may race to set it; the attribute call is idempotent)
+  static std::atomic<int> sms[kMaxDevices];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (sms[dev] == 0) {
+  int n_sm = sms[dev].load(std::memory_order_acquire);
+  if (n_sm == 0) {
     e = cudaFuncSetAttribute(mlp_forward_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_TOTAL);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    sms[dev] = n > 0 ? n : 1;
+    n_sm = n > 0 ? n : 1;
+    sms[dev].store(n_sm, std::memory_order_release);
   }
   const int ntiles = (a.M + TM - 1) / TM;
-  mlp_forward_tc_kernel<<<ntiles < sms[dev] ? ntiles : sms[dev], THREADS, SM_TOTAL, st>>>(a);
+  mlp_forward_tc_kernel<<<ntiles < n_sm ? ntiles : n_sm, THREADS, SM_TOTAL, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -31,6 +31,9 @@ namespace {
 constexpr int RT = 1024;
 constexpr int KEY_BITS = 52;
 constexpr int KR = 4;  // samples per thread whose keys stay in registers (N <= 4096 entirely)
+// up to this many elites are staged in shared memory as FP64 rows for the
+// statistics (18 parameters: 72 KB); more are read through L2
+constexpr int KSTAGE = 512;
 
 __device__ __forceinline__ uint32_t order_bits(float x) {
   const uint32_t u = __float_as_uint(x);
@@ -229,13 +232,34 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
       }
       __syncthreads();
     } else {
+      // keff <= KSTAGE: the elite rows once into shared memory (X[e][d] as
+      // FP64), centred after the mean, so each covariance term is one FP64
+      // multiply-add on shared operands; the sums run in the same order and
+      // give the same values as the L2 path
+      const bool staged = keff <= KSTAGE;
+      double* X = reinterpret_cast<double*>(dyn + sizeof(uint64_t) * (size_t)P);
+      if (staged) {
+        for (int q = tid; q < keff * D; q += RT) {
+          const int e = q / D;
+          X[q] = (double)eth(e, q - e * D);
+        }
+        __syncthreads();
+      }
       double v = 0.0;
-      if (grp < D)
-        for (int e = part; e < keff; e += 4) v += (double)eth(e, grp);
+      if (grp < D) {
+        if (staged)
+          for (int e = part; e < keff; e += 4) v += X[e * D + grp];
+        else
+          for (int e = part; e < keff; e += 4) v += (double)eth(e, grp);
+      }
       v += __shfl_down_sync(0xffffffffu, v, 2);
       v += __shfl_down_sync(0xffffffffu, v, 1);
       if (grp < D && part == 0) s_mean[grp] = v * s_invk;
       __syncthreads();
+      if (staged) {
+        for (int q = tid; q < keff * D; q += RT) X[q] -= s_mean[q % D];
+        __syncthreads();
+      }
       const int npair = D * (D + 1) / 2;
       int pi = 0, pj = 0;
       if (grp < npair) {  // pair index -> (pi, pj), pi <= pj
@@ -249,8 +273,12 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
       }
       v = 0.0;
       if (grp < npair) {
-        const double mi = s_mean[pi], mj = s_mean[pj];
-        for (int e = part; e < keff; e += 4) v += ((double)eth(e, pi) - mi) * ((double)eth(e, pj) - mj);
+        if (staged) {
+          for (int e = part; e < keff; e += 4) v += X[e * D + pi] * X[e * D + pj];
+        } else {
+          const double mi = s_mean[pi], mj = s_mean[pj];
+          for (int e = part; e < keff; e += 4) v += ((double)eth(e, pi) - mi) * ((double)eth(e, pj) - mj);
+        }
       }
       v += __shfl_down_sync(0xffffffffu, v, 2);
       v += __shfl_down_sync(0xffffffffu, v, 1);
@@ -334,10 +362,10 @@ __global__ void __launch_bounds__(RT) refit_batch_kernel(const RefitArgs* __rest
 }  // namespace
 
 size_t refit_smem_bytes(int K, int D) {
-  (void)D;
   int P = 1;
   while (P < K) P <<= 1;
-  return sizeof(uint64_t) * (size_t)P;
+  const int ks = K < KSTAGE ? K : KSTAGE;
+  return sizeof(uint64_t) * (size_t)P + sizeof(double) * (size_t)(ks > 0 ? ks : 0) * (size_t)(D > 0 ? D : 0);
 }
 
 cudaError_t configure_refit() {

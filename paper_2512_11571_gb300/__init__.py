@@ -318,6 +318,7 @@ def _check(rc):
 # surrogate handle (sizes that the C calls take from the handle):
 _SCENE_D: dict[int, int] = {}
 _SUR_IN: dict[int, int] = {}
+_BATCH_N: dict[int, int] = {}  # problems of each live batch handle
 FEATURES = 48  # cem_surrogate_features writes x[N][48]
 
 
@@ -513,6 +514,7 @@ def cem_batch_create(problems):
         params[i].problem = pr.get("problem", i)
     h = C.c_void_p()
     _check(load().cem_batch_create(scenes, skels, params, n, C.byref(h)))
+    _BATCH_N[h.value] = n
     return h
 
 
@@ -521,7 +523,10 @@ def cem_batch_set_randomization(h, M, delta_mu, delta_mass, seed):
 
 
 def cem_batch_set_active(h, active):
-    a = np.ascontiguousarray(np.asarray(active, np.int32))
+    a = np.ascontiguousarray(np.asarray(active, np.int32)).reshape(-1)
+    n = _BATCH_N.get(getattr(h, "value", h))
+    if n is not None and a.size != n:
+        raise ValueError(f"active: expected one flag per problem ({n}), got {a.size}")
     _check(load().cem_batch_set_active(h, a.ctypes.data_as(C.POINTER(C.c_int32))))
 
 
@@ -554,6 +559,7 @@ def cem_multiplan_solve(scene: dict, plans: list, seed, N, K, iters, halving_ite
 
 def cem_batch_destroy(h):
     _check(load().cem_batch_destroy(h))
+    _BATCH_N.pop(getattr(h, "value", h), None)
 
 
 def cem_batch_reset(h, stream=None):
@@ -565,6 +571,9 @@ def cem_batch_iterate(h, iters, use_graph=True, stream=None):
 
 
 def cem_batch_read(h, n_problems, stream=None):
+    n = _BATCH_N.get(getattr(h, "value", h))
+    if n is not None and n_problems != n:
+        raise ValueError(f"n_problems: the batch holds {n} problems, got {n_problems}")
     out = (cem_result * n_problems)()
     _check(load().cem_batch_read(h, out, _stream(stream)))
     return out

@@ -102,6 +102,10 @@ def test_batch_active_set(P):
         probs.append(dict(scene=sc, skel=sk, N=300, K=20, seed=9, problem=50 + i))
     with P.Batch(probs) as B:
         B.iterate(2)
+        with pytest.raises(ValueError, match="one flag per problem"):
+            B.set_active([1, 0, 1])
+        with pytest.raises(ValueError, match="holds 4 problems"):
+            P.cem_batch_read(B.h, 3)
         B.set_active([1, 0, 1, 0])
         B.iterate(3)
         got = B.read()

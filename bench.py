@@ -391,6 +391,8 @@ def run_gb300(args):
         torch.distributed.barrier()
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     roll_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    samp_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    refit_ms = [e[2].elapsed_time(e[3]) for e in evs]
     ms = sum(step_ms) / args.steps
     units, secs = aggregate(N * T * args.steps, sum(step_ms) / 1e3, world)
     value = units / secs
@@ -453,7 +455,8 @@ def run_gb300(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(sc, sk, cm), "N": N, "T": T, "D": D, "K": K,
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
-                       "rollout_ms": roll_avg, "wall_s": wall},
+                       "rollout_ms": roll_avg, "sample_ms": sum(samp_ms) / len(samp_ms),
+                       "refit_ms": sum(refit_ms) / len(refit_ms), "wall_s": wall},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": rollout_traffic(),
                          "algorithmic_bytes": N * D * 4 + N * 5,

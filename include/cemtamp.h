@@ -433,8 +433,9 @@ int cem_surrogate_gradient(cem_surrogate_handle s, const float* x_d, const float
  * NULL.  Synchronous. */
 int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t_d, int M, int batch, int steps,
                         float lr, float weight_decay, uint64_t seed, int normalize, float* loss_hist_h);
-/* Training target of simulated samples: t_d[n] = log(1 + J_d[n] + 10 *
- * cls_d[n]) (non-finite costs map to log(1 + 1e6)), monotone in the CE key. */
+/* Training target of simulated samples: t_d[n] = log(1 + max(J_d[n], 0) +
+ * 10 * cls_d[n]); a non-finite cost maps to log(1 + 1e6).  For costs below
+ * 10 it is ordered like the CE key (class first, then J). */
 int cem_surrogate_targets(const float* J_d, const uint8_t* cls_d, int N, float* t_d, void* stream);
 /* The surrogate's input features of N parameter vectors (FP32 x_d[N][48]). */
 int cem_surrogate_features(cem_surrogate_handle s, const float* theta_d, int N, int D, const float* lo_h,

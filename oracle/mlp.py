@@ -9,7 +9,9 @@ rounding points (weights, layer inputs and activations rounded to BF16 with
 round-to-nearest-even; products accumulated exactly here, in FP32 on the GPU).
 
 Pins (tests/test_oracle_mlp.py): central finite differences of the FP64
-loss, torch.autograd in float64, and torch.optim.AdamW in float64.
+loss, torch.autograd in float64, and torch.optim.AdamW in float64; the
+regression targets at closed-form points (e - 1, e^3 - 11, a non-finite
+cost, a negative cost) and their class-first order for costs below 10.
 """
 from __future__ import annotations
 
@@ -137,3 +139,15 @@ def features(theta, lo, hi, scene16):
     x[:, :D] = (theta - 0.5 * (lo + hi)) / (0.5 * (hi - lo))
     x[:, 32:48] = np.asarray(scene16, np.float64)[None, :]
     return x
+
+
+def targets(J, cls):
+    """Regression target of a simulated sample: log(1 + max(J, 0) + 10 class),
+    and log(1 + 1e6) where the cost is not finite.  The class term ranks
+    classes first as the CE key does while costs stay below 10; the
+    logarithm compresses large costs."""
+    J = np.asarray(J, np.float64)
+    c = np.asarray(cls, np.float64)
+    with np.errstate(invalid="ignore"):
+        t = np.log1p(np.maximum(J, 0.0) + 10.0 * c)
+    return np.where(np.isfinite(J), t, math.log1p(1e6))

@@ -530,8 +530,9 @@ __global__ void force_keep_kernel(float* __restrict__ score, int n_explore) {
   if (i < n_explore) score[i] = -3.402823466e38f;
 }
 
-// training target of a simulated sample: log(1 + J + 10 * class), which
-// orders samples like the CE key (class first) and compresses large costs
+// training target of a simulated sample: log(1 + max(J, 0) + 10 * class),
+// which orders samples like the CE key (class first) while costs stay below
+// 10, and compresses large costs
 __global__ void score_target_kernel(const float* __restrict__ J, const uint8_t* __restrict__ cls, int N,
                                     float* __restrict__ t) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -1,5 +1,7 @@
 """Pins of the FP64 surrogate MLP oracle: finite differences, torch autograd
 (float64) and torch's AdamW (float64).  CPU only."""
+import math
+
 import numpy as np
 import pytest
 
@@ -113,3 +115,20 @@ def test_features_layout():
     np.testing.assert_allclose(x[0, :3], [-1, 0, 1])
     assert np.all(x[0, 3:32] == 0)
     np.testing.assert_allclose(x[0, 32:], np.arange(16))
+
+
+def test_targets_closed_forms_and_order():
+    e = math.e
+    # 1 + J + 10 class = 1, e, e^3
+    t = mlp.targets([0.0, e - 1, e ** 3 - 11, np.inf, np.nan, -3.0, 5.0],
+                    [0, 0, 1, 2, 0, 2, 3])
+    np.testing.assert_allclose(t[:3], [0.0, 1.0, 3.0], rtol=0, atol=1e-14)
+    assert t[3] == t[4] == pytest.approx(13.815511557963774, abs=1e-12)  # ln(1 000 001)
+    assert t[5] == pytest.approx(math.log(21.0), abs=1e-15)  # a negative cost counts as 0
+    assert t[6] == pytest.approx(math.log(36.0), abs=1e-15)
+    # costs below 10: sorted by (class, J) gives increasing targets
+    rng = np.random.default_rng(0)
+    J = rng.uniform(0, 9.99, 500)
+    c = rng.integers(0, 4, 500)
+    order = np.lexsort((J, c))
+    assert np.all(np.diff(mlp.targets(J, c)[order]) > 0)

@@ -32,6 +32,21 @@ def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
 
 
+@pytest.mark.parametrize("N", [1, 257, 1000])
+def test_targets_match_oracle(P, N):
+    """Regression targets of simulated samples (FP32 log1p) against the FP64
+    definition, with negative, infinite and NaN costs and every class."""
+    rng = np.random.default_rng(N)
+    J = rng.uniform(-1.0, 30.0, N).astype(np.float32)
+    cls = rng.integers(0, 4, N).astype(np.uint8)
+    J[::7] = np.inf
+    J[3::11] = np.nan
+    t = torch.empty(N, dtype=torch.float32, device="cuda")
+    P.cem_surrogate_targets(dev(J), torch.as_tensor(cls).cuda(), t)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(t.cpu().numpy(), mlp.targets(J, cls), rtol=1e-5, atol=1e-5)
+
+
 @pytest.mark.parametrize("M,width,depth", [(1, 256, 4), (1000, 256, 4), (4097, 64, 2), (300, 200, 3)])
 def test_forward_matches_oracle(P, M, width, depth):
     params = mlp.init_params(48, width, depth, seed=M)

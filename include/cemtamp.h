@@ -192,10 +192,12 @@ int cem_philox_words(cem_handle h, uint64_t seed, uint32_t iter, uint32_t proble
  * succeeded, psi_g false), 2 (otherwise), 3 (non-finite cost). */
 int cem_rollout_batch(cem_handle h, const float* theta_d, int N, float* J_d, uint8_t* cls_d, void* stream);
 
-/* Per-step state of each rollout for `steps` steps: states_d[N][steps][20]
- * (layout documented in DESIGN; planar: base x,y,yaw,vx,vy,w, block ditto,
- * action; pick-place: base x,y,vx,vy, q1,q2,dq1,dq2, azimuth, object
- * x,y,z,vx,vy,vz, attached, action, end-effector x,y,z). */
+/* Per-step state of each rollout for `steps` steps: states_d[N][steps][20],
+ * the state after each step.  Planar scenes: base x, y, yaw, vx, vy, w, then
+ * the block's six values, then the index of the active action, zeros after.
+ * Pick-place: base x, y, vx, vy, joints q1, q2, dq1, dq2, arm azimuth,
+ * object x, y, z, vx, vy, vz, attached (0/1), action index, end-effector
+ * x, y, z. */
 int cem_rollout_trace(cem_handle h, const float* theta_d, int N, int steps, float* states_d, void* stream);
 
 /* Update step of Algorithm 1 with the elite rules of Sec. III-B: rank by
@@ -284,11 +286,14 @@ int cem_n_env(int n0, int n1, int j1, int j);
  * same sample -> rollout -> refit loop on `stream`, keeping every
  * intermediate in one 2 MiB file-scope device array that every GPU loading
  * the library holds until the process exits.  Limits: N * D <= 262144,
- * iters <= 4096, otherwise CEM_ERR_UNSUPPORTED.  The first call on a device
- * looks up the array's address; make it before any stream capture.  All
- * calls share the array (the loop state is rewritten at the start of each
- * call), so calls that overlap on the GPU race: serialise them.  p->use_graph
- * is ignored.  Synchronous; results as cem_solve (elapsed_ms = 0). */
+ * iters <= 4096, otherwise CEM_ERR_UNSUPPORTED.  Every call looks up the
+ * array's address on the current device (so a device reset needs nothing
+ * special); the first call on a device also loads the module, so make it
+ * before any stream capture.  All calls share the array (the loop state is
+ * rewritten at the start of each call), so calls that overlap on the GPU
+ * race: serialise them.  A call that fails after queuing work waits for that
+ * work before it returns.  p->use_graph is ignored.  Synchronous; results as
+ * cem_solve (elapsed_ms = 0). */
 int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_desc* skel, const cem_solve_params* p,
                      cem_result* out, void* stream);
 

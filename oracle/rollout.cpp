@@ -21,7 +21,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <thread>
+#include <utility>
 #include <vector>
 
 // ------------------------------------------------------------------ reals
@@ -65,6 +68,24 @@ inline double Min(double a, double b) { return std::fmin(a, b); }
 inline double Max(double a, double b) { return std::fmax(a, b); }
 inline double Val(double a) { return a; }
 
+// The footprint's mean radius is a constant of the rectangle: the midpoint
+// integral (or_mean_radius, 4e6 square roots) runs once per (a, b) for the
+// whole process and is then looked up, so a rollout call times the dynamics,
+// not this integral.  The value is the same either way.
+double mean_radius_cached(double a, double b) {
+  static std::mutex mu;
+  static std::map<std::pair<double, double>, double> memo;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = memo.find({a, b});
+    if (it != memo.end()) return it->second;
+  }
+  const double r = or_mean_radius(a, b);
+  std::lock_guard<std::mutex> lock(mu);
+  memo[{a, b}] = r;
+  return r;
+}
+
 // Scene-derived constants computed once per call (not per step).
 struct Prep {
   double Ib, Ik, rbar_b, rbar_k;
@@ -76,8 +97,8 @@ Prep prepare(const or_scene& s) {
   // Inertia of a box about its centre: m (w^2 + l^2) / 12 with full sides.
   p.Ib = s.base_mass * (4 * s.base_half[0] * s.base_half[0] + 4 * s.base_half[1] * s.base_half[1]) / 12.0;
   p.Ik = s.block_mass * (4 * s.block_half[0] * s.block_half[0] + 4 * s.block_half[1] * s.block_half[1]) / 12.0;
-  p.rbar_b = or_mean_radius(s.base_half[0], s.base_half[1]);
-  p.rbar_k = s.kind == OR_PUSH ? or_mean_radius(s.block_half[0], s.block_half[1]) : 0.0;
+  p.rbar_b = mean_radius_cached(s.base_half[0], s.base_half[1]);
+  p.rbar_k = s.kind == OR_PUSH ? mean_radius_cached(s.block_half[0], s.block_half[1]) : 0.0;
   if (s.kind == OR_PICKPLACE && s.base_ctrl == 1) base_graph(s, p.base);
   return p;
 }

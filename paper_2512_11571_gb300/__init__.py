@@ -553,6 +553,7 @@ def cem_multiplan_solve(scene: dict, plans: list, seed, N, K, iters, halving_ite
         r, D = out[i], out[i].D
         res.append(dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                         mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
+                        chol=np.array(r.chol[:D * D]).reshape(D, D),
                         iters_done=r.iters_done, iters_run=int(its[i])))
     return res, best.value
 
@@ -631,7 +632,7 @@ class Batch:
             D = r.D
             res.append(dict(best_theta=np.array(r.best_theta[:D]), best_J=r.best_J, best_cls=r.best_class,
                             mean=np.array(r.mean[:D]), cov=np.array(r.cov[:D * D]).reshape(D, D),
-                            iters_done=r.iters_done))
+                            chol=np.array(r.chol[:D * D]).reshape(D, D), iters_done=r.iters_done))
         return res
 
     def autotune(self):

@@ -15,9 +15,15 @@
 // Properties callers must know:
 //   - The array (kScratchBytes, 2 MiB) is part of the library image: every
 //     GPU that loads the library holds it until the process exits.
-//   - The first call on a device looks up the array's device address (and
-//     opts the refit kernel into its shared memory); make that first call
-//     before any stream capture on that device.
+//   - Every call looks up the array's device address for the current device
+//     and opts the refit kernel into its shared memory (both are cheap host
+//     calls after the first, and neither allocates), so a device reset,
+//     which reloads the module at a possibly different address, needs no
+//     special handling.  The first call on a device also loads the module;
+//     make that first call before any stream capture on that device.
+//   - If a launch fails after the call has started writing the array, the
+//     call waits for the work it already queued before it returns the error,
+//     so no kernel of a failed call still uses the array afterwards.
 //   - All calls share the array and it keeps the previous call's contents;
 //     the loop state is fully rewritten at the start of every call.  Calls
 //     that overlap on the GPU (different streams or threads at once) race on
@@ -86,34 +92,39 @@ Layout layout(int N, int D) {
 }
 
 std::mutex g_setup_mu;
-unsigned char* g_dev_ptr[kMaxDevices] = {nullptr};
 
 int fail(int code, const std::string& m) { return set_last_error(code, m); }
 
-// device address of g_scratch for the current device (set up once per device)
+// Device address of g_scratch on the current device, looked up on every call
+// together with the refit kernel's shared-memory attribute: after a device
+// reset the module is loaded again (possibly at another address, and without
+// the attribute), and a fresh lookup is right in every case.
 int scratch_ptr(unsigned char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return fail(CEM_ERR_UNSUPPORTED, "device index beyond 63");
   std::lock_guard<std::mutex> lk(g_setup_mu);
-  if (!g_dev_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(CEM_ERR_CUDA, std::string("cudaGetSymbolAddress(g_scratch): ") + cudaGetErrorString(e));
-    e = configure_refit();
-    if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("refit kernel set-up: ") + cudaGetErrorString(e));
-    g_dev_ptr[dev] = static_cast<unsigned char*>(p);
-  }
-  *out = g_dev_ptr[dev];
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess || !p)
+    return fail(CEM_ERR_CUDA, std::string("cudaGetSymbolAddress(g_scratch): ") + cudaGetErrorString(e));
+  e = configure_refit();
+  if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("refit kernel set-up: ") + cudaGetErrorString(e));
+  *out = static_cast<unsigned char*>(p);
   return CEM_OK;
 }
 
-#define STATIC_CUDA(call)                                                               \
-  do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess) return fail(CEM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+// Failure of a call that has already queued work on the array: wait for that
+// work (its own result ignored) before reporting, so that nothing of this
+// call still reads or writes the array when the caller moves on.
+#define STATIC_CUDA(call)                                                                 \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      cudaStreamSynchronize(st);                                                          \
+      return fail(CEM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));        \
+    }                                                                                     \
   } while (0)
 
 }  // namespace

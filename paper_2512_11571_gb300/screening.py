@@ -52,9 +52,7 @@ def training_set(n_scenes=64, per_dist=8192, stages=(4, 8, 16), seed0=10 ** 6, s
             B.iterate(st - done)
             done = st
             for s, r in enumerate(B.read()):
-                lo = specs[s][3]
-                chol = np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo)))
-                dists[s].append((_dev(r["mean"]), _dev(chol)))
+                dists[s].append((_dev(r["mean"]), _dev(r["chol"])))
     scenes = [Scene(sc, sk) for sc, sk, *_ in specs]
     X, T = [], []
     try:
@@ -102,7 +100,7 @@ def training_set_serial(n_scenes=64, per_dist=8192, stages=(4, 8, 16), seed0=10 
                 dists = [((lo + hi) / 2, np.diag((hi - lo) / 4))]
                 for st in stages:
                     r = S.solve(s, 4096, 256, st)
-                    dists.append((r["mean"], np.linalg.cholesky(r["cov"] + 1e-9 * np.eye(len(lo)))))
+                    dists.append((r["mean"], r["chol"]))
                 for j, (m, c) in enumerate(dists):
                     th = S.sample(_dev(m), _dev(c), 77 + s, j, per_dist)
                     J, cls = S.rollout(th)

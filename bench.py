@@ -1,14 +1,19 @@
 """Benchmark of the CE plan-realization hot path on GB300.
 
-One step = one cross-entropy iteration of Algorithm 1 on the move-and-push
-workload (N = 4096 samples, T = 1000 steps, D = 6, K = 200): Philox sample ->
-fused rollout -> elite select + refit, all on the device through the C ABI.
-Reported value: simulated steps per second (N x T / time per iteration).
+One step = one cross-entropy iteration of Algorithm 1 for the 64-problem
+batch (skeletons of 1..6 actions, N per problem log-uniform in [512, 8192],
+T = 400 / 1000 / 3000, 4.5e8 simulated steps per iteration): the batched
+Philox sampler -> ONE persistent rollout launch -> the segmented select +
+refit, replayed from a CUDA graph, all on the device through the C ABI.
+The timed steps are iterations 0..K-1 of one CE run from the initial
+distributions.  Reported value: simulated steps per second (sum of N x T
+over problems / time per iteration).  The single-problem move-and-push and
+pick-place workloads are reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
 Under torchrun each rank runs an independent replica (its own Philox
-problem id) on its own GPU: weak scaling, no data-path collective.
+problem ids) on its own GPU: weak scaling, no data-path collective.
 """
 from __future__ import annotations
 
@@ -30,22 +35,10 @@ import workload  # noqa: E402
 
 METRIC = "sim steps/sec (N×T) on 1 GB300 & FP32-peak fraction; CEM time-to-cost vs plain"
 UNIT = "sim-steps/s"
-CONFIG = 1  # the move-and-push workload
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 SATURATED_N = 48 * 4096  # enough rollouts to give every SM scheduler several warps
-# DRAM bytes (read + write) of one rollout launch of this workload from the
-# ncu capture in profiles/rollout_push_N4096_T1000.md; reported only while the
-# kernel source still matches the one the counters were taken on
-ROLLOUT_TRAFFIC = {"rollout.cu sha256[:16]": "6c45f86787854617", "bytes": 127232}
-
-
-def rollout_traffic():
-    import hashlib
-
-    path = os.path.join(ROOT, "paper_2512_11571_gb300", "csrc", "rollout.cu")
-    with open(path, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()[:16]
-    return ROLLOUT_TRAFFIC["bytes"] if h == ROLLOUT_TRAFFIC["rollout.cu sha256[:16]"] else None
+CPU_FRACTION = 4  # the CPU legs roll out 1 / CPU_FRACTION of every problem's samples per iteration
+REF_FRACTION = 8  # the reference arm: 1 / REF_FRACTION per step
 
 
 def parse():
@@ -96,6 +89,43 @@ def dist_env():
 def workload_desc(sc, sk, cm):
     return (f"{cm['name']}: N={cm['N']} T={sc['T']} D={len(sk['lo'])} K={cm['K']} dt={sc['dt']} "
             f"(one CE iteration per step, initial distribution)")
+
+
+def batch_problems(seed, rank):
+    """The 64-problem batch with this rank's Philox problem ids."""
+    probs = workload.batch_problems(seed)
+    for i, p in enumerate(probs):
+        p["seed"] = seed
+        p["problem"] = 1000 * rank + i
+    return probs
+
+
+def batch_desc(probs, seed):
+    steps = sum(p["N"] * p["scene"]["T"] for p in probs)
+    by_len = {}
+    for p in probs:
+        by_len[p["L"]] = by_len.get(p["L"], 0) + 1
+    return (f"batched-64: {len(probs)} CE problems (workload.batch_problems(seed={seed})), skeletons of 1..6 "
+            f"actions (problems per length {dict(sorted(by_len.items()))}), N per problem in "
+            f"[{min(p['N'] for p in probs)}, {max(p['N'] for p in probs)}], T = 400 / 1000 / 3000, "
+            f"K = max(8, N/20), full covariance; {steps} simulated steps per CE iteration; "
+            f"one step = one CE iteration of every problem (iterations 0..K-1 of one run)")
+
+
+def batch_flops(probs, seed):
+    """Algorithmic flops of one batch iteration: sum over problems of
+    flops/step x N x T, from the oracle's counts (per problem for the batch
+    the counts were taken on, else the mean per skeleton length)."""
+    with open(os.path.join(ROOT, "workload", "flops_per_step.json")) as f:
+        tab = json.load(f)["batch-64"]
+    per = tab["problems"]
+    exact = tab["seed"] == seed and len(per) == len(probs) and all(
+        q["L"] == p["L"] and q["N"] == p["N"] for q, p in zip(per, probs))
+    tot = 0.0
+    for i, p in enumerate(probs):
+        fps = per[i]["flops"] if exact else tab["flops_by_length"][str(p["L"])]
+        tot += fps * p["N"] * p["scene"]["T"]
+    return tot, ("per problem" if exact else "per skeleton length")
 
 
 def aggregate(value_units: float, seconds: float, world: int):
@@ -170,35 +200,55 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(sc, sk, cm, seconds=10.0, max_reps=20):
-    """The FP64 oracle, as it stands, on this host's cores: full CE
-    iterations of the same workload until ~`seconds` have passed."""
+def oracle_batch_iteration(oracle, probs, it, frac, cores):
+    """One CE iteration of the FP64 oracle, as it stands, over every problem
+    of the batch on a bounded sample: ceil(N / frac) samples per problem
+    drawn from its initial distribution at Philox iteration `it`, rolled
+    out on `cores` threads, then select + refit with K scaled alike.
+    Returns the simulated steps."""
+    steps = 0
+    for p in probs:
+        sc, sk = p["scene"], p["skel"]
+        lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+        n = -(-p["N"] // frac)
+        th = oracle.sample(p["seed"], it, p["problem"], n, (lo + hi) / 2, np.diag((hi - lo) / 4))
+        J, cls = oracle.rollout(sc, sk, th, nthreads=cores)
+        idx = oracle.select(J.astype(np.float32), cls, max(1, -(-p["K"] // frac)))
+        if len(idx):
+            oracle.refit(th, idx, lo, hi)
+        steps += n * sc["T"]
+    return steps
+
+
+def cpu_baseline(probs, seconds=10.0, max_iters=50):
+    """The FP64 oracle on this host's cores on the same 64-problem batch:
+    CE iterations on 1 / CPU_FRACTION of every problem's samples until
+    ~`seconds` have passed."""
     import oracle
 
     oracle.build()
-    lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
-    mean, chol = (lo + hi) / 2, np.diag((hi - lo) / 4)
     cores = os.cpu_count() or 1
-    N, T = cm["N"], sc["T"]
-    reps, t0 = 0, time.perf_counter()
-    while reps < max_reps and (time.perf_counter() - t0 < seconds or reps == 0):
-        th = oracle.sample(1, reps, 0, N, mean, chol)
-        J, cls = oracle.rollout(sc, sk, th, nthreads=cores)
-        idx = oracle.select(J.astype(np.float32), cls, cm["K"])
-        oracle.refit(th, idx, lo, hi)
-        reps += 1
+    it, steps, t0 = 0, 0, time.perf_counter()
+    while it < max_iters and (time.perf_counter() - t0 < seconds or it == 0):
+        steps += oracle_batch_iteration(oracle, probs, it, CPU_FRACTION, cores)
+        it += 1
     el = time.perf_counter() - t0
-    # one thread: rollouts of a bounded slice of the same batch
-    n1 = min(N, 1024)
-    th = oracle.sample(1, 0, 0, n1, mean, chol)
+    # one thread: a slice of the largest pick-place problem
+    big = max((p for p in probs if p["L"] >= 3), key=lambda p: p["N"])
+    lo, hi = np.array(big["skel"]["lo"]), np.array(big["skel"]["hi"])
+    n1 = 64
+    th = oracle.sample(big["seed"], 0, big["problem"], n1, (lo + hi) / 2, np.diag((hi - lo) / 4))
     t1 = time.perf_counter()
-    oracle.rollout(sc, sk, th, nthreads=1)
+    oracle.rollout(big["scene"], big["skel"], th, nthreads=1)
     el1 = time.perf_counter() - t1
-    return {"value": reps * N * T / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{reps} full CE iterations (N={N}, T={T}) of the same workload, FP64, "
+    T1 = big["scene"]["T"]
+    return {"value": steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{it} CE iterations of the 64-problem batch on 1/{CPU_FRACTION} of every problem's "
+                      f"samples ({steps // max(it, 1)} simulated steps per iteration), FP64, "
                       f"{cores} threads, {el:.1f} s",
-            "single_thread": {"value": n1 * T / el1, "unit": UNIT,
-                              "sample": f"rollouts of {n1} samples (T={T}), 1 thread, {el1:.2f} s"},
+            "single_thread": {"value": n1 * T1 / el1, "unit": UNIT,
+                              "sample": f"rollouts of {n1} samples of a {big['L']}-action pick-place problem "
+                                        f"(T={T1}), 1 thread, {el1:.2f} s"},
             "cpu_model": cpu_model()}
 
 
@@ -224,71 +274,169 @@ def cpu_model():
 
 
 def run_reference(args):
+    """The oracle (the reference is a paper without code) on the same
+    64-problem batch: each step is one CE iteration of every problem on
+    1 / REF_FRACTION of its samples, on this host's cores."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    sc, sk, cm = workload.config(CONFIG, seed=args.seed)
     import oracle
 
     oracle.build()
-    lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
-    mean, chol = (lo + hi) / 2, np.diag((hi - lo) / 4)
+    probs = batch_problems(args.seed, 0)
     cores = os.cpu_count() or 1
-    n_sample = 512  # bounded sample of the N = 4096 batch per step
-    T = sc["T"]
-
-    def step(j):
-        th = oracle.sample(1, j, 0, n_sample, mean, chol)
-        J, cls = oracle.rollout(sc, sk, th, nthreads=cores)
-        idx = oracle.select(J.astype(np.float32), cls, min(cm["K"], n_sample))
-        oracle.refit(th, idx, lo, hi)
-
     for j in range(args.warmup):
-        step(j)
+        oracle_batch_iteration(oracle, probs, j, REF_FRACTION, cores)
     t0 = time.perf_counter()
+    steps = 0
     for j in range(args.steps):
-        step(args.warmup + j)
+        steps += oracle_batch_iteration(oracle, probs, args.warmup + j, REF_FRACTION, cores)
     el = time.perf_counter() - t0
-    v = args.steps * n_sample * T / el
+    v = steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(sc, sk, cm), "l2": "n/a (host)"},
+        "config": {"workload": batch_desc(probs, args.seed), "l2": "n/a (host)"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{n_sample} of the {cm['N']} samples per CE iteration, T={T}, FP64"},
+                         "sample": f"1/{REF_FRACTION} of every problem's samples per CE iteration "
+                                   f"({steps // max(args.steps, 1)} simulated steps per step), FP64, "
+                                   f"{cores} threads"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def batched_measurement(P, seed, rank, iters=3):
-    """64 independent problems (skeletons of 1..6 actions, uneven N and T)
-    advanced together: CE iterations per second and simulated steps per
-    second of the whole batch, launch shape chosen by the autotuner."""
+def batch_headline(P, args, rank, world, local):
+    """The headline: CE iterations of the 64-problem batch, one graph replay
+    per step, the L2 flushed (untimed) before each, device-timed with CUDA
+    events on the launching stream; the library's own stage events give the
+    persistent rollout kernel's time for the roofline.  Then the same run
+    end to end through the public API with the state on the host: each step
+    restores the state from host memory, iterates once and reads it back."""
     import torch
 
-    probs = workload.batch_problems(seed)
-    for i, p in enumerate(probs):
-        p["seed"] = seed
-        p["problem"] = 1000 * rank + i
+    probs = batch_problems(args.seed, rank)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    out = {}
     with P.Batch(probs) as B:
-        warps, ctas, _ = B.autotune()
-        B.reset()
-        B.iterate(1, use_graph=True)  # capture + warm-up
+        warps, ctas, best = B.autotune()
+        tpr = B.launch()[2]
+        B.set_timing(True)
+        B.reset(stream)
+        B.iterate(args.warmup, use_graph=True, stream=stream)  # capture + warm-up
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        st = torch.cuda.current_stream()
-        e0.record(st)
-        B.iterate(iters, use_graph=True, stream=st)
-        e1.record(st)
+        B.reset(stream)  # the timed steps are iterations 0..K-1 of one run
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+        stages = []
+        if world > 1:
+            torch.distributed.barrier()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / iters
-        steps = B.steps_per_iteration
-    return {"problems": len(probs), "sim_steps_per_iteration": steps, "ms_per_iteration": ms,
-            "sim_steps_per_s": steps / (ms / 1e3), "launch": {"warps_per_cta": warps, "ctas_per_sm": ctas},
-            "kernels_per_iteration": 3}
+        with Clocks(local) as clk:
+            t0 = time.perf_counter()
+            for j in range(args.steps):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(j))  # evict the previous step's data from L2 (untimed)
+                evs[j][0].record(stream)
+                B.iterate(1, use_graph=True, stream=stream)
+                evs[j][1].record(stream)
+                stages.append(B.stage_ms())  # waits for this step
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        if world > 1:
+            torch.distributed.barrier()
+        res = B.read(stream)
+        step_ms = [e[0].elapsed_time(e[1]) for e in evs]
+        steps_per_iter = B.steps_per_iteration
+        # end to end: the CE state crosses the PCIe/C2C link every step
+        B.set_timing(False)
+        B.reset(stream)
+        host = B.read_raw(stream)
+        nbytes = B.state_bytes
+        B.iterate(1, use_graph=True, stream=stream)  # re-capture without timing events
+        torch.cuda.synchronize()
+        B.reset(stream)
+        host = B.read_raw(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for j in range(args.steps):
+            B.set_state(host, stream)
+            B.iterate(1, use_graph=True, stream=stream)
+            host = B.read_raw(stream)
+        e2e_s = time.perf_counter() - t0
+        e2e_same = all(int(host[i].best_class) == int(res[i]["best_cls"]) and float(host[i].best_J) == float(res[i]["best_J"])
+                       for i in range(len(probs)))
+    units, secs = aggregate(steps_per_iter * args.steps, sum(step_ms) / 1e3, world)
+    e_units, e_secs = aggregate(steps_per_iter * args.steps, e2e_s, world)
+    out.update(probs=probs, steps_per_iter=steps_per_iter, step_ms=step_ms, stages=stages, wall=wall,
+               clocks=clk.summary() if rank == 0 else None, value=units / secs,
+               e2e=e_units / e_secs, e2e_bytes=nbytes, e2e_same_result=e2e_same,
+               launch={"warps_per_cta": warps, "ctas_per_sm": ctas, "lanes_per_pickplace_rollout": tpr,
+                       "autotune_best_ms": best},
+               classes=np.bincount([r["best_cls"] for r in res], minlength=5).tolist())
+    return out
+
+
+def single_problem(P, cfg, args, rank, steps):
+    """One CE iteration from the initial distribution per step on a
+    single-problem workload (sample -> rollout -> refit through the C ABI,
+    CUDA events around each call, L2 flushed before each step)."""
+    import torch
+
+    sc, sk, cm = workload.config(cfg, seed=args.seed)
+    N, K, T, D = cm["N"], cm["K"], sc["T"], len(sk["lo"])
+    lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
+    mean0 = torch.tensor((lo + hi) / 2, device="cuda")
+    chol0 = torch.diag(torch.tensor((hi - lo) / 4, device="cuda"))
+    cov0 = torch.diag(torch.tensor(((hi - lo) / 4) ** 2, device="cuda"))
+    stream = torch.cuda.Stream()
+    theta = torch.empty((N, D), device="cuda")
+    J = torch.empty(N, device="cuda")
+    cls = torch.empty(N, dtype=torch.uint8, device="cuda")
+    mean, cov, chol = mean0.clone(), cov0.clone(), chol0.clone()
+    idx = torch.empty(K, dtype=torch.int32, device="cuda")
+    keff = torch.empty(1, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    with P.Scene(sc, sk) as S:
+        def step(j, ev=None):
+            with torch.cuda.stream(stream):
+                mean.copy_(mean0)
+                cov.copy_(cov0)
+                chol.copy_(chol0)
+                if ev:
+                    ev[0].record(stream)
+                P.cem_sample(S.h, mean, chol, args.seed, j, rank, N, theta, stream)
+                if ev:
+                    ev[1].record(stream)
+                P.cem_rollout_batch(S.h, theta, N, J, cls, stream)
+                if ev:
+                    ev[2].record(stream)
+                P.cem_refit(S.h, theta, J, cls, N, K, 0, mean, cov, chol, idx, keff, stream)
+                if ev:
+                    ev[3].record(stream)
+
+        for j in range(3):
+            step(j)
+        torch.cuda.synchronize()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        for j in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(j))
+            step(3 + j, evs[j])
+        torch.cuda.synchronize()
+        block, tpr = S.launch(N)
+    step_ms = float(np.mean([e[0].elapsed_time(e[3]) for e in evs]))
+    roll_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    fps = flops_per_step(cm["name"])["flops"]
+    return {"workload": workload_desc(sc, sk, cm), "ms_per_iteration": step_ms,
+            "sim_steps_per_s": N * T / (step_ms / 1e3), "rollout_ms": roll_ms,
+            "sample_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
+            "refit_ms": float(np.mean([e[2].elapsed_time(e[3]) for e in evs])),
+            "rollout_tflops": fps * N * T / (roll_ms / 1e3) / 1e12, "flops_per_step": fps,
+            "launch": {"block": block, "lanes_per_rollout": tpr}, "steps": steps}
 
 
 def time_to_cost(seed):
@@ -337,151 +485,84 @@ def run_gb300(args):
 
     build.build()
     P.load()
-    sc, sk, cm = workload.config(CONFIG, seed=args.seed)
-    N, K, T, D = cm["N"], cm["K"], sc["T"], len(sk["lo"])
+    hd = batch_headline(P, args, rank, world, local)
+    probs = hd["probs"]
+
+    # the single-problem workloads beside it (move-and-push N = 4096,
+    # pick-place N = 16384), and the move-and-push rollout with the GPU full
+    push = single_problem(P, 1, args, rank, steps=10)
+    pick = single_problem(P, 2, args, rank, steps=5)
+    sc, sk, cm = workload.config(1, seed=args.seed)
     lo, hi = np.array(sk["lo"], np.float32), np.array(sk["hi"], np.float32)
-    mean0 = torch.tensor((lo + hi) / 2, device="cuda")
-    chol0 = torch.tensor(np.diag((hi - lo) / 4), device="cuda")
-    cov0 = chol0 @ chol0.T
-    S = P.Scene(sc, sk)
-    stream = torch.cuda.Stream()
-    theta = torch.empty((N, D), device="cuda")
-    J = torch.empty(N, device="cuda")
-    cls = torch.empty(N, dtype=torch.uint8, device="cuda")
-    mean, cov, chol = mean0.clone(), cov0.clone(), chol0.clone()
-    idx = torch.empty(K, dtype=torch.int32, device="cuda")
-    keff = torch.empty(1, dtype=torch.int32, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    problem = rank
-
-    def step(j, ev=None):
-        # every step: one CE iteration from the initial distribution
-        with torch.cuda.stream(stream):
-            mean.copy_(mean0)
-            cov.copy_(cov0)
-            chol.copy_(chol0)
-            if ev:
-                ev[0].record(stream)
-            P.cem_sample(S.h, mean, chol, args.seed, j, problem, N, theta, stream)
-            if ev:
-                ev[1].record(stream)
-            P.cem_rollout_batch(S.h, theta, N, J, cls, stream)
-            if ev:
-                ev[2].record(stream)
-            P.cem_refit(S.h, theta, J, cls, N, K, 0, mean, cov, chol, idx, keff, stream)
-            if ev:
-                ev[3].record(stream)
-
-    for j in range(args.warmup):
-        step(j)
-    torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        t0 = time.perf_counter()
-        for j in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(float(j))  # evict the previous step's data from L2 (untimed)
-            step(args.warmup + j, evs[j])
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    roll_ms = [e[1].elapsed_time(e[2]) for e in evs]
-    samp_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    refit_ms = [e[2].elapsed_time(e[3]) for e in evs]
-    ms = sum(step_ms) / args.steps
-    units, secs = aggregate(N * T * args.steps, sum(step_ms) / 1e3, world)
-    value = units / secs
-
-    # the same rollout kernel with the GPU full (context for the roofline
-    # fraction: N = 4096 leaves most SM schedulers without a warp)
-    th_sat = torch.empty((SATURATED_N, D), device="cuda")
-    J_sat = torch.empty(SATURATED_N, device="cuda")
-    c_sat = torch.empty(SATURATED_N, dtype=torch.uint8, device="cuda")
-    with torch.cuda.stream(stream):
-        P.cem_sample(S.h, mean0, chol0, args.seed, 0, problem, SATURATED_N, th_sat, stream)
-        P.cem_rollout_batch(S.h, th_sat, SATURATED_N, J_sat, c_sat, stream)  # warm-up
+    D, T = len(sk["lo"]), sc["T"]
+    with P.Scene(sc, sk) as S:
+        mean0 = torch.tensor((lo + hi) / 2, device="cuda")
+        chol0 = torch.diag(torch.tensor((hi - lo) / 4, device="cuda"))
+        th_sat = torch.empty((SATURATED_N, D), device="cuda")
+        J_sat = torch.empty(SATURATED_N, device="cuda")
+        c_sat = torch.empty(SATURATED_N, dtype=torch.uint8, device="cuda")
+        st = torch.cuda.current_stream()
+        P.cem_sample(S.h, mean0, chol0, args.seed, 0, rank, SATURATED_N, th_sat, st)
+        P.cem_rollout_batch(S.h, th_sat, SATURATED_N, J_sat, c_sat, st)  # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(st)
         for _ in range(3):
-            P.cem_rollout_batch(S.h, th_sat, SATURATED_N, J_sat, c_sat, stream)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    sat_ms = e0.elapsed_time(e1) / 3
-
-    # the 64-problem batched workload: one persistent launch per iteration
-    batch = batched_measurement(P, args.seed, rank)
+            P.cem_rollout_batch(S.h, th_sat, SATURATED_N, J_sat, c_sat, st)
+        e1.record(st)
+        torch.cuda.synchronize()
+        sat_ms = e0.elapsed_time(e1) / 3
 
     # CE time-to-cost: surrogate-screened vs plain (pick-place)
     ttc = time_to_cost(args.seed) if rank == 0 and not args.skip_surrogate else None
     sur = surrogate_roofline(P, args.seed) if rank == 0 and not args.skip_surrogate else None
 
-    # end to end through the public API with host buffers: cem_solve, one
-    # iteration per step, distribution in from pinned host memory and the
-    # best sample / new distribution back to the host
-    init_mean = np.ascontiguousarray((lo + hi) / 2, np.float32)
-    init_cov = np.ascontiguousarray(np.diag(((hi - lo) / 4) ** 2), np.float32)
-    S.solve(args.seed, N, K, 1, init_mean=init_mean, init_cov=init_cov)  # allocate + capture
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    t0 = time.perf_counter()
-    for j in range(args.steps):
-        S.solve(args.seed, N, K, 1, init_mean=init_mean, init_cov=init_cov, start_iter=j)
-    e2e_s = time.perf_counter() - t0
-    e_units, e_secs = aggregate(N * T * args.steps, e2e_s, world)
-    # cem_solve moves its small state as one block each way (capi.cu: loop
-    # state 96 B, status, k_eff, mean / cov / chol at the 18-parameter
-    # maximum, each 16-byte aligned: 2800 B), plus the 1-iteration histories
-    # the binding asks for (best cost, k_eff, class counts)
-    h2d = 2800
-    d2h = 2800 + 4 + 4 + 16
-
     if rank == 0:
-        fps = flops_per_step(cm["name"])
         peaks, src = measured_peaks()
-        clocks = clk.summary()
         sms = torch.cuda.get_device_properties(0).multi_processor_count
-        peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roll_avg = sum(roll_ms) / len(roll_ms)
-        achieved = fps["flops"] * N * T / (roll_avg / 1e3) / 1e12
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        flops, basis = batch_flops(probs, args.seed)
+        roll = [s[1] for s in hd["stages"]]
+        roll_avg = sum(roll) / len(roll)
+        achieved = flops / (roll_avg / 1e3) / 1e12
+        ms = sum(hd["step_ms"]) / len(hd["step_ms"])
+        fps_push = push["flops_per_step"]
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": hd["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(sc, sk, cm), "N": N, "T": T, "D": D, "K": K,
+            "config": {"workload": batch_desc(probs, args.seed), "problems": len(probs),
+                       "sim_steps_per_iteration": hd["steps_per_iter"],
                        "l2": "flushed between timed steps (256 MiB write, untimed)",
-                       "rollout_ms": roll_avg, "sample_ms": sum(samp_ms) / len(samp_ms),
-                       "refit_ms": sum(refit_ms) / len(refit_ms), "wall_s": wall},
+                       "sample_ms": float(np.mean([s[0] for s in hd["stages"]])), "rollout_ms": roll_avg,
+                       "refit_ms": float(np.mean([s[2] for s in hd["stages"]])), "wall_s": hd["wall"],
+                       "launch": hd["launch"], "graph": "one CUDA graph replay per CE iteration",
+                       "final_best_class_counts": hd["classes"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": rollout_traffic(),
-                         "algorithmic_bytes": N * D * 4 + N * 5,
-                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)} MHz "
-                                       f"({src} max SM clock)",
-                         "kernel": "rollout_kernel<PUSH>",
-                         "flops_per_step": fps["flops"]},
-            "roofline_saturated": {"N": SATURATED_N, "rollout_ms": sat_ms,
-                                   "sim_steps_per_s": SATURATED_N * T / (sat_ms / 1e3),
-                                   "achieved": fps["flops"] * SATURATED_N * T / (sat_ms / 1e3) / 1e12,
-                                   "frac": fps["flops"] * SATURATED_N * T / (sat_ms / 1e3) / 1e12 / peak,
+                         "frac": achieved / peak, "traffic": None,
+                         "algorithmic_bytes": int(sum(p["N"] * (len(p["skel"]["lo"]) * 4 + 5) for p in probs)),
+                         "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {mhz} MHz ({src} max SM clock)",
+                         "kernel": "rollout_persistent_kernel",
+                         "flops_per_iteration": flops, "flops_basis": f"oracle op counts, {basis}",
+                         "timing": "library stage events on the launching stream, every timed step"},
+            "e2e": {"value": hd["e2e"], "unit": UNIT, "h2d_bytes_per_step": hd["e2e_bytes"],
+                    "d2h_bytes_per_step": hd["e2e_bytes"], "api": "cem_batch_set_state -> cem_batch_iterate -> "
+                    "cem_batch_read each step, state in host memory", "same_result_as_device_run": hd["e2e_same_result"]},
+            "move_push_N4096": push,
+            "pickplace_N16384": pick,
+            "roofline_saturated": {"workload": "move-push rollout kernel alone, N = 196,608", "N": SATURATED_N,
+                                   "rollout_ms": sat_ms, "sim_steps_per_s": SATURATED_N * T / (sat_ms / 1e3),
+                                   "achieved": fps_push * SATURATED_N * T / (sat_ms / 1e3) / 1e12,
+                                   "frac": fps_push * SATURATED_N * T / (sat_ms / 1e3) / 1e12 / peak,
                                    "unit": "TFLOP/s"},
-            "e2e": {"value": e_units / e_secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "batched_64": batch,
             "time_to_cost": ttc,
             "roofline_surrogate": sur,
             "gpu_launches": 3 * args.steps,
-            "gpu_launches_outside_timed_region": 5 + 3 * (args.steps + 1),
-            "clocks": clocks,
+            "clocks": hd["clocks"],
         }
         if world == 1:
-            line["cpu_baseline"] = cpu_baseline(sc, sk, cm)
+            line["cpu_baseline"] = cpu_baseline(probs)
         print(json.dumps(line), flush=True)
-    S.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

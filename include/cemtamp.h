@@ -334,6 +334,27 @@ int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm)
 int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float* best_ms_out);
 /* Simulated steps of one batch iteration: sum over problems of N * T. */
 long long cem_batch_steps_per_iteration(cem_batch_handle h);
+/* Restores every problem's CE state from in[n_problems] as cem_batch_read
+ * wrote it: mean, cov, chol, the best sample (best_class 4 = none yet) and
+ * iters_done, taken as the Philox iteration of the next sample (a batch
+ * counts iterations from 0 after cem_batch_reset).  Reading after an
+ * iteration and restoring before the next continues the run exactly (the
+ * checkpoint/resume of a batch).  Errors: CEM_ERR_INVALID_ARG if a
+ * problem's D differs or a class is outside 0..4.  Synchronous. */
+int cem_batch_set_state(cem_batch_handle h, const cem_result* in, void* stream);
+/* Bytes of device state that cem_batch_set_state writes and cem_batch_read
+ * reads (per-problem distribution slots of the 18-parameter maximum, the
+ * best-sample track and the status word). */
+size_t cem_batch_state_bytes(cem_batch_handle h);
+/* Stage timing of batch iterations: with on != 0 every iteration records
+ * CUDA events on its stream at the stage boundaries (event record nodes in
+ * a captured graph, so the graph is re-captured when this changes);
+ * cem_batch_stage_ms waits for the last iteration and writes its sample,
+ * persistent rollout and refit times in ms to ms_out[3] (the rollout time
+ * is the persistent kernel alone).  Errors: CEM_ERR_INVALID_ARG while
+ * timing is off. */
+int cem_batch_set_timing(cem_batch_handle h, int on);
+int cem_batch_stage_ms(cem_batch_handle h, float* ms_out);
 /* Domain randomisation of every problem of the batch, as
  * cem_set_randomization for a single problem (environments of each problem's
  * own iteration and Philox problem id, under `seed`): a batched problem
@@ -417,12 +438,24 @@ int cem_surrogate_forward_path(cem_surrogate_handle s);
  * tcgen05 GEMM (128 x 64 tiles, both operand majors read straight
  * by the tensor core, fused bias + GELU / GELU' / split-K epilogues; a layer
  * whose shape it does not take runs on the tiled kernel), 1 = the tiled
- * mma.sync GEMM.  Same products, FP32 accumulation order differs.  Errors:
- * CEM_ERR_INVALID_ARG for another value.  A tcgen05 GEMM whose bounded wait
- * expires sets status 1 / 2 (read by cem_surrogate_status). */
+ * mma.sync GEMM.  Same products, FP32 accumulation order differs.  3 = an
+ * FP32 debug path for cem_surrogate_gradient only: FP32 inputs, the FP32
+ * master weights, FP32 activations and gradients, FP32 SIMT products summed
+ * in ascending index order (no BF16 rounding anywhere; slow); training and
+ * inference then take the automatic path.  Errors: CEM_ERR_INVALID_ARG for
+ * another value.  A tcgen05 GEMM whose bounded wait expires sets status
+ * 1 / 2 (read by cem_surrogate_status). */
 int cem_surrogate_set_gemm_path(cem_surrogate_handle s, int path);
-/* The path training GEMMs take now: 1 tiled, 2 tcgen05; -1 for NULL. */
+/* The path training GEMMs take now: 1 tiled, 2 tcgen05, 3 the FP32 debug
+ * gradient; -1 for NULL. */
 int cem_surrogate_gemm_path(cem_surrogate_handle s);
+/* One AdamW step of the training loop's optimiser with a given gradient
+ * grad_h (num_params floats, host): the same kernel and state (FP32 master
+ * weights, FP32 moments, the step counter that sets the bias correction,
+ * beta 0.9 / 0.999, eps 1e-8, decoupled decay on weights only) as
+ * cem_surrogate_train; the BF16 copy is refreshed.  set_params clears the
+ * moments and the counter.  Synchronous. */
+int cem_surrogate_adamw_step(cem_surrogate_handle s, const float* grad_h, float lr, float weight_decay);
 /* Synchronises, writes and clears the tcgen05 forward's status word: 0, or
  * 1 / 2 if a wait for the weight copy / the MMAs expired.  A non-zero code
  * also makes cem_solve_screened return CEM_ERR_TIMEOUT. */

@@ -179,6 +179,7 @@ def lib():
             L.or_sample_uniform.argtypes = [sp, C.c_uint64, C.c_uint32, C.c_int, dp]
             L.or_rollout.argtypes = [sp, dp, C.c_int, dp, u8p, C.c_int]
             L.or_rollout_trace.argtypes = [sp, dp, C.c_int, dp]
+            L.or_pickplace_final.argtypes = [sp, dp, C.c_int, C.c_double, dp, C.POINTER(C.c_int)]
             L.or_rollout_count.argtypes = [sp, dp, C.POINTER(_Ops)]
             L.or_rollout_count.restype = C.c_int
             L.or_select.argtypes = [fp, u8p, C.c_int, C.c_int, i32p]
@@ -268,6 +269,19 @@ def trace(scene, skel, theta, steps):
     out = np.zeros((steps, TRACE_W), np.float64)
     lib().or_rollout_trace(C.byref(s), _p(th, C.c_double), steps, _p(out, C.c_double))
     return out
+
+
+def pickplace_final(scene, skel, state, complete, t_done):
+    """(J, class) that a pick-place rollout ending in `state` (one row of the
+    trace layout) with every action done (complete) by t_done gets."""
+    s = pack(scene, skel)
+    st = np.zeros(TRACE_W, np.float64)
+    st[:len(state)] = state
+    J = C.c_double()
+    c = C.c_int()
+    lib().or_pickplace_final(C.byref(s), _p(st, C.c_double), int(bool(complete)), float(t_done), C.byref(J),
+                             C.byref(c))
+    return J.value, c.value
 
 
 def count_ops(scene, skel, theta, T=None):

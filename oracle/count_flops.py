@@ -1,6 +1,7 @@
 """Algorithmic FP32 work per simulated step of each workload, tallied by the
 oracle's counting real type over rollouts drawn from the initial CE
-distribution (mean = mid-bounds, cov = diag((range/4)^2)).  Writes
+distribution (mean = mid-bounds, cov = diag((range/4)^2)); for the
+64-problem batch, per problem.  Writes
 workload/flops_per_step.json, which the benchmark reads for its roofline.
 Run: python oracle/count_flops.py
 """
@@ -27,12 +28,30 @@ def tally(scene, skel, n=128, seed=1):
     return per
 
 
+def batch_tally(seed=0, n=64):
+    """Per problem of the 64-problem batch (workload.batch_problems(seed)):
+    flops per step over n samples of its initial distribution, plus the
+    mean per skeleton length weighted by each problem's N x T."""
+    per, by_len = [], {}
+    for p in workload.batch_problems(seed):
+        t = tally(p["scene"], p["skel"], n=n)
+        per.append(dict(L=p["L"], N=p["N"], T=p["scene"]["T"], D=len(p["skel"]["lo"]), flops=t["flops"],
+                        div=t["div"], sqrt=t["sqrt"], transc=t["transc"]))
+        w = p["N"] * p["scene"]["T"]
+        acc = by_len.setdefault(str(p["L"]), [0.0, 0.0])
+        acc[0] += w * t["flops"]
+        acc[1] += w
+    return dict(seed=seed, samples_per_problem=n, distribution="initial", problems=per,
+                flops_by_length={L: v[0] / v[1] for L, v in sorted(by_len.items())})
+
+
 def main():
     out = {}
     for cfg in (0, 1, 2):
         sc, sk, cm = workload.config(cfg, seed=0)
         out[cm["name"]] = dict(tally(sc, sk), N=cm["N"], T=sc["T"], D=len(sk["lo"]),
                                samples=128, distribution="initial")
+    out["batch-64"] = batch_tally()
     path = os.path.join(ROOT, "workload", "flops_per_step.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)

@@ -10,6 +10,8 @@ round-to-nearest-even; products accumulated exactly here, in FP32 on the GPU).
 
 Pins (tests/test_oracle_mlp.py): central finite differences of the FP64
 loss, torch.autograd in float64, and torch.optim.AdamW in float64; the
+BF16-emulating backward against torch.autograd run on the same rounded
+operands (a hand-written chain through BF16-rounded tensors); the
 regression targets at closed-form points (e - 1, e^3 - 11, a non-finite
 cost, a negative cost) and their class-first order for costs below 10.
 """
@@ -71,9 +73,19 @@ def forward(params, X, emulate_bf16=False):
             return z[:, 0], (acts, pre)
 
 
-def loss_and_grads(params, X, t):
-    """MSE loss mean((y - t)^2) and its gradient with respect to every W, b."""
-    y, (acts, pre) = forward(params, X)
+def loss_and_grads(params, X, t, emulate_bf16=False):
+    """MSE loss mean((y - t)^2) and its gradient with respect to every W, b,
+    by the chain rule: dL/dy = 2 (y - t) / M; for layer l with input a_l and
+    pre-activation z_l, dL/dW_l = dz_l^T a_l, dL/db_l = sum over rows of dz_l
+    and dz_{l-1} = (dz_l W_l) * GELU'(z_{l-1}).
+
+    emulate_bf16 rounds where the library's BF16 training path stores BF16
+    values, with everything in between exact: the inputs, every weight
+    matrix, every hidden activation (forward), and every hidden-layer
+    gradient dz (backward; the output layer's dL/dy stays FP32).  Only the
+    library's FP32 accumulation then differs."""
+    q = bf16 if emulate_bf16 else (lambda v: v)
+    y, (acts, pre) = forward(params, X, emulate_bf16=emulate_bf16)
     M = X.shape[0]
     r = y - t
     loss = float(np.mean(r * r))
@@ -83,7 +95,7 @@ def loss_and_grads(params, X, t):
         W, _ = params[l]
         grads[l] = (dz.T @ acts[l], dz.sum(0))
         if l > 0:
-            dz = (dz @ W) * gelu_grad(pre[l - 1])
+            dz = q((dz @ q(W)) * gelu_grad(pre[l - 1]))
     return loss, grads
 
 

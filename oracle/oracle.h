@@ -116,6 +116,11 @@ void or_rollout_dr(const or_scene* s, const double* theta, int N, int M, double 
                    uint32_t iter, uint32_t problem, double* J, uint8_t* cls, int nthreads);
 /* Per-step state trace of one rollout: states[(steps) * OR_TRACE_W]. */
 void or_rollout_trace(const or_scene* s, const double* theta, int steps, double* states);
+/* The end of a pick-place rollout on a given final state (trace layout:
+ * base x, y at 0, 1, object x, y, z at 9, 10, 11, attached at 15): the goal
+ * test psi_g, the plan cost J = w_time t_done + w_obj d_obj + w_base d_base
+ * and the class (complete = every action succeeded). */
+void or_pickplace_final(const or_scene* s, const double* state, int complete, double t_done, double* J, int* cls);
 /* Flop tally of one rollout (added into *ops); returns the step count. */
 int or_rollout_count(const or_scene* s, const double* theta, or_ops* ops);
 /* Elite selection on FP32 costs: ascending (class, J, index); writes the

@@ -419,6 +419,28 @@ void arm_fk(const or_scene& s, R bx, R by, R beta, R q1, R q2, R& ex, R& ey, R& 
 }
 
 template <class R>
+void pickplace_final(const or_scene& s, R bx, R by, R ox, R oy, R oz, bool attached, bool complete, R t_done,
+                     R& J_out, int& cls_out);
+
+// Velocity of the end effector: the base's velocity plus the arm's, the
+// time derivative of the forward kinematics at fixed azimuth, with the
+// shoulder-to-tip radius r = l1 cos q1 + l2 cos(q1 + q2) and height
+// z = l1 sin q1 + l2 sin(q1 + q2):
+//   dr/dt = -(l1 sin q1 dq1 + l2 sin(q1 + q2) (dq1 + dq2)),
+//   dz/dt = l1 cos q1 dq1 + l2 cos(q1 + q2) (dq1 + dq2),
+//   v = (bvx + dr/dt cos beta, bvy + dr/dt sin beta, dz/dt).
+// The azimuth beta is set kinematically when a grasp or place starts, so
+// it has no rate; its jumps move the end effector but give it no speed.
+template <class R>
+void arm_ee_velocity(const or_scene& s, R bvx, R bvy, R beta, R q1, R q2, R dq1, R dq2, R& vx, R& vy, R& vz) {
+  const R w1 = dq1, w12 = dq1 + dq2;
+  const R dr = -(R(s.arm_l1) * Sin(q1) * w1 + R(s.arm_l2) * Sin(q1 + q2) * w12);
+  vz = R(s.arm_l1) * Cos(q1) * w1 + R(s.arm_l2) * Cos(q1 + q2) * w12;
+  vx = bvx + dr * Cos(beta);
+  vy = bvy + dr * Sin(beta);
+}
+
+template <class R>
 void pickplace_rollout(const or_scene& s, const Prep& pp, const double* th, int T, R& J_out, int& cls_out,
                        double* trace) {
   const double dt = s.dt, m = s.base_mass, mo = s.obj_mass, h = s.obj_half;
@@ -544,7 +566,7 @@ void pickplace_rollout(const or_scene& s, const Prep& pp, const double* th, int 
     // object
     if (attached) {
       ox = nex + offx; oy = ney + offy; oz = nez + offz;
-      ovx = (nex - ex) / R(dt); ovy = (ney - ey) / R(dt); ovz = (nez - ez) / R(dt);
+      arm_ee_velocity(s, bvx, bvy, beta, q1, q2, dq1, dq2, ovx, ovy, ovz);
     } else {
       R cnx[OR_MAX_GEOM], cny[OR_MAX_GEOM], cnz[OR_MAX_GEOM], cfn[OR_MAX_GEOM];
       int nc = 0;
@@ -612,7 +634,21 @@ void pickplace_rollout(const or_scene& s, const Prep& pp, const double* th, int 
       for (int i = 0; i < OR_TRACE_W; ++i) o[i] = v[i];
     }
   }
-  const bool complete = a == L;
+  pickplace_final(s, bx, by, ox, oy, oz, attached, a == L, t_done, J_out, cls_out);
+}
+
+// End of a pick-place rollout (Problem 2, Sec. IV-A): the goal psi_g and the
+// plan cost from the final state.  The goal holds when every flagged part
+// does: the object at rest in its region and not held (goal_obj_region),
+// the object held (goal_obj_held), the base inside its region
+// (goal_base_region).  J = w_time t_done + w_obj d_obj + w_base d_base with
+// the Euclidean distances of object and base to their boxes (a held-object
+// goal counts d_obj = 0 if held, 1 if not).  Class 0: every action
+// succeeded and the goal holds; 1: every action succeeded, goal false; 2:
+// an action unfinished; 3: non-finite cost.
+template <class R>
+void pickplace_final(const or_scene& s, R bx, R by, R ox, R oy, R oz, bool attached, bool complete, R t_done,
+                     R& J_out, int& cls_out) {
   bool goal = true;
   R d_obj = R(0.0), d_base = R(0.0);
   if (s.goal_obj_region) {
@@ -664,6 +700,12 @@ void rollout_one(const or_scene& s, const Prep& pp, const double* theta, int T, 
   }
 }
 }  // namespace
+
+extern "C" void or_pickplace_final(const or_scene* s, const double* state, int complete, double t_done,
+                                   double* J, int* cls) {
+  pickplace_final<double>(*s, state[0], state[1], state[9], state[10], state[11], state[15] != 0.0,
+                          complete != 0, t_done, *J, *cls);
+}
 
 extern "C" double or_mean_radius(double a, double b) {
   // mean of sqrt(x^2 + y^2) over [0,a] x [0,b] by the midpoint rule

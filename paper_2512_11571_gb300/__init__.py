@@ -35,13 +35,14 @@ EXPORTS = [
     "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
     "cem_set_randomization",
     "cem_batch_set_active", "cem_multiplan_solve", "cem_base_path",
-    "cem_batch_set_randomization",
+    "cem_batch_set_randomization", "cem_batch_set_state", "cem_batch_state_bytes", "cem_batch_set_timing",
+    "cem_batch_stage_ms",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
     "cem_solve_screened_ft",
     "cem_surrogate_set_forward_path", "cem_surrogate_forward_path", "cem_surrogate_status",
-    "cem_surrogate_set_gemm_path", "cem_surrogate_gemm_path",
+    "cem_surrogate_set_gemm_path", "cem_surrogate_gemm_path", "cem_surrogate_adamw_step",
     "cem_last_error", "cem_version",
 ]
 
@@ -266,6 +267,10 @@ def load(path: str = LIB_PATH):
     L.cem_batch_set_launch.argtypes = [H, C.c_int, C.c_int]
     L.cem_batch_autotune.argtypes = [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]
     L.cem_batch_steps_per_iteration.argtypes = [H]
+    L.cem_batch_set_state.argtypes = [H, C.POINTER(cem_result), vp]
+    L.cem_batch_state_bytes.argtypes = [H]
+    L.cem_batch_set_timing.argtypes = [H, C.c_int]
+    L.cem_batch_stage_ms.argtypes = [H, C.POINTER(C.c_float)]
     ip = C.POINTER(C.c_int)
     L.cem_batch_set_threads_per_rollout.argtypes = [H, C.c_int]
     L.cem_batch_get_launch.argtypes = [H, ip, ip, ip]
@@ -282,6 +287,7 @@ def load(path: str = LIB_PATH):
     L.cem_surrogate_forward_path.argtypes = [H]
     L.cem_surrogate_set_gemm_path.argtypes = [H, C.c_int]
     L.cem_surrogate_gemm_path.argtypes = [H]
+    L.cem_surrogate_adamw_step.argtypes = [H, fptr, C.c_float, C.c_float]
     L.cem_surrogate_test_expire_wait.argtypes = [H, C.c_int]
     L.cem_surrogate_status.argtypes = [H, C.POINTER(C.c_int)]
     L.cem_surrogate_gradient.argtypes = [H, vp, vp, C.c_int, fptr, fptr]
@@ -302,6 +308,7 @@ def load(path: str = LIB_PATH):
         if name not in ("cem_last_error", "cem_version"):
             getattr(L, name).restype = C.c_int
     L.cem_batch_steps_per_iteration.restype = C.c_longlong
+    L.cem_batch_state_bytes.restype = C.c_size_t
     _lib = L
     return L
 
@@ -580,6 +587,31 @@ def cem_batch_read(h, n_problems, stream=None):
     return out
 
 
+def cem_batch_set_state(h, results, stream=None):
+    """Restore every problem's state from a cem_result array of
+    cem_batch_read (the same object, or one built field by field)."""
+    n = _BATCH_N.get(getattr(h, "value", h))
+    if n is not None and len(results) != n:
+        raise ValueError(f"results: the batch holds {n} problems, got {len(results)}")
+    if not isinstance(results, C.Array) or results._type_ is not cem_result:
+        raise TypeError("results must be a ctypes array of cem_result (as cem_batch_read returns)")
+    _check(load().cem_batch_set_state(h, results, _stream(stream)))
+
+
+def cem_batch_state_bytes(h):
+    return int(load().cem_batch_state_bytes(h))
+
+
+def cem_batch_set_timing(h, on):
+    _check(load().cem_batch_set_timing(h, int(bool(on))))
+
+
+def cem_batch_stage_ms(h):
+    ms = (C.c_float * 3)()
+    _check(load().cem_batch_stage_ms(h, ms))
+    return float(ms[0]), float(ms[1]), float(ms[2])
+
+
 def cem_batch_set_launch(h, warps_per_cta, ctas_per_sm=0):
     _check(load().cem_batch_set_launch(h, warps_per_cta, ctas_per_sm))
 
@@ -624,6 +656,25 @@ class Batch:
 
     def iterate(self, iters, use_graph=True, stream=None):
         cem_batch_iterate(self.h, iters, use_graph, stream)
+
+    def read_raw(self, stream=None):
+        """The cem_result array of cem_batch_read, as the C call wrote it."""
+        return cem_batch_read(self.h, self.n, stream)
+
+    def set_state(self, results, stream=None):
+        """Restore the state that read_raw returned (exact resume)."""
+        cem_batch_set_state(self.h, results, stream)
+
+    @property
+    def state_bytes(self):
+        return cem_batch_state_bytes(self.h)
+
+    def set_timing(self, on=True):
+        cem_batch_set_timing(self.h, on)
+
+    def stage_ms(self):
+        """(sample, persistent rollout, refit) ms of the last iteration."""
+        return cem_batch_stage_ms(self.h)
 
     def read(self, stream=None):
         out = cem_batch_read(self.h, self.n, stream)
@@ -730,6 +781,11 @@ def cem_surrogate_gemm_path(s):
     return int(load().cem_surrogate_gemm_path(s))
 
 
+def cem_surrogate_adamw_step(s, grad, lr=1e-3, weight_decay=1e-4):
+    g, gp = _f32(grad, cem_surrogate_num_params(s), "grad")
+    _check(load().cem_surrogate_adamw_step(s, gp, float(lr), float(weight_decay)))
+
+
 def cem_surrogate_status(s):
     code = C.c_int(0)
     _check(load().cem_surrogate_status(s, C.byref(code)))
@@ -832,7 +888,7 @@ class Surrogate:
         return cem_surrogate_forward_path(self.h)
 
     def set_gemm_path(self, path):
-        """Training GEMMs: 0 automatic, 1 tiled mma.sync, 2 tcgen05."""
+        """Training GEMMs: 0 automatic, 1 tiled mma.sync, 2 tcgen05, 3 the FP32 debug gradient."""
         cem_surrogate_set_gemm_path(self.h, path)
 
     @property
@@ -842,6 +898,10 @@ class Surrogate:
     def test_expire_wait(self, on):
         """Failure-detection hook: make the tcgen05 forward's first wait run out."""
         cem_surrogate_test_expire_wait(self.h, on)
+
+    def adamw_step(self, grad, lr=1e-3, weight_decay=1e-4):
+        """One optimiser step of the training loop with the given gradient."""
+        cem_surrogate_adamw_step(self.h, grad, lr, weight_decay)
 
     def status(self):
         """Reads and clears the fused kernel's status word (0 = no wait expired)."""

@@ -60,6 +60,10 @@ struct cem_batch_ctx {
   DrArgs dr{};
   cudaGraphExec_t graph = nullptr;
   long long steps_per_iter = 0;
+  // stage timing (cem_batch_set_timing): events before the sample, before
+  // and after the persistent rollout, after the refit of each iteration
+  bool timing = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -67,6 +71,10 @@ namespace {
 void batch_free(cem_batch_ctx* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+  for (cudaEvent_t& e : h->ev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   void* ptrs[] = {h->scenes_d, h->probs_d, h->items_d, h->counter_d, h->theta_d, h->J_d, h->cls_d,
                   h->mean_d,   h->cov_d,   h->chol_d,  h->keff_d,    h->status_d, h->track_d, h->args_d};
   for (void* p : ptrs) cudaFree(p);
@@ -106,16 +114,36 @@ int set_active(cem_batch_ctx* h, const std::vector<int>& active) {
   return CEM_OK;
 }
 
+// With timing on, an event is recorded at each stage boundary (as event
+// record nodes when the iteration is captured into a graph).
+cudaError_t mark(cem_batch_ctx* h, int i, cudaStream_t st) {
+  if (!h->timing) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(st, &cs);
+  if (e != cudaSuccess) return e;
+  // an external event node inside a captured graph, a plain record otherwise
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(h->ev[i], st, cudaEventRecordExternal)
+                                             : cudaEventRecord(h->ev[i], st);
+}
+
 cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st) {
-  cudaError_t e = launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, st);
+  cudaError_t e = mark(h, 0, st);
+  if (e != cudaSuccess) return e;
+  e = launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  e = mark(h, 1, st);
   if (e != cudaSuccess) return e;
   e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
                                       h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, h->track_d,
                                       h->dr_on ? &h->dr : nullptr, st);
   if (e != cudaSuccess) return e;
-  return launch_refit_batch(h->args_d, h->P, h->maxK, h->maxD, st);
+  e = mark(h, 2, st);
+  if (e != cudaSuccess) return e;
+  e = launch_refit_batch(h->args_d, h->P, h->maxK, h->maxD, st);
+  if (e != cudaSuccess) return e;
+  return mark(h, 3, st);
 }
 
 }  // namespace
@@ -437,6 +465,67 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
 }
 
 long long cem_batch_steps_per_iteration(cem_batch_handle h) { return h ? h->steps_per_iter : 0; }
+
+int cem_batch_set_state(cem_batch_handle h, const cem_result* in, void* stream) {
+  if (!h || !in) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t P = h->P;
+  std::vector<float> mean(P * kMS, 0.0f), cov(P * kMC, 0.0f), chol(P * kMC, 0.0f);
+  std::vector<Track> tr(P);
+  for (size_t p = 0; p < P; ++p) {
+    const cem_result& r = in[p];
+    const int D = h->probs[p].D;
+    if (r.D != D) return fail(CEM_ERR_INVALID_ARG, "problem " + std::to_string(p) + ": D differs from the batch's");
+    if (r.iters_done < 0) return fail(CEM_ERR_INVALID_ARG, "problem " + std::to_string(p) + ": iters_done < 0");
+    if (r.best_class < 0 || r.best_class > 4)
+      return fail(CEM_ERR_INVALID_ARG, "problem " + std::to_string(p) + ": best_class outside 0..4");
+    for (int d = 0; d < D; ++d) mean[p * kMS + d] = r.mean[d];
+    for (int i = 0; i < D * D; ++i) {
+      cov[p * kMC + i] = r.cov[i];
+      chol[p * kMC + i] = r.chol[i];
+    }
+    std::memset(&tr[p], 0, sizeof(Track));
+    tr[p].iter = (uint32_t)r.iters_done;
+    tr[p].base_iter = 0;
+    tr[p].best_cls = r.best_class;
+    tr[p].best_J = r.best_class == 4 ? INFINITY : r.best_J;
+    for (int d = 0; d < D; ++d) tr[p].best_theta[d] = r.best_theta[d];
+  }
+  std::vector<int32_t> zeros(P, 0);
+  BATCH_CUDA(cudaMemcpyAsync(h->mean_d, mean.data(), sizeof(float) * P * kMS, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->cov_d, cov.data(), sizeof(float) * P * kMC, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->chol_d, chol.data(), sizeof(float) * P * kMC, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->track_d, tr.data(), sizeof(Track) * P, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaMemcpyAsync(h->status_d, zeros.data(), sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+  BATCH_CUDA(cudaStreamSynchronize(st));  // the host vectors die at return
+  return CEM_OK;
+}
+
+size_t cem_batch_state_bytes(cem_batch_handle h) {
+  if (!h) return 0;
+  const size_t P = h->P;
+  return P * (sizeof(float) * (kMS + 2 * kMC) + sizeof(Track) + sizeof(int32_t));
+}
+
+int cem_batch_set_timing(cem_batch_handle h, int on) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (on && !h->ev[0])
+    for (cudaEvent_t& e : h->ev) BATCH_CUDA(cudaEventCreate(&e));
+  if ((on != 0) != h->timing && h->graph) {
+    cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+  }
+  h->timing = on != 0;
+  return CEM_OK;
+}
+
+int cem_batch_stage_ms(cem_batch_handle h, float* ms_out) {
+  if (!h || !ms_out) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  if (!h->timing) return fail(CEM_ERR_INVALID_ARG, "stage timing is off (cem_batch_set_timing)");
+  BATCH_CUDA(cudaEventSynchronize(h->ev[3]));
+  for (int i = 0; i < 3; ++i) BATCH_CUDA(cudaEventElapsedTime(&ms_out[i], h->ev[i], h->ev[i + 1]));
+  return CEM_OK;
+}
 
 int cem_batch_set_randomization(cem_batch_handle h, int M, float delta_mu, float delta_mass, uint64_t seed) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");

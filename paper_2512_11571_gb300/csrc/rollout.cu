@@ -692,8 +692,12 @@ __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, fl
 // Forward kinematics.  Joint angles stay within (-pi, pi), where the
 // hardware sine/cosine is accurate to ~5e-7 absolute (~2e-7 m at the end
 // effector), far inside the per-step state tolerance.
+struct ArmTrig {
+  float s1, c1, s12, c12;  // sin / cos of q1 and of q1 + q2
+};
+
 __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, float cb, float sb, float q1, float q2,
-                                       float& ex, float& ey, float& ez) {
+                                       float& ex, float& ey, float& ez, ArmTrig* trig = nullptr) {
   float s1, c1, s12, c12;
   __sincosf(q1, &s1, &c1);
   __sincosf(q1 + q2, &s12, &c12);
@@ -701,6 +705,20 @@ __device__ __forceinline__ void arm_fk(const DevScene& s, float bx, float by, fl
   ez = s.arm_z + s.arm_l1 * s1 + s.arm_l2 * s12;
   ex = bx + r * cb;
   ey = by + r * sb;
+  if (trig) *trig = ArmTrig{s1, c1, s12, c12};
+}
+
+// End-effector velocity: the base's plus the arm's (the forward kinematics
+// differentiated at fixed azimuth: dr/dt = -(l1 sin q1 dq1 + l2 sin(q1 + q2)
+// (dq1 + dq2)), dz/dt = l1 cos q1 dq1 + l2 cos(q1 + q2) (dq1 + dq2)).  The
+// azimuth is set kinematically when a grasp or place starts and has no rate.
+__device__ __forceinline__ void arm_ee_velocity(const DevScene& s, const ArmTrig& t, float cb, float sb, float bvx,
+                                                float bvy, float dq1, float dq2, float& vx, float& vy, float& vz) {
+  const float w12 = dq1 + dq2;
+  const float dr = -(s.arm_l1 * t.s1 * dq1 + s.arm_l2 * t.s12 * w12);
+  vz = s.arm_l1 * t.c1 * dq1 + s.arm_l2 * t.c12 * w12;
+  vx = bvx + dr * cb;
+  vy = bvy + dr * sb;
 }
 
 template <int G, bool TRACE>
@@ -708,7 +726,6 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
                                                float sm, float& J_out, int& cls_out, float* tr) {
   const Group<G> grp;
   const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps;
-  const float inv_dt = 1.0f / dt;  // the held object's velocity: a product, not three divisions per step
   const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap * smu, bcap2 = bcap * bcap;
   const ObjPhys op{s.obj_cap * smu, s.mo * sm, s.dt_mo / sm};
   const float kc = s.k_contact, cc = s.c_contact, akp = s.arm_kp, akd = s.arm_kd;
@@ -868,7 +885,8 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
     q1 += dt * dq1;
     q2 += dt * dq2;
     float nex, ney, nez;
-    arm_fk(s, bx, by, cbeta, sbeta, q1, q2, nex, ney, nez);
+    ArmTrig trig;
+    arm_fk(s, bx, by, cbeta, sbeta, q1, q2, nex, ney, nez, &trig);
     // object (a warp-wide rebuild of the object lists, see above)
     const bool orebuild = __any_sync(
         lanes, !attached && fmaxf(fmaxf(fabsf(ox - orx), fabsf(oy - ory)), fabsf(oz - orz)) >= kRebuild);
@@ -876,9 +894,7 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
       ox = nex + offx;
       oy = ney + offy;
       oz = nez + offz;
-      ovx = (nex - ex) * inv_dt;
-      ovy = (ney - ey) * inv_dt;
-      ovz = (nez - ez) * inv_dt;
+      arm_ee_velocity(s, trig, cbeta, sbeta, bvx, bvy, dq1, dq2, ovx, ovy, ovz);
     } else {
       if (orebuild) {
         omask = near_list<false, G>(s, n_geoms, ox, oy, oz, h, h, h, kSkin, grp);

@@ -549,6 +549,88 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t*
   dst[t] = src[(size_t)idx[r] * D + c];
 }
 
+// ---- FP32 debug path (gemm path 3): every input, weight, activation and
+// gradient in FP32 and every reduction in ascending index order, one output
+// element per thread.  Slow; it exists to check gradients against an exact
+// FP64 chain rule without the BF16 rounding of the fast paths.
+struct GemmF32 {
+  int M, N, K;
+  const float* A;
+  int lda, a_kmajor;
+  const float* B;
+  int ldb, b_kmajor;
+  float* C;  // EPI_F32: product; EPI_BIAS_GELU: pre-activation z
+  int ldc;
+  float* Cf;  // EPI_BIAS_GELU: GELU(z); EPI_GELU_BWD: product * GELU'(zsave)
+  int ldcf;
+  const float* bias;
+  const float* zsave;
+  int ldz;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(256) gemm_f32_kernel(GemmF32 g) {
+  __shared__ float As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int m = blockIdx.y * 16 + ty, n = blockIdx.x * 16 + tx;
+  float acc = 0.0f;
+  for (int k0 = 0; k0 < g.K; k0 += 16) {
+    const int ak = k0 + tx, bk = k0 + ty, bn = blockIdx.x * 16 + tx;
+    As[ty][tx] = (m < g.M && ak < g.K) ? (g.a_kmajor ? g.A[(size_t)m * g.lda + ak] : g.A[(size_t)ak * g.lda + m]) : 0.0f;
+    Bs[ty][tx] = (bk < g.K && bn < g.N) ? (g.b_kmajor ? g.B[(size_t)bn * g.ldb + bk] : g.B[(size_t)bk * g.ldb + bn])
+                                        : 0.0f;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+    __syncthreads();
+  }
+  if (m >= g.M || n >= g.N) return;
+  if (EPI == EPI_F32) {
+    g.C[(size_t)m * g.ldc + n] = acc;
+  } else if (EPI == EPI_BIAS_GELU) {
+    const float z = acc + g.bias[n];
+    g.C[(size_t)m * g.ldc + n] = z;
+    g.Cf[(size_t)m * g.ldcf + n] = gelu(z);
+  } else {
+    g.Cf[(size_t)m * g.ldcf + n] = acc * gelu_grad(g.zsave[(size_t)m * g.ldz + n]);
+  }
+}
+
+template <int EPI>
+cudaError_t gemm_f32(const GemmF32& g, cudaStream_t st) {
+  gemm_f32_kernel<EPI><<<dim3((g.N + 15) / 16, (g.M + 15) / 16), 256, 0, st>>>(g);
+  return cudaGetLastError();
+}
+
+// raw[m] = sum_j a[m][j] w[j] + b (FP32, j ascending)
+__global__ void output_layer_f32_kernel(const float* __restrict__ a, int M, int W, const float* __restrict__ w,
+                                        const float* __restrict__ b, float* __restrict__ raw) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  float s = 0.0f;
+  for (int j = 0; j < W; ++j) s = fmaf(a[(size_t)m * W + j], w[j], s);
+  raw[m] = s + b[0];
+}
+
+// out[j] = sum_m (w ? w[m] : 1) X[m][j] (FP32, m ascending)
+__global__ void colsum_f32_kernel(const float* __restrict__ X, const float* __restrict__ w, int M, int N,
+                                  float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  float s = 0.0f;
+  for (int m = 0; m < M; ++m) s = fmaf(w ? w[m] : 1.0f, X[(size_t)m * N + j], s);
+  out[j] = s;
+}
+
+// dz[m][j] = dy[m] w[j] GELU'(z[m][j]) (FP32)
+__global__ void output_backward_f32_kernel(const float* __restrict__ dy, const float* __restrict__ w,
+                                           const float* __restrict__ z, int M, int W, float* __restrict__ dz) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (size_t)M * W) return;
+  const int m = (int)(i / W), j = (int)(i % W);
+  dz[i] = dy[m] * w[j] * gelu_grad(z[i]);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ handle
@@ -794,6 +876,117 @@ cudaError_t backward_rows(cem_surrogate_ctx* s, int M, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Gradient of mean((raw - (t - mu)/sigma)^2) over the M rows x_d, t_d in
+// FP32 end to end (gemm path 3): FP32 inputs, the FP32 master weights,
+// FP32 activations and gradients, the kernels above; the workspace beyond
+// the shared row buffers is allocated for the call and freed after it.
+int gradient_f32(cem_surrogate_ctx* s, const float* x_d, const float* t_d, int M) {
+  int rc = ensure_rows(s, M);
+  if (rc != CEM_OK) return rc;
+  const int L = s->depth, W = s->width;
+  std::vector<float*> act(L, nullptr);
+  float* dz = nullptr;
+  float* dz_next = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (auto& a : act)
+    if (e == cudaSuccess) e = cudaMalloc(&a, sizeof(float) * (size_t)M * W);
+  if (e == cudaSuccess) e = cudaMalloc(&dz, sizeof(float) * (size_t)M * W);
+  if (e == cudaSuccess) e = cudaMalloc(&dz_next, sizeof(float) * (size_t)M * W);
+  auto release = [&]() {
+    for (auto* a : act) cudaFree(a);
+    cudaFree(dz);
+    cudaFree(dz_next);
+  };
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(CEM_ERR_NO_MEMORY, "FP32 gradient workspace allocation failed");
+  }
+  cudaStream_t st = 0;
+  e = cudaMemcpyAsync(s->tb, t_d, sizeof(float) * M, cudaMemcpyDeviceToDevice, st);
+  const float* a = x_d;
+  int K = s->in_dim;
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    GemmF32 g;
+    std::memset(&g, 0, sizeof(g));
+    g.M = M;
+    g.N = W;
+    g.K = K;
+    g.A = a;
+    g.lda = K;
+    g.a_kmajor = 1;
+    g.B = s->p + s->w_off[l];
+    g.ldb = K;
+    g.b_kmajor = 1;
+    g.C = s->pre[l];
+    g.ldc = W;
+    g.Cf = act[l];
+    g.ldcf = W;
+    g.bias = s->p + s->b_off[l];
+    e = gemm_f32<EPI_BIAS_GELU>(g, st);
+    a = act[l];
+    K = W;
+  }
+  const int blocks = (M + 255) / 256;
+  if (e == cudaSuccess) {
+    output_layer_f32_kernel<<<blocks, 256, 0, st>>>(act[L - 1], M, W, s->p + s->w_off[L], s->p + s->b_off[L],
+                                                     s->raw);
+    loss_kernel<<<blocks, 256, 0, st>>>(s->raw, s->tb, s->norm, M, s->dy, s->partial);
+    finish_sum_kernel<<<1, 256, 0, st>>>(s->partial, blocks, s->loss_d);
+    colsum_f32_kernel<<<(W + 255) / 256, 256, 0, st>>>(act[L - 1], s->dy, M, W, s->g + s->w_off[L]);
+    finish_sum_kernel<<<1, 256, 0, st>>>(s->dy, M, s->g + s->b_off[L]);
+    const size_t n = (size_t)M * W;
+    output_backward_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->dy, s->p + s->w_off[L],
+                                                                             s->pre[L - 1], M, W, dz);
+    e = cudaGetLastError();
+  }
+  for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
+    const int Kl = l == 0 ? s->in_dim : W;
+    const float* a_in = l == 0 ? x_d : act[l - 1];
+    GemmF32 g;  // dW_l [W x Kl] = dz^T a_in
+    std::memset(&g, 0, sizeof(g));
+    g.M = W;
+    g.N = Kl;
+    g.K = M;
+    g.A = dz;
+    g.lda = W;
+    g.a_kmajor = 0;
+    g.B = a_in;
+    g.ldb = Kl;
+    g.b_kmajor = 0;
+    g.C = s->g + s->w_off[l];
+    g.ldc = Kl;
+    e = gemm_f32<EPI_F32>(g, st);
+    if (e == cudaSuccess) {
+      colsum_f32_kernel<<<(W + 255) / 256, 256, 0, st>>>(dz, nullptr, M, W, s->g + s->b_off[l]);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && l > 0) {  // dz_{l-1} = (dz W_l) * GELU'(z_{l-1})
+      GemmF32 h;
+      std::memset(&h, 0, sizeof(h));
+      h.M = M;
+      h.N = Kl;
+      h.K = W;
+      h.A = dz;
+      h.lda = W;
+      h.a_kmajor = 1;
+      h.B = s->p + s->w_off[l];
+      h.ldb = Kl;
+      h.b_kmajor = 0;
+      h.Cf = dz_next;
+      h.ldcf = Kl;
+      h.zsave = s->pre[l - 1];
+      h.ldz = W;
+      e = gemm_f32<EPI_GELU_BWD>(h, st);
+      std::swap(dz, dz_next);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  release();
+  if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("FP32 gradient: ") + cudaGetErrorString(e));
+  return CEM_OK;
+}
+
 Segs param_segments(const cem_surrogate_ctx* s) {
   Segs sg;
   std::memset(&sg, 0, sizeof(sg));
@@ -966,12 +1159,29 @@ int cem_surrogate_forward_path(cem_surrogate_handle s) { return s ? (use_tc(s) ?
 
 int cem_surrogate_set_gemm_path(cem_surrogate_handle s, int path) {
   if (!s) return fail(CEM_ERR_INVALID_ARG, "null handle");
-  if (path < 0 || path > 2) return fail(CEM_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+  if (path < 0 || path > 3) return fail(CEM_ERR_INVALID_ARG, "path must be 0, 1, 2 or 3");
   s->gemm_path = path;
   return CEM_OK;
 }
 
-int cem_surrogate_gemm_path(cem_surrogate_handle s) { return s ? (use_tc_gemm(s) ? 2 : 1) : -1; }
+int cem_surrogate_gemm_path(cem_surrogate_handle s) {
+  return s ? (s->gemm_path == 3 ? 3 : use_tc_gemm(s) ? 2 : 1) : -1;
+}
+
+int cem_surrogate_adamw_step(cem_surrogate_handle s, const float* grad_h, float lr, float weight_decay) {
+  if (!s || !grad_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  if (!(lr >= 0.0f) || !(weight_decay >= 0.0f)) return fail(CEM_ERR_INVALID_ARG, "lr and weight decay must be >= 0");
+  SUR_CUDA(cudaMemcpy(s->g, grad_h, sizeof(float) * s->total, cudaMemcpyHostToDevice));
+  SUR_CUDA(cudaMemcpy(s->adam_t_d, &s->adam_step, sizeof(long long), cudaMemcpyHostToDevice));
+  const Segs segs = param_segments(s);
+  adamw_kernel<<<(s->total + 255) / 256, 256>>>(s->p, s->g, s->m1, s->m2, s->pb, s->total, segs, lr, 0.9f, 0.999f,
+                                                1e-8f, weight_decay, s->adam_t_d);
+  SUR_CUDA(cudaGetLastError());
+  SUR_CUDA(cudaDeviceSynchronize());
+  s->adam_step += 1;
+  s->tc_pack_valid = false;
+  return CEM_OK;
+}
 
 int cem_surrogate_status(cem_surrogate_handle s, int* status_h) {
   if (!s || !status_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
@@ -986,11 +1196,16 @@ int cem_surrogate_gradient(cem_surrogate_handle s, const float* x_d, const float
   if (!s || !grad_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
   if (M < 1 || M > (1 << 22)) return fail(CEM_ERR_UNSUPPORTED, "M must be in 1..2^22");
   if (!is_dev(x_d) || !is_dev(t_d)) return fail(CEM_ERR_INVALID_ARG, "x and t must be device pointers");
-  int rc = load_features(s, x_d, M, 0);
-  if (rc != CEM_OK) return rc;
-  SUR_CUDA(cudaMemcpy(s->tb, t_d, sizeof(float) * M, cudaMemcpyDeviceToDevice));
-  SUR_CUDA(forward_rows(s, M, nullptr, use_tc_gemm(s), 0));
-  SUR_CUDA(backward_rows(s, M, 0));
+  if (s->gemm_path == 3) {
+    int rc = gradient_f32(s, x_d, t_d, M);
+    if (rc != CEM_OK) return rc;
+  } else {
+    int rc = load_features(s, x_d, M, 0);
+    if (rc != CEM_OK) return rc;
+    SUR_CUDA(cudaMemcpy(s->tb, t_d, sizeof(float) * M, cudaMemcpyDeviceToDevice));
+    SUR_CUDA(forward_rows(s, M, nullptr, use_tc_gemm(s), 0));
+    SUR_CUDA(backward_rows(s, M, 0));
+  }
   SUR_CUDA(cudaDeviceSynchronize());
   SUR_CUDA(cudaMemcpy(grad_h, s->g, sizeof(float) * s->total, cudaMemcpyDeviceToHost));
   if (loss_h) {

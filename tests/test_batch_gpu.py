@@ -108,3 +108,75 @@ def test_sixty_four_problem_workload(P):
     assert all(np.isfinite(g["best_J"]) and g["best_cls"] <= 2 for g in got)
     for i in (0, 17, 42, 63):  # spot-check problems against the single-problem loop
         same(got[i], single(P, probs[i], 2))
+
+
+def test_batch_state_round_trip_resumes_exactly(P):
+    """Reading the state after every iteration and restoring it from host
+    memory before the next (the path the end-to-end benchmark times) gives
+    the same distributions and best samples, bit for bit, as iterating on
+    the device; set_state also resumes a checkpoint in a fresh batch."""
+    probs = mixed_problems()
+    with P.Batch(probs) as B:
+        B.iterate(4, use_graph=True)
+        ref = B.read()
+        B.reset()
+        host = B.read_raw()
+        assert all(r.best_class == 4 and r.iters_done == 0 for r in host)
+        for _ in range(4):
+            B.set_state(host)
+            B.iterate(1, use_graph=True)
+            host = B.read_raw()
+        got = B.read()
+        for a, b in zip(got, ref):
+            same(a, b)
+            assert a["iters_done"] == b["iters_done"] == 4
+        assert B.state_bytes == len(probs) * (4 * (18 + 2 * 324) + 96 + 4)
+    # a checkpoint taken after 2 iterations continues in another batch
+    with P.Batch(probs) as B1:
+        B1.iterate(2)
+        ck = B1.read_raw()
+    with P.Batch(probs) as B2:
+        B2.set_state(ck)
+        B2.iterate(2)
+        for a, b in zip(B2.read(), ref):
+            same(a, b)
+
+
+def test_batch_stage_timing(P):
+    """With timing on, every iteration (graph or not) reports positive
+    sample, rollout and refit times; results are unchanged by timing; the
+    call is refused while timing is off."""
+    probs = mixed_problems()
+    with P.Batch(probs) as B:
+        B.iterate(2)
+        ref = B.read()
+        B.reset()
+        with pytest.raises(P.CemError):
+            B.stage_ms()
+        B.set_timing(True)
+        for use_graph in (True, False):
+            B.reset()
+            B.iterate(2, use_graph=use_graph)
+            ms = B.stage_ms()
+            assert len(ms) == 3 and all(m > 0 for m in ms)
+            assert ms[1] > ms[0] and ms[1] > ms[2]  # the rollout dominates
+            for a, b in zip(B.read(), ref):
+                same(a, b)
+        B.set_timing(False)
+        with pytest.raises(P.CemError):
+            B.stage_ms()
+
+
+def test_batch_set_state_rejects_bad_input(P):
+    probs = mixed_problems()
+    with P.Batch(probs) as B:
+        host = B.read_raw()
+        host[1].D = 5
+        with pytest.raises(P.CemError):
+            B.set_state(host)
+        host = B.read_raw()
+        host[0].best_class = 7
+        with pytest.raises(P.CemError):
+            B.set_state(host)
+        with pytest.raises(ValueError):
+            B.set_state(host[:3])

@@ -132,3 +132,72 @@ def test_targets_closed_forms_and_order():
     c = rng.integers(0, 4, 500)
     order = np.lexsort((J, c))
     assert np.all(np.diff(mlp.targets(J, c)[order]) > 0)
+
+
+def _bf16_torch(x):
+    """Round a float64 tensor to BF16 and back (torch's own conversion,
+    round to nearest even)."""
+    return x.to(torch.bfloat16).to(torch.float64)
+
+
+class _RoundFwd(torch.autograd.Function):
+    """BF16 rounding of a stored operand: rounds the value, passes the
+    gradient through unchanged."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return _bf16_torch(x)
+
+    @staticmethod
+    def backward(ctx, g):
+        return g
+
+
+class _RoundBwd(torch.autograd.Function):
+    """BF16 rounding of a stored gradient: identity forward, rounds the
+    gradient flowing back."""
+
+    @staticmethod
+    def forward(ctx, x):
+        return x.clone()
+
+    @staticmethod
+    def backward(ctx, g):
+        return _bf16_torch(g)
+
+
+def test_bf16_emulating_backward_matches_autograd_through_rounding_ops():
+    """The emulated backward against torch autograd on a network whose
+    stored values pass through rounding ops: inputs, weights and hidden
+    activations rounded going forward, hidden-layer gradients dz rounded
+    going back, the output layer's gradient left in full precision.  Also
+    different from the exact gradients by far more than rounding order, so
+    a rounding point left out or added fails."""
+    rng = np.random.default_rng(5)
+    params = mlp.init_params(48, 32, 3, seed=4)
+    X = rng.uniform(-1.5, 1.5, (40, 48))
+    t = rng.standard_normal(40)
+    a = _RoundFwd.apply(torch.from_numpy(X))
+    Ws, bs = [], []
+    for l, (W, b) in enumerate(params):
+        Wt = torch.from_numpy(W.copy()).requires_grad_(True)
+        bt = torch.from_numpy(b.copy()).requires_grad_(True)
+        Ws.append(Wt)
+        bs.append(bt)
+        z = a @ _RoundFwd.apply(Wt).T + bt
+        if l < len(params) - 1:
+            z = _RoundBwd.apply(z)
+            a = _RoundFwd.apply(0.5 * z * (1.0 + torch.special.erf(z / math.sqrt(2.0))))
+        else:
+            y = z[:, 0]
+    loss_t = torch.mean((y - torch.from_numpy(t)) ** 2)
+    loss_t.backward()
+    loss, grads = mlp.loss_and_grads(params, X, t, emulate_bf16=True)
+    assert abs(loss - loss_t.item()) < 1e-12
+    _, exact = mlp.loss_and_grads(params, X, t)
+    far = 0.0
+    for (gW, gb), (eW, eb), Wt, bt in zip(grads, exact, Ws, bs):
+        np.testing.assert_allclose(gW, Wt.grad.numpy(), rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(gb, bt.grad.numpy(), rtol=1e-9, atol=1e-12)
+        far = max(far, np.abs(gW - eW).max() / np.abs(eW).max())
+    assert far > 1e-4

@@ -197,6 +197,76 @@ def test_body_contact_elastic_without_damping(orc):
     assert abs(E[-1] - E[0]) / E[0] < 0.02
 
 
+def _corner_contact(block_yaw, depth_fn):
+    """A base at rest at the origin (yaw 0) and a block at rest rotated by
+    block_yaw, placed so that its corners left of the base's front face
+    (x = 0.25) penetrate it as depth_fn(corners) says; no friction anywhere,
+    no controller force on the block.  Returns the scene, the skeleton, the
+    block centre and its corners."""
+    sc, sk = workload.push_scene(0, T=2)
+    sc.update(base_mu=0.0, block_mu=0.0, contact_mu=0.0, c_contact=50.0, yaw_kp=0.0, yaw_kd=0.0,
+              base_start=(0.0, 0.0, 0.0), base_v0=(0.0, 0.0, 0.0), block_v0=(0.0, 0.0, 0.0))
+    h = sc["block_half"][0]
+    c, s = math.cos(block_yaw), math.sin(block_yaw)
+    local = np.array([(-h, -h), (h, -h), (-h, h), (h, h)])
+    rot = local @ np.array([[c, s], [-s, c]])  # corner offsets in the world frame
+    cx = 0.25 - rot[:, 0].min() - depth_fn(rot)
+    cy = 0.05
+    sc["block_start"] = (cx, cy, block_yaw)
+    return sc, sk, np.array([cx, cy]), rot + np.array([cx, cy])
+
+
+def _block_first_step(orc, sc, sk):
+    th = np.array([0.0, 0.0, 5.0, 0.0, 0.0, 5.0])
+    tr = orc.trace(sc, sk, th, 1)
+    return tr[0, 9:12]  # block vx, vy, w after one step from rest
+
+
+def test_single_corner_contact_point_is_that_corner(orc):
+    """One corner of a block rotated by 0.5 rad penetrates the base's front
+    face by 1 mm: the minimum-overlap axis is the face normal +x, the depth
+    1 mm, and the contact point is that corner, so after one step from rest
+    the block has v = dt k d / m along +x and spin w = dt (r x F) / I with r
+    from its centre to the corner (the centres' midpoint, or any other
+    point, gives another spin)."""
+    d = 1e-3
+    sc, sk, ctr, corners = _corner_contact(0.5, lambda rot: d)
+    inside = corners[:, 0] < 0.25
+    assert inside.sum() == 1
+    q = corners[inside][0]
+    dt, k, m = sc["dt"], sc["k_contact"], sc["block_mass"]
+    I = m * (4 * sc["block_half"][0] ** 2 + 4 * sc["block_half"][1] ** 2) / 12
+    F = np.array([k * d, 0.0])
+    r = q - ctr
+    v, w = _block_first_step(orc, sc, sk)[:2], _block_first_step(orc, sc, sk)[2]
+    np.testing.assert_allclose(v, dt * F / m, rtol=0, atol=1e-12)
+    assert abs(w - dt * (r[0] * F[1] - r[1] * F[0]) / I) < 1e-9
+    assert abs(w) > 1e-3  # the corner's lever arm is what spins the block
+
+
+def test_two_corner_contact_point_is_penetration_weighted(orc):
+    """A block rotated by 0.03 rad with both left corners 0.4 mm and about
+    3.4 mm inside the base's front face: depth = the deeper corner's, and
+    the contact point is the corners' mean weighted by their penetrations
+    below the face (not their plain mean), which fixes the block's first
+    spin."""
+    sc, sk, ctr, corners = _corner_contact(0.03, lambda rot: 3.4e-3)
+    inside = corners[:, 0] < 0.25
+    assert inside.sum() == 2
+    pen = 0.25 - corners[inside, 0]
+    q = (pen[:, None] * corners[inside]).sum(0) / pen.sum()
+    q_plain = corners[inside].mean(0)
+    dt, k, m = sc["dt"], sc["k_contact"], sc["block_mass"]
+    I = m * (4 * sc["block_half"][0] ** 2 + 4 * sc["block_half"][1] ** 2) / 12
+    F = np.array([k * pen.max(), 0.0])
+    out = _block_first_step(orc, sc, sk)
+    np.testing.assert_allclose(out[:2], dt * F / m, rtol=0, atol=1e-12)
+    w_weighted = dt * ((q - ctr)[0] * F[1] - (q - ctr)[1] * F[0]) / I
+    w_plain = dt * ((q_plain - ctr)[0] * F[1] - (q_plain - ctr)[1] * F[0]) / I
+    assert abs(out[2] - w_weighted) < 1e-9
+    assert abs(w_weighted - w_plain) > 1e-3  # the two rules are told apart
+
+
 def _object_scene(T, geoms, obj_start, obj_v0=(0, 0, 0), mu=0.3, c=50.0):
     # the object alone: the robot only runs a moveTo far away from it
     sc, _ = workload.pickplace_scene(0, T=T)

@@ -354,16 +354,25 @@ def test_solve_quadratic_reaches_minimiser(P):
         assert r["best_cls"] == 0 and r["best_J"] < 1e-4
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
+# Converged CE settings per workload: the full reach and move-and-push
+# settings; pick-place at N = 2048, K = 128, 10 iterations (the full 16384
+# samples x 25 iterations x 8 seeds would keep the FP64 oracle busy for
+# minutes; the CE rules, the rollout and the refit are the same).
+CE_CASES = {0: dict(N=256, K=25, iters=10), 1: dict(N=4096, K=200, iters=20), 2: dict(N=2048, K=128, iters=10)}
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2])
 def test_converged_cost_matches_oracle_cem(P, orc, cfg):
-    # Converged CE cost against the FP64 oracle's CE, seed by seed (each seed
-    # is its own scene).  CE on a multimodal cost can settle in a different
-    # mode once FP32 rounding changes one early elite set (the paper reports
-    # such per-seed mode spread, Sec. IV-B), so the bar is: at least 6 of the
-    # 8 seeds within 2%, with the same feasibility class.
+    """Converged CE cost against the FP64 oracle's CE over 8 seeds (each seed
+    its own scene): the mean best cost over the 8 seeds within 2 % of the
+    oracle's, and seed by seed at least 6 of 8 within 2 % with the same
+    feasibility class.  CE on a multimodal cost can settle in another mode
+    once FP32 rounding changes one early elite set (the paper reports such
+    per-seed mode spread, Sec. IV-B), hence 6 of 8 per seed."""
+    cm = CE_CASES[cfg]
     gpu, ref, cls_g, cls_r = [], [], [], []
     for seed in range(8):
-        sc, sk, cm = workload.config(cfg, seed=seed)
+        sc, sk, _ = workload.config(cfg, seed=seed)
         with P.Scene(sc, sk) as S:
             r = S.solve(seed, cm["N"], cm["K"], cm["iters"])
         o = orc.cem(sc, sk, seed, cm["N"], cm["K"], cm["iters"])
@@ -372,6 +381,7 @@ def test_converged_cost_matches_oracle_cem(P, orc, cfg):
         cls_g.append(r["best_cls"])
         cls_r.append(o["best_cls"])
     gpu, ref = np.array(gpu), np.array(ref)
+    assert abs(gpu.mean() - ref.mean()) <= 0.02 * ref.mean(), (gpu, ref)
     close = np.abs(gpu - ref) / ref <= 0.02
     assert close.sum() >= 6, (gpu, ref)
     assert np.all(np.array(cls_g)[close] == np.array(cls_r)[close])

@@ -74,6 +74,11 @@ def parse():
                          "every plan to the end vs successive halving")
     ap.add_argument("--mlp-only", type=int, default=0,
                     help="time only the surrogate forward on this many rows (profiling driver)")
+    ap.add_argument("--batch-only", type=int, default=0,
+                    help="time only CE iterations of the first P problems of the 64-problem batch, fixed launch "
+                         "shape (--warps, --ctas, --tpr), no graph (profiling driver)")
+    ap.add_argument("--warps", type=int, default=4, help="warps per CTA of the persistent launch for --batch-only")
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs per SM of the persistent launch for --batch-only (0 = resident maximum)")
     ap.add_argument("--train-only", type=int, default=0,
                     help="time this many surrogate training steps (batch 4096) on each GEMM path (profiling driver)")
     return ap.parse_args()
@@ -119,7 +124,7 @@ def batch_flops(probs, seed):
     with open(os.path.join(ROOT, "workload", "flops_per_step.json")) as f:
         tab = json.load(f)["batch-64"]
     per = tab["problems"]
-    exact = tab["seed"] == seed and len(per) == len(probs) and all(
+    exact = tab["seed"] == seed and len(probs) <= len(per) and all(
         q["L"] == p["L"] and q["N"] == p["N"] for q, p in zip(per, probs))
     tot = 0.0
     for i, p in enumerate(probs):
@@ -690,6 +695,43 @@ def surrogate_roofline(P, seed, M=65536, reps=20):
             "peak_basis": f"bf16_tflops ({src}, burst)", "launches": reps}
 
 
+def run_batch_only(args):
+    """CE iterations of the first --batch-only problems of the 64-problem
+    batch with a fixed persistent launch shape: --warmup iterations, then
+    --steps iterations each timed by the library's stage events.  Prints one
+    JSON line with the persistent rollout's time and FP32 fraction."""
+    import torch
+
+    import paper_2512_11571_gb300 as P
+    from paper_2512_11571_gb300 import build
+
+    build.build()
+    P.load()
+    probs = batch_problems(args.seed, 0)[:args.batch_only]
+    with P.Batch(probs) as B:
+        B.set_threads_per_rollout(args.tpr)
+        B.set_launch(args.warps, args.ctas)
+        B.set_timing(True)
+        B.reset()
+        B.iterate(args.warmup, use_graph=False)
+        roll = []
+        for _ in range(args.steps):
+            B.iterate(1, use_graph=False)
+            roll.append(B.stage_ms()[1])
+        torch.cuda.synchronize()
+        launch = B.launch()
+        steps = B.steps_per_iteration
+    peaks, src = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = sms * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    flops, basis = batch_flops(probs, args.seed)
+    ms = float(np.mean(roll))
+    tf = flops / (ms / 1e3) / 1e12
+    print(json.dumps({"batch_only": len(probs), "sim_steps_per_iteration": steps, "rollout_ms": ms,
+                      "rollout_ms_all": roll, "sim_steps_per_s": steps / (ms / 1e3), "achieved_tflops": tf,
+                      "frac": tf / peak, "launch": launch, "flops_basis": basis}), flush=True)
+
+
 def run_train_only(args):
     """Times --train-only AdamW steps of the surrogate (48 -> 4 x 256 -> 1,
     batch 4096 drawn from 65,536 stored rows) with the dense layers on the
@@ -877,6 +919,9 @@ def main():
         return
     if args.train_only:
         run_train_only(args)
+        return
+    if args.batch_only:
+        run_batch_only(args)
         return
     if args.mlp_only:
         run_mlp_only(args)

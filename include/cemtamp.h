@@ -375,7 +375,6 @@ int cem_batch_set_active(cem_batch_handle h, const int32_t* active_h);
 int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr);
 /* The current persistent launch shape (CTAs per SM resolved when automatic). */
 int cem_batch_get_launch(cem_batch_handle h, int* warps_out, int* ctas_out, int* tpr_out);
-
 /* ---- Multi-plan search (Sec. III: the optimiser could search several
  * candidate plans at once; Sec. V: evaluating many plans is expensive) ----
  * One scene, n_plans candidate skeletons, each realised by Algorithm 1 as a
@@ -456,6 +455,12 @@ int cem_surrogate_gemm_path(cem_surrogate_handle s);
  * cem_surrogate_train; the BF16 copy is refreshed.  set_params clears the
  * moments and the counter.  Synchronous. */
 int cem_surrogate_adamw_step(cem_surrogate_handle s, const float* grad_h, float lr, float weight_decay);
+/* The optimiser's state: first and second moments (num_params floats each,
+ * host) and the AdamW steps taken so far (the next step's bias correction
+ * uses steps_taken + 1).  Set it to check or resume one step from a known
+ * state; get it to checkpoint.  get synchronises. */
+int cem_surrogate_set_adam_state(cem_surrogate_handle s, const float* m1_h, const float* m2_h, long long steps_taken);
+int cem_surrogate_get_adam_state(cem_surrogate_handle s, float* m1_h, float* m2_h, long long* steps_taken);
 /* Synchronises, writes and clears the tcgen05 forward's status word: 0, or
  * 1 / 2 if a wait for the weight copy / the MMAs expired.  A non-zero code
  * also makes cem_solve_screened return CEM_ERR_TIMEOUT. */

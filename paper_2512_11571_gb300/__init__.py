@@ -43,6 +43,7 @@ EXPORTS = [
     "cem_solve_screened_ft",
     "cem_surrogate_set_forward_path", "cem_surrogate_forward_path", "cem_surrogate_status",
     "cem_surrogate_set_gemm_path", "cem_surrogate_gemm_path", "cem_surrogate_adamw_step",
+    "cem_surrogate_set_adam_state", "cem_surrogate_get_adam_state",
     "cem_last_error", "cem_version",
 ]
 
@@ -288,6 +289,8 @@ def load(path: str = LIB_PATH):
     L.cem_surrogate_set_gemm_path.argtypes = [H, C.c_int]
     L.cem_surrogate_gemm_path.argtypes = [H]
     L.cem_surrogate_adamw_step.argtypes = [H, fptr, C.c_float, C.c_float]
+    L.cem_surrogate_set_adam_state.argtypes = [H, fptr, fptr, C.c_longlong]
+    L.cem_surrogate_get_adam_state.argtypes = [H, fptr, fptr, C.POINTER(C.c_longlong)]
     L.cem_surrogate_test_expire_wait.argtypes = [H, C.c_int]
     L.cem_surrogate_status.argtypes = [H, C.POINTER(C.c_int)]
     L.cem_surrogate_gradient.argtypes = [H, vp, vp, C.c_int, fptr, fptr]
@@ -786,6 +789,22 @@ def cem_surrogate_adamw_step(s, grad, lr=1e-3, weight_decay=1e-4):
     _check(load().cem_surrogate_adamw_step(s, gp, float(lr), float(weight_decay)))
 
 
+def cem_surrogate_set_adam_state(s, m1, m2, steps_taken):
+    n = cem_surrogate_num_params(s)
+    a, ap = _f32(m1, n, "m1")
+    b, bp = _f32(m2, n, "m2")
+    _check(load().cem_surrogate_set_adam_state(s, ap, bp, int(steps_taken)))
+
+
+def cem_surrogate_get_adam_state(s):
+    n = cem_surrogate_num_params(s)
+    m1, m2 = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    t = C.c_longlong()
+    _check(load().cem_surrogate_get_adam_state(s, m1.ctypes.data_as(C.POINTER(C.c_float)),
+                                               m2.ctypes.data_as(C.POINTER(C.c_float)), C.byref(t)))
+    return m1, m2, t.value
+
+
 def cem_surrogate_status(s):
     code = C.c_int(0)
     _check(load().cem_surrogate_status(s, C.byref(code)))
@@ -902,6 +921,13 @@ class Surrogate:
     def adamw_step(self, grad, lr=1e-3, weight_decay=1e-4):
         """One optimiser step of the training loop with the given gradient."""
         cem_surrogate_adamw_step(self.h, grad, lr, weight_decay)
+
+    def set_adam_state(self, m1, m2, steps_taken):
+        cem_surrogate_set_adam_state(self.h, m1, m2, steps_taken)
+
+    def adam_state(self):
+        """(first moments, second moments, steps taken)."""
+        return cem_surrogate_get_adam_state(self.h)
 
     def status(self):
         """Reads and clears the fused kernel's status word (0 = no wait expired)."""

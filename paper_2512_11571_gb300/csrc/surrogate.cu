@@ -552,7 +552,27 @@ __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t*
 // ---- FP32 debug path (gemm path 3): every input, weight, activation and
 // gradient in FP32 and every reduction in ascending index order, one output
 // element per thread.  Slow; it exists to check gradients against an exact
-// FP64 chain rule without the BF16 rounding of the fast paths.
+// FP64 chain rule without the BF16 rounding of the fast paths.  The sums use
+// the compensated dot product Dot2 of Ogita, Rump and Oishi ("Accurate sum
+// and dot product", SIAM J. Sci. Comput. 26, 2005): each product's rounding
+// error from an FMA, each addition's from TwoSum, both carried in a second
+// accumulator, so a sum of thousands of rows is as accurate as if formed in
+// twice the working precision and only the elementwise FP32 functions
+// (GELU, GELU') limit the result.  Explicit-rounding intrinsics keep the
+// compiler from fusing the steps.
+struct Dot2 {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);  // a b = p + ep exactly
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float es = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));  // s + p = t + es exactly
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(es, ep));
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
 struct GemmF32 {
   int M, N, K;
   const float* A;
@@ -573,7 +593,7 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmF32 g) {
   __shared__ float As[16][17], Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int m = blockIdx.y * 16 + ty, n = blockIdx.x * 16 + tx;
-  float acc = 0.0f;
+  Dot2 dot;
   for (int k0 = 0; k0 < g.K; k0 += 16) {
     const int ak = k0 + tx, bk = k0 + ty, bn = blockIdx.x * 16 + tx;
     As[ty][tx] = (m < g.M && ak < g.K) ? (g.a_kmajor ? g.A[(size_t)m * g.lda + ak] : g.A[(size_t)ak * g.lda + m]) : 0.0f;
@@ -581,14 +601,16 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmF32 g) {
                                         : 0.0f;
     __syncthreads();
 #pragma unroll
-    for (int kk = 0; kk < 16; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+    for (int kk = 0; kk < 16; ++kk) dot.add(As[ty][kk], Bs[kk][tx]);
     __syncthreads();
   }
   if (m >= g.M || n >= g.N) return;
+  const float acc = dot.value();
   if (EPI == EPI_F32) {
     g.C[(size_t)m * g.ldc + n] = acc;
   } else if (EPI == EPI_BIAS_GELU) {
-    const float z = acc + g.bias[n];
+    dot.add(g.bias[n], 1.0f);
+    const float z = dot.value();
     g.C[(size_t)m * g.ldc + n] = z;
     g.Cf[(size_t)m * g.ldcf + n] = gelu(z);
   } else {
@@ -607,9 +629,10 @@ __global__ void output_layer_f32_kernel(const float* __restrict__ a, int M, int 
                                         const float* __restrict__ b, float* __restrict__ raw) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  float s = 0.0f;
-  for (int j = 0; j < W; ++j) s = fmaf(a[(size_t)m * W + j], w[j], s);
-  raw[m] = s + b[0];
+  Dot2 dot;
+  for (int j = 0; j < W; ++j) dot.add(a[(size_t)m * W + j], w[j]);
+  dot.add(b[0], 1.0f);
+  raw[m] = dot.value();
 }
 
 // out[j] = sum_m (w ? w[m] : 1) X[m][j] (FP32, m ascending)
@@ -617,9 +640,9 @@ __global__ void colsum_f32_kernel(const float* __restrict__ X, const float* __re
                                   float* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  float s = 0.0f;
-  for (int m = 0; m < M; ++m) s = fmaf(w ? w[m] : 1.0f, X[(size_t)m * N + j], s);
-  out[j] = s;
+  Dot2 dot;
+  for (int m = 0; m < M; ++m) dot.add(w ? w[m] : 1.0f, X[(size_t)m * N + j]);
+  out[j] = dot.value();
 }
 
 // dz[m][j] = dy[m] w[j] GELU'(z[m][j]) (FP32)
@@ -934,7 +957,7 @@ int gradient_f32(cem_surrogate_ctx* s, const float* x_d, const float* t_d, int M
     loss_kernel<<<blocks, 256, 0, st>>>(s->raw, s->tb, s->norm, M, s->dy, s->partial);
     finish_sum_kernel<<<1, 256, 0, st>>>(s->partial, blocks, s->loss_d);
     colsum_f32_kernel<<<(W + 255) / 256, 256, 0, st>>>(act[L - 1], s->dy, M, W, s->g + s->w_off[L]);
-    finish_sum_kernel<<<1, 256, 0, st>>>(s->dy, M, s->g + s->b_off[L]);
+    colsum_f32_kernel<<<1, 256, 0, st>>>(s->dy, nullptr, M, 1, s->g + s->b_off[L]);
     const size_t n = (size_t)M * W;
     output_backward_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->dy, s->p + s->w_off[L],
                                                                              s->pre[L - 1], M, W, dz);
@@ -1166,6 +1189,24 @@ int cem_surrogate_set_gemm_path(cem_surrogate_handle s, int path) {
 
 int cem_surrogate_gemm_path(cem_surrogate_handle s) {
   return s ? (s->gemm_path == 3 ? 3 : use_tc_gemm(s) ? 2 : 1) : -1;
+}
+
+int cem_surrogate_set_adam_state(cem_surrogate_handle s, const float* m1_h, const float* m2_h, long long steps_taken) {
+  if (!s || !m1_h || !m2_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  if (steps_taken < 0) return fail(CEM_ERR_INVALID_ARG, "steps_taken must be >= 0");
+  SUR_CUDA(cudaMemcpy(s->m1, m1_h, sizeof(float) * s->total, cudaMemcpyHostToDevice));
+  SUR_CUDA(cudaMemcpy(s->m2, m2_h, sizeof(float) * s->total, cudaMemcpyHostToDevice));
+  s->adam_step = steps_taken;
+  return CEM_OK;
+}
+
+int cem_surrogate_get_adam_state(cem_surrogate_handle s, float* m1_h, float* m2_h, long long* steps_taken) {
+  if (!s || !m1_h || !m2_h) return fail(CEM_ERR_INVALID_ARG, "null argument");
+  SUR_CUDA(cudaDeviceSynchronize());
+  SUR_CUDA(cudaMemcpy(m1_h, s->m1, sizeof(float) * s->total, cudaMemcpyDeviceToHost));
+  SUR_CUDA(cudaMemcpy(m2_h, s->m2, sizeof(float) * s->total, cudaMemcpyDeviceToHost));
+  if (steps_taken) *steps_taken = s->adam_step;
+  return CEM_OK;
 }
 
 int cem_surrogate_adamw_step(cem_surrogate_handle s, const float* grad_h, float lr, float weight_decay) {

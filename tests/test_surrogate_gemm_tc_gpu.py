@@ -48,7 +48,9 @@ def test_gemm_path_selection(P):
         assert S.gemm_path == 1
         S.set_gemm_path(2)
         assert S.gemm_path == 2
-        for bad in (-1, 3):
+        S.set_gemm_path(3)  # the FP32 debug gradient
+        assert S.gemm_path == 3
+        for bad in (-1, 4):
             with pytest.raises(P.CemError):
                 S.set_gemm_path(bad)
 

@@ -216,6 +216,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
   h->n_items = (int)items.size();
   const size_t P = n_problems;
   cudaError_t e = configure_refit();
+  if (e == cudaSuccess) e = configure_rollout_batch();
   auto M = [&](void** ptr, size_t bytes) {
     if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
   };

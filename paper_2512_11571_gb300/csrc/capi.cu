@@ -365,11 +365,29 @@ DevScene prepare(const cem_scene_desc& s, const cem_skeleton_desc& k) {
   for (int gi = 0; gi < s.n_geoms; ++gi) {
     d.geom_nslab[gi] = s.geom[gi].n_slabs;
     d.geom_flags[gi] = (s.geom[gi].collide_base ? 1 : 0) | (s.geom[gi].collide_object ? 2 : 0);
+    int nb = 0;
     for (int si = 0; si < s.geom[gi].n_slabs; ++si) {
-      for (int j = 0; j < 3; ++j) d.slab[gi][si][j] = s.geom[gi].slab[si].n[j];
-      d.slab[gi][si][3] = s.geom[gi].slab[si].lo;
-      d.slab[gi][si][4] = s.geom[gi].slab[si].hi;
+      const cem_slab& sl = s.geom[gi].slab[si];
+      for (int j = 0; j < 3; ++j) d.slab[gi][si][j] = sl.n[j];
+      d.slab[gi][si][3] = sl.lo;
+      d.slab[gi][si][4] = sl.hi;
+      // the movers' supports along n folded in (pick-and-place contacts)
+      const double ro = (double)s.obj_half * (std::fabs((double)sl.n[0]) + std::fabs((double)sl.n[1]) +
+                                              std::fabs((double)sl.n[2]));
+      for (int j = 0; j < 3; ++j) d.oslab[gi][si][j] = sl.n[j];
+      d.oslab[gi][si][3] = (float)((double)sl.lo - ro);
+      d.oslab[gi][si][4] = (float)((double)sl.hi + ro);
+      if (sl.n[2] == 0.0f) {
+        const double rb = (double)s.base_half[0] * std::fabs((double)sl.n[0]) +
+                          (double)s.base_half[1] * std::fabs((double)sl.n[1]);
+        d.bslab[gi][nb][0] = sl.n[0];
+        d.bslab[gi][nb][1] = sl.n[1];
+        d.bslab[gi][nb][2] = (float)((double)sl.lo - rb);
+        d.bslab[gi][nb][3] = (float)((double)sl.hi + rb);
+        ++nb;
+      }
     }
+    d.bslab_n[gi] = nb;
   }
   for (int i = 0; i < CEM_MAX_D; ++i) d.theta_star[i] = s.theta_star[i];
   for (int i = 0; i < k.D * k.D; ++i) d.A[i] = s.A[i];

@@ -46,6 +46,14 @@ struct DevScene {
   // geometry
   int32_t geom_nslab[CEM_MAX_GEOMS], geom_flags[CEM_MAX_GEOMS];  // bit0 base, bit1 object
   float slab[CEM_MAX_GEOMS][CEM_MAX_SLABS][5];
+  // the same slabs with a pick-and-place mover's support folded in: oslab =
+  // (n, lo - r, hi + r) with r = h (|n_x| + |n_y| + |n_z|) for the object
+  // cube; bslab = (n_x, n_y, lo - r, hi + r) with r = bhx |n_x| + bhy |n_y|
+  // for the base footprint, its slabs with n_z == 0 only (bslab_n of them,
+  // in their original order)
+  float oslab[CEM_MAX_GEOMS][CEM_MAX_SLABS][5];
+  float bslab[CEM_MAX_GEOMS][CEM_MAX_SLABS][4];
+  int32_t bslab_n[CEM_MAX_GEOMS];
   // quadratic
   float theta_star[CEM_MAX_D];
   float A[CEM_MAX_D * CEM_MAX_D];
@@ -148,6 +156,9 @@ cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const Batc
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
                                             int tpr, const Track* tracks, const DrArgs* dr, cudaStream_t st);
 int rollout_batch_max_ctas_per_sm(int warps, int tpr);
+// opts the persistent kernel into its dynamic shared memory (one DevScene
+// per warp; before any capture)
+cudaError_t configure_rollout_batch();
 
 // host helpers shared by the C entry points (capi.cu)
 int validate_descriptors(const cem_scene_desc* s, const cem_skeleton_desc* k);

@@ -339,32 +339,51 @@ __device__ __noinline__ void planar_rollout(const DevScene& s, const float* __re
 }
 
 // --------------------------------------------------------------- pick-place
-// Minimum-overlap contact of an axis-aligned mover against static geometry g
-// (slabs).  PLANAR: base footprint, slabs with n_z == 0 only.
+// Minimum-overlap contact of an axis-aligned mover against static geometry g.
+// The mover's support along each slab normal is folded into the slab when
+// the scene is prepared (DevScene::oslab for the object cube, ::bslab for
+// the base footprint's slabs with n_z == 0), so a slab costs one projection
+// and two differences: overlap through the 'hi' side hi' - p.n, through the
+// 'lo' side p.n - lo'.  The smallest overlap (first on ties) gives the
+// outward normal and the depth; any separating slab means no contact.
 template <bool PLANAR>
-__device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px, float py, float pz, float hx,
-                                             float hy, float hz, float& nx, float& ny, float& nz, float& depth) {
+__device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px, float py, float pz, float& nx,
+                                             float& ny, float& nz, float& depth) {
   bool any = false;
   float best = 0.0f;
-  const int ns = s.geom_nslab[g];
+  const int ns = PLANAR ? s.bslab_n[g] : s.geom_nslab[g];
   for (int i = 0; i < ns; ++i) {
-    const float* sl = s.slab[g][i];
-    if (PLANAR && sl[2] != 0.0f) continue;
     // rounding pinned (no contraction choices left to the compiler): every
     // lane-group width evaluates a contact with the same operations
-    const float r = __fmaf_rn(hx, fabsf(sl[0]), __fmaf_rn(hy, fabsf(sl[1]), __fmul_rn(hz, fabsf(sl[2]))));
-    const float sp = __fmaf_rn(sl[0], px, __fmaf_rn(sl[1], py, __fmul_rn(sl[2], pz)));
-    const float ov_pos = __fsub_rn(sl[4], __fsub_rn(sp, r));
-    const float ov_neg = __fsub_rn(__fadd_rn(sp, r), sl[3]);
+    float n0, n1, n2, sp, lo, hi;
+    if (PLANAR) {
+      const float* sl = s.bslab[g][i];
+      n0 = sl[0];
+      n1 = sl[1];
+      n2 = 0.0f;
+      sp = __fmaf_rn(n0, px, __fmul_rn(n1, py));
+      lo = sl[2];
+      hi = sl[3];
+    } else {
+      const float* sl = s.oslab[g][i];
+      n0 = sl[0];
+      n1 = sl[1];
+      n2 = sl[2];
+      sp = __fmaf_rn(n0, px, __fmaf_rn(n1, py, __fmul_rn(n2, pz)));
+      lo = sl[3];
+      hi = sl[4];
+    }
+    const float ov_pos = __fsub_rn(hi, sp);
+    const float ov_neg = __fsub_rn(sp, lo);
     if (ov_pos <= 0.0f || ov_neg <= 0.0f) return false;
     const float ov = fminf(ov_pos, ov_neg);
     if (!any || ov < best) {
       best = ov;
       any = true;
       const float sg = ov_pos <= ov_neg ? 1.0f : -1.0f;
-      nx = sg * sl[0];
-      ny = sg * sl[1];
-      nz = sg * sl[2];
+      nx = sg * n0;
+      ny = sg * n1;
+      nz = sg * n2;
     }
   }
   depth = best;
@@ -399,7 +418,7 @@ __device__ __forceinline__ int nth_bit(uint32_t m, int k) {
 __device__ __forceinline__ bool base_force(const DevScene& s, int g, float bx, float by, float bvx, float bvy,
                                            float kc, float cc, float& cx, float& cy) {
   float nx, ny, nz, dep;
-  if (!slab_contact<true>(s, g, bx, by, 0.0f, s.bhx, s.bhy, 0.0f, nx, ny, nz, dep)) return false;
+  if (!slab_contact<true>(s, g, bx, by, 0.0f, nx, ny, nz, dep)) return false;
   const float vn = __fmaf_rn(bvx, nx, __fmul_rn(bvy, ny));
   const float Fn = fmaxf(0.0f, __fsub_rn(__fmul_rn(kc, dep), __fmul_rn(cc, vn)));
   cx = __fmul_rn(Fn, nx);
@@ -411,7 +430,7 @@ __device__ __forceinline__ bool base_force(const DevScene& s, int g, float bx, f
 __device__ __forceinline__ bool obj_force(const DevScene& s, int g, float px, float py, float pz, float vx, float vy,
                                           float vz, float kc, float cc, float& nx, float& ny, float& nz, float& Fn) {
   float dep;
-  if (!slab_contact<false>(s, g, px, py, pz, s.oh, s.oh, s.oh, nx, ny, nz, dep)) return false;
+  if (!slab_contact<false>(s, g, px, py, pz, nx, ny, nz, dep)) return false;
   const float vn = __fmaf_rn(vx, nx, __fmaf_rn(vy, ny, __fmul_rn(vz, nz)));
   Fn = fmaxf(0.0f, __fsub_rn(__fmul_rn(kc, dep), __fmul_rn(cc, vn)));
   return true;
@@ -419,22 +438,23 @@ __device__ __forceinline__ bool obj_force(const DevScene& s, int g, float px, fl
 
 // Jacobi friction impulse of one of nc object contacts (normal n, force Fn)
 // from the trial velocity v: the tangential velocity removed, capped by
-// mu F_n dt; returned as the impulse per unit mass to subtract.
+// mu F_n dt; returned as the impulse per unit mass to subtract.  With t the
+// tangential velocity and j = min(mu dt F_n, m |t| / nc) the impulse, the
+// velocity change is (j / (m |t|)) t = min(mu dt F_n / (m |t|), 1 / nc) t,
+// formed here from one reciprocal square root and no division.
 // The object's friction and mass terms of one (possibly randomised)
-// environment: cap = mu dt, its mass, dt / mass.
+// environment: cap = mu dt, its mass, dt / mass, 1 / mass.
 struct ObjPhys {
-  float cap, mo, dt_mo;
+  float cap, mo, dt_mo, inv_mo;
 };
 
 __device__ __forceinline__ bool obj_friction(const ObjPhys& op, float nx, float ny, float nz, float Fn, float vx,
-                                             float vy, float vz, int nc, float& cx, float& cy, float& cz) {
+                                             float vy, float vz, float inv_nc, float& cx, float& cy, float& cz) {
   const float vn = __fmaf_rn(vx, nx, __fmaf_rn(vy, ny, __fmul_rn(vz, nz)));
   const float tx = __fmaf_rn(-vn, nx, vx), ty = __fmaf_rn(-vn, ny, vy), tz = __fmaf_rn(-vn, nz, vz);
-  const float vt = __fsqrt_rn(__fmaf_rn(tx, tx, __fmaf_rn(ty, ty, __fmul_rn(tz, tz))));
-  if (!(vt > 0.0f)) return false;
-  const float mvt = __fmul_rn(op.mo, vt);
-  const float jm = fminf(__fmul_rn(op.cap, Fn), __fdiv_rn(mvt, (float)nc));
-  const float f = __fdiv_rn(jm, mvt);
+  const float vt2 = __fmaf_rn(tx, tx, __fmaf_rn(ty, ty, __fmul_rn(tz, tz)));
+  if (!(vt2 > 0.0f)) return false;
+  const float f = fminf(__fmul_rn(__fmul_rn(__fmul_rn(op.cap, Fn), op.inv_mo), rsqrtf(vt2)), inv_nc);
   cx = __fmul_rn(f, tx);
   cy = __fmul_rn(f, ty);
   cz = __fmul_rn(f, tz);
@@ -528,6 +548,11 @@ __device__ __forceinline__ void base_contacts(const DevScene& s, uint32_t nbr, f
   }
 }
 
+// 1 / nc, the share of one of nc simultaneous contacts (exact for 1, 2, 4)
+__device__ __forceinline__ float contact_share(int nc) {
+  return nc == 1 ? 1.0f : nc == 2 ? 0.5f : __frcp_rn((float)nc);
+}
+
 // One object step against the static geometry in `nbr` (not attached):
 // penalty forces from the pre-step state, the trial velocity with gravity,
 // then one Jacobi friction impulse per contact from that trial velocity,
@@ -541,12 +566,20 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, const ObjPhys
   float fsx = 0.f, fsy = 0.f, fsz = 0.f;
   float jx = 0.f, jy = 0.f, jz = 0.f;
   if (G == 1) {
+    // the first two contacts (in ascending geometry order) are kept for the
+    // friction pass; a third or later one is evaluated again there
     uint32_t cm = 0;
     int nc = 0;
+    float n0x = 0.f, n0y = 0.f, n0z = 0.f, F0 = 0.f, n1x = 0.f, n1y = 0.f, n1z = 0.f, F1 = 0.f;
     for (uint32_t m = nbr; m; m &= m - 1u) {
       const int g = __ffs(m) - 1;
       float nx, ny, nz, Fn;
       if (obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx, ny, nz, Fn) && Fn > 0.0f) {
+        if (nc == 0) {
+          n0x = nx; n0y = ny; n0z = nz; F0 = Fn;
+        } else if (nc == 1) {
+          n1x = nx; n1y = ny; n1z = nz; F1 = Fn;
+        }
         cm |= 1u << g;
         ++nc;
         fsx = __fadd_rn(fsx, __fmul_rn(Fn, nx));
@@ -557,15 +590,32 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, const ObjPhys
     ovx = __fmaf_rn(op.dt_mo, fsx, pvx);
     ovy = __fmaf_rn(op.dt_mo, fsy, pvy);
     ovz = __fsub_rn(__fmaf_rn(op.dt_mo, fsz, pvz), __fmul_rn(s.g, s.dt));
-    // the same contacts again (identical arithmetic) for the friction
-    for (uint32_t m = cm; m; m &= m - 1u) {
-      const int g = __ffs(m) - 1;
-      float nx, ny, nz, Fn, cx, cy, cz;
-      obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx, ny, nz, Fn);
-      if (obj_friction(op, nx, ny, nz, Fn, ovx, ovy, ovz, nc, cx, cy, cz)) {
+    if (nc > 0) {
+      const float inv_nc = contact_share(nc);
+      float cx, cy, cz;
+      if (obj_friction(op, n0x, n0y, n0z, F0, ovx, ovy, ovz, inv_nc, cx, cy, cz)) {
         jx = __fsub_rn(jx, cx);
         jy = __fsub_rn(jy, cy);
         jz = __fsub_rn(jz, cz);
+      }
+      if (nc > 1 && obj_friction(op, n1x, n1y, n1z, F1, ovx, ovy, ovz, inv_nc, cx, cy, cz)) {
+        jx = __fsub_rn(jx, cx);
+        jy = __fsub_rn(jy, cy);
+        jz = __fsub_rn(jz, cz);
+      }
+      // contacts after the second (identical arithmetic to the first pass)
+      uint32_t rest = cm;
+      rest &= rest - 1u;
+      rest &= rest - 1u;
+      for (uint32_t m = rest; m; m &= m - 1u) {
+        const int g = __ffs(m) - 1;
+        float nx, ny, nz, Fn;
+        obj_force(s, g, ox, oy, oz, pvx, pvy, pvz, kc, cc, nx, ny, nz, Fn);
+        if (obj_friction(op, nx, ny, nz, Fn, ovx, ovy, ovz, inv_nc, cx, cy, cz)) {
+          jx = __fsub_rn(jx, cx);
+          jy = __fsub_rn(jy, cy);
+          jz = __fsub_rn(jz, cz);
+        }
       }
     }
   } else {
@@ -585,6 +635,7 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, const ObjPhys
     }
     const uint32_t cm = grp.any_bits(hit);
     const int nc = __popc(cm);
+    const float inv_nc = contact_share(nc);
     // forces in ascending geometry order, each from its owner lane
     for (uint32_t m = cm; m; m &= m - 1u) {
       const int g = __ffs(m) - 1;
@@ -614,7 +665,7 @@ __device__ __forceinline__ void object_contacts(const DevScene& s, const ObjPhys
       const int k = grp.rank + j * G;
       if (k < nn) {
         const int g = nth_bit(nbr, k);
-        if (((cm >> g) & 1u) && obj_friction(op, nx[j], ny[j], nz[j], Fn[j], ovx, ovy, ovz, nc, fx[j], fy[j], fz[j]))
+        if (((cm >> g) & 1u) && obj_friction(op, nx[j], ny[j], nz[j], Fn[j], ovx, ovy, ovz, inv_nc, fx[j], fy[j], fz[j]))
           fr |= 1u << g;
       }
     }
@@ -727,7 +778,7 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
   const Group<G> grp;
   const float dt = s.dt, h = s.oh, eps2 = s.eps * s.eps;
   const float mb = s.mb, dt_mb = s.dt_mb, bcap = s.base_cap * smu, bcap2 = bcap * bcap;
-  const ObjPhys op{s.obj_cap * smu, s.mo * sm, s.dt_mo / sm};
+  const ObjPhys op{s.obj_cap * smu, s.mo * sm, s.dt_mo / sm, 1.0f / (s.mo * sm)};
   const float kc = s.k_contact, cc = s.c_contact, akp = s.arm_kp, akd = s.arm_kd;
   const int n_geoms = s.n_geoms;
   float bx = s.base_start[0], by = s.base_start[1], bvx = s.base_v0[0], bvy = s.base_v0[1];
@@ -1117,7 +1168,8 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
                                                                  const float* __restrict__ theta,
                                                                  float* __restrict__ J, uint8_t* __restrict__ cls,
                                                                  const Track* __restrict__ tracks, const DrArgs dr) {
-  __shared__ DevScene sc[kMaxBatchWarps];
+  extern __shared__ __align__(16) unsigned char psm[];  // one DevScene per warp
+  DevScene* sc = reinterpret_cast<DevScene*>(psm);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   DevScene& s = sc[w];
   int cur = -1;
@@ -1207,12 +1259,24 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
 
 }  // namespace
 
+cudaError_t configure_rollout_batch() {
+  const int bytes = (int)(sizeof(DevScene) * kMaxBatchWarps);
+  cudaError_t e = cudaFuncSetAttribute(rollout_persistent_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_persistent_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_persistent_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
 int rollout_batch_max_ctas_per_sm(int warps, int tpr) {
   int n = 0;
   cudaError_t e;
-  if (tpr == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<8>, warps * 32, 0);
-  else if (tpr == 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<32>, warps * 32, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<1>, warps * 32, 0);
+  const size_t smem = sizeof(DevScene) * (size_t)warps;
+  if (tpr == 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<8>, warps * 32, smem);
+  else if (tpr == 32)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<32>, warps * 32, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, rollout_persistent_kernel<1>, warps * 32, smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -1232,13 +1296,13 @@ cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const Batc
     dr = *dr_in;
   }
   if (tpr == 8)
-    rollout_persistent_kernel<8><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
+    rollout_persistent_kernel<8><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
                                                              J, cls, tracks, dr);
   else if (tpr == 32)
-    rollout_persistent_kernel<32><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
+    rollout_persistent_kernel<32><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
                                                               J, cls, tracks, dr);
   else if (tpr == 1)
-    rollout_persistent_kernel<1><<<grid, warps * 32, 0, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
+    rollout_persistent_kernel<1><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
                                                              J, cls, tracks, dr);
   else
     return cudaErrorInvalidValue;

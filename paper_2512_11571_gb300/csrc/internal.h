@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -46,13 +47,14 @@ struct DevScene {
   // geometry
   int32_t geom_nslab[CEM_MAX_GEOMS], geom_flags[CEM_MAX_GEOMS];  // bit0 base, bit1 object
   float slab[CEM_MAX_GEOMS][CEM_MAX_SLABS][5];
-  // the same slabs with a pick-and-place mover's support folded in: oslab =
-  // (n, lo - r, hi + r) with r = h (|n_x| + |n_y| + |n_z|) for the object
-  // cube; bslab = (n_x, n_y, lo - r, hi + r) with r = bhx |n_x| + bhy |n_y|
-  // for the base footprint, its slabs with n_z == 0 only (bslab_n of them,
-  // in their original order)
-  float oslab[CEM_MAX_GEOMS][CEM_MAX_SLABS][5];
-  float bslab[CEM_MAX_GEOMS][CEM_MAX_SLABS][4];
+  // the same slabs with a pick-and-place mover's support folded in, laid
+  // out for 16-byte loads: oslab = (n_x, n_y, n_z, lo - r | hi + r, unused)
+  // with r = h (|n_x| + |n_y| + |n_z|) for the object cube; bslab = (n_x,
+  // n_y, lo - r, hi + r) with r = bhx |n_x| + bhy |n_y| for the base
+  // footprint, its slabs with n_z == 0 only (bslab_n of them, in their
+  // original order)
+  alignas(16) float oslab[CEM_MAX_GEOMS][CEM_MAX_SLABS][8];
+  alignas(16) float bslab[CEM_MAX_GEOMS][CEM_MAX_SLABS][4];
   int32_t bslab_n[CEM_MAX_GEOMS];
   // quadratic
   float theta_star[CEM_MAX_D];
@@ -64,6 +66,9 @@ struct DevScene {
   float corner[CEM_MAX_CORNERS][2];
   uint64_t corner_vis[CEM_MAX_CORNERS];
 };
+
+static_assert(offsetof(DevScene, oslab) % 16 == 0 && offsetof(DevScene, bslab) % 16 == 0,
+              "mover slabs are read with 16-byte loads");
 
 // Best-ever sample and iteration counter of a device-resident CE loop.
 struct Track {

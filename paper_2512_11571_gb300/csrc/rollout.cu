@@ -357,21 +357,21 @@ __device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px,
     // lane-group width evaluates a contact with the same operations
     float n0, n1, n2, sp, lo, hi;
     if (PLANAR) {
-      const float* sl = s.bslab[g][i];
-      n0 = sl[0];
-      n1 = sl[1];
+      const float4 sl = *reinterpret_cast<const float4*>(s.bslab[g][i]);
+      n0 = sl.x;
+      n1 = sl.y;
       n2 = 0.0f;
       sp = __fmaf_rn(n0, px, __fmul_rn(n1, py));
-      lo = sl[2];
-      hi = sl[3];
+      lo = sl.z;
+      hi = sl.w;
     } else {
-      const float* sl = s.oslab[g][i];
-      n0 = sl[0];
-      n1 = sl[1];
-      n2 = sl[2];
+      const float4 sl = *reinterpret_cast<const float4*>(s.oslab[g][i]);
+      n0 = sl.x;
+      n1 = sl.y;
+      n2 = sl.z;
       sp = __fmaf_rn(n0, px, __fmaf_rn(n1, py, __fmul_rn(n2, pz)));
-      lo = sl[3];
-      hi = sl[4];
+      lo = sl.w;
+      hi = s.oslab[g][i][4];
     }
     const float ov_pos = __fsub_rn(hi, sp);
     const float ov_neg = __fsub_rn(sp, lo);
@@ -703,9 +703,12 @@ __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, fl
                                        float& beta, float& cbeta, float& sbeta, float& q1, float& q2) {
   const float dx = tx - bx, dy = ty - by;
   const float r2 = dx * dx + dy * dy;
-  float rr = sqrtf(r2);
-  if (rr > 0.0f) {
-    const float inv = __fdividef(1.0f, rr);  // fast reciprocal (2 ulp; 0 < rr, far below 2^126)
+  // horizontal reach and the plane's unit vector from one hardware
+  // reciprocal square root (~2 ulp), no square root or division
+  float rr = 0.0f;
+  if (r2 > 0.0f) {
+    const float inv = rsqrtf(r2);
+    rr = r2 * inv;
     cbeta = dx * inv;
     sbeta = dy * inv;
   } else {
@@ -714,21 +717,21 @@ __device__ __forceinline__ void arm_ik(const DevScene& s, float bx, float by, fl
   }
   if (WANT_ANGLE) beta = atan2f(dy, dx);
   float zz = tz - s.arm_z;
-  float rho = sqrtf(rr * rr + zz * zz);
+  float rho2 = rr * rr + zz * zz;
   const float l1 = s.arm_l1, l2 = s.arm_l2;
   const float rmax = l1 + l2 - 1e-3f, rmin = fabsf(l1 - l2) + 1e-3f;
-  if (rho > rmax) {
-    const float f = rmax / rho;
+  if (rho2 > rmax * rmax) {  // pulled onto the reachable shell
+    const float f = rmax * rsqrtf(rho2);
     rr *= f;
     zz *= f;
-    rho = rmax;
-  } else if (rho < rmin) {
-    const float f = rmin / fmaxf(rho, 1e-9f);
+    rho2 = rmax * rmax;
+  } else if (rho2 < rmin * rmin) {
+    const float f = rmin * rsqrtf(fmaxf(rho2, 1e-18f));
     rr *= f;
     zz *= f;
-    rho = rmin;
+    rho2 = rmin * rmin;
   }
-  float c2 = (rho * rho - (l1 * l1 + l2 * l2)) / (2.0f * l1 * l2);
+  float c2 = (rho2 - (l1 * l1 + l2 * l2)) * __frcp_rn(2.0f * l1 * l2);
   c2 = fminf(fmaxf(c2, -1.0f), 1.0f);
   q2 = -acosf(c2);
   const float a = atan2f(zz, rr);

@@ -444,16 +444,15 @@ def single_problem(P, cfg, args, rank, steps):
             "launch": {"block": block, "lanes_per_rollout": tpr}, "steps": steps}
 
 
-def time_to_cost(seed):
-    """CE time-to-cost, surrogate-screened vs plain, on the pick-place task:
-    a surrogate trained on 2,097,152 simulator rollouts (64 training scenes,
+def time_to_cost(seed, n_scenes=6):
+    """CE time-to-cost, surrogate-screened vs plain, on the pick-place task,
+    every CE run one batch of the held-out scenes timed per iteration: a
+    surrogate trained on 2,097,152 simulator rollouts (64 training scenes,
     8192 samples each from the initial distribution and after 4, 8 and 16 CE
-    iterations),
-    then plain CE (N = 16384, K = 512, 25 iterations) and screened CE (pool
-    65536, the same 16384 rollouts per iteration, 8192 of them unscreened)
-    on three held-out scenes; a third run fine-tunes the surrogate on its own
-    samples (100 AdamW steps of 4096 after every 5 iterations, replay ring of
-    65,536)."""
+    iterations), then plain CE (N = 16384, K = 512, 25 iterations), screened
+    CE with the same 16384 rollouts per iteration (8192 unscreened + the
+    8192 best-scored of the rest of a pool of 65,536) and the literal
+    setting (pool 65,536, the 8192 best-scored simulated, K = 512)."""
     import time as _t
 
     from paper_2512_11571_gb300 import screening
@@ -466,14 +465,28 @@ def time_to_cost(seed):
     sur, hist = screening.train_surrogate(X, t, steps=3000)
     t_train = _t.perf_counter() - t0
     del X, t
-    ft = dict(every=5, steps=100, batch=4096, capacity=65536, lr=5e-4, weight_decay=1e-4)
-    rows = screening.compare(sur, [seed, seed + 1, seed + 2], finetune=ft)
+    rows, per_iter = screening.compare_batched(sur, list(range(seed, seed + n_scenes)))
     sur.close()
+
+    def mean(key):
+        return float(np.mean([r[key] for r in rows]))
+
+    def faster(name):
+        return sum(1 for r in rows if r[f"{name}_ttc_ms"] is not None and r["plain_ttc_ms"] is not None
+                   and r[f"{name}_ttc_ms"] < r["plain_ttc_ms"])
+
+    saved = [r["plain_ttc_ms"] - r["screened_ttc_ms"] for r in rows
+             if r["screened_ttc_ms"] is not None and r["plain_ttc_ms"] is not None]
     return {"training_rollouts": n_rollouts, "data_s": t_data, "train_s": t_train,
-            "train_loss_first_last": [float(hist[:10].mean()), float(hist[-10:].mean())], "scenes": rows,
-            "mean_plain_J": float(np.mean([r["plain_J"] for r in rows])),
-            "mean_screened_J": float(np.mean([r["screened_J"] for r in rows])),
-            "finetune": ft, "mean_finetuned_J": float(np.mean([r["finetuned_J"] for r in rows]))}
+            "train_loss_first_last": [float(hist[:10].mean()), float(hist[-10:].mean())],
+            "batched": "each run one batch of the held-out scenes; per-iteration CUDA events",
+            "ms_per_iteration": per_iter, "scenes": rows,
+            "mean_J": {name: mean(f"{name}_J") for name in ("plain", "screened", "literal")},
+            "scenes_faster_than_plain": {name: faster(name) for name in ("screened", "literal")},
+            "amortisation": {"surrogate_cost_s": t_data + t_train,
+                             "mean_ms_saved_per_scene_run": float(np.mean(saved)) if saved else None,
+                             "scene_runs_to_repay": (t_data + t_train) * 1e3 / float(np.mean(saved))
+                             if saved and np.mean(saved) > 0 else None}}
 
 
 def run_gb300(args):

@@ -518,6 +518,26 @@ typedef struct {
 int cem_solve_screened_ft(cem_handle h, cem_surrogate_handle s, const float* scene16_h, const cem_solve_params* p,
                           int n_pool, int n_explore, const cem_finetune_params* ft, cem_result* out);
 
+/* Surrogate screening of every problem of the batch (not in the paper):
+ * each screened iteration draws n_pool candidates per problem from its
+ * distribution exactly as the single-problem screened loop does, scores
+ * them with the surrogate s (features from the problem's bounds and its 16
+ * scene values scene16_h[p * 16 ...]), and rolls out N_p of them: the first
+ * n_explore draws and the N_p - n_explore best-scored of the rest; elites
+ * come from simulated costs only.  A problem's screened batch iterations
+ * equal cem_solve_screened of that problem bit for bit.  The batch keeps the
+ * pointer s (keep the surrogate alive); s = NULL switches screening off.
+ * Errors: CEM_ERR_UNSUPPORTED unless every N_p <= n_pool <= 2^20 and the
+ * surrogate takes the 48 standard features, CEM_ERR_INVALID_ARG unless
+ * 0 <= n_explore <= every N_p.  Synchronous (copies the tables once). */
+int cem_batch_set_screening(cem_batch_handle h, cem_surrogate_handle s, const float* scene16_h, int n_pool,
+                            int n_explore);
+/* `iters` screened CE iterations of every active problem on `stream`
+ * (asynchronous, not graph-captured).  A tcgen05 forward whose bounded wait
+ * expired leaves NaN scores and its status word set (cem_surrogate_status).
+ * Errors: CEM_ERR_INVALID_ARG without cem_batch_set_screening. */
+int cem_batch_iterate_screened(cem_batch_handle h, int iters, void* stream);
+
 /* Threads per block of the rollout kernel: 0 (automatic), 2, 4, 8, 16 or a
  * multiple of 32 up to 256. */
 int cem_set_launch(cem_handle h, int block_threads);

@@ -36,7 +36,7 @@ EXPORTS = [
     "cem_set_randomization",
     "cem_batch_set_active", "cem_multiplan_solve", "cem_base_path",
     "cem_batch_set_randomization", "cem_batch_set_state", "cem_batch_state_bytes", "cem_batch_set_timing",
-    "cem_batch_stage_ms",
+    "cem_batch_stage_ms", "cem_batch_set_screening", "cem_batch_iterate_screened",
     "cem_surrogate_create", "cem_surrogate_destroy", "cem_surrogate_num_params", "cem_surrogate_set_params",
     "cem_surrogate_get_params", "cem_surrogate_forward", "cem_surrogate_gradient", "cem_surrogate_train",
     "cem_surrogate_features", "cem_surrogate_screen", "cem_solve_screened", "cem_surrogate_targets",
@@ -272,6 +272,8 @@ def load(path: str = LIB_PATH):
     L.cem_batch_state_bytes.argtypes = [H]
     L.cem_batch_set_timing.argtypes = [H, C.c_int]
     L.cem_batch_stage_ms.argtypes = [H, C.POINTER(C.c_float)]
+    L.cem_batch_set_screening.argtypes = [H, H, C.POINTER(C.c_float), C.c_int, C.c_int]
+    L.cem_batch_iterate_screened.argtypes = [H, C.c_int, vp]
     ip = C.POINTER(C.c_int)
     L.cem_batch_set_threads_per_rollout.argtypes = [H, C.c_int]
     L.cem_batch_get_launch.argtypes = [H, ip, ip, ip]
@@ -615,6 +617,20 @@ def cem_batch_stage_ms(h):
     return float(ms[0]), float(ms[1]), float(ms[2])
 
 
+def cem_batch_set_screening(h, s, scene16, n_pool, n_explore):
+    """scene16: [n_problems x 16] scene values (s = None switches screening off)."""
+    n = _BATCH_N.get(getattr(h, "value", h))
+    if s is None:
+        _check(load().cem_batch_set_screening(h, None, None, 0, 0))
+        return
+    t, tp = _f32(scene16, None if n is None else 16 * n, "scene16")
+    _check(load().cem_batch_set_screening(h, s, tp, int(n_pool), int(n_explore)))
+
+
+def cem_batch_iterate_screened(h, iters, stream=None):
+    _check(load().cem_batch_iterate_screened(h, int(iters), _stream(stream)))
+
+
 def cem_batch_set_launch(h, warps_per_cta, ctas_per_sm=0):
     _check(load().cem_batch_set_launch(h, warps_per_cta, ctas_per_sm))
 
@@ -671,6 +687,15 @@ class Batch:
     @property
     def state_bytes(self):
         return cem_batch_state_bytes(self.h)
+
+    def set_screening(self, surrogate, scene16, n_pool, n_explore=0):
+        """Screen every problem's candidates with `surrogate` (a Surrogate, or
+        None to switch off); scene16: [n_problems x 16]."""
+        self._surrogate = surrogate
+        cem_batch_set_screening(self.h, None if surrogate is None else surrogate.h, scene16, n_pool, n_explore)
+
+    def iterate_screened(self, iters, stream=None):
+        cem_batch_iterate_screened(self.h, iters, stream)
 
     def set_timing(self, on=True):
         cem_batch_set_timing(self.h, on)

@@ -64,6 +64,11 @@ struct cem_batch_ctx {
   // and after the persistent rollout, after the refit of each iteration
   bool timing = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // surrogate screening (cem_batch_set_screening): per problem the bounds
+  // and scene values the features take, [P][2 * 18 + 16]
+  cem_surrogate_handle sur = nullptr;
+  float* screen_tab_d = nullptr;
+  int n_pool = 0, n_explore = 0;
 };
 
 namespace {
@@ -76,7 +81,8 @@ void batch_free(cem_batch_ctx* h) {
     e = nullptr;
   }
   void* ptrs[] = {h->scenes_d, h->probs_d, h->items_d, h->counter_d, h->theta_d, h->J_d, h->cls_d,
-                  h->mean_d,   h->cov_d,   h->chol_d,  h->keff_d,    h->status_d, h->track_d, h->args_d};
+                  h->mean_d,   h->cov_d,   h->chol_d,  h->keff_d,    h->status_d, h->track_d, h->args_d,
+                  h->screen_tab_d};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -126,10 +132,31 @@ cudaError_t mark(cem_batch_ctx* h, int i, cudaStream_t st) {
                                              : cudaEventRecord(h->ev[i], st);
 }
 
-cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st) {
+constexpr int kTab = 2 * CEM_MAX_D + 16;  // per problem: lo, hi, scene values
+
+// The candidates of one screened iteration: for every active problem, a pool
+// of n_pool draws from its distribution scored by the surrogate, of which
+// the first n_explore and the best-scored N_p - n_explore of the rest become
+// its theta rows (as in the single-problem screened loop).
+cudaError_t enqueue_screen(cem_batch_ctx* h, cudaStream_t st) {
+  for (int p = 0; p < h->P; ++p) {
+    const BatchProblem& b = h->probs[p];
+    if (!b.active) continue;
+    cudaError_t e = surrogate_screen_into(h->sur, h->mean_d + (size_t)p * kMS, h->chol_d + (size_t)p * kMC, b.seed,
+                                          &h->track_d[p].iter, b.problem, h->n_pool, b.N, h->n_explore, b.D,
+                                          h->screen_tab_d + (size_t)p * kTab,
+                                          h->screen_tab_d + (size_t)p * kTab + 2 * CEM_MAX_D,
+                                          h->theta_d + b.theta_off, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st, bool screened = false) {
   cudaError_t e = mark(h, 0, st);
   if (e != cudaSuccess) return e;
-  e = launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, st);
+  e = screened ? enqueue_screen(h, st)
+               : launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
@@ -466,6 +493,49 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
 }
 
 long long cem_batch_steps_per_iteration(cem_batch_handle h) { return h ? h->steps_per_iter : 0; }
+
+int cem_batch_set_screening(cem_batch_handle h, cem_surrogate_handle s, const float* scene16_h, int n_pool,
+                            int n_explore) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (!s) {
+    h->sur = nullptr;
+    return CEM_OK;
+  }
+  if (!scene16_h) return fail(CEM_ERR_INVALID_ARG, "null scene values");
+  if (n_pool < h->maxN || n_pool > CEM_MAX_N)
+    return fail(CEM_ERR_UNSUPPORTED, "n_pool must hold every problem's N and be at most 2^20");
+  for (const BatchProblem& b : h->probs)
+    if (n_explore < 0 || n_explore > b.N) return fail(CEM_ERR_INVALID_ARG, "0 <= n_explore <= N of every problem");
+  int rc = surrogate_reserve_pool(s, n_pool, h->maxN, h->maxD);
+  if (rc != CEM_OK) return rc;
+  if (!h->screen_tab_d) BATCH_CUDA(cudaMalloc(&h->screen_tab_d, sizeof(float) * kTab * (size_t)h->P));
+  std::vector<float> tab((size_t)kTab * h->P, 0.0f);
+  for (int p = 0; p < h->P; ++p) {
+    float* t = tab.data() + (size_t)p * kTab;
+    for (int d = 0; d < h->probs[p].D; ++d) {
+      t[d] = h->skels[p].lo[d];
+      t[CEM_MAX_D + d] = h->skels[p].hi[d];
+    }
+    for (int i = 0; i < 16; ++i) t[2 * CEM_MAX_D + i] = scene16_h[(size_t)p * 16 + i];
+  }
+  BATCH_CUDA(cudaMemcpy(h->screen_tab_d, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
+  h->sur = s;
+  h->n_pool = n_pool;
+  h->n_explore = n_explore;
+  return CEM_OK;
+}
+
+int cem_batch_iterate_screened(cem_batch_handle h, int iters, void* stream) {
+  if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
+  if (!h->sur) return fail(CEM_ERR_INVALID_ARG, "no surrogate set (cem_batch_set_screening)");
+  if (iters < 0 || iters > 100000) return fail(CEM_ERR_UNSUPPORTED, "iters must be in 0..1e5");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int j = 0; j < iters; ++j) {
+    cudaError_t e = enqueue(h, st, true);
+    if (e != cudaSuccess) return fail(CEM_ERR_CUDA, std::string("screened batch iteration: ") + cudaGetErrorString(e));
+  }
+  return CEM_OK;
+}
 
 int cem_batch_set_state(cem_batch_handle h, const cem_result* in, void* stream) {
   if (!h || !in) return fail(CEM_ERR_INVALID_ARG, "null argument");

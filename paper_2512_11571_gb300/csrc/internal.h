@@ -201,6 +201,19 @@ int handle_init_distribution(cem_handle h, const cem_solve_params* p, SolveBuffe
 // copies the loop's results to the host, synchronises and fills *out
 int handle_read_result(cem_handle h, const cem_solve_params* p, SolveBuffers* b, cem_result* out);
 
+// ---- screening of the batched CE (surrogate.cu)
+// reserves the surrogate's pool workspace for n_pool candidates
+int surrogate_reserve_pool(cem_surrogate_handle s, int n_pool, int n_keep, int D);
+// draws n_pool candidates of one problem from (mean, chol) at Philox
+// iteration *iter_ptr, scores them (features from the device tables lohi[2 x
+// 18] and scene16[16]), keeps the first n_explore draws and the best-scored
+// n_keep - n_explore of the rest, in ascending pool order, into theta_keep
+cudaError_t surrogate_screen_into(cem_surrogate_handle s, const float* mean, const float* chol, uint64_t seed,
+                                  const uint32_t* iter_ptr, uint32_t problem, int n_pool, int n_keep, int n_explore,
+                                  int D, const float* lohi, const float* scene16, float* theta_keep, cudaStream_t st);
+// reads and clears the tcgen05 forward's status word (-1 on a copy error)
+int surrogate_status_word(cem_surrogate_handle s);
+
 // ---- fused tcgen05 surrogate forward (48 -> 4 x 256 GELU -> 1)
 struct MlpTcOffsets {
   int w[4];  // element offsets of W0..W3 in the flat BF16 parameter vector

@@ -1393,10 +1393,11 @@ int ensure_pool(cem_surrogate_ctx* s, int P, int N, int D) {
 }
 
 // pool theta (already sampled, P x D) -> scores -> indices of the N best ->
-// theta_keep (N x D), all on `st`
-cudaError_t screen_pool(cem_surrogate_ctx* s, int P, int N, int n_explore, int D, float* theta_keep,
-                        cudaStream_t st) {
-  features_kernel<bf16><<<(P + 127) / 128, 128, 0, st>>>(s->pool_theta, P, D, s->lohi, s->scene16, s->xin);
+// theta_keep (N x D), all on `st`; features from the bounds lohi[2 x 18]
+// and the scene values scene16[16] (device)
+cudaError_t screen_pool_tab(cem_surrogate_ctx* s, int P, int N, int n_explore, int D, const float* lohi,
+                            const float* scene16, float* theta_keep, cudaStream_t st) {
+  features_kernel<bf16><<<(P + 127) / 128, 128, 0, st>>>(s->pool_theta, P, D, lohi, scene16, s->xin);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = infer_rows(s, P, s->pool_score, st);
@@ -1413,6 +1414,11 @@ cudaError_t screen_pool(cem_surrogate_ctx* s, int P, int N, int n_explore, int D
   return cudaGetLastError();
 }
 
+cudaError_t screen_pool(cem_surrogate_ctx* s, int P, int N, int n_explore, int D, float* theta_keep,
+                        cudaStream_t st) {
+  return screen_pool_tab(s, P, N, n_explore, D, s->lohi, s->scene16, theta_keep, st);
+}
+
 int set_tables(cem_surrogate_ctx* s, const cem_skeleton_desc& k, const float* scene16_h, cudaStream_t st) {
   float tab[2 * CEM_MAX_D];
   for (int d = 0; d < CEM_MAX_D; ++d) {
@@ -1426,6 +1432,32 @@ int set_tables(cem_surrogate_ctx* s, const cem_skeleton_desc& k, const float* sc
 }
 
 }  // namespace
+
+namespace cem {
+
+int surrogate_reserve_pool(cem_surrogate_handle s, int n_pool, int n_keep, int D) {
+  if (!s) return fail(CEM_ERR_INVALID_ARG, "null surrogate");
+  if (s->in_dim != 48) return fail(CEM_ERR_UNSUPPORTED, "screening needs the 48-feature surrogate input");
+  return ensure_pool(s, n_pool, n_keep, D);
+}
+
+cudaError_t surrogate_screen_into(cem_surrogate_handle s, const float* mean, const float* chol, uint64_t seed,
+                                  const uint32_t* iter_ptr, uint32_t problem, int n_pool, int n_keep, int n_explore,
+                                  int D, const float* lohi, const float* scene16, float* theta_keep,
+                                  cudaStream_t st) {
+  cudaError_t e = launch_sample(mean, chol, seed, iter_ptr, 0, problem, n_pool, D, s->pool_theta, st);
+  if (e != cudaSuccess) return e;
+  return screen_pool_tab(s, n_pool, n_keep, n_explore, D, lohi, scene16, theta_keep, st);
+}
+
+int surrogate_status_word(cem_surrogate_handle s) {
+  int v = 0;
+  if (!s || cudaMemcpy(&v, s->tc_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (v) cudaMemset(s->tc_status, 0, sizeof(int));
+  return v;
+}
+
+}  // namespace cem
 
 extern "C" {
 

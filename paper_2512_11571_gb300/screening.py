@@ -19,7 +19,7 @@ import numpy as np
 
 import workload
 
-from . import COV, Batch, Scene, Surrogate, cem_surrogate_targets
+from . import COV, Batch, Scene, Surrogate, cem_surrogate_targets  # noqa: F401
 
 
 def _dev(a):
@@ -157,3 +157,65 @@ def compare(sur, scene_seeds, N=16384, K=512, iters=25, n_pool=65536, n_explore=
         rows.append(row)
     sur.set_params(w0, n0)
     return rows
+
+
+def _batched_run(specs, sur, N, K, iters, n_pool=0, n_explore=0):
+    """One CE run of every held-out scene as one batch (plain when sur is
+    None, else screened): device time of each iteration (CUDA events on the
+    launching stream around it) and every scene's best cost after it."""
+    import torch
+
+    probs = [dict(scene=sc, skel=sk, N=N, K=K, seed=s, problem=s) for s, sc, sk, _ in specs]
+    f16 = np.stack([f for *_, f in specs])
+    st = torch.cuda.current_stream()
+    with Batch(probs) as B:
+        if sur is not None:
+            B.set_screening(sur, f16, n_pool, n_explore)
+        step = (lambda: B.iterate_screened(1, st)) if sur is not None else (lambda: B.iterate(1, True, st))
+        step()  # warm-up (workspaces, graph capture), then a fresh run
+        B.reset()
+        ms, best = [], []
+        for _ in range(iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            step()
+            e1.record(st)
+            res = B.read()  # synchronises
+            ms.append(e0.elapsed_time(e1))
+            best.append([(r["best_cls"], float(r["best_J"])) for r in res])
+        if sur is not None and sur.status() != 0:
+            raise RuntimeError("surrogate forward: a bounded pipeline wait expired")
+    return np.array(ms), best
+
+
+def compare_batched(sur, scene_seeds, N=16384, K=512, iters=25, n_pool=65536, n_explore=8192, n_literal=8192):
+    """Plain CE and surrogate-screened CE on held-out pick-place scenes, each
+    run as ONE batch of all the scenes, timed per iteration with CUDA events:
+      plain     -- N = 16384 rollouts per scene and iteration;
+      screened  -- the same N rollouts: n_explore unscreened draws and the
+                   best-scored N - n_explore of the rest of a pool of n_pool;
+      literal   -- a pool of n_pool, the n_literal best-scored simulated
+                   (no unscreened draws), K elites from simulated costs.
+    Per scene: final best cost of each run, and the device time each run
+    takes to first reach the plain run's final cost within 1%."""
+    specs = []
+    for s in scene_seeds:
+        sc, sk, _ = workload.config(2, seed=s)
+        specs.append((s, sc, sk, workload.scene_features(sc)))
+    runs = {"plain": _batched_run(specs, None, N, K, iters),
+            "screened": _batched_run(specs, sur, N, K, iters, n_pool, n_explore),
+            "literal": _batched_run(specs, sur, n_literal, K, iters, n_pool, 0)}
+    rows = []
+    for i, (s, *_rest) in enumerate(specs):
+        plain_cls, plain_J = runs["plain"][1][-1][i]
+        target = 1.01 * plain_J
+        row = dict(scene=s, plain_J=plain_J, plain_cls=plain_cls)
+        for name, (ms, best) in runs.items():
+            cum = np.cumsum(ms)
+            hit = [j for j in range(iters) if best[j][i][0] <= plain_cls and best[j][i][1] <= target]
+            row[f"{name}_J"] = best[-1][i][1]
+            row[f"{name}_cls"] = best[-1][i][0]
+            row[f"{name}_ttc_ms"] = float(cum[hit[0]]) if hit else None
+        rows.append(row)
+    per_iter = {name: float(np.mean(ms)) for name, (ms, _) in runs.items()}
+    return rows, per_iter

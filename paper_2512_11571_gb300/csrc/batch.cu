@@ -50,6 +50,7 @@ struct cem_batch_ctx {
   float* chol_d = nullptr;  // [P][18*18]
   int32_t* keff_d = nullptr;
   int32_t* status_d = nullptr;
+  int32_t* perm_d = nullptr;  // rollout order of every problem's samples (launch_order_batch)
   Track* track_d = nullptr;
   RefitArgs* args_d = nullptr;
   int warps = 4, ctas_per_sm = 0;  // persistent launch shape (0 = occupancy)
@@ -82,7 +83,7 @@ void batch_free(cem_batch_ctx* h) {
   }
   void* ptrs[] = {h->scenes_d, h->probs_d, h->items_d, h->counter_d, h->theta_d, h->J_d, h->cls_d,
                   h->mean_d,   h->cov_d,   h->chol_d,  h->keff_d,    h->status_d, h->track_d, h->args_d,
-                  h->screen_tab_d};
+                  h->screen_tab_d, h->perm_d};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -158,13 +159,16 @@ cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st, bool screened = false) {
   e = screened ? enqueue_screen(h, st)
                : launch_sample_batch(h->probs_d, h->P, h->maxN, h->mean_d, h->chol_d, h->track_d, h->theta_d, st);
   if (e != cudaSuccess) return e;
+  const bool order = !h->dr_on;  // the randomised path keeps the identity order
+  if (order) e = launch_order_batch(h->scenes_d, h->probs_d, h->P, h->theta_d, h->perm_d, st);
+  if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = mark(h, 1, st);
   if (e != cudaSuccess) return e;
   e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
                                       h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, h->track_d,
-                                      h->dr_on ? &h->dr : nullptr, st);
+                                      h->dr_on ? &h->dr : nullptr, st, order ? h->perm_d : nullptr);
   if (e != cudaSuccess) return e;
   e = mark(h, 2, st);
   if (e != cudaSuccess) return e;
@@ -254,6 +258,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
   M((void**)&h->theta_d, sizeof(float) * (size_t)theta_total);
   M((void**)&h->J_d, sizeof(float) * (size_t)sample_total);
   M((void**)&h->cls_d, (size_t)sample_total);
+  M((void**)&h->perm_d, sizeof(int32_t) * (size_t)sample_total);
   M((void**)&h->mean_d, sizeof(float) * P * kMS);
   M((void**)&h->cov_d, sizeof(float) * P * kMC);
   M((void**)&h->chol_d, sizeof(float) * P * kMC);

@@ -156,10 +156,17 @@ cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int
                                 const float* chols, const Track* tracks, float* theta, cudaStream_t st);
 // persistent rollout over a work queue of (problem, 32-sample chunk) items;
 // *counter must be zero at launch
+// perm (may be null = identity): lane position k of a problem rolls out
+// sample perm[sample_off + k] (the randomised path keeps the identity)
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
-                                            int tpr, const Track* tracks, const DrArgs* dr, cudaStream_t st);
+                                            int tpr, const Track* tracks, const DrArgs* dr, cudaStream_t st,
+                                            const int32_t* perm = nullptr);
+// the rollout order of every problem of a batch (see order_batch_kernel):
+// perm[sample_off + k] for k < N, from the theta just sampled
+cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* probs_d, int n_problems,
+                               const float* theta, int32_t* perm, cudaStream_t st);
 int rollout_batch_max_ctas_per_sm(int warps, int tpr);
 // opts the persistent kernel into its dynamic shared memory (one DevScene
 // per warp; before any capture)

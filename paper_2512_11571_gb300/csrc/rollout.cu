@@ -1155,6 +1155,71 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
   return cudaGetLastError();
 }
 
+// Rollout order of a batch (a schedule, not arithmetic): the persistent
+// kernel rolls sample perm[k] out on the lane that takes position k, so
+// samples that will be in the same action at the same time share a warp
+// and its lanes take the same branches.  For a pick-and-place problem of at
+// most kMaxOrdered samples the order is by a cheap forecast from theta: the
+// samples whose grip height lies within the grasp tolerance (they can grasp)
+// first, then by the first moveTo's gain (how soon they arrive), ties by
+// sample index; every other problem keeps the identity.  Each sample's
+// result is the same wherever it runs.  One CTA per problem, a bitonic sort
+// of 64-bit keys (forecast << 32 | index) in shared memory.
+constexpr int kMaxOrdered = 8192;
+constexpr int kOrderThreads = 512;
+
+__global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevScene* __restrict__ scenes,
+                                                                    const BatchProblem* __restrict__ probs,
+                                                                    const float* __restrict__ theta,
+                                                                    int32_t* __restrict__ perm) {
+  extern __shared__ unsigned long long okeys[];
+  const BatchProblem pb = probs[blockIdx.x];
+  int32_t* out = perm + pb.sample_off;
+  const DevScene& s = scenes[blockIdx.x];
+  int grasp = -1, first_move = -1;
+  if (s.kind == CEM_SCENE_PICKPLACE && s.base_ctrl == 0)
+    for (int i = 0; i < s.n_act; ++i) {
+      if (first_move < 0 && s.act_kind[i] == CEM_ACT_MOVE) first_move = i;
+      if (grasp < 0 && s.act_kind[i] == CEM_ACT_GRASP) grasp = i;
+    }
+  if (!pb.active || pb.N > kMaxOrdered || grasp < 0 || first_move < 0) {
+    for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[k] = k;
+    return;
+  }
+  int P2 = 1;
+  while (P2 < pb.N) P2 <<= 1;
+  const int gi = s.act_off[grasp] + 1, ki = s.act_off[first_move] + 2;
+  const float tol = s.grip_tol;
+  for (int k = threadIdx.x; k < P2; k += blockDim.x) {
+    unsigned long long key = ~0ull;
+    if (k < pb.N) {
+      const float* row = theta + pb.theta_off + (size_t)k * pb.D;
+      const float grip = fminf(fmaxf(row[gi], s.lo[gi]), s.hi[gi]);
+      const float kp = fminf(fmaxf(row[ki], s.lo[ki]), s.hi[ki]);
+      const uint32_t f = (fabsf(grip) <= tol ? 0u : 0x80000000u) | (__float_as_uint(kp) >> 1);
+      key = ((unsigned long long)f << 32) | (uint32_t)k;
+    }
+    okeys[k] = key;
+  }
+  __syncthreads();
+  for (int size = 2; size <= P2; size <<= 1)
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int k = threadIdx.x; k < P2; k += blockDim.x) {
+        const int j = k ^ stride;
+        if (j > k) {
+          const bool up = (k & size) == 0;
+          const unsigned long long a = okeys[k], b = okeys[j];
+          if ((a > b) == up) {
+            okeys[k] = b;
+            okeys[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[k] = (int32_t)(uint32_t)(okeys[k] & 0xffffffffull);
+}
+
 // Persistent batched rollout: every warp of a resident CTA repeatedly takes
 // the next (problem, 32-sample chunk) item from a global queue and rolls the
 // chunk out with that problem's scene, staged in the warp's own shared-memory
@@ -1170,7 +1235,8 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
                                                                  int* __restrict__ counter,
                                                                  const float* __restrict__ theta,
                                                                  float* __restrict__ J, uint8_t* __restrict__ cls,
-                                                                 const Track* __restrict__ tracks, const DrArgs dr) {
+                                                                 const Track* __restrict__ tracks, const DrArgs dr,
+                                                                 const int32_t* __restrict__ perm) {
   extern __shared__ __align__(16) unsigned char psm[];  // one DevScene per warp
   DevScene* sc = reinterpret_cast<DevScene*>(psm);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1227,8 +1293,9 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
     } else if (G > 1 && s.kind == CEM_SCENE_PICKPLACE) {
       // G lanes per rollout: the 32-sample item in G passes of 32 / G
       for (int sub = 0; sub < G; ++sub) {
-        const int n = item.first + sub * (32 / G) + lane / G;
-        if (n < pb.N) {
+        const int k = item.first + sub * (32 / G) + lane / G;
+        if (k < pb.N) {
+          const int n = perm ? perm[pb.sample_off + k] : k;
           const float* row = theta + pb.theta_off + (size_t)n * pb.D;
           float Jn;
           int c;
@@ -1241,8 +1308,9 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
         __syncwarp();
       }
     } else {
-      const int n = item.first + lane;
-      if (n < pb.N) {
+      const int k = item.first + lane;
+      if (k < pb.N) {
+        const int n = perm ? perm[pb.sample_off + k] : k;
         const float* row = theta + pb.theta_off + (size_t)n * pb.D;
         float Jn;
         int c;
@@ -1264,7 +1332,10 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
 
 cudaError_t configure_rollout_batch() {
   const int bytes = (int)(sizeof(DevScene) * kMaxBatchWarps);
-  cudaError_t e = cudaFuncSetAttribute(rollout_persistent_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(order_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(unsigned long long) * kMaxOrdered));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(rollout_persistent_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(rollout_persistent_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -1287,10 +1358,19 @@ int rollout_batch_max_ctas_per_sm(int warps, int tpr) {
   return n > 0 ? n : 1;
 }
 
+cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* probs_d, int n_problems,
+                               const float* theta, int32_t* perm, cudaStream_t st) {
+  if (n_problems <= 0) return cudaSuccess;
+  order_batch_kernel<<<n_problems, kOrderThreads, sizeof(unsigned long long) * kMaxOrdered, st>>>(scenes_d, probs_d,
+                                                                                                  theta, perm);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
-                                            int tpr, const Track* tracks, const DrArgs* dr_in, cudaStream_t st) {
+                                            int tpr, const Track* tracks, const DrArgs* dr_in, cudaStream_t st,
+                                            const int32_t* perm) {
   if (n_items <= 0) return cudaSuccess;
   if (warps < 1 || warps > kMaxBatchWarps || grid < 1) return cudaErrorInvalidValue;
   DrArgs dr{};  // M = 0: off
@@ -1300,13 +1380,13 @@ cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const Batc
   }
   if (tpr == 8)
     rollout_persistent_kernel<8><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                             J, cls, tracks, dr);
+                                                             J, cls, tracks, dr, perm);
   else if (tpr == 32)
     rollout_persistent_kernel<32><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                              J, cls, tracks, dr);
+                                                              J, cls, tracks, dr, perm);
   else if (tpr == 1)
     rollout_persistent_kernel<1><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                             J, cls, tracks, dr);
+                                                             J, cls, tracks, dr, perm);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

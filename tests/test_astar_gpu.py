@@ -5,7 +5,10 @@ The device planner (FP32 queries on a host-built FP64 corner graph) must
 return the oracle's waypoints; rollouts that plan at every moveTo must match
 the oracle per step and in cost at the plain parity tolerances, with the
 same "borderline" exclusion (a discrete event within rounding of the
-sample), and lane groups must stay bit-identical to one lane."""
+sample), both from the initial distribution (600 steps) and from a
+converged one over the whole horizon (every action of the plan, each moveTo
+planned from where the base stands), and lane groups must stay
+bit-identical to one lane."""
 import numpy as np
 import pytest
 
@@ -144,3 +147,77 @@ def test_controller_validation(P):
     with P.Scene(*workload.pickplace_scene(0)) as S:  # no planner graph
         with pytest.raises(P.CemError):
             S.base_path((0, 0), (1, 1))
+
+
+def converged_astar(seed, n, sample_seed):
+    """The A* scene of a pick-and-place seed with n samples of the
+    distribution the oracle's CE converged to on the same scene with the
+    straight-line base controller (the plan's parameters mean the same
+    under both controllers: the targets, gains, grasp and place offsets)."""
+    from pickplace_common import converged
+
+    _, _, mean, L = converged(seed)
+    sc, sk = workload.pickplace_scene(seed, controller="astar")
+    th = oracle.sample(sample_seed, 0, 0, n, mean, L).astype(np.float32)
+    return sc, sk, th
+
+
+def test_full_horizon_cost_and_class_through_every_action(P):
+    """256 converged samples per scene over T = 3000 with A* planning at
+    every moveTo: cost within 1e-3 and class exactly except for borderline
+    samples (FP64 cost moves by more than 1e-3 when theta moves by 1e-6 of
+    its range: a success test, contact onset or waypoint switch within
+    rounding), which stay below 2 %; a third of the samples or more finish
+    all five actions on every scene."""
+    from pickplace_common import SEEDS, borderline
+
+    n_bl = n_all = 0
+    for seed in SEEDS:
+        sc, sk, th = converged_astar(seed, 256, 4321)
+        with P.Scene(sc, sk) as S:
+            J, cls = S.rollout(dev(th))
+        J, cls = J.cpu().numpy(), cls.cpu().numpy()
+        Jr, cr = oracle.rollout(sc, sk, th.astype(np.float64))
+        assert np.isin(cr, (0, 1)).mean() >= 1 / 3, (seed, np.bincount(cr, minlength=4))
+        r = np.abs(J - Jr) / np.maximum(np.abs(Jr), 1e-3)
+        bad = np.where((r > 1e-3) | (cls != cr))[0]
+        bl = borderline(lambda t: oracle.rollout(sc, sk, t)[0], sk, th, Jr, bad)
+        hard = bad[~bl]
+        assert len(hard) == 0, (seed, hard[:8], J[hard[:8]], Jr[hard[:8]], cls[hard[:8]], cr[hard[:8]])
+        n_bl += int(bl.sum())
+        n_all += len(th)
+    assert n_bl <= 0.02 * n_all, (n_bl, n_all)
+
+
+def test_per_step_state_through_every_action(P):
+    """8 converged samples per scene traced over the whole horizon with A*
+    planning: every action's end on the oracle's step (or one step apart
+    with the cost still within 1e-3: a crossing within FP32 rounding of eps,
+    at most 2 of the 24), and the state from step 0 to 25 steps after the
+    release within the shared pick-and-place bar (1e-4 m / rad, 1e-3 m/s,
+    flags exactly)."""
+    from pickplace_common import ACT, SEEDS, events, state_error, transitions
+
+    n_cmp = n_shift = 0
+    for seed in SEEDS:
+        sc, sk, th = converged_astar(seed, 8, 99)
+        T = sc["T"]
+        with P.Scene(sc, sk) as S:
+            st = S.trace(dev(th), T).cpu().numpy().astype(np.float64)
+            J, cls = S.rollout(dev(th))
+        J, cls = J.cpu().numpy(), cls.cpu().numpy()
+        for i in range(th.shape[0]):
+            ref = oracle.trace(sc, sk, th[i].astype(np.float64), T)
+            tg, tr_ = transitions(st[i]), transitions(ref)
+            if tg != tr_:
+                assert tg.keys() == tr_.keys() and all(abs(tg[k] - tr_[k]) <= 1 for k in tg), (seed, i, tg, tr_)
+                Jr, cr = oracle.rollout(sc, sk, th[i:i + 1].astype(np.float64))
+                assert abs(J[i] - Jr[0]) <= 1e-3 * max(abs(Jr[0]), 1e-3) and cls[i] == cr[0], (seed, i)
+                n_shift += 1
+                continue
+            ka, kr = events(ref)
+            end = min(kr + 25, T) if kr is not None else T
+            worst, where = state_error(st[i, :end], ref[:end])
+            assert worst <= 1.0, (seed, i, where, worst, st[i, where[0]], ref[where[0]])
+            n_cmp += ref[-1, ACT] == 5
+    assert n_shift <= 2 and n_cmp >= 8, (n_shift, n_cmp)

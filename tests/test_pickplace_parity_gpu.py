@@ -12,7 +12,7 @@ the exit within the horizon.  Checked through the C ABI:
     the borderline rate must stay below 1 % over all scenes;
   * the per-step state from step 0 through 25 steps after the release
     (grasp, carry, place and release included): every action's end on the
-    oracle's step and the state within the bar given below.
+    oracle's step and the state within the shared bar of pickplace_common.
 
 Each test asserts that at least half of its samples finish all five
 actions, so the grasp-to-exit path is what is being compared.
@@ -20,7 +20,7 @@ actions, so the grasp-to-exit path is what is being compared.
 import numpy as np
 import pytest
 
-from pickplace_common import ACT, ATT, SEEDS, converged, events
+from pickplace_common import ACT, SEEDS, borderline, converged, events, state_error, transitions
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -46,20 +46,6 @@ def draw(orc, seed, n, sample_seed=4321):
     return sc, sk, th
 
 
-def borderline(orc, sc, sk, th, J0, idx, tol=1e-3, reps=8, seed=0):
-    rng = np.random.default_rng(seed)
-    span = np.array(sk["hi"]) - np.array(sk["lo"])
-    out = []
-    for i in idx:
-        thp = []
-        for _ in range(reps):
-            u = rng.standard_normal(len(span))
-            thp.append(th[i].astype(np.float64) + 1e-6 * span * u / np.linalg.norm(u))
-        Jp, _ = orc.rollout(sc, sk, np.array(thp))
-        out.append(bool(np.any(np.abs(Jp - J0[i]) / max(abs(J0[i]), 1e-3) > tol)))
-    return np.array(out, bool)
-
-
 def test_full_horizon_cost_and_class_through_every_action(P, orc):
     n, n_bl, n_all = 256, 0, 0
     for seed in SEEDS:
@@ -73,7 +59,7 @@ def test_full_horizon_cost_and_class_through_every_action(P, orc):
         assert done.mean() >= 0.5, f"scene {seed}: only {done.mean():.2f} finish all five actions"
         r = np.abs(J - Jr) / np.maximum(np.abs(Jr), 1e-3)
         bad = np.where((r > 1e-3) | (cls != cr))[0]
-        bl = borderline(orc, sc, sk, th, Jr, bad)
+        bl = borderline(lambda t: orc.rollout(sc, sk, t)[0], sk, th, Jr, bad)
         hard = bad[~bl]
         assert len(hard) == 0, (seed, hard[:8], J[hard[:8]], Jr[hard[:8]], cls[hard[:8]], cr[hard[:8]])
         n_bl += int(bl.sum())
@@ -81,49 +67,16 @@ def test_full_horizon_cost_and_class_through_every_action(P, orc):
     assert n_bl <= 0.01 * n_all, (n_bl, n_all)
 
 
-# Per-step state bound over the whole grasp -> carry -> place -> release
-# segment (up to 25 steps after the release).  Each FP32 step rounds every
-# state variable by ~6e-8 |x|; the PD laws and friction clamps damp these
-# errors with time constants of ~100 steps, so they settle near a few
-# 1e-6 m (measured: positions <= 2.3e-6 m, angles <= 2.3e-6 rad, velocities
-# <= 7e-5 m/s over 3 scenes x 64 samples).  The bar is 1e-4 m / 1e-4 rad
-# for positions and angles and 1e-3 m/s / rad/s for velocities: some 40x
-# above that error scale and 500x below the success tolerance eps = 0.05 m
-# that decides every action's end, so a sequencing slip of the kind the
-# oracle's pins target (an offset, a release velocity, a wrong step) is far
-# outside it.  The azimuth is compared modulo 2 pi; the attachment flag and
-# the action index exactly.
-POS_COLS = (0, 1, 4, 5, 9, 10, 11, 17, 18, 19)
-VEL_COLS = (2, 3, 6, 7, 12, 13, 14)
-
-
-def state_error(gpu, ref):
-    """(worst ratio to the bar, its (step, column)) of one trace segment."""
-    d = np.abs(gpu - ref)
-    d[:, 8] = np.abs((gpu[:, 8] - ref[:, 8] + np.pi) % (2 * np.pi) - np.pi)
-    bar = np.full(d.shape[1], np.inf)
-    bar[list(POS_COLS) + [8]] = 1e-4
-    bar[list(VEL_COLS)] = 1e-3
-    ratio = d / bar
-    ratio[:, [ATT, ACT]] = np.where(d[:, [ATT, ACT]] == 0.0, 0.0, np.inf)
-    i = np.unravel_index(np.argmax(ratio), ratio.shape)
-    return float(ratio[i]), i
-
-
-def transitions(tr):
-    """Step at which each action index is first reached."""
-    a = tr[:, ACT].astype(int)
-    return {int(k): int(np.argmax(a >= k)) for k in range(1, a.max() + 1)}
-
-
 def test_per_step_state_through_grasp_carry_place_release(P, orc):
     """For 16 samples per scene, every action's end falls on the oracle's
     step, and the whole state from step 0 to 25 steps after the release
     (the grasp, the carry, the place and the release included) stays within
-    the bar above.  A sample whose action end falls one step apart (a
+    the bar.  A sample whose action end falls one step apart (a
     distance within FP32 rounding of eps at that step) must still match the
     oracle's cost to 1e-3 (the interpolated crossing time absorbs the
-    step); at most 2 of the 48 may do so."""
+    step); at most 2 of the 48 may do so.  The bar is the shared one of
+    pickplace_common: 1e-4 m / rad for positions and angles, 1e-3 m/s for
+    velocities, the flags exactly."""
     n_cmp, n_shift = 0, 0
     for seed in SEEDS:
         sc, sk, th = draw(orc, seed, 16, sample_seed=99)

@@ -226,7 +226,8 @@ struct MlpTcOffsets {
   int w[4];  // element offsets of W0..W3 in the flat BF16 parameter vector
 };
 struct MlpTcArgs {
-  const void* x;         // BF16 [M x 48] features
+  const void* x;         // BF16 [M x 48] features (used when xf is null)
+  const float* xf;       // FP32 [M x 48] features, rounded to BF16 in the kernel (16-byte aligned), or null
   int M;
   const void* wpack;     // canonical weight image from mlp_tc_pack
   const float* bias[4];  // FP32 biases of the hidden layers

@@ -1,23 +1,26 @@
 // Fused surrogate forward on the 5th-generation tensor cores (tcgen05).
 //
 // Scores candidates through the whole MLP (48 -> 4 x 256 GELU -> 1) in one
-// persistent launch: one CTA per SM walks over 128-row tiles.  Per CTA, one
-// warp issues the weight copies (cp.async.bulk) and the tcgen05.mma sequence
-// (M = 128, N = 256, K = 16, BF16 x BF16 -> FP32); 16 epilogue warps drain
-// the accumulator with tcgen05.ld, add the bias, apply GELU and write BF16
-// activations back into shared memory as the next layer's A operand.
+// persistent launch: one CTA per SM walks over 128-row tiles, two tiles in
+// flight.  Per CTA, one warp streams the hidden weights into shared memory
+// (cp.async.bulk), one warp issues the tcgen05.mma sequence (M = 128,
+// N = 256, K = 16, BF16 x BF16 -> FP32), and 16 epilogue warps drain a
+// tile's 256-column FP32 accumulator in TMEM with tcgen05.ld, add the bias,
+// apply GELU and write BF16 activations back into that tile's shared-memory
+// buffer as the next layer's A operand.
 //
-// Pipeline.  Two 256-column FP32 accumulators in TMEM serve alternate
-// layers, so the next layer's MMAs run while the epilogue still reads the
-// current one: the epilogue works in two steps of 32 columns per warp, and
-// as soon as every warp has written step c (K-slices c, c + 2, c + 4, c + 6
-// of the next layer's A) the MMA warp issues those slices' MMAs.  Hidden
-// weights stream through shared memory in 16 KB K-slices: slice j of the
-// next layer (or of layer 1 of the next tile) is copied in as soon as the
-// MMAs reading slice j of the current layer have finished.  W0 [256 x 48]
-// stays resident.  The last layer's epilogue writes no activations, so it
-// stages the next tile's input features into the A buffer and the MMA warp
-// starts that tile's first layer while the output dot product is finished.
+// Pipeline.  Each tile in flight has its own accumulator (2 x 256 of the 512
+// TMEM columns) and its own activation buffer.  The MMA warp and the
+// epilogue warps walk the same sequence of (tile, layer) jobs: tile a layer
+// l, tile b layer l, tile a layer l + 1, ..., so the epilogue drains one
+// tile's accumulator while the tensor core computes the other tile's layer.
+// Hidden weights stream through a ring of four 16 KB K-slices in the order
+// the MMAs use them (every hidden layer's eight slices, once per tile), each
+// slice refilled as soon as the MMAs reading it finish; W0 [256 x 48] stays
+// resident.  While a tile's last layer is drained, the next tile's input
+// rows are copied into the tile's buffer with cp.async (BF16 rows straight
+// into place; FP32 rows into its upper half, rounded to BF16 after the
+// drain), so no separate conversion pass reads the features.
 //
 // Arithmetic.  Rounding points are those of the tiled GEMM path: BF16
 // inputs, weights and activations, FP32 accumulation, FP32 bias and GELU.
@@ -26,8 +29,7 @@
 // activation), evaluated on pairs of activations with the packed FP32x2
 // instructions (fma/mul/add.rn.f32x2: two IEEE operations per
 // instruction); TMEM loads are double-buffered; biases and output weights
-// are staged in shared memory.  The K-slices of a layer accumulate in the
-// order the epilogue releases them (0, 2, 4, 6, 1, 3, 5, 7).
+// are staged in shared memory.  The K-slices of a layer accumulate in order.
 //
 // Operands use the canonical K-major layout without swizzling: 8-row x
 // 16-byte core matrices stored contiguously (128 B), core matrices adjacent
@@ -49,17 +51,21 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int TM = 128;       // rows per CTA (MMA M)
+constexpr int TM = 128;       // rows per tile (MMA M)
 constexpr int WIDTH = 256;    // hidden width (MMA N)
 constexpr int IN = 48;        // input features
 constexpr int DEPTH = 4;      // hidden layers
 constexpr int KC = 32;        // K per streamed weight slice
 constexpr int NCH = WIDTH / KC;  // slices per hidden layer
-constexpr int NSTEP = 2;         // epilogue steps per layer (32 columns per warp each)
+constexpr int NSLOT = 4;         // weight slices resident at a time
+constexpr int INFLIGHT = 2;      // tiles in flight, each with its own accumulator and buffer
 constexpr int EWARPS = 16;       // epilogue warps: 4 TMEM lane quadrants x 4 column quarters
 constexpr int ETHREADS = EWARPS * 32;
-constexpr int THREADS = ETHREADS + 32;  // + the MMA warp
+constexpr int MMA_WARP = EWARPS, LOAD_WARP = EWARPS + 1;
+constexpr int THREADS = (EWARPS + 2) * 32;
+constexpr int QCOLS = WIDTH / 4;  // columns per epilogue warp
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // give up on a pipeline wait after 1 s
+constexpr uint32_t kSuspendNs = 20000;  // a waiting thread sleeps until the phase completes, at most this long
 constexpr uint32_t kChunk = 16384;  // bytes per bulk copy
 
 // bytes of a [rows x K] BF16 operand
@@ -83,18 +89,23 @@ constexpr uint32_t kPackBytes = operand_bytes(WIDTH, IN) + 3u * operand_bytes(WI
 constexpr uint32_t kSliceBytes = operand_bytes(WIDTH, KC);
 
 // shared memory plan (bytes)
-constexpr uint32_t SM_A = 0;                                     // activations [128 x 256]
-constexpr uint32_t SM_W = SM_A + operand_bytes(TM, WIDTH);        // hidden weights, 8 slices
-constexpr uint32_t SM_W0 = SM_W + operand_bytes(WIDTH, WIDTH);    // W0 [256 x 48]
-constexpr uint32_t SM_PART = SM_W0 + operand_bytes(WIDTH, IN);    // 3 x 128 partial dot products
-constexpr uint32_t SM_BAR = SM_PART + 3 * TM * 4;
-// mbarriers: W0 copy, slice copies [8], a step's slices free [2 of 8 used],
-// activation steps [2], accumulator ready, drain, next input staged
-constexpr int NBAR = 1 + 2 * NCH + NSTEP + 3;
-constexpr uint32_t SM_TMEM = SM_BAR + NBAR * 8;                   // TMEM base from tcgen05.alloc
+constexpr uint32_t SM_A = 0;                                            // activations [128 x 256] per tile in flight
+constexpr uint32_t kABytes = operand_bytes(TM, WIDTH);
+constexpr uint32_t kXf32Off = 32768;  // FP32 input rows [128 x 48] staged here inside a tile's buffer
+constexpr uint32_t SM_W0 = SM_A + INFLIGHT * kABytes;                   // W0 [256 x 48]
+constexpr uint32_t SM_W = SM_W0 + operand_bytes(WIDTH, IN);             // weight slice ring
+constexpr uint32_t SM_PART = SM_W + NSLOT * kSliceBytes;                // per tile in flight: 4 x 128 partial dots
+constexpr uint32_t SM_BAR = SM_PART + INFLIGHT * 4 * TM * 4;
+// mbarriers: W0 copy, slot full [4], slot free [4], accumulator ready [2],
+// activations (or next input) written [2], drain
+constexpr int NBAR = 1 + 2 * NSLOT + 2 * INFLIGHT + 1;
+constexpr uint32_t SM_TMEM = SM_BAR + NBAR * 8;                         // TMEM base from tcgen05.alloc
 constexpr uint32_t SM_TOTAL = SM_TMEM + 16;
 static_assert(SM_TOTAL + (DEPTH + 1) * WIDTH * 4 + 64 <= 227 * 1024, "shared memory plan exceeds 227 KB");
 static_assert(operand_bytes(WIDTH, IN) % 16 == 0 && kSliceBytes % 16 == 0, "bulk copies move whole 16-byte units");
+static_assert(INFLIGHT * WIDTH <= 512, "one 256-column accumulator per tile in flight");
+static_assert(operand_bytes(TM, IN) <= kXf32Off && kXf32Off + TM * IN * 4 <= kABytes,
+              "FP32 input rows fit above the BF16 input inside a tile's buffer");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -136,9 +147,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
   for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(phase)
+        : "r"(bar), "r"(phase), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
     const uint64_t t = global_ns();
@@ -160,21 +171,23 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const uint8_t* src, uint
   }
 }
 
-// mbar_wait that also gives up as soon as *fail is set by another thread
-__device__ __forceinline__ bool mbar_wait_or(uint32_t bar, uint32_t phase, volatile int* fail) {
+// mbar_wait that also gives up as soon as *fail is set by another thread,
+// or after limit_ns
+__device__ __forceinline__ bool mbar_wait_or(uint32_t bar, uint32_t phase, volatile int* fail,
+                                             uint64_t limit_ns = kWaitLimitNs) {
   uint64_t t0 = 0;
   for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(bar), "r"(phase)
+        : "r"(bar), "r"(phase), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
     if (*fail) return false;
     const uint64_t t = global_ns();
     if (t0 == 0) t0 = t;
-    else if (t - t0 > kWaitLimitNs) return false;
+    else if (t - t0 > limit_ns) return false;
   }
 }
 
@@ -297,268 +310,323 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
+// Input rows of a tile: unit i (0 .. 767) is the 16-byte piece (row i % 128,
+// features 8 (i / 128) ..) of the BF16 operand in its canonical K = 48 layout.
+constexpr int kUnits = TM * (IN / 8);
+constexpr int kUnitsPerThread = (kUnits + ETHREADS - 1) / ETHREADS;
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+
+// start copying tile t's input rows into a tile buffer (rows past M read as
+// zero): BF16 rows straight into the operand layout, FP32 rows (xf) raw
+// into the buffer's upper half
+__device__ __forceinline__ void input_copy(uint32_t buf, const MlpTcArgs& a, int t, int tid) {
+#pragma unroll
+  for (int u = 0; u < kUnitsPerThread; ++u) {
+    const int i = tid + u * ETHREADS;
+    if (i >= kUnits) break;
+    const int r = i % TM, kb = i / TM, m = t * TM + r;
+    const bool in = m < a.M;
+    const size_t e = (size_t)(in ? m : 0) * IN + (size_t)kb * 8;
+    if (a.xf) {
+      const uint32_t d = buf + kXf32Off + (uint32_t)(r * IN + kb * 8) * 4u;
+      cp_async16(d, a.xf + e, in ? 16u : 0u);
+      cp_async16(d + 16u, a.xf + e + 4, in ? 16u : 0u);
+    } else {
+      cp_async16(buf + canon_off(r, kb * 8, IN), static_cast<const bf16*>(a.x) + e, in ? 16u : 0u);
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// ask L2 for tile t's input rows (they are contiguous: 128 rows of 48 values),
+// one 128-byte line per thread, so that the later input_copy finds them there
+__device__ __forceinline__ void input_prefetch(const MlpTcArgs& a, int t, int tid) {
+  const size_t row0 = (size_t)t * TM, rows = (size_t)min(TM, a.M - t * TM);
+  const char* base = a.xf ? reinterpret_cast<const char*>(a.xf + row0 * IN)
+                          : reinterpret_cast<const char*>(static_cast<const bf16*>(a.x) + row0 * IN);
+  const size_t bytes = rows * IN * (a.xf ? 4 : 2);
+  if ((size_t)tid * 128 < bytes) asm volatile("prefetch.global.L2 [%0];" ::"l"(base + (size_t)tid * 128));
+}
+
+// once this thread's input_copy has landed (cp.async.wait_all): its FP32
+// pieces are rounded to BF16 into the operand layout (the same units the
+// same thread copied, so no other thread's copies are read)
+__device__ __forceinline__ void input_finish(uint8_t* buf, const MlpTcArgs& a, int tid) {
+  if (!a.xf) return;
+#pragma unroll
+  for (int u = 0; u < kUnitsPerThread; ++u) {
+    const int i = tid + u * ETHREADS;
+    if (i >= kUnits) break;
+    const int r = i % TM, kb = i / TM;
+    const float4* f = reinterpret_cast<const float4*>(buf + kXf32Off + (uint32_t)(r * IN + kb * 8) * 4u);
+    const float4 lo = f[0], hi = f[1];
+    *reinterpret_cast<uint4*>(buf + canon_off(r, kb * 8, IN)) =
+        make_uint4(pack_bf16x2(lo.x, lo.y), pack_bf16x2(lo.z, lo.w), pack_bf16x2(hi.x, hi.y), pack_bf16x2(hi.z, hi.w));
+  }
+}
+
+// the score of row r of tile t from the four column quarters' partial dots (pb[q * 128 + r])
+__device__ __forceinline__ void write_score(const MlpTcArgs& a, const float* pb, int t, int r) {
+  const int m = t * TM + r;
+  if (m < a.M) a.y[m] = a.norm[0] + a.norm[1] * (((pb[r] + pb[TM + r]) + (pb[2 * TM + r] + pb[3 * TM + r])) + a.b_out[0]);
+}
+
 __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcArgs a) {
   extern __shared__ __align__(1024) uint8_t sm[];
   __shared__ volatile int s_fail;
   __shared__ __align__(16) float sbias[DEPTH * WIDTH];
   __shared__ __align__(16) float swout[WIDTH];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t sA = smem_u32(sm + SM_A), sW = smem_u32(sm + SM_W), sW0 = smem_u32(sm + SM_W0);
-  const uint32_t wbar0 = smem_u32(sm + SM_BAR);
-  const uint32_t wbar = wbar0 + 8, wfree = wbar + 8 * NCH, abar = wfree + 8 * NCH;
-  const uint32_t bar_mma = abar + 8 * NSTEP, bar_drain = bar_mma + 8, xbar = bar_drain + 8;
+  const uint32_t sW0 = smem_u32(sm + SM_W0), sW = smem_u32(sm + SM_W);
+  const uint32_t w0bar = smem_u32(sm + SM_BAR);
+  const uint32_t fullb = w0bar + 8, freeb = fullb + 8 * NSLOT, accb = freeb + 8 * NSLOT, actb = accb + 8 * INFLIGHT;
+  const uint32_t drainb = actb + 8 * INFLIGHT;
   const int ntiles = (a.M + TM - 1) / TM;
+  // this CTA's tiles: k = 0 .. n - 1 is tile blockIdx.x + k gridDim.x, held in buffer k % INFLIGHT
+  const int n = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   float* part = reinterpret_cast<float*>(sm + SM_PART);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + SM_TMEM);
   const uint8_t* wpack = static_cast<const uint8_t*>(a.wpack);
-  const bf16* x = static_cast<const bf16*>(a.x);
   const bf16* w_out = static_cast<const bf16*>(a.w_out);
 
   if (tid == 0) {
     s_fail = 0;
-    mbar_init(wbar0, 1);
-    for (int j = 0; j < NCH; ++j) {
-      mbar_init(wbar + 8 * j, 1);
-      mbar_init(wfree + 8 * j, 1);
+    mbar_init(w0bar, 1);
+    for (int j = 0; j < NSLOT; ++j) {
+      mbar_init(fullb + 8 * j, 1);
+      mbar_init(freeb + 8 * j, 1);
     }
-    for (int c = 0; c < NSTEP; ++c) mbar_init(abar + 8 * c, EWARPS);
-    mbar_init(bar_mma, 1);
-    mbar_init(bar_drain, 1);
-    mbar_init(xbar, EWARPS);
+    for (int b = 0; b < INFLIGHT; ++b) {
+      mbar_init(accb + 8 * b, 1);
+      mbar_init(actb + 8 * b, EWARPS);
+    }
+    mbar_init(drainb, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
-  if (warp == 0) {  // two 256-column FP32 accumulators, used by alternate layers
+  if (warp == 0) {  // one 256-column FP32 accumulator per tile in flight
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(2 * WIDTH));
+                 "r"(INFLIGHT * WIDTH));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-#pragma unroll
-  for (int l = 0; l < DEPTH; ++l)
-    for (int i = tid; i < WIDTH; i += THREADS) sbias[l * WIDTH + i] = a.bias[l][i];
-  for (int i = tid; i < WIDTH; i += THREADS) swout[i] = 0.5f * __bfloat162float(w_out[i]);  // see gelu2
-  for (int i = tid; i < TM * (IN / 8); i += THREADS) {
-    const int r = i % TM, kb = i / TM;  // consecutive threads: consecutive rows, conflict-free stores
-    const int m = (int)blockIdx.x * TM + r;
-    uint4 q = make_uint4(0u, 0u, 0u, 0u);
-    if (m < a.M) q = *reinterpret_cast<const uint4*>(x + (size_t)m * IN + kb * 8);
-    *reinterpret_cast<uint4*>(sm + SM_A + canon_off(r, kb * 8, IN)) = q;
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == EWARPS) {
-    // ---- MMA warp: one lane issues the weight copies and the MMAs ----
+  if (warp == LOAD_WARP) {
+    // ---- weight stream: one lane copies W0, then every hidden layer's slices in MMA order ----
+    if (lane == 0) {
+      int fail = 0;
+      bool w0_pending = false;
+      uint32_t issued = 0;  // slices copied so far; slice i goes to slot i % NSLOT
+      // (the failure-detection test leaves W0's barrier without its arrival)
+      if (!a.expire_test) {
+        bulk_load(sW0, wpack + w_offset(0), operand_bytes(WIDTH, IN), w0bar);
+        w0_pending = true;
+      }
+      for (int p = 0; INFLIGHT * p < n && !fail; ++p)
+        for (int l = 1; l < DEPTH && !fail; ++l)
+          for (int b = 0; b < INFLIGHT && !fail; ++b) {
+            if (INFLIGHT * p + b >= n) continue;
+            for (int j = 0; j < NCH; ++j) {
+              const uint32_t slot = issued % NSLOT, round = issued / NSLOT;
+              // the MMA warp's waits are the ones that report (this one only ends the stream)
+              if (!mbar_wait_or(freeb + 8 * slot, (round & 1u) ^ 1u, &s_fail, 2 * kWaitLimitNs)) {
+                fail = 6;
+                break;
+              }
+              copy_async(sW + slot * kSliceBytes, wpack + w_offset(l) + (uint32_t)j * kSliceBytes, kSliceBytes,
+                         fullb + 8 * slot);
+              ++issued;
+            }
+          }
+      if (fail && !s_fail) s_fail = fail;
+      if (s_fail) {  // every copy this lane issued lands before the CTA lets go of its shared memory (bounded)
+        if (w0_pending) mbar_wait(w0bar, 0);
+        for (uint32_t i = issued > (uint32_t)NSLOT ? issued - NSLOT : 0u; i < issued; ++i)
+          mbar_wait(fullb + 8 * (i % NSLOT), (i / NSLOT) & 1u);
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ---- MMA issue: one lane, the two tiles in flight alternating layer by layer ----
     if (lane == 0) {
       const uint32_t idesc = make_idesc(TM, WIDTH);
       int fail = 0;
-      uint32_t pend_w = 0;  // bit j < NCH: slice j copy not yet waited for; bit NCH: W0
-      uint32_t pph = 0;     // bit j: the parity that copy completes
-      bool pend_mma = false;
-      // (the failure-detection test leaves W0's barrier without its arrival)
-      if (!a.expire_test) {
-        bulk_load(sW0, wpack + w_offset(0), operand_bytes(WIDTH, IN), wbar0);
-        pend_w |= 1u << NCH;
-      }
-      for (int j = 0; j < NCH; ++j)
-        copy_async(sW + j * kSliceBytes, wpack + w_offset(1) + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
-      pend_w |= (1u << NCH) - 1u;
-      if (!mbar_wait_or(wbar0, 0, &s_fail)) fail = 1;
-      else pend_w &= ~(1u << NCH);
-      const uint32_t sbo0 = (uint32_t)(IN >> 3) * 128u;
-      for (int t = blockIdx.x, it = 0; t < ntiles && !fail; t += gridDim.x, ++it) {
-        const bool has_next = t + (int)gridDim.x < ntiles;
-        // layer 0: K = 48 from this tile's input (written by the epilogue warps after the first tile)
-        if (it > 0 && !mbar_wait_or(xbar, (uint32_t)(it - 1) & 1u, &s_fail)) {
-          fail = 5;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int k0 = 0; k0 < IN; k0 += 16)
-          mma_bf16(tmem, make_desc(sA + (uint32_t)(k0 >> 3) * 128u, 128u, sbo0),
-                   make_desc(sW0 + (uint32_t)(k0 >> 3) * 128u, 128u, sbo0), idesc, k0 > 0 ? 1u : 0u);
-        mma_commit(bar_mma);
-        pend_mma = true;
-        for (int l = 1; l < DEPTH && !fail; ++l) {
-          const uint32_t ph = (uint32_t)(it + l - 1) & 1u;  // this layer's slices and activations
-          const uint32_t nph = (uint32_t)(it + l) & 1u;     // the refill's completion
-          const uint32_t dcol = (uint32_t)(l & 1) * WIDTH;
-          const bool refill = l + 1 < DEPTH || has_next;
-          const uint8_t* nsrc = wpack + w_offset(l + 1 < DEPTH ? l + 1 : 1);
-          for (int cc = 0; cc < NSTEP && !fail; ++cc) {
-            // this step's slices first (their copies finished long before), then the activations
-            for (int h = 0; h < 4 && !fail; ++h) {
-              const int j = NSTEP * h + cc;
-              if (!mbar_wait_or(wbar + 8 * j, ph, &s_fail)) fail = 3;
-              else pend_w &= ~(1u << j);
-            }
-            if (fail || !mbar_wait_or(abar + 8 * cc, ph, &s_fail)) {
+      bool pend = false;
+      uint32_t used = 0;                      // slices consumed, in the stream's order (a multiple of NCH)
+      uint32_t jobs[INFLIGHT] = {0u, 0u};     // layers issued per buffer: the phase of its barriers
+      // descriptors: a step of 8 K-elements (one core matrix, 128 B) adds 8 to the start-address field
+      const uint64_t w0d = make_desc(sW0, 128u, (uint32_t)(IN >> 3) * 128u);
+      const uint64_t wsd = make_desc(sW, 128u, (uint32_t)(KC >> 3) * 128u);
+      static_assert(NCH % NSLOT == 0, "every hidden layer starts at slot 0");
+      if (!mbar_wait_or(w0bar, 0, &s_fail)) fail = 1;
+      for (int p = 0; INFLIGHT * p < n && !fail; ++p)
+        for (int l = 0; l < DEPTH && !fail; ++l)
+          for (int b = 0; b < INFLIGHT && !fail; ++b) {
+            if (INFLIGHT * p + b >= n) continue;
+            // this tile's input (l = 0) or previous layer's activations are written, its accumulator drained
+            if (!mbar_wait_or(actb + 8 * b, jobs[b] & 1u, &s_fail)) {
               fail = 3;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sA = smem_u32(sm + SM_A + (uint32_t)b * kABytes);
+            const uint32_t d = tmem + (uint32_t)(b * WIDTH);
+            if (l == 0) {
+              const uint64_t a0 = make_desc(sA, 128u, (uint32_t)(IN >> 3) * 128u);
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-              const int j = NSTEP * h + cc;  // the slice step cc of column quarter h wrote
-#pragma unroll
-              for (int kk = 0; kk < KC; kk += 16) {
-                const uint64_t ad =
-                    make_desc(sA + (uint32_t)((j * KC + kk) >> 3) * 128u, 128u, (uint32_t)(WIDTH >> 3) * 128u);
-                const uint64_t bd =
-                    make_desc(sW + j * kSliceBytes + (uint32_t)(kk >> 3) * 128u, 128u, (uint32_t)(KC >> 3) * 128u);
-                mma_bf16(tmem + dcol, ad, bd, idesc, (cc | h | kk) ? 1u : 0u);
-              }
-            }
-            if (refill) mma_commit(wfree + 8 * cc);
-            if (cc == NSTEP - 1) mma_commit(bar_mma);
-            // the previous step's slices are free: refill them with the next layer's
-            if (refill && cc >= 1) {
-              if (!mbar_wait_or(wfree + 8 * (cc - 1), ph, &s_fail)) {
-                fail = 4;
-              } else {
-                for (int h = 0; h < 4; ++h) {
-                  const int j = NSTEP * h + cc - 1;
-                  copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
-                  pend_w |= 1u << j;
-                  pph = (pph & ~(1u << j)) | (nph << j);
-                }
-              }
-            }
-          }
-          if (refill && !fail) {
-            if (!mbar_wait_or(wfree + 8 * (NSTEP - 1), ph, &s_fail)) {
-              fail = 4;
+              for (int k0 = 0; k0 < IN; k0 += 16)
+                mma_bf16(d, a0 + (uint64_t)(k0 >> 3) * 8u, w0d + (uint64_t)(k0 >> 3) * 8u, idesc, k0 > 0 ? 1u : 0u);
             } else {
-              for (int h = 0; h < 4; ++h) {
-                const int j = NSTEP * h + NSTEP - 1;
-                copy_async(sW + j * kSliceBytes, nsrc + j * kSliceBytes, kSliceBytes, wbar + 8 * j);
-                pend_w |= 1u << j;
-                pph = (pph & ~(1u << j)) | (nph << j);
+              const uint64_t a0 = make_desc(sA, 128u, (uint32_t)(WIDTH >> 3) * 128u);
+              const uint32_t ph = (used / NSLOT) & 1u;  // the parity of slots 0..3 for slices 0..3
+#pragma unroll
+              for (int j = 0; j < NCH; ++j) {
+                const uint32_t slot = (uint32_t)(j % NSLOT);
+                if (!mbar_wait_or(fullb + 8 * slot, ph ^ (uint32_t)((j / NSLOT) & 1), &s_fail)) {
+                  fail = 4;
+                  break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+                for (int kk = 0; kk < KC; kk += 16)
+                  mma_bf16(d, a0 + (uint64_t)((j * KC + kk) >> 3) * 8u,
+                           wsd + (uint64_t)(slot * (kSliceBytes >> 4)) + (uint64_t)(kk >> 3) * 8u, idesc,
+                           (j | kk) ? 1u : 0u);
+                mma_commit(freeb + 8 * slot);  // the slot refills once these MMAs are done
               }
+              used += NCH;
             }
+            pend = true;
+            if (fail) break;
+            mma_commit(accb + 8 * b);
+            ++jobs[b];
           }
-        }
-      }
-      if (fail) {
-        s_fail = fail;
-        // drain (bounded): every MMA issued and every copy not yet waited for
-        if (pend_mma) {
-          mma_commit(bar_drain);
-          mbar_wait(bar_drain, 0);
-        }
-        for (int j = 0; j <= NCH; ++j)
-          if (pend_w & (1u << j)) mbar_wait(j == NCH ? wbar0 : wbar + 8 * j, (pph >> j) & 1u);
+      if (fail && !s_fail) s_fail = fail;
+      if (s_fail && pend) {  // drain (bounded): every MMA issued
+        mma_commit(drainb);
+        mbar_wait(drainb, 0);
       }
     }
   } else {
-    // ---- epilogue warps: TMEM -> bias + GELU -> BF16 activations, step by step ----
-    const int quad = warp & 3, qtr = warp >> 2;  // TMEM lane quadrant, column quarter
+    // ---- epilogue: TMEM -> bias + GELU -> BF16 activations, job by job ----
+    const int quad = warp & 3, qtr = warp >> 2;  // TMEM lane quadrant (= warp % 4), column quarter
     const int r_local = quad * 32 + lane;
-    const int tid_e = tid;  // 0 .. ETHREADS - 1
-    bool stop = false;  // the same value in every epilogue thread (barrier reduction)
-    for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-      const bool has_next = t + (int)gridDim.x < ntiles;
-      float dq[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      int l = 0;
-      for (; l < DEPTH; ++l) {
-        if (!mbar_wait_or(bar_mma, (uint32_t)l & 1u, &s_fail)) {
-          if (!s_fail) s_fail = 2;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // the last layer leaves A free: fetch the next tile's input now, store it after the first step
-        uint4 xin[2];
-        const bool fetch = l + 1 == DEPTH && has_next;
-        if (fetch) {
-          const int tn = t + (int)gridDim.x;
+    // the first tiles' inputs start to arrive while the biases are staged
+    for (int b = 0; b < INFLIGHT && b < n; ++b)
+      input_copy(smem_u32(sm + SM_A + (uint32_t)b * kABytes), a, (int)blockIdx.x + b * (int)gridDim.x, tid);
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int i = tid_e + u * ETHREADS;
-            const int m = tn * TM + i % TM;
-            xin[u] = m < a.M && i < TM * (IN / 8) ? *reinterpret_cast<const uint4*>(x + (size_t)m * IN + (i / TM) * 8)
-                             : make_uint4(0u, 0u, 0u, 0u);
-          }
-        }
-        const float* bl = sbias + l * WIDTH;
-        const uint32_t tbase =
-            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(l & 1) * WIDTH + (uint32_t)(qtr * 64);
-        uint32_t ra[32], rb[32];
-        tmem_issue32(tbase, ra);
-        tmem_wait32(ra);
-#pragma unroll
-        for (int cc = 0; cc < NSTEP; ++cc) {
-          uint32_t* cur = (cc & 1) ? rb : ra;
-          uint32_t* nxt = (cc & 1) ? ra : rb;
-          if (cc + 1 < NSTEP) tmem_issue32(tbase + 32u * (uint32_t)(cc + 1), nxt);
-          const int c0 = qtr * 64 + 32 * cc;
-          float v[32];
-#pragma unroll
-          for (int j = 0; j < 32; j += 2) {
-            const float2 b2 = *reinterpret_cast<const float2*>(bl + c0 + j);
-            const f32x2 g =
-                gelu2(fadd2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])), pk2(b2.x, b2.y)));
-            upk2(g, v[j], v[j + 1]);
-          }
-          if (l + 1 < DEPTH) {
-#pragma unroll
-            for (int kb = 0; kb < 4; ++kb) {
-              const uint4 q =
-                  make_uint4(pack_bf16x2(v[8 * kb], v[8 * kb + 1]), pack_bf16x2(v[8 * kb + 2], v[8 * kb + 3]),
-                             pack_bf16x2(v[8 * kb + 4], v[8 * kb + 5]), pack_bf16x2(v[8 * kb + 6], v[8 * kb + 7]));
-              *reinterpret_cast<uint4*>(sm + SM_A + canon_off(r_local, c0 + 8 * kb, WIDTH)) = q;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) bar_arrive(abar + 8 * cc);
-            __syncwarp();
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-              dq[0] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j])), swout[c0 + j], dq[0]);
-              dq[1] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j + 1])), swout[c0 + j + 1], dq[1]);
-              dq[2] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j + 2])), swout[c0 + j + 2], dq[2]);
-              dq[3] = fmaf(__bfloat162float(__float2bfloat16_rn(v[j + 3])), swout[c0 + j + 3], dq[3]);
-            }
-            if (cc == 0 && fetch) {
-#pragma unroll
-              for (int u = 0; u < 2; ++u) {
-                const int i = tid_e + u * ETHREADS;
-                if (i < TM * (IN / 8))
-                  *reinterpret_cast<uint4*>(sm + SM_A + canon_off(i % TM, (i / TM) * 8, IN)) = xin[u];
-              }
-              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-              asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-              __syncwarp();
-              if (lane == 0) bar_arrive(xbar);
-              __syncwarp();
-            }
-          }
-          if (cc + 1 < NSTEP) tmem_wait32(nxt);
-        }
-        // this layer's TMEM reads precede the arrivals that let a later layer overwrite them
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      }
-      const float dot = (dq[0] + dq[1]) + (dq[2] + dq[3]);
-      if (qtr > 0) part[(qtr - 1) * TM + r_local] = dot;
-      asm volatile("bar.sync 1, %0;" ::"n"(ETHREADS));
-      if (qtr == 0 && l == DEPTH) {
-        const int m = t * TM + r_local;
-        const float sum = (dot + part[r_local]) + (part[TM + r_local] + part[2 * TM + r_local]);
-        if (m < a.M) a.y[m] = a.norm[0] + a.norm[1] * (sum + a.b_out[0]);
-      }
-      // part is rewritten by the next tile; all epilogue threads leave together
-      int anyfail;
-      asm volatile(
-          "{\n .reg .pred q, p;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.s32 %0, 1, 0, p;\n}\n"
-          : "=r"(anyfail)
-          : "r"((int)s_fail), "n"(ETHREADS)
-          : "memory");
-      stop = anyfail != 0;
+    for (int l = 0; l < DEPTH; ++l)
+      for (int i = tid; i < WIDTH; i += ETHREADS) sbias[l * WIDTH + i] = a.bias[l][i];
+    for (int i = tid; i < WIDTH; i += ETHREADS) swout[i] = 0.5f * __bfloat162float(w_out[i]);  // see gelu2
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    for (int b = 0; b < INFLIGHT && b < n; ++b) {
+      input_finish(sm + SM_A + (uint32_t)b * kABytes, a, tid);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(actb + 8 * b);
+      __syncwarp();
     }
+    asm volatile("bar.sync 1, %0;" ::"n"(ETHREADS));  // biases and output weights staged
+    uint32_t jobs[INFLIGHT] = {0u, 0u};
+    bool ok = true;  // this thread's waits all succeeded
+    for (int p = 0; INFLIGHT * p < n; ++p)
+      for (int l = 0; l < DEPTH; ++l)
+        for (int b = 0; b < INFLIGHT; ++b) {
+          const int k = INFLIGHT * p + b;
+          if (k >= n) continue;
+          const uint32_t A = SM_A + (uint32_t)b * kABytes;
+          float* pb = part + b * 4 * TM;
+          const bool last = l + 1 == DEPTH, next = last && k + INFLIGHT < n;
+          // (a thread that saw a failure runs through the remaining jobs without waiting or working,
+          // but still takes part in every quadrant barrier)
+          bool work = ok && !s_fail;
+          if (work && !mbar_wait_or(accb + 8 * b, jobs[b] & 1u, &s_fail, 2 * kWaitLimitNs)) {
+            if (!s_fail) s_fail = 2;  // the MMA warp's waits are the ones that report a stalled pipeline first
+            ok = work = false;
+          }
+          ++jobs[b];
+          if (work) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (l == 1 && k + INFLIGHT < n) input_prefetch(a, (int)blockIdx.x + (k + INFLIGHT) * (int)gridDim.x, tid);
+            // the last layer's MMAs no longer read the buffer: the next tile's input starts to arrive
+            if (next) input_copy(smem_u32(sm + A), a, (int)blockIdx.x + (k + INFLIGHT) * (int)gridDim.x, tid);
+            const float* bl = sbias + l * WIDTH;
+            const uint32_t tbase =
+                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * WIDTH) + (uint32_t)(qtr * QCOLS);
+            f32x2 dq01 = pk2(0.0f, 0.0f), dq23 = pk2(0.0f, 0.0f);
+            uint32_t ra[32], rb[32];
+            tmem_issue32(tbase, ra);
+            tmem_wait32(ra);
+#pragma unroll
+            for (int cc = 0; cc < QCOLS / 32; ++cc) {
+              uint32_t* cur = (cc & 1) ? rb : ra;
+              uint32_t* nxt = (cc & 1) ? ra : rb;
+              if (cc + 1 < QCOLS / 32) tmem_issue32(tbase + 32u * (uint32_t)(cc + 1), nxt);
+              const int c0 = qtr * QCOLS + 32 * cc;
+              float v[32];
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                const float4 b4 = *reinterpret_cast<const float4*>(bl + c0 + j);
+                const f32x2 g0 =
+                    gelu2(fadd2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])), pk2(b4.x, b4.y)));
+                const f32x2 g1 =
+                    gelu2(fadd2(pk2(__uint_as_float(cur[j + 2]), __uint_as_float(cur[j + 3])), pk2(b4.z, b4.w)));
+                upk2(g0, v[j], v[j + 1]);
+                upk2(g1, v[j + 2], v[j + 3]);
+              }
+              if (!last) {
+#pragma unroll
+                for (int kb = 0; kb < 4; ++kb) {
+                  const uint4 q = make_uint4(pack_bf16x2(v[8 * kb], v[8 * kb + 1]),
+                                             pack_bf16x2(v[8 * kb + 2], v[8 * kb + 3]),
+                                             pack_bf16x2(v[8 * kb + 4], v[8 * kb + 5]),
+                                             pack_bf16x2(v[8 * kb + 6], v[8 * kb + 7]));
+                  *reinterpret_cast<uint4*>(sm + A + canon_off(r_local, c0 + 8 * kb, WIDTH)) = q;
+                }
+              } else {
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                  // the BF16 activation (as the next layer would see it) times the output weight
+                  const float4 w4 = *reinterpret_cast<const float4*>(swout + c0 + j);
+                  const uint32_t h01 = pack_bf16x2(v[j], v[j + 1]), h23 = pack_bf16x2(v[j + 2], v[j + 3]);
+                  dq01 = ffma2(pk2(__uint_as_float(h01 << 16), __uint_as_float(h01 & 0xffff0000u)), pk2(w4.x, w4.y), dq01);
+                  dq23 = ffma2(pk2(__uint_as_float(h23 << 16), __uint_as_float(h23 & 0xffff0000u)), pk2(w4.z, w4.w), dq23);
+                }
+              }
+              if (cc + 1 < QCOLS / 32) tmem_wait32(nxt);
+            }
+            // this layer's TMEM reads precede the arrival that lets the next MMAs overwrite the accumulator
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            if (last) {
+              float d0, d1, d2, d3;
+              upk2(dq01, d0, d1);
+              upk2(dq23, d2, d3);
+              pb[qtr * TM + r_local] = (d0 + d1) + (d2 + d3);
+              if (next) {  // this thread's pieces of the next input, rounded in place
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                input_finish(sm + A, a, tid);
+              }
+            }
+            if (!last || next) {
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              __syncwarp();
+              if (lane == 0) bar_arrive(actb + 8 * b);
+              __syncwarp();
+            }
+          }
+          if (last) {
+            // the four column quarters of this lane quadrant (warps quad, quad + 4, ...) meet: the score
+            asm volatile("bar.sync %0, %1;" ::"r"(2 + quad), "n"(4 * 32) : "memory");
+            if (work && qtr == 0 && !s_fail) write_score(a, pb, (int)blockIdx.x + k * (int)gridDim.x, r_local);
+          }
+        }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -567,7 +635,8 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
       if (tid < TM && t * TM + tid < a.M) a.y[t * TM + tid] = __int_as_float(0x7fc00000);
   }
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * WIDTH));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(INFLIGHT * WIDTH));
 }
 
 // W0..W3 (BF16, out x in row-major, at element offsets off.w[l] of the flat

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -799,9 +800,10 @@ bool use_tc(const cem_surrogate_ctx* s) {
   return s->fwd_path != 1 && mlp_tc_supported(s->in_dim, s->width, s->depth);
 }
 
-// scores of M rows already in s->xin, no activations kept: the fused tcgen05
-// kernel where the shape allows, else the tiled GEMM forward
-cudaError_t infer_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st) {
+// scores of M rows, no activations kept: the fused tcgen05 kernel where the
+// shape allows, else the tiled GEMM forward.  The rows are BF16 in s->xin,
+// or (tcgen05 kernel only) FP32 in xf, which the kernel rounds as it loads.
+cudaError_t infer_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st, const float* xf = nullptr) {
   if (!use_tc(s)) return forward_rows(s, M, y, s->fwd_path != 1 && use_tc_gemm(s), st);
   if (!s->tc_pack_valid) {
     MlpTcOffsets off;
@@ -812,6 +814,7 @@ cudaError_t infer_rows(cem_surrogate_ctx* s, int M, float* y, cudaStream_t st) {
   }
   MlpTcArgs a;
   a.x = s->xin;
+  a.xf = xf;
   a.M = M;
   a.wpack = s->tc_pack;
   for (int l = 0; l < 4; ++l) a.bias[l] = s->p + s->b_off[l];
@@ -1157,6 +1160,10 @@ int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float
   if (M == 0) return CEM_OK;
   if (!is_dev(x_d) || !is_dev(y_d)) return fail(CEM_ERR_INVALID_ARG, "x and y must be device pointers");
   cudaStream_t st = (cudaStream_t)stream;
+  if (use_tc(s) && ((uintptr_t)x_d & 15u) == 0) {  // the fused kernel reads the FP32 rows itself
+    SUR_CUDA(infer_rows(s, M, y_d, st, x_d));
+    return CEM_OK;
+  }
   int rc = load_features(s, x_d, M, st);
   if (rc != CEM_OK) return rc;
   SUR_CUDA(infer_rows(s, M, y_d, st));

@@ -79,6 +79,26 @@ def test_tc_matches_tiled_gemm(P):
     assert d.max() <= 2e-2 * scale
 
 
+@pytest.mark.parametrize("M", [129, 65536 + 77])
+def test_fp32_rows_read_in_kernel_equal_converted_rows(P, M):
+    """The kernel rounds 16-byte-aligned FP32 feature rows to BF16 as it loads
+    them; rows at an address that is not 16-byte aligned go through the
+    separate BF16 conversion first.  Both round to nearest even, so the
+    scores are bit-identical (ragged last tile included)."""
+    params = mlp.init_params(48, 256, 4, seed=5)
+    X = np.random.default_rng(M + 1).uniform(-2, 2, (M, 48)).astype(np.float32)
+    buf = torch.empty(M * 48 + 1, dtype=torch.float32, device="cuda")
+    shifted = buf[1:].view(M, 48)  # 4 bytes past a 16-byte boundary
+    shifted.copy_(torch.as_tensor(X))
+    assert shifted.data_ptr() % 16 == 4
+    with P.Surrogate(256, 4) as S:
+        S.set_params(mlp.flatten(params), np.array([0.1, 2.0]))
+        y_in_kernel = S.forward(dev(X)).cpu().numpy()
+        y_converted = S.forward(shifted).cpu().numpy()
+        assert S.status() == 0
+    assert np.array_equal(y_in_kernel.view(np.uint32), y_converted.view(np.uint32))
+
+
 def test_tc_follows_parameter_updates(P):
     rng = np.random.default_rng(5)
     X = rng.uniform(-1, 1, (8192, 48)).astype(np.float32)

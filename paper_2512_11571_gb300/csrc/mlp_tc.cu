@@ -243,6 +243,36 @@ __device__ __forceinline__ void tmem_wait32(uint32_t* r) {
       : "memory");
 }
 
+// store 32 consecutive FP32 columns of this thread's TMEM lane (complete
+// after tmem_wait_st)
+__device__ __forceinline__ void tmem_store32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// the bias of layer l for this warp's 32 columns c0 .. c0 + 31 into TMEM at
+// taddr (every lane: the same values), as the start of the next accumulation
+__device__ __forceinline__ void store_bias32(uint32_t taddr, const float* __restrict__ bias_l, int c0) {
+  uint32_t r[32];
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 b4 = *reinterpret_cast<const float4*>(bias_l + c0 + j);
+    r[j] = __float_as_uint(b4.x);
+    r[j + 1] = __float_as_uint(b4.y);
+    r[j + 2] = __float_as_uint(b4.z);
+    r[j + 3] = __float_as_uint(b4.w);
+  }
+  tmem_store32(taddr, r);
+}
+
 // a pair of FP32 values in one 64-bit register (low, high)
 typedef unsigned long long f32x2;
 
@@ -480,7 +510,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
               const uint64_t a0 = make_desc(sA, 128u, (uint32_t)(IN >> 3) * 128u);
 #pragma unroll
               for (int k0 = 0; k0 < IN; k0 += 16)
-                mma_bf16(d, a0 + (uint64_t)(k0 >> 3) * 8u, w0d + (uint64_t)(k0 >> 3) * 8u, idesc, k0 > 0 ? 1u : 0u);
+                mma_bf16(d, a0 + (uint64_t)(k0 >> 3) * 8u, w0d + (uint64_t)(k0 >> 3) * 8u, idesc, 1u);
             } else {
               const uint64_t a0 = make_desc(sA, 128u, (uint32_t)(WIDTH >> 3) * 128u);
               const uint32_t ph = (used / NSLOT) & 1u;  // the parity of slots 0..3 for slices 0..3
@@ -496,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
                 for (int kk = 0; kk < KC; kk += 16)
                   mma_bf16(d, a0 + (uint64_t)((j * KC + kk) >> 3) * 8u,
                            wsd + (uint64_t)(slot * (kSliceBytes >> 4)) + (uint64_t)(kk >> 3) * 8u, idesc,
-                           (j | kk) ? 1u : 0u);
+                           1u);
                 mma_commit(freeb + 8 * slot);  // the slot refills once these MMAs are done
               }
               used += NCH;
@@ -523,6 +553,14 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
     for (int l = 0; l < DEPTH; ++l)
       for (int i = tid; i < WIDTH; i += ETHREADS) sbias[l * WIDTH + i] = a.bias[l][i];
     for (int i = tid; i < WIDTH; i += ETHREADS) swout[i] = 0.5f * __bfloat162float(w_out[i]);  // see gelu2
+    asm volatile("bar.sync 1, %0;" ::"n"(ETHREADS));  // biases and output weights staged
+    for (int b = 0; b < INFLIGHT && b < n; ++b)  // the first accumulations start from layer 0's bias
+#pragma unroll
+      for (int cc = 0; cc < QCOLS / 32; ++cc)
+        store_bias32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * WIDTH) + (uint32_t)(qtr * QCOLS + 32 * cc),
+                     sbias, qtr * QCOLS + 32 * cc);
+    tmem_wait_st();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     asm volatile("cp.async.wait_all;" ::: "memory");
     for (int b = 0; b < INFLIGHT && b < n; ++b) {
       input_finish(sm + SM_A + (uint32_t)b * kABytes, a, tid);
@@ -531,7 +569,6 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
       if (lane == 0) bar_arrive(actb + 8 * b);
       __syncwarp();
     }
-    asm volatile("bar.sync 1, %0;" ::"n"(ETHREADS));  // biases and output weights staged
     uint32_t jobs[INFLIGHT] = {0u, 0u};
     bool ok = true;  // this thread's waits all succeeded
     for (int p = 0; INFLIGHT * p < n; ++p)
@@ -555,7 +592,7 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
             if (l == 1 && k + INFLIGHT < n) input_prefetch(a, (int)blockIdx.x + (k + INFLIGHT) * (int)gridDim.x, tid);
             // the last layer's MMAs no longer read the buffer: the next tile's input starts to arrive
             if (next) input_copy(smem_u32(sm + A), a, (int)blockIdx.x + (k + INFLIGHT) * (int)gridDim.x, tid);
-            const float* bl = sbias + l * WIDTH;
+            const float* bnext = sbias + (last ? 0 : l + 1) * WIDTH;  // layer 0 of the next tile after the last
             const uint32_t tbase =
                 tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * WIDTH) + (uint32_t)(qtr * QCOLS);
             f32x2 dq01 = pk2(0.0f, 0.0f), dq23 = pk2(0.0f, 0.0f);
@@ -570,14 +607,9 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
               const int c0 = qtr * QCOLS + 32 * cc;
               float v[32];
 #pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                const float4 b4 = *reinterpret_cast<const float4*>(bl + c0 + j);
-                const f32x2 g0 =
-                    gelu2(fadd2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])), pk2(b4.x, b4.y)));
-                const f32x2 g1 =
-                    gelu2(fadd2(pk2(__uint_as_float(cur[j + 2]), __uint_as_float(cur[j + 3])), pk2(b4.z, b4.w)));
-                upk2(g0, v[j], v[j + 1]);
-                upk2(g1, v[j + 2], v[j + 3]);
+              for (int j = 0; j < 32; j += 2) {
+                const f32x2 g = gelu2(pk2(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1])));
+                upk2(g, v[j], v[j + 1]);
               }
               if (!last) {
 #pragma unroll
@@ -598,9 +630,13 @@ __global__ void __launch_bounds__(THREADS, 1) mlp_forward_tc_kernel(const MlpTcA
                   dq23 = ffma2(pk2(__uint_as_float(h23 << 16), __uint_as_float(h23 & 0xffff0000u)), pk2(w4.z, w4.w), dq23);
                 }
               }
+              // these columns now start the next accumulation of this buffer: its bias
+              if (!last || next) store_bias32(tbase + 32u * (uint32_t)cc, bnext, c0);
               if (cc + 1 < QCOLS / 32) tmem_wait32(nxt);
             }
-            // this layer's TMEM reads precede the arrival that lets the next MMAs overwrite the accumulator
+            // this layer's TMEM reads and bias stores precede the arrival that lets the next MMAs
+            // accumulate
+            if (!last || next) tmem_wait_st();
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             if (last) {
               float d0, d1, d2, d3;

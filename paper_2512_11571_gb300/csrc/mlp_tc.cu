@@ -331,7 +331,7 @@ __device__ __forceinline__ f32x2 gelu2(f32x2 z) {
   q = fmul2(q, q);
   float q0, q1;
   upk2(q, q0, q1);
-  const f32x2 nr = pk2(-rcp_approx(q0), -rcp_approx(q1));
+  const f32x2 nr = pk2(rcp_approx(-q0), rcp_approx(-q1));  // -1/q: the sign rides on the reciprocal
   return ffma2(a, nr, fadd2(z, a));
 }
 

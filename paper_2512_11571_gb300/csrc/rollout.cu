@@ -1158,21 +1158,22 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
 // Rollout order of a batch (a schedule, not arithmetic): the persistent
 // kernel rolls sample perm[k] out on the lane that takes position k, so
 // samples that will be in the same action at the same time share a warp
-// and its lanes take the same branches.  For a pick-and-place problem of at
-// most kMaxOrdered samples the order is by a cheap forecast from theta: the
-// samples whose grip height lies within the grasp tolerance (they can grasp)
-// first, then by the first moveTo's gain (how soon they arrive), ties by
-// sample index; every other problem keeps the identity.  Each sample's
-// result is the same wherever it runs.  One CTA per problem, a bitonic sort
-// of 64-bit keys (forecast << 32 | index) in shared memory.
-constexpr int kMaxOrdered = 8192;
-constexpr int kOrderThreads = 512;
+// and its lanes take the same branches.  For a pick-and-place problem the
+// samples are grouped by a cheap forecast from theta: those whose grip
+// height lies within the grasp tolerance (they can grasp) first, then by
+// the first moveTo's gain (how soon they arrive) in 256 steps over its
+// range; every other problem keeps the identity.  One CTA per problem, a
+// counting sort over the 512 forecast bins with shared-memory atomics (the
+// order inside a bin may differ from run to run; each sample's result is
+// the same wherever it runs).
+constexpr int kOrderBins = 512;
+constexpr int kOrderThreads = 1024;
 
 __global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevScene* __restrict__ scenes,
                                                                     const BatchProblem* __restrict__ probs,
                                                                     const float* __restrict__ theta,
                                                                     int32_t* __restrict__ perm) {
-  extern __shared__ unsigned long long okeys[];
+  __shared__ int count[kOrderBins];
   const BatchProblem pb = probs[blockIdx.x];
   int32_t* out = perm + pb.sample_off;
   const DevScene& s = scenes[blockIdx.x];
@@ -1182,42 +1183,43 @@ __global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevSce
       if (first_move < 0 && s.act_kind[i] == CEM_ACT_MOVE) first_move = i;
       if (grasp < 0 && s.act_kind[i] == CEM_ACT_GRASP) grasp = i;
     }
-  if (!pb.active || pb.N > kMaxOrdered || grasp < 0 || first_move < 0) {
+  if (!pb.active || grasp < 0 || first_move < 0) {
     for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[k] = k;
     return;
   }
-  int P2 = 1;
-  while (P2 < pb.N) P2 <<= 1;
   const int gi = s.act_off[grasp] + 1, ki = s.act_off[first_move] + 2;
-  const float tol = s.grip_tol;
-  for (int k = threadIdx.x; k < P2; k += blockDim.x) {
-    unsigned long long key = ~0ull;
-    if (k < pb.N) {
-      const float* row = theta + pb.theta_off + (size_t)k * pb.D;
-      const float grip = fminf(fmaxf(row[gi], s.lo[gi]), s.hi[gi]);
-      const float kp = fminf(fmaxf(row[ki], s.lo[ki]), s.hi[ki]);
-      const uint32_t f = (fabsf(grip) <= tol ? 0u : 0x80000000u) | (__float_as_uint(kp) >> 1);
-      key = ((unsigned long long)f << 32) | (uint32_t)k;
+  const float tol = s.grip_tol, klo = s.lo[ki], kspan = s.hi[ki] - s.lo[ki];
+  const float kscale = kspan > 0.0f ? 255.0f / kspan : 0.0f;
+  auto bin_of = [&](int k) {
+    const float* row = theta + pb.theta_off + (size_t)k * pb.D;
+    const float grip = fminf(fmaxf(row[gi], s.lo[gi]), s.hi[gi]);
+    const float kp = fminf(fmaxf(row[ki], klo), s.hi[ki]);
+    return (fabsf(grip) <= tol ? 0 : 256) + (int)fminf((kp - klo) * kscale, 255.0f);
+  };
+  for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) count[b] = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) atomicAdd(&count[bin_of(k)], 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive prefix sum: each lane 16 consecutive bins
+    const int lane = threadIdx.x;
+    int v[kOrderBins / 32], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kOrderBins / 32; ++i) {
+      v[i] = sum;
+      sum += count[lane * (kOrderBins / 32) + i];
     }
-    okeys[k] = key;
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int base = incl - sum;
+#pragma unroll
+    for (int i = 0; i < kOrderBins / 32; ++i) count[lane * (kOrderBins / 32) + i] = base + v[i];
   }
   __syncthreads();
-  for (int size = 2; size <= P2; size <<= 1)
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int k = threadIdx.x; k < P2; k += blockDim.x) {
-        const int j = k ^ stride;
-        if (j > k) {
-          const bool up = (k & size) == 0;
-          const unsigned long long a = okeys[k], b = okeys[j];
-          if ((a > b) == up) {
-            okeys[k] = b;
-            okeys[j] = a;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[k] = (int32_t)(uint32_t)(okeys[k] & 0xffffffffull);
+  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[atomicAdd(&count[bin_of(k)], 1)] = k;
 }
 
 // Persistent batched rollout: every warp of a resident CTA repeatedly takes
@@ -1332,10 +1334,7 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
 
 cudaError_t configure_rollout_batch() {
   const int bytes = (int)(sizeof(DevScene) * kMaxBatchWarps);
-  cudaError_t e = cudaFuncSetAttribute(order_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(unsigned long long) * kMaxOrdered));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(rollout_persistent_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e = cudaFuncSetAttribute(rollout_persistent_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(rollout_persistent_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e == cudaSuccess)
@@ -1361,8 +1360,7 @@ int rollout_batch_max_ctas_per_sm(int warps, int tpr) {
 cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* probs_d, int n_problems,
                                const float* theta, int32_t* perm, cudaStream_t st) {
   if (n_problems <= 0) return cudaSuccess;
-  order_batch_kernel<<<n_problems, kOrderThreads, sizeof(unsigned long long) * kMaxOrdered, st>>>(scenes_d, probs_d,
-                                                                                                  theta, perm);
+  order_batch_kernel<<<n_problems, kOrderThreads, 0, st>>>(scenes_d, probs_d, theta, perm);
   return cudaGetLastError();
 }
 

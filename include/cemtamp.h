@@ -415,10 +415,14 @@ int cem_surrogate_num_params(cem_surrogate_handle s);
  * set_params also clears the optimiser state. */
 int cem_surrogate_set_params(cem_surrogate_handle s, const float* params_h, const float* norm_h);
 int cem_surrogate_get_params(cem_surrogate_handle s, float* params_h, float* norm_h);
-/* x_d[M][48] FP32 -> y_d[M] scores (stream-ordered).  With width 256 and
- * depth 4 this (and screening) runs one fused tcgen05 kernel per 128 rows;
- * if one of its bounded pipeline waits expires, that CTA's scores are NaN
- * and cem_surrogate_status reports the code. */
+/* x_d[M][48] FP32 -> y_d[M] scores (stream-ordered).  Features are rounded
+ * to BF16 (nearest even) before the first layer.  With width 256 and depth 4
+ * this (and screening) runs one persistent fused tcgen05 kernel (128-row
+ * tiles, two per SM in flight); when x_d is 16-byte aligned that kernel
+ * reads and rounds the FP32 rows itself, otherwise a conversion pass runs
+ * first (same scores, bit for bit).  If one of its bounded pipeline waits
+ * expires, that CTA's scores are NaN and cem_surrogate_status reports the
+ * code. */
 int cem_surrogate_forward(cem_surrogate_handle s, const float* x_d, int M, float* y_d, void* stream);
 /* Forward path for inference: 0 automatic (tcgen05 where the shape allows),
  * 1 the tiled mma.sync GEMM, 2 tcgen05 (CEM_ERR_UNSUPPORTED unless width 256

@@ -173,6 +173,7 @@ def lib():
             u8p, i32p, u32p = C.POINTER(C.c_uint8), C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
             sp = C.POINTER(_Scene)
             L.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            L.or_set_exhaustive_contacts.argtypes = [C.c_int]
             L.or_philox_words.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, u32p]
             L.or_normals.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, dp]
             L.or_sample.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, C.c_int, dp, dp, dp]
@@ -369,6 +370,12 @@ def cem_paper(scene, skel, seed, n0=3000, n1=300, j1=10, K=50, iters=20, problem
         raise RuntimeError(f"oracle CE loop failed: {rc}")
     return dict(best_theta=bt, best_J=bJ.value, best_cls=bc.value, mean=mean, cov=cov, history=hist,
                 class_counts=counts, n_env=ns)
+
+
+def set_exhaustive_contacts(on):
+    """Test switch: run the push base-block contact test on every step instead
+    of only where the block's bounding circle reaches the base."""
+    lib().or_set_exhaustive_contacts(int(bool(on)))
 
 
 def dr_factors(seed, it, problem, M, dmu, dm):

@@ -89,6 +89,10 @@ typedef struct {
 
 #ifdef __cplusplus
 extern "C" {
+/* Test switch: when on, the push base-block contact test runs on every step
+ * instead of only where the block's bounding circle reaches the base (the
+ * skip is exact; results must be identical either way). */
+void or_set_exhaustive_contacts(int on);
 #endif
 /* Philox4x32-10 block: out = philox(ctr, key). */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -19,6 +19,7 @@
 #include "oracle.h"
 #include "plan2d.h"
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -32,6 +33,9 @@
 // math call on a Cnt is counted; comparisons, abs, min and max are not).
 namespace {
 thread_local or_ops g_ops;
+// test switch: run the exact base-block contact test on every step (the
+// broad phase's skip is exact, so results must not change)
+std::atomic<int> g_exhaustive_contacts{0};
 
 struct Cnt {
   double v;
@@ -270,11 +274,14 @@ void planar_rollout(const or_scene& s, const Prep& pp, const double* th, int T, 
     R rax = R(0.0), ray = R(0.0), rbx = R(0.0), rby = R(0.0);
     if (has_block) {
       // broad phase: the rectangles can only touch if the block's bounding
-      // circle reaches the base rectangle (tested in the base frame)
+      // circle reaches the base rectangle (tested in the base frame); the
+      // skip is exact (a block outside that slab cannot overlap the base),
+      // so it changes no result, only the operations the counter sees
       R cdx = k.x - b.x, cdy = k.y - b.y;
       R cbp = Cos(b.psi), sbp = Sin(b.psi);
       const double rk = std::sqrt(s.block_half[0] * s.block_half[0] + s.block_half[1] * s.block_half[1]);
-      if (Abs(cdx * cbp + cdy * sbp) < R(s.base_half[0] + rk) && Abs(cdy * cbp - cdx * sbp) < R(s.base_half[1] + rk))
+      if (g_exhaustive_contacts.load(std::memory_order_relaxed) ||
+          (Abs(cdx * cbp + cdy * sbp) < R(s.base_half[0] + rk) && Abs(cdy * cbp - cdx * sbp) < R(s.base_half[1] + rk)))
         hit = sat_rect(b, s.base_half[0], s.base_half[1], k, s.block_half[0], s.block_half[1], nx, ny, dep, qx, qy);
       if (hit) {
         rax = qx - b.x; ray = qy - b.y; rbx = qx - k.x; rby = qy - k.y;
@@ -774,6 +781,8 @@ extern "C" int or_rollout_count(const or_scene* s, const double* theta, or_ops* 
 // body's mass by s_m = 1 + dm (2 u1 - 1), with (u0, u1) from the first two
 // words of the Philox block (m, 256, iter, problem) under key `seed` and
 // u = (word + 1) 2^-32.  All samples of an iteration share the environments.
+extern "C" void or_set_exhaustive_contacts(int on) { g_exhaustive_contacts.store(on ? 1 : 0); }
+
 extern "C" void or_dr_factors(uint64_t seed, uint32_t iter, uint32_t problem, int M, double dmu, double dm,
                               double* smu, double* sm) {
   const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};

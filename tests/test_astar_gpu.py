@@ -106,11 +106,16 @@ def test_cost_parity_600_steps(P, seed, regions):
     r = np.abs(J - Jr) / np.maximum(np.abs(Jr), 1e-3)
     bad = np.where((r > 1e-3) | (cls != cr))[0]
     bl = borderline(sc, sk, th.astype(np.float64), Jr, T, bad)
-    hard = bad[~bl]
     # a waypoint switch decided one step apart in FP32 and FP64 is a discrete
-    # event too; allow a handful beyond the borderline probe
-    assert len(hard) <= 0.02 * len(th), (len(hard), hard[:10])
-    assert bl.sum() <= 0.02 * len(th)
+    # event the 1e-6 probe can miss; such a sample must still show an outcome
+    # of the FP64 model close by (theta moved by 1e-6 or 1e-5 of its range)
+    from pickplace_common import nearby_outcome
+
+    rest = bad[~bl]
+    near = nearby_outcome(lambda t: oracle.rollout(sc, sk, t, T=T), sk, th, rest, J, cls)
+    hard = rest[~near]
+    assert len(hard) == 0, (hard[:10], J[hard[:10]], Jr[hard[:10]])
+    assert len(bad) - len(hard) <= 0.02 * len(th), len(bad)
 
 
 def test_lane_groups_are_bit_identical_with_planning(P):

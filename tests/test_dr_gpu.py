@@ -68,10 +68,17 @@ def test_randomised_cost_matches_oracle(P, task, T, M):
         J, c = gpu_rollout(P, S, th)
     Jo, co = oracle.rollout_dr(sc, sk, th.astype(np.float64), M, 0.3, 0.4, seed=1234, it=0, problem=0, T=T)
     rel = np.abs(J - Jo) / np.maximum(np.abs(Jo), 1e-3)
-    # samples on a success threshold may flip in one environment (FP32 vs FP64
-    # trajectories), exactly as in the plain parity; they must stay rare
-    ok = (rel <= 1e-3) & (c == co)
-    assert ok.mean() >= 0.97, (task, ok.mean())
+    # a sample on a success threshold may flip in one environment (FP32 vs
+    # FP64 trajectories), exactly as in the plain parity: its device result
+    # must then be the FP64 outcome of a theta within 1e-6 or 1e-5 of its range,
+    # and such samples stay rare
+    from pickplace_common import nearby_outcome
+
+    bad = np.where((rel > 1e-3) | (c != co))[0]
+    roll = lambda t: oracle.rollout_dr(sc, sk, t, M, 0.3, 0.4, seed=1234, it=0, problem=0, T=T)
+    near = nearby_outcome(roll, sk, th, bad, J, c)
+    assert near.all(), (task, bad[~near][:8], J[bad[~near][:8]], Jo[bad[~near][:8]])
+    assert len(bad) <= 0.03 * len(th), (task, len(bad))
 
 
 def test_randomised_pickplace_through_every_action(P):

@@ -188,6 +188,39 @@ def test_body_contact_conserves_momentum(orc):
     assert E[-1] < E[0]
 
 
+def test_push_broad_phase_skip_is_exact(orc):
+    # the push rollout tests base-block contact only where the block's
+    # bounding circle reaches the base; running the exact test on every step
+    # instead must give the same trajectories, costs and classes bit for bit
+    # (initial distribution and converged-style samples, contact-heavy),
+    # while the op tally shows the skipped work
+    results = []
+    for seed in (0, 3):
+        sc, sk = workload.push_scene(seed, T=600)
+        lo, hi = np.array(sk["lo"]), np.array(sk["hi"])
+        th = np.random.default_rng(seed).uniform(lo, hi, (48, len(lo)))
+        for exhaustive in (False, True):
+            orc.set_exhaustive_contacts(exhaustive)
+            try:
+                J, c = orc.rollout(sc, sk, th)
+                tr = orc.trace(sc, sk, th[0], 600)
+                ops = orc.count_ops(sc, sk, th[:8])
+            finally:
+                orc.set_exhaustive_contacts(False)
+            results.append((J, c, tr, ops))
+        (J0, c0, t0, o0), (J1, c1, t1, o1) = results[-2:]
+        assert np.array_equal(J0, J1) and np.array_equal(c0, c1) and np.array_equal(t0, t1)
+        assert o1["add"] + o1["mul"] > o0["add"] + o0["mul"]  # the exact test ran more often
+    sc, sk = _push_free()
+    tr0 = orc.trace(sc, sk, np.zeros(6), 400)
+    orc.set_exhaustive_contacts(True)
+    try:
+        tr1 = orc.trace(sc, sk, np.zeros(6), 400)
+    finally:
+        orc.set_exhaustive_contacts(False)
+    assert np.array_equal(tr0, tr1) and np.abs(tr0[-1, 9:12]).max() > 0.1  # a real collision, unchanged
+
+
 def test_body_contact_elastic_without_damping(orc):
     # no damping, no friction: the penalty spring returns the energy
     sc, sk = _push_free(T=600, mu_c=0.0, c=0.0)

@@ -1158,15 +1158,18 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
 // Rollout order of a batch (a schedule, not arithmetic): the persistent
 // kernel rolls sample perm[k] out on the lane that takes position k, so
 // samples that will be in the same action at the same time share a warp
-// and its lanes take the same branches.  For a pick-and-place problem the
-// samples are grouped by a cheap forecast from theta: those whose grip
-// height lies within the grasp tolerance (they can grasp) first, then by
-// the first moveTo's gain (how soon they arrive) in 256 steps over its
+// and its lanes take the same branches.  For a pick-and-place problem with
+// the PD base controller the samples are grouped by a cheap forecast from
+// theta: first those whose first moveTo can end (its target lies outside
+// every obstacle footprint grown by the base, and its gain exceeds mu g /
+// eps, below which the PD law stalls short of the target), then those
+// whose grip height lies within the grasp tolerance (they can grasp), then
+// by the first moveTo's gain (how soon they arrive) in 256 steps over its
 // range; every other problem keeps the identity.  One CTA per problem, a
-// counting sort over the 512 forecast bins with shared-memory atomics (the
+// counting sort over the 1024 forecast bins with shared-memory atomics (the
 // order inside a bin may differ from run to run; each sample's result is
 // the same wherever it runs).
-constexpr int kOrderBins = 512;
+constexpr int kOrderBins = 1024;
 constexpr int kOrderThreads = 1024;
 
 __global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevScene* __restrict__ scenes,
@@ -1187,20 +1190,33 @@ __global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevSce
     for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[k] = k;
     return;
   }
-  const int gi = s.act_off[grasp] + 1, ki = s.act_off[first_move] + 2;
+  const int gi = s.act_off[grasp] + 1, mo = s.act_off[first_move], ki = mo + 2;
   const float tol = s.grip_tol, klo = s.lo[ki], kspan = s.hi[ki] - s.lo[ki];
   const float kscale = kspan > 0.0f ? 255.0f / kspan : 0.0f;
+  const float kp_stall = s.base_cap / (s.dt * s.eps);  // mu g / eps
   auto bin_of = [&](int k) {
     const float* row = theta + pb.theta_off + (size_t)k * pb.D;
     const float grip = fminf(fmaxf(row[gi], s.lo[gi]), s.hi[gi]);
     const float kp = fminf(fmaxf(row[ki], klo), s.hi[ki]);
-    return (fabsf(grip) <= tol ? 0 : 256) + (int)fminf((kp - klo) * kscale, 255.0f);
+    const float tx = s.act_nom[first_move][0] + fminf(fmaxf(row[mo], s.lo[mo]), s.hi[mo]);
+    const float ty = s.act_nom[first_move][1] + fminf(fmaxf(row[mo + 1], s.lo[mo + 1]), s.hi[mo + 1]);
+    bool never = kp < kp_stall;
+    for (int g = 0; g < s.n_geoms && !never; ++g) {
+      if (!(s.geom_flags[g] & 1) || s.bslab_n[g] == 0) continue;
+      bool inside = true;
+      for (int j = 0; j < s.bslab_n[g] && inside; ++j) {
+        const float v = s.bslab[g][j][0] * tx + s.bslab[g][j][1] * ty;
+        inside = v >= s.bslab[g][j][2] && v <= s.bslab[g][j][3];
+      }
+      never = inside;
+    }
+    return (never ? 512 : 0) + (fabsf(grip) <= tol ? 0 : 256) + (int)fminf((kp - klo) * kscale, 255.0f);
   };
   for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) count[b] = 0;
   __syncthreads();
   for (int k = threadIdx.x; k < pb.N; k += blockDim.x) atomicAdd(&count[bin_of(k)], 1);
   __syncthreads();
-  if (threadIdx.x < 32) {  // exclusive prefix sum: each lane 16 consecutive bins
+  if (threadIdx.x < 32) {  // exclusive prefix sum: each lane 32 consecutive bins
     const int lane = threadIdx.x;
     int v[kOrderBins / 32], sum = 0;
 #pragma unroll

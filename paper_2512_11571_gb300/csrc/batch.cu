@@ -51,11 +51,14 @@ struct cem_batch_ctx {
   int32_t* keff_d = nullptr;
   int32_t* status_d = nullptr;
   int32_t* perm_d = nullptr;  // rollout order of every problem's samples (launch_order_batch)
+  int32_t* dorder_d = nullptr;  // dispatch order of the work items (launch_dispatch_order)
+  uint32_t* idur_d = nullptr;   // each work item's last duration (128 ns units), or its estimate
   Track* track_d = nullptr;
   RefitArgs* args_d = nullptr;
   int warps = 4, ctas_per_sm = 0;  // persistent launch shape (0 = occupancy)
   int tpr = 1;                     // lanes per pick-and-place rollout (1, 8 or 32)
   std::vector<int> order;          // problems by descending work (the queue order)
+  std::vector<uint32_t> weight;    // per problem: the work estimate behind that order
   bool has_pickplace = false;
   bool dr_on = false;  // domain randomisation of every problem's rollouts
   DrArgs dr{};
@@ -83,7 +86,7 @@ void batch_free(cem_batch_ctx* h) {
   }
   void* ptrs[] = {h->scenes_d, h->probs_d, h->items_d, h->counter_d, h->theta_d, h->J_d, h->cls_d,
                   h->mean_d,   h->cov_d,   h->chol_d,  h->keff_d,    h->status_d, h->track_d, h->args_d,
-                  h->screen_tab_d, h->perm_d};
+                  h->screen_tab_d, h->perm_d, h->dorder_d, h->idur_d};
   for (void* p : ptrs) cudaFree(p);
 }
 
@@ -92,6 +95,17 @@ int grid_size(const cem_batch_ctx* h) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr);
   return sms * per_sm;
+}
+
+// Before any duration is recorded, a work item is estimated by its problem's
+// horizon (four times as heavy for pick-and-place), which gives the
+// heavier-first dispatch order; the persistent kernel then records real
+// durations for the next iteration's order.
+cudaError_t upload_item_estimates(cem_batch_ctx* h, const std::vector<BatchItem>& items) {
+  std::vector<uint32_t> est(items.size());
+  for (size_t i = 0; i < items.size(); ++i) est[i] = h->weight[items[i].problem];
+  if (items.empty()) return cudaSuccess;
+  return cudaMemcpy(h->idur_d, est.data(), sizeof(uint32_t) * est.size(), cudaMemcpyHostToDevice);
 }
 
 // Which problems take part in the next iterations: flags on the device
@@ -113,6 +127,7 @@ int set_active(cem_batch_ctx* h, const std::vector<int>& active) {
   }
   if (!items.empty())
     BATCH_CUDA(cudaMemcpy(h->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+  BATCH_CUDA(upload_item_estimates(h, items));
   h->n_items = (int)items.size();
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
@@ -162,13 +177,16 @@ cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st, bool screened = false) {
   const bool order = !h->dr_on;  // the randomised path keeps the identity order
   if (order) e = launch_order_batch(h->scenes_d, h->probs_d, h->P, h->theta_d, h->perm_d, st);
   if (e != cudaSuccess) return e;
+  e = launch_dispatch_order(h->idur_d, h->n_items, h->dorder_d, st);
+  if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   e = mark(h, 1, st);
   if (e != cudaSuccess) return e;
   e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
                                       h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, h->track_d,
-                                      h->dr_on ? &h->dr : nullptr, st, order ? h->perm_d : nullptr);
+                                      h->dr_on ? &h->dr : nullptr, st, order ? h->perm_d : nullptr, h->dorder_d,
+                                      h->idur_d);
   if (e != cudaSuccess) return e;
   e = mark(h, 2, st);
   if (e != cudaSuccess) return e;
@@ -241,6 +259,9 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
     return wa > wb;
   });
   h->order = order;
+  h->weight.resize(n_problems);
+  for (int p = 0; p < n_problems; ++p)
+    h->weight[p] = host[p].kind == CEM_SCENE_QUADRATIC ? 1u : (uint32_t)host[p].T * (host[p].kind == CEM_SCENE_PICKPLACE ? 4u : 1u);
   std::vector<BatchItem> items;
   for (int p : order)
     for (int f = 0; f < h->probs[p].N; f += 32) items.push_back(BatchItem{p, f});
@@ -259,6 +280,8 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
   M((void**)&h->J_d, sizeof(float) * (size_t)sample_total);
   M((void**)&h->cls_d, (size_t)sample_total);
   M((void**)&h->perm_d, sizeof(int32_t) * (size_t)sample_total);
+  M((void**)&h->dorder_d, sizeof(int32_t) * items.size());
+  M((void**)&h->idur_d, sizeof(uint32_t) * items.size());
   M((void**)&h->mean_d, sizeof(float) * P * kMS);
   M((void**)&h->cov_d, sizeof(float) * P * kMC);
   M((void**)&h->chol_d, sizeof(float) * P * kMC);
@@ -270,6 +293,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
   if (e == cudaSuccess) e = cudaMemcpy(h->probs_d, h->probs.data(), sizeof(BatchProblem) * P, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(h->items_d, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = upload_item_estimates(h, items);
   if (e == cudaSuccess) {
     std::vector<RefitArgs> args(P);
     for (size_t p = 0; p < P; ++p) {
@@ -319,9 +343,14 @@ int cem_batch_reset(cem_batch_handle h, void* stream) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   bool all = true;
   for (const BatchProblem& b : h->probs) all = all && b.active;
-  if (!all) {  // every problem takes part again
+  if (!all) {  // every problem takes part again (which also resets the dispatch estimates)
     const int rc = set_active(h, std::vector<int>(h->P, 1));
     if (rc != CEM_OK) return rc;
+  } else {  // the first iteration's dispatch order comes from the estimates again
+    std::vector<BatchItem> items;
+    for (int p : h->order)
+      for (int f = 0; f < h->probs[p].N; f += 32) items.push_back(BatchItem{p, f});
+    BATCH_CUDA(upload_item_estimates(h, items));
   }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t P = h->P;

@@ -1254,7 +1254,9 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
                                                                  const float* __restrict__ theta,
                                                                  float* __restrict__ J, uint8_t* __restrict__ cls,
                                                                  const Track* __restrict__ tracks, const DrArgs dr,
-                                                                 const int32_t* __restrict__ perm) {
+                                                                 const int32_t* __restrict__ perm,
+                                                                 const int32_t* __restrict__ dorder,
+                                                                 uint32_t* __restrict__ idur) {
   extern __shared__ __align__(16) unsigned char psm[];  // one DevScene per warp
   DevScene* sc = reinterpret_cast<DevScene*>(psm);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1265,7 +1267,10 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
     if (lane == 0) it = atomicAdd(counter, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= n_items) break;
-    const BatchItem item = items[it];
+    const int src_it = dorder ? dorder[it] : it;  // the dispatch order (longest item first)
+    const BatchItem item = items[src_it];
+    uint64_t t_item = 0;
+    if (idur && lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_item));
     if (item.problem != cur) {
       const uint32_t* src = reinterpret_cast<const uint32_t*>(scenes + item.problem);
       uint32_t* dst = reinterpret_cast<uint32_t*>(&s);
@@ -1343,6 +1348,11 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
       }
     }
     __syncwarp();
+    if (idur && lane == 0) {  // this item's duration, in 128 ns units, orders the next dispatch
+      uint64_t t_end;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+      idur[src_it] = (uint32_t)min((t_end - t_item) >> 7, (uint64_t)0xffffffffu);
+    }
   }
 }
 
@@ -1380,11 +1390,56 @@ cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* pro
   return cudaGetLastError();
 }
 
+// The dispatch order of a batch's work items (a schedule, not arithmetic):
+// longest first by each item's recorded duration (the previous CE
+// iteration's, or a static estimate before the first), so that the items
+// the persistent kernel starts last are the short ones and its warps finish
+// together.  One CTA, a counting sort over 1024 duration bins of 16.4 us
+// (the last bin holds everything longer), longest bin first; the order
+// inside a bin may differ from run to run.
+constexpr int kDispatchBins = 1024;
+
+__global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __restrict__ idur, int n_items,
+                                                              int32_t* __restrict__ dorder) {
+  __shared__ int count[kDispatchBins];
+  auto bin_of = [&](int i) { return kDispatchBins - 1 - (int)min(idur[i] >> 7, (uint32_t)(kDispatchBins - 1)); };
+  for (int b = threadIdx.x; b < kDispatchBins; b += blockDim.x) count[b] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_items; i += blockDim.x) atomicAdd(&count[bin_of(i)], 1);
+  __syncthreads();
+  if (threadIdx.x < 32) {  // exclusive prefix sum: each lane 32 consecutive bins
+    const int lane = threadIdx.x;
+    int v[kDispatchBins / 32], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kDispatchBins / 32; ++i) {
+      v[i] = sum;
+      sum += count[lane * (kDispatchBins / 32) + i];
+    }
+    int incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const int base = incl - sum;
+#pragma unroll
+    for (int i = 0; i < kDispatchBins / 32; ++i) count[lane * (kDispatchBins / 32) + i] = base + v[i];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_items; i += blockDim.x) dorder[atomicAdd(&count[bin_of(i)], 1)] = i;
+}
+
+cudaError_t launch_dispatch_order(const uint32_t* idur, int n_items, int32_t* dorder, cudaStream_t st) {
+  if (n_items <= 0) return cudaSuccess;
+  dispatch_order_kernel<<<1, 1024, 0, st>>>(idur, n_items, dorder);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
                                             int tpr, const Track* tracks, const DrArgs* dr_in, cudaStream_t st,
-                                            const int32_t* perm) {
+                                            const int32_t* perm, const int32_t* dorder, uint32_t* idur) {
   if (n_items <= 0) return cudaSuccess;
   if (warps < 1 || warps > kMaxBatchWarps || grid < 1) return cudaErrorInvalidValue;
   DrArgs dr{};  // M = 0: off
@@ -1394,13 +1449,13 @@ cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const Batc
   }
   if (tpr == 8)
     rollout_persistent_kernel<8><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                             J, cls, tracks, dr, perm);
+                                                             J, cls, tracks, dr, perm, dorder, idur);
   else if (tpr == 32)
     rollout_persistent_kernel<32><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                              J, cls, tracks, dr, perm);
+                                                              J, cls, tracks, dr, perm, dorder, idur);
   else if (tpr == 1)
     rollout_persistent_kernel<1><<<grid, warps * 32, sizeof(DevScene) * warps, st>>>(scenes_d, probs_d, items_d, n_items, counter_d, theta,
-                                                             J, cls, tracks, dr, perm);
+                                                             J, cls, tracks, dr, perm, dorder, idur);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

@@ -575,7 +575,7 @@ def run_gb300(args):
                                    "unit": "TFLOP/s"},
             "time_to_cost": ttc,
             "roofline_surrogate": sur,
-            "gpu_launches": 4 * args.steps,  # sample, order, persistent rollout, refit
+            "gpu_launches": 5 * args.steps,  # sample, sample order, dispatch order, persistent rollout, refit
             "clocks": hd["clocks"],
         }
         if world == 1:

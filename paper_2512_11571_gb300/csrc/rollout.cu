@@ -1171,12 +1171,14 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
 // the same wherever it runs).
 constexpr int kOrderBins = 1024;
 constexpr int kOrderThreads = 1024;
+constexpr int kOrderKeep = 8192;
 
-__global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevScene* __restrict__ scenes,
+__global__ void __launch_bounds__(kOrderThreads, 1) order_batch_kernel(const DevScene* __restrict__ scenes,
                                                                     const BatchProblem* __restrict__ probs,
                                                                     const float* __restrict__ theta,
                                                                     int32_t* __restrict__ perm) {
   __shared__ int count[kOrderBins];
+  __shared__ uint16_t sbin[kOrderKeep];  // the bins of the first kOrderKeep samples, between the two passes
   const BatchProblem pb = probs[blockIdx.x];
   int32_t* out = perm + pb.sample_off;
   const DevScene& s = scenes[blockIdx.x];
@@ -1214,7 +1216,11 @@ __global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevSce
   };
   for (int b = threadIdx.x; b < kOrderBins; b += blockDim.x) count[b] = 0;
   __syncthreads();
-  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) atomicAdd(&count[bin_of(k)], 1);
+  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) {
+    const int b = bin_of(k);
+    if (k < kOrderKeep) sbin[k] = (uint16_t)b;
+    atomicAdd(&count[b], 1);
+  }
   __syncthreads();
   if (threadIdx.x < 32) {  // exclusive prefix sum: each lane 32 consecutive bins
     const int lane = threadIdx.x;
@@ -1235,7 +1241,8 @@ __global__ void __launch_bounds__(kOrderThreads) order_batch_kernel(const DevSce
     for (int i = 0; i < kOrderBins / 32; ++i) count[lane * (kOrderBins / 32) + i] = base + v[i];
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < pb.N; k += blockDim.x) out[atomicAdd(&count[bin_of(k)], 1)] = k;
+  for (int k = threadIdx.x; k < pb.N; k += blockDim.x)
+    out[atomicAdd(&count[k < kOrderKeep ? (int)sbin[k] : bin_of(k)], 1)] = k;
 }
 
 // Persistent batched rollout: every warp of a resident CTA repeatedly takes

@@ -52,7 +52,7 @@ struct cem_batch_ctx {
   int32_t* status_d = nullptr;
   int32_t* perm_d = nullptr;  // rollout order of every problem's samples (launch_order_batch)
   int32_t* dorder_d = nullptr;  // dispatch order of the work items (launch_dispatch_order)
-  uint32_t* idur_d = nullptr;   // each work item's last duration (128 ns units), or its estimate
+  uint32_t* idur_d = nullptr;   // each work item's running-average duration (128 ns units), or its estimate
   Track* track_d = nullptr;
   RefitArgs* args_d = nullptr;
   int warps = 4, ctas_per_sm = 0;  // persistent launch shape (0 = occupancy)
@@ -99,8 +99,8 @@ int grid_size(const cem_batch_ctx* h) {
 
 // Before any duration is recorded, a work item is estimated by its problem's
 // horizon (four times as heavy for pick-and-place), which gives the
-// heavier-first dispatch order; the persistent kernel then records real
-// durations for the next iteration's order.
+// heavier-first dispatch order; the persistent kernel then keeps a running
+// average of real durations for the next iterations' order.
 cudaError_t upload_item_estimates(cem_batch_ctx* h, const std::vector<BatchItem>& items) {
   std::vector<uint32_t> est(items.size());
   for (size_t i = 0; i < items.size(); ++i) est[i] = h->weight[items[i].problem];
@@ -177,7 +177,7 @@ cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st, bool screened = false) {
   const bool order = !h->dr_on;  // the randomised path keeps the identity order
   if (order) e = launch_order_batch(h->scenes_d, h->probs_d, h->P, h->theta_d, h->perm_d, st);
   if (e != cudaSuccess) return e;
-  e = launch_dispatch_order(h->idur_d, h->n_items, h->dorder_d, st);
+  e = launch_dispatch_order(h->idur_d, h->items_d, h->n_items, h->dorder_d, st);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(h->counter_d, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;

@@ -159,16 +159,18 @@ cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int
 // perm (may be null = identity): lane position k of a problem rolls out
 // sample perm[sample_off + k] (the randomised path keeps the identity);
 // dorder (may be null = identity): the k-th item taken is items[dorder[k]];
-// idur (may be null): each item's duration is recorded there
+// idur (may be null): a running average of each item's duration is kept there
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
                                             int tpr, const Track* tracks, const DrArgs* dr, cudaStream_t st,
                                             const int32_t* perm = nullptr, const int32_t* dorder = nullptr,
                                             uint32_t* idur = nullptr);
-// the dispatch order of the work items, longest recorded duration first
-// (idur: per item, 128 ns units, written by the persistent kernel)
-cudaError_t launch_dispatch_order(const uint32_t* idur, int n_items, int32_t* dorder, cudaStream_t st);
+// the dispatch order of the work items, longest forecast duration first
+// (idur: per item, 128 ns units, a running average the persistent kernel
+// keeps; blended with the item's problem mean)
+cudaError_t launch_dispatch_order(const uint32_t* idur, const BatchItem* items, int n_items, int32_t* dorder,
+                                  cudaStream_t st);
 // the rollout order of every problem of a batch (see order_batch_kernel):
 // perm[sample_off + k] for k < N, from the theta just sampled
 cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* probs_d, int n_problems,

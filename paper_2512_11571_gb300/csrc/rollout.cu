@@ -1355,10 +1355,11 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
       }
     }
     __syncwarp();
-    if (idur && lane == 0) {  // this item's duration, in 128 ns units, orders the next dispatch
+    if (idur && lane == 0) {  // running average of this item's duration (128 ns units): the next dispatch
       uint64_t t_end;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-      idur[src_it] = (uint32_t)min((t_end - t_item) >> 7, (uint64_t)0xffffffffu);
+      const uint32_t d = (uint32_t)min((t_end - t_item) >> 7, (uint64_t)0x7fffffffu);
+      idur[src_it] = (idur[src_it] >> 1) + (d >> 1);
     }
   }
 }
@@ -1398,18 +1399,40 @@ cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* pro
 }
 
 // The dispatch order of a batch's work items (a schedule, not arithmetic):
-// longest first by each item's recorded duration (the previous CE
-// iteration's, or a static estimate before the first), so that the items
-// the persistent kernel starts last are the short ones and its warps finish
-// together.  One CTA, a counting sort over 1024 duration bins of 16.4 us
-// (the last bin holds everything longer), longest bin first; the order
-// inside a bin may differ from run to run.
+// longest first by a duration forecast, so that the items the persistent
+// kernel starts last are the short ones and its warps finish together.
+// The forecast of an item is the mean of its own recorded duration (a
+// running average over CE iterations, or a static estimate before the
+// first) and its problem's mean item duration (steadier: an item's samples
+// are redrawn every iteration).  One CTA, a counting sort over 1024 bins of
+// 16.4 us (the last bin holds everything longer), longest bin first; the
+// order inside a bin may differ from run to run.
 constexpr int kDispatchBins = 1024;
+constexpr int kDispatchProblems = 256;  // problems per batch the mean is kept for (more share slots)
 
-__global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __restrict__ idur, int n_items,
+__global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __restrict__ idur,
+                                                              const BatchItem* __restrict__ items, int n_items,
                                                               int32_t* __restrict__ dorder) {
   __shared__ int count[kDispatchBins];
-  auto bin_of = [&](int i) { return kDispatchBins - 1 - (int)min(idur[i] >> 7, (uint32_t)(kDispatchBins - 1)); };
+  __shared__ unsigned long long psum[kDispatchProblems];
+  __shared__ int pcnt[kDispatchProblems];
+  for (int b = threadIdx.x; b < kDispatchProblems; b += blockDim.x) {
+    psum[b] = 0ull;
+    pcnt[b] = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
+    const int pr = items[i].problem % kDispatchProblems;
+    atomicAdd(&psum[pr], (unsigned long long)idur[i]);
+    atomicAdd(&pcnt[pr], 1);
+  }
+  __syncthreads();
+  auto bin_of = [&](int i) {
+    const int pr = items[i].problem % kDispatchProblems;
+    const uint32_t mean = (uint32_t)(psum[pr] / (unsigned long long)max(pcnt[pr], 1));
+    const uint32_t key = (mean >> 1) + (idur[i] >> 1);
+    return kDispatchBins - 1 - (int)min(key >> 7, (uint32_t)(kDispatchBins - 1));
+  };
   for (int b = threadIdx.x; b < kDispatchBins; b += blockDim.x) count[b] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < n_items; i += blockDim.x) atomicAdd(&count[bin_of(i)], 1);
@@ -1436,9 +1459,10 @@ __global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __
   for (int i = threadIdx.x; i < n_items; i += blockDim.x) dorder[atomicAdd(&count[bin_of(i)], 1)] = i;
 }
 
-cudaError_t launch_dispatch_order(const uint32_t* idur, int n_items, int32_t* dorder, cudaStream_t st) {
+cudaError_t launch_dispatch_order(const uint32_t* idur, const BatchItem* items, int n_items, int32_t* dorder,
+                                  cudaStream_t st) {
   if (n_items <= 0) return cudaSuccess;
-  dispatch_order_kernel<<<1, 1024, 0, st>>>(idur, n_items, dorder);
+  dispatch_order_kernel<<<1, 1024, 0, st>>>(idur, items, n_items, dorder);
   return cudaGetLastError();
 }
 

@@ -57,6 +57,32 @@ def same(a, b):
     assert np.array_equal(a["cov"], b["cov"])
 
 
+def test_large_pickplace_problems_keep_single_solve_results(P):
+    """Pick-place problems above 8192 samples (the rollout order recomputes
+    their forecast bins instead of keeping them in shared memory) and an
+    obstacle-heavy scene, beside a small one: every problem equals its own
+    cem_solve bit for bit, also after a reset (the work items' dispatch order
+    then starts from the horizon estimate again)."""
+    probs = []
+    sc, sk = workload.pickplace_scene(7, n_actions=5, T=300)
+    probs.append(dict(scene=sc, skel=sk, N=8192 + 96, K=64, seed=41, problem=200))
+    sc, sk = workload.pickplace_scene(8, n_actions=4, T=300, obstacle="box")
+    probs.append(dict(scene=sc, skel=sk, N=9000, K=50, seed=42, problem=201))
+    sc, sk = workload.reach_scene(1)
+    probs.append(dict(scene=sc, skel=sk, N=96, K=8, seed=43, problem=202))
+    iters = 3
+    with P.Batch(probs) as B:
+        B.iterate(iters, use_graph=True)
+        got = B.read()
+        B.reset()
+        B.iterate(iters, use_graph=False)
+        again = B.read()
+    for pr, g, g2 in zip(probs, got, again):
+        ref = single(P, pr, iters)
+        same(g, ref)
+        same(g2, ref)
+
+
 def test_batch_equals_single_problem_solves(P):
     probs = mixed_problems()
     iters = 4

@@ -1401,10 +1401,11 @@ cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* pro
 // The dispatch order of a batch's work items (a schedule, not arithmetic):
 // longest first by a duration forecast, so that the items the persistent
 // kernel starts last are the short ones and its warps finish together.
-// The forecast of an item is the mean of its own recorded duration (a
+// The forecast of an item is the larger of its own recorded duration (a
 // running average over CE iterations, or a static estimate before the
 // first) and its problem's mean item duration (steadier: an item's samples
-// are redrawn every iteration).  One CTA, a counting sort over 1024 bins of
+// are redrawn every iteration); erring long costs nothing, since only an
+// item that runs longer than forecast and starts late lengthens the launch.  One CTA, a counting sort over 1024 bins of
 // 16.4 us (the last bin holds everything longer), longest bin first; the
 // order inside a bin may differ from run to run.
 constexpr int kDispatchBins = 1024;
@@ -1430,7 +1431,7 @@ __global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __
   auto bin_of = [&](int i) {
     const int pr = items[i].problem % kDispatchProblems;
     const uint32_t mean = (uint32_t)(psum[pr] / (unsigned long long)max(pcnt[pr], 1));
-    const uint32_t key = (mean >> 1) + (idur[i] >> 1);
+    const uint32_t key = max(mean, idur[i]);
     return kDispatchBins - 1 - (int)min(key >> 7, (uint32_t)(kDispatchBins - 1));
   };
   for (int b = threadIdx.x; b < kDispatchBins; b += blockDim.x) count[b] = 0;

@@ -5,9 +5,11 @@
 // flight.  Per CTA, one warp streams the hidden weights into shared memory
 // (cp.async.bulk), one warp issues the tcgen05.mma sequence (M = 128,
 // N = 256, K = 16, BF16 x BF16 -> FP32), and 16 epilogue warps drain a
-// tile's 256-column FP32 accumulator in TMEM with tcgen05.ld, add the bias,
-// apply GELU and write BF16 activations back into that tile's shared-memory
-// buffer as the next layer's A operand.
+// tile's 256-column FP32 accumulator in TMEM with tcgen05.ld, apply GELU and
+// write BF16 activations back into that tile's shared-memory buffer as the
+// next layer's A operand.  Each accumulation starts from the layer's bias:
+// while draining, the epilogue stores the next layer's bias (tcgen05.st)
+// into the columns it has read, and every MMA accumulates onto it.
 //
 // Pipeline.  Each tile in flight has its own accumulator (2 x 256 of the 512
 // TMEM columns) and its own activation buffer.  The MMA warp and the
@@ -20,7 +22,10 @@
 // resident.  While a tile's last layer is drained, the next tile's input
 // rows are copied into the tile's buffer with cp.async (BF16 rows straight
 // into place; FP32 rows into its upper half, rounded to BF16 after the
-// drain), so no separate conversion pass reads the features.
+// drain), so no separate conversion pass reads the features; they were
+// asked into L2 two layers earlier.  A tile's score is the sum of four
+// column quarters' partial dot products, met per TMEM lane quadrant by a
+// 4-warp barrier, the only barrier inside the job loop.
 //
 // Arithmetic.  Rounding points are those of the tiled GEMM path: BF16
 // inputs, weights and activations, FP32 accumulation, FP32 bias and GELU.
@@ -29,7 +34,8 @@
 // activation), evaluated on pairs of activations with the packed FP32x2
 // instructions (fma/mul/add.rn.f32x2: two IEEE operations per
 // instruction); TMEM loads are double-buffered; biases and output weights
-// are staged in shared memory.  The K-slices of a layer accumulate in order.
+// are staged in shared memory.  The bias enters the FP32 sum first, then the
+// K-slices of the layer in order.
 //
 // Operands use the canonical K-major layout without swizzling: 8-row x
 // 16-byte core matrices stored contiguously (128 B), core matrices adjacent

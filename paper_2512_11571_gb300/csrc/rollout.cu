@@ -803,8 +803,11 @@ __device__ __noinline__ void pickplace_rollout(const DevScene& s, const float* _
   // Neighbour lists (bit g = geometry g) and the positions they were built
   // at.  A warp rebuilds all its lanes' lists together as soon as one lane
   // needs it (rebuilding early is always valid), so the rebuild loop runs
-  // once per event instead of once per lane.
-  constexpr float kSkin = 0.15f, kRebuild = 0.075f;
+  // once per event instead of once per lane.  A body left out is at least
+  // kSkin away along some axis; a rebuild once any lane has moved kRebuild
+  // keeps it at least 1 cm clear (far above FP32 rounding), and the later
+  // the rebuild, the fewer of them a warp runs.
+  constexpr float kSkin = 0.15f, kRebuild = 0.14f;
   const unsigned lanes = __activemask();
   // A* base controller: waypoints of the current moveTo, integral state
   const bool astar = s.base_ctrl != 0;

@@ -1418,22 +1418,24 @@ __global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __
                                                               const BatchItem* __restrict__ items, int n_items,
                                                               int32_t* __restrict__ dorder) {
   __shared__ int count[kDispatchBins];
-  __shared__ unsigned long long psum[kDispatchProblems];
+  // per problem: summed durations in 2.05 us units (32 bits hold 2^32 of them,
+  // far beyond any problem's item total) and the item count
+  __shared__ uint32_t psum[kDispatchProblems];
   __shared__ int pcnt[kDispatchProblems];
   for (int b = threadIdx.x; b < kDispatchProblems; b += blockDim.x) {
-    psum[b] = 0ull;
+    psum[b] = 0u;
     pcnt[b] = 0;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
     const int pr = items[i].problem % kDispatchProblems;
-    atomicAdd(&psum[pr], (unsigned long long)idur[i]);
+    atomicAdd(&psum[pr], idur[i] >> 4);
     atomicAdd(&pcnt[pr], 1);
   }
   __syncthreads();
   auto bin_of = [&](int i) {
     const int pr = items[i].problem % kDispatchProblems;
-    const uint32_t mean = (uint32_t)(psum[pr] / (unsigned long long)max(pcnt[pr], 1));
+    const uint32_t mean = (psum[pr] / (uint32_t)max(pcnt[pr], 1)) << 4;
     const uint32_t key = max(mean, idur[i]);
     return kDispatchBins - 1 - (int)min(key >> 7, (uint32_t)(kDispatchBins - 1));
   };

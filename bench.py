@@ -677,11 +677,31 @@ def run_refit_only(args):
     print(json.dumps(out), flush=True)
 
 
-def surrogate_roofline(P, seed, M=65536, reps=20):
+def time_forward_flushed(P, S, x, y, reps):
+    """Device time of `reps` surrogate forwards, each after an untimed L2
+    flush (the 12.6 MB of features would otherwise stay in the 129 MB L2) and
+    between its own CUDA events on the launching stream: (mean, median) ms."""
+    import torch
+
+    st = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for j in range(reps):
+        flush.fill_(float(j))
+        ev[j][0].record(st)
+        P.cem_surrogate_forward(S.h, x, y, st)
+        ev[j][1].record(st)
+    torch.cuda.synchronize()
+    t = np.array([a.elapsed_time(b) for a, b in ev])
+    return float(t.mean()), float(np.median(t))
+
+
+def surrogate_roofline(P, seed, M=65536, reps=50, warm=5):
     """The fused tcgen05 surrogate forward (48 -> 4 x 256 GELU -> 1, BF16
-    operands, FP32 accumulation) on M rows: one untimed call, then `reps`
-    calls between CUDA events on the launching stream.  Dense BF16
-    contraction, so the roofline is the measured BF16 tensor peak."""
+    operands, FP32 accumulation) on M rows: `warm` untimed calls, then `reps`
+    calls, each after an untimed L2 flush and between its own CUDA events on
+    the launching stream; `achieved` uses the mean.  Dense BF16 contraction,
+    so the roofline is the measured BF16 tensor peak."""
     import torch
 
     x = torch.rand((M, 48), device="cuda", generator=torch.Generator("cuda").manual_seed(seed)) * 2 - 1
@@ -691,21 +711,17 @@ def surrogate_roofline(P, seed, M=65536, reps=20):
     with P.Surrogate(256, 4, seed=seed) as S:
         S.set_forward_path(2)
         y = S.forward(x)
-        st = torch.cuda.current_stream()
+        for _ in range(warm):
+            P.cem_surrogate_forward(S.h, x, y, torch.cuda.current_stream())
         torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        for _ in range(reps):
-            P.cem_surrogate_forward(S.h, x, y, st)
-        e1.record(st)
-        torch.cuda.synchronize()
+        ms, med = time_forward_flushed(P, S, x, y, reps)
         if S.status() != 0:
             raise SystemExit("surrogate forward: a bounded pipeline wait expired")
-    ms = e0.elapsed_time(e1) / reps
     tf = flops / (ms / 1e3) / 1e12
-    return {"bound": "tensor", "kernel": "mlp_forward_tc_kernel", "rows": M, "ms": ms, "achieved": tf,
-            "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
-            "peak_basis": f"bf16_tflops ({src}, burst)", "launches": reps}
+    return {"bound": "tensor", "kernel": "mlp_forward_tc_kernel", "rows": M, "ms": ms, "ms_median": med,
+            "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+            "peak_basis": f"bf16_tflops ({src}, burst)", "launches": reps,
+            "l2": "flushed before each timed call (256 MiB write, untimed)"}
 
 
 def run_batch_only(args):
@@ -781,7 +797,8 @@ def run_train_only(args):
 def run_mlp_only(args):
     """Times the surrogate's BF16 tensor-core forward (4 x 256-wide layers) on
     --mlp-only rows through both paths (the tiled mma.sync GEMM and the fused
-    tcgen05 kernel): one untimed call each, then `reps` calls between events."""
+    tcgen05 kernel): four untimed calls each, then `reps` calls, each after an
+    untimed L2 flush and between its own events."""
     import torch
 
     import paper_2512_11571_gb300 as P
@@ -799,17 +816,13 @@ def run_mlp_only(args):
         for path, name in ((1, "tiled_mma_sync"), (2, "fused_tcgen05")):
             S.set_forward_path(path)
             y = S.forward(x)
+            for _ in range(3):
+                P.cem_surrogate_forward(S.h, x, y, torch.cuda.current_stream())
             torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            st = torch.cuda.current_stream()
-            e0.record(st)
-            for _ in range(args.reps):
-                P.cem_surrogate_forward(S.h, x, y, st)
-            e1.record(st)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.reps
+            ms, med = time_forward_flushed(P, S, x, y, args.reps)
             tf = flops / (ms / 1e3) / 1e12
-            out[name] = {"ms": ms, "tflops": tf, "frac_of_bf16": tf / peak}
+            out[name] = {"ms": ms, "ms_median": med, "tflops": tf, "frac_of_bf16": tf / peak,
+                         "l2": "flushed before each timed call"}
         if S.status() != 0:
             raise SystemExit("surrogate forward: a bounded pipeline wait expired")
     print(json.dumps(out), flush=True)

@@ -94,6 +94,40 @@ def test_batch_equals_single_problem_solves(P):
         same(g, single(P, pr, iters))
 
 
+def tiny_problems():
+    """Problems of 1, 31 and 33 samples: a lone sample (K_eff = 1 and its
+    noise rule), a single partial 32-sample item, one full item plus a
+    1-sample tail, with the sample and dispatch orders of pick-and-place."""
+    probs = []
+    sc, sk = workload.reach_scene(5)
+    probs.append(dict(scene=sc, skel=sk, N=1, K=1, seed=41))
+    sc, sk = workload.push_scene(6)
+    probs.append(dict(scene=sc, skel=sk, N=31, K=1, seed=42))
+    sc, sk = workload.pickplace_scene(7, n_actions=5, T=500)
+    probs.append(dict(scene=sc, skel=sk, N=33, K=4, seed=43))
+    sc, sk = workload.pickplace_scene(8, n_actions=3, T=500)
+    probs.append(dict(scene=sc, skel=sk, N=1, K=1, seed=44))
+    for i, p in enumerate(probs):
+        p["problem"] = 200 + i
+    return probs
+
+
+def test_tiny_problems_equal_single_solves(P):
+    probs = tiny_problems()
+    iters = 3
+    with P.Batch(probs) as B:
+        B.iterate(iters, use_graph=True)
+        got = B.read()
+    for pr, g in zip(probs, got):
+        assert g["iters_done"] == iters
+        same(g, single(P, pr, iters))
+    for pr in (probs[2], probs[3]):  # a batch of one problem
+        with P.Batch([pr]) as B:
+            B.iterate(iters, use_graph=False)
+            (g,) = B.read()
+        same(g, single(P, pr, iters))
+
+
 @pytest.mark.parametrize("warps,ctas", [(1, 1), (2, 3), (8, 1)])
 def test_launch_shape_does_not_change_results(P, warps, ctas):
     probs = mixed_problems()

@@ -37,8 +37,9 @@ def dev(a):
 
 
 # 1 row, one full tile, tile +- 1 (ragged tail), many tiles with a tail,
-# and more CTAs than one wave of 152 SMs with a tail
-@pytest.mark.parametrize("M", [1, 127, 128, 129, 1000, 65536 + 77])
+# 153 tiles (on 152 SMs one CTA runs a second, one-row tile), and more
+# tiles than one wave of 152 SMs with a tail
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 1000, 152 * 128 + 1, 65536 + 77])
 def test_tc_forward_matches_oracle(P, M):
     params = mlp.init_params(48, 256, 4, seed=M % 997)
     rng = np.random.default_rng(M)

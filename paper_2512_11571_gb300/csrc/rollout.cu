@@ -1418,8 +1418,15 @@ __global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __
                                                               const BatchItem* __restrict__ items, int n_items,
                                                               int32_t* __restrict__ dorder) {
   __shared__ int count[kDispatchBins];
-  // per problem: summed durations in 2.05 us units (32 bits hold 2^32 of them,
-  // far beyond any problem's item total) and the item count
+  // per problem: summed durations in 2.05 us units and the item count.  A
+  // slot holds at most 1024 / 256 problems of 2^20 / 32 items each, 2^17
+  // items, so capping each item's share at 2^15 - 1 units (67 ms) keeps the
+  // 32-bit sum from wrapping; only the problem mean sees the cap, and an item
+  // that runs longer (many lanes or environments per sample) still sorts by
+  // its own duration.
+  constexpr uint32_t kShareCap = (1u << 15) - 1u;
+  static_assert((uint64_t)kShareCap * (CEM_MAX_BATCH / kDispatchProblems) * (CEM_MAX_N / 32) < (1ull << 32),
+                "problem duration sums must fit 32 bits");
   __shared__ uint32_t psum[kDispatchProblems];
   __shared__ int pcnt[kDispatchProblems];
   for (int b = threadIdx.x; b < kDispatchProblems; b += blockDim.x) {
@@ -1429,7 +1436,7 @@ __global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __
   __syncthreads();
   for (int i = threadIdx.x; i < n_items; i += blockDim.x) {
     const int pr = items[i].problem % kDispatchProblems;
-    atomicAdd(&psum[pr], idur[i] >> 4);
+    atomicAdd(&psum[pr], min(idur[i] >> 4, kShareCap));
     atomicAdd(&pcnt[pr], 1);
   }
   __syncthreads();

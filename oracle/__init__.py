@@ -7,9 +7,11 @@ CPU-baseline / reference legs may import this package.  It shares no code
 with the CUDA path; both consume the dictionaries of the ``workload``
 package, each with its own marshalling.
 
-Parity status: see ``oracle.h``.  Whole-task rollout costs are "parity
-unpinned" against the paper (it prints no values); their building blocks
-are pinned by closed forms in ``tests/test_oracle_*.py``.
+Parity status: see ``oracle.h``.  The paper prints no worked example, so no
+whole-task rollout cost is pinned to a printed value; every part of each
+rollout (controllers, contacts, friction, integration, action switching,
+goal tests and costs) is pinned by closed forms, invariants and hand-built
+special cases in ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
 

@@ -22,12 +22,17 @@
  *   - Philox4x32-10 from Salmon et al., SC'11, "Parallel random numbers: as
  *     easy as 1, 2, 3", and the Box-Muller transform.
  *
- * Parity status: Philox, Box-Muller statistics, selection, refit, the CE
- * loop on a quadratic, ground friction, PD response, contact energy and
- * resting penetration are pinned by closed forms in tests/.  Whole-task
- * rollout costs (reach, push, pick-place) have no printed values in the
- * paper: parity unpinned against the paper, pinned only through the
- * closed-form sub-cases above.
+ * Parity status (tests/test_oracle_*.py): Philox (published known-answer
+ * vectors), Box-Muller statistics, selection, refit, the CE loop on a
+ * quadratic; in the rollouts, ground friction, the position and heading PD
+ * responses, the time-to-reach cost, body-contact momentum and energy, the
+ * contact point, the force-limit penalty, free flight, resting penetration,
+ * ramp statics and sliding, IK/FK, the pick-and-place action sequencing
+ * (attach, grip tolerance, release velocity, settling) and the goal tests
+ * and costs of every task are pinned by closed forms, invariants and
+ * hand-built special cases.  The paper prints no worked example, so no
+ * whole-task cost is pinned to a printed value; the whole-task costs are
+ * pinned through those parts.
  */
 #ifndef CEM_ORACLE_H
 #define CEM_ORACLE_H

@@ -221,6 +221,105 @@ def test_push_broad_phase_skip_is_exact(orc):
     assert np.array_equal(tr0, tr1) and np.abs(tr0[-1, 9:12]).max() > 0.1  # a real collision, unchanged
 
 
+def _push_head_on(T, force_limit, weights=(0.0, 0.0, 1.0)):
+    """A base sliding at 1.2 m/s along +x into a block at rest, both at yaw 0
+    and centred on y = 0, nothing rubbing (ground, contact and controllers
+    off, kp = 0): the contact normal stays +x and the contact point on the x
+    axis, so the block only translates and every normal impulse goes into its
+    x momentum.  weights = (w_time, w_goal, w_viol)."""
+    sc, sk = workload.push_scene(0, T=T)
+    sc.update(base_mu=0.0, block_mu=0.0, contact_mu=0.0, yaw_kp=0.0, yaw_kd=0.0,
+              base_start=(0.3, 0.0, 0.0), base_v0=(1.2, 0.0, 0.0), block_start=(1.0, 0.0, 0.0),
+              force_limit=force_limit, w_time=weights[0], w_goal=weights[1], w_viol=weights[2])
+    sk["lo"][2] = 0.0
+    sk["lo"][5] = 0.0
+    return sc, sk
+
+
+def test_force_limit_penalty_is_the_impulse_above_the_limit(orc):
+    """With only the violation weight on, J = sum_t max(F_n,t - F_lim, 0) dt.
+    F_n,t is read back from the block's x momentum (m dv = F_n dt each step,
+    nothing else acts on it): at F_lim = 0 the penalty is the whole normal
+    impulse m v_T; a wrong threshold sign, a missing dt or a penalty on
+    |F_n| fails here."""
+    T = 400
+    sc, sk = _push_head_on(T, 0.0)
+    tr = orc.trace(sc, sk, np.zeros(6), T)
+    vx = np.concatenate([[0.0], tr[:, 9]])
+    mk, dt = sc["block_mass"], sc["dt"]
+    Fn = mk * np.diff(vx) / dt
+    assert vx[-1] > 1.0 and np.all(Fn >= -1e-9) and (Fn > 1.0).sum() >= 5  # a real collision
+    np.testing.assert_allclose(tr[:, 10:12], 0.0, atol=0.0)  # the block never turns or drifts in y
+    J0, cls0 = orc.rollout(sc, sk, np.zeros((1, 6)))
+    assert abs(J0[0] - mk * vx[-1]) <= 1e-12 * mk * vx[-1]
+    for flim in (0.3 * Fn.max(), 0.8 * Fn.max(), 2.0 * Fn.max()):
+        sc, sk = _push_head_on(T, flim)
+        J, _ = orc.rollout(sc, sk, np.zeros((1, 6)))
+        expect = np.sum(np.maximum(Fn - flim, 0.0)) * dt
+        assert abs(J[0] - expect) <= 1e-9 * max(expect, 1.0), (flim, J[0], expect)
+    assert J[0] == 0.0  # below the limit throughout
+
+
+def _at_rest_on_targets(kind, base_xy, block_xy=None):
+    """Every action's success target (its nominal point) put where the base
+    rests with kp = 0, so action i succeeds at step i with the base inside
+    eps from the start (crossing fraction 0): t_done = (L - 1) dt."""
+    if kind == "reach":
+        sc, sk = workload.reach_scene(T=3)
+        sk["lo"][2] = 0.0
+    else:
+        sc, sk = workload.push_scene(0, T=3)
+        sk["lo"][2] = sk["lo"][5] = 0.0
+        sc.update(block_start=(block_xy[0], block_xy[1], 0.0), block_mu=0.0)
+    sc.update(base_start=(base_xy[0], base_xy[1], 0.0), base_mu=0.0, yaw_kp=0.0, yaw_kd=0.0)
+    for a in sk["actions"]:
+        a["nominal"] = (base_xy[0], base_xy[1], 0.0)
+    return sc, sk
+
+
+def test_push_goal_test_and_region_distance(orc):
+    """Both actions done at steps 0 and 1 (t_done = dt) with the block at rest
+    far from the base: class 0 exactly when the block centre is inside the
+    goal rectangle (a hair inside a corner included), else class 1 (a micron
+    outside included), and J = w_time dt + w_goal * (distance from the block
+    centre to the rectangle)."""
+    sc0, _ = workload.push_scene(0)
+    (cx, cy, _), (hx, hy, _) = sc0["goal_center"], sc0["goal_half"]
+    cases = [((0.0, 0.0), 0, 0.0), ((hx - 1e-9, -(hy - 1e-9)), 0, 0.0), ((hx + 1e-6, 0.0), 1, 1e-6),
+             ((hx + 0.3, 0.1), 1, 0.3), ((-(hx + 0.3), hy + 0.4), 1, 0.5), ((0.05, -(hy + 0.25)), 1, 0.25)]
+    for (dx, dy), cls_expect, dist in cases:
+        sc, sk = _at_rest_on_targets("push", (cx - 3.0, cy - 3.0), (cx + dx, cy + dy))
+        J, cls = orc.rollout(sc, sk, np.zeros((1, 6)))
+        assert cls[0] == cls_expect, (dx, dy)
+        assert abs(J[0] - (sc["w_time"] * sc["dt"] + sc["w_goal"] * dist)) < 1e-12, (dx, dy, J[0])
+
+
+def test_reach_goal_test_and_distance(orc):
+    """A one-action reach done at step 0 (t_done = 0) with the base at rest:
+    class 0 at the goal centre, class 1 when the action's target lies 0.5 m
+    from it (the action succeeds, the task does not), J = 10 * distance."""
+    for off, cls_expect in ((0.0, 0), (0.04, 0), (0.5, 1)):
+        sc, sk = _at_rest_on_targets("reach", (2.0 + off, 1.0))
+        J, cls = orc.rollout(sc, sk, np.zeros((1, 3)))
+        assert cls[0] == cls_expect and abs(J[0] - sc["w_goal"] * off) < 1e-12, (off, J[0], cls[0])
+
+
+def test_yaw_pd_step_response(orc):
+    """Heading control alone (no translation, no ground friction): the yaw
+    follows semi-implicit Euler of the unit-inertia PD law toward the
+    action's heading, exactly the matrix recurrence of the position test."""
+    ykp, ykd, dt, T, yaw_t = 25.0, 10.0, 0.002, 800, 0.6
+    sc, sk = _reach(T, dt, base_mu=0.0, yaw_kp=ykp, yaw_kd=ykd)
+    sk["actions"][0]["yaw"] = yaw_t
+    tr = orc.trace(sc, sk, np.zeros(3), T)
+    M = np.array([[1 - dt * dt * ykp, dt * (1 - dt * ykd)], [-dt * ykp, 1 - dt * ykd]])
+    e0 = np.array([0.0 - yaw_t, 0.0])
+    E = np.array([np.linalg.matrix_power(M, k + 1) @ e0 for k in range(T)])
+    np.testing.assert_allclose(tr[:, 2] - yaw_t, E[:, 0], atol=1e-12)
+    np.testing.assert_allclose(tr[:, 5], E[:, 1], atol=1e-11)
+    np.testing.assert_allclose(tr[:, 0:2], 0.0, atol=0.0)  # the base turns in place
+
+
 def test_body_contact_elastic_without_damping(orc):
     # no damping, no friction: the penalty spring returns the energy
     sc, sk = _push_free(T=600, mu_c=0.0, c=0.0)

@@ -275,6 +275,20 @@ int cem_solve_paper(cem_handle h, const cem_paper_params* p, cem_result* out);
  * written to xy_h[2 i], xy_h[2 i + 1].  CEM_ERR_UNSUPPORTED without the A*
  * controller.  Synchronous. */
 int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* xy_h, int cap, int* n_out);
+/* Bounds checks of the debug build (libcemtamp_debug.so, built with
+ * CEM_DEBUG): every kernel index checked there that left its buffer was
+ * clamped into range and its code recorded (the first per source file).
+ * Synchronises the device, writes the first recorded code to *code_out (0:
+ * none; 1 dispatch-order entry, 2 rollout-order entry, 3 rollout-order
+ * position, 4 order bin, 5 dispatch-order position, 6 geometry index,
+ * 7 parameter index, 8 elite index) and, if reset, clears the record.  A
+ * release build writes 0 and returns CEM_ERR_UNSUPPORTED. */
+int cem_debug_status(int* code_out, int reset);
+/* Debug build only: one in-bounds kernel indexes a 3-element array at 5
+ * through the checks, which clamp it to element 2 and record code 99 for
+ * cem_debug_status (shows that the checks are compiled in and fire).
+ * Synchronous.  A release build returns CEM_ERR_UNSUPPORTED. */
+int cem_debug_selftest(void);
 /* n_env of iteration j under the schedule (n0, n1, j1) (host function). */
 int cem_n_env(int n0, int n1, int j1, int j);
 

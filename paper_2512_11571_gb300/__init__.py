@@ -17,6 +17,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcemtamp.so")
+# the same library with the kernels' bounds checks compiled in (build.build(debug=True))
+DEBUG_LIB_PATH = os.path.join(HERE, "libcemtamp_debug.so")
 
 MAX_D, MAX_ACTIONS, MAX_GEOMS, MAX_SLABS, MAX_K, TRACE_W = 18, 6, 16, 6, 4096, 20
 SCENE_KIND = {"quadratic": 0, "reach": 1, "push": 2, "pickplace": 3}
@@ -32,7 +34,7 @@ EXPORTS = [
     "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
-    "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_surrogate_test_expire_wait",
+    "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_debug_status", "cem_debug_selftest", "cem_surrogate_test_expire_wait",
     "cem_set_randomization",
     "cem_batch_set_active", "cem_multiplan_solve", "cem_base_path",
     "cem_batch_set_randomization", "cem_batch_set_state", "cem_batch_state_bytes", "cem_batch_set_timing",
@@ -228,12 +230,13 @@ _lib = None
 
 
 def load(path: str = LIB_PATH):
-    """Load libcemtamp.so; raises if it has not been built (no fallback)."""
+    """Load libcemtamp.so (or DEBUG_LIB_PATH, the bounds-checked build) once
+    per process; raises if it has not been built (no fallback)."""
     global _lib
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"libcemtamp.so is not built ({path}); run paper_2512_11571_gb300/build.py")
+        raise ImportError(f"{os.path.basename(path)} is not built ({path}); run paper_2512_11571_gb300/build.py")
     L = C.CDLL(path)
     vp, fp, u8p, i32p, u32p = C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p
     H = C.c_void_p
@@ -248,6 +251,8 @@ def load(path: str = LIB_PATH):
     L.cem_solve_paper.argtypes = [H, C.POINTER(cem_paper_params), C.POINTER(cem_result)]
     L.cem_sample_uniform.argtypes = [H, C.c_uint64, C.c_uint32, C.c_int, vp, vp]
     L.cem_n_env.argtypes = [C.c_int] * 4
+    L.cem_debug_status.argtypes = [C.POINTER(C.c_int), C.c_int]
+    L.cem_debug_selftest.argtypes = []
     L.cem_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
     L.cem_batch_set_active.argtypes = [H, C.POINTER(C.c_int32)]
     L.cem_batch_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
@@ -470,6 +475,19 @@ def cem_base_path(h, start, goal):
 
 def cem_n_env(n0, n1, j1, j):
     return int(load().cem_n_env(n0, n1, j1, j))
+
+
+def cem_debug_status(reset=False):
+    """First bounds-check code the debug library recorded (0: none); raises
+    CemError (CEM_ERR_UNSUPPORTED) on the release library."""
+    code = C.c_int(0)
+    _check(load().cem_debug_status(C.byref(code), int(bool(reset))))
+    return code.value
+
+
+def cem_debug_selftest():
+    """Debug library only: makes one clamped check fire (code 99)."""
+    _check(load().cem_debug_selftest())
 
 
 def cem_solve_static(scene: dict, skel: dict, params: cem_solve_params, stream=None):

@@ -16,6 +16,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libcemtamp.so")
 BUILD = os.path.join(HERE, "_build")
+# the debug build: the same sources with the kernels' bounds checks compiled in
+# (-DCEM_DEBUG; see cem_debug_status), in its own object folder and library
+DEBUG_OUT = os.path.join(HERE, "libcemtamp_debug.so")
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
 SOURCES = ["capi.cu", "sample.cu", "rollout.cu", "refit.cu", "batch.cu", "surrogate.cu", "mlp_tc.cu", "gemm_tc.cu", "solve_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
@@ -34,18 +38,19 @@ def _deps():
     return hdrs
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
+    out, folder = (DEBUG_OUT, DEBUG_BUILD) if debug else (OUT, BUILD)
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     paths = [os.path.join(CSRC, s) for s in srcs]
     newest = max(os.path.getmtime(p) for p in paths + _deps() + [__file__])
-    if not force and os.path.exists(OUT) and os.path.getmtime(OUT) >= newest:
-        return OUT
-    os.makedirs(BUILD, exist_ok=True)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    os.makedirs(folder, exist_ok=True)
     cc = nvcc()
-    extra = extra or []
+    extra = (extra or []) + (["-DCEM_DEBUG"] if debug else [])
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(folder, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -56,15 +61,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(paths))) as ex:
         objs = list(ex.map(compile_one, paths))
-    tmp = OUT + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas-v" in sys.argv else None, debug="--debug" in sys.argv))

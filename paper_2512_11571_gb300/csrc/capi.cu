@@ -926,6 +926,32 @@ int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* x
   return CEM_OK;
 }
 
+int cem_debug_status(int* code_out, int reset) {
+  if (!code_out) return fail(CEM_ERR_INVALID_ARG, "cem_debug_status: code_out is NULL");
+  *code_out = 0;
+#ifdef CEM_DEBUG
+  int c_rollout = 0, c_refit = 0;  // rollout.cu (rollouts, orders) and refit.cu
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = debug_status_rollout(&c_rollout, reset != 0);
+  if (e == cudaSuccess) e = debug_status_refit(&c_refit, reset != 0);
+  if (e != cudaSuccess) return cuda_fail(e, "cem_debug_status");
+  *code_out = c_rollout ? c_rollout : c_refit;
+  return CEM_OK;
+#else
+  (void)reset;
+  return fail(CEM_ERR_UNSUPPORTED, "cem_debug_status: a release build (no bounds checks)");
+#endif
+}
+
+int cem_debug_selftest(void) {
+#ifdef CEM_DEBUG
+  const cudaError_t e = debug_selftest_rollout();
+  return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_debug_selftest");
+#else
+  return fail(CEM_ERR_UNSUPPORTED, "cem_debug_selftest: a release build (no bounds checks)");
+#endif
+}
+
 int cem_n_env(int n0, int n1, int j1, int j) {
   if (j1 <= 0) return j <= 0 ? n0 : n1;
   if (j >= j1) return n1;

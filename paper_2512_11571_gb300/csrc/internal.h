@@ -293,4 +293,38 @@ bool gemm_tc_supported(const GemmArgs& g);
 // pipeline wait that runs out sets *status (device int) non-zero
 cudaError_t gemm_tc(int epi, const GemmArgs& g, int* status, cudaStream_t st);
 
+// Bounds checks of the debug build (compiled with -DCEM_DEBUG into
+// libcemtamp_debug.so by build.build(debug=True)).  CEM_DIDX(i, n, code)
+// is i when 0 <= i < n; otherwise it records `code` in the translation
+// unit's status word (the first code stays) and returns the nearest index
+// in range, so the access stays inside its buffer and no thread takes
+// another path (the warp-collective code around the sites is unchanged).
+// The release build compiles it to i.  Check sites guarantee n >= 1.
+#ifdef CEM_DEBUG
+static __device__ int g_cem_dbg_status;  // one word per translation unit
+__device__ __forceinline__ int cem_didx(int i, int n, int code) {
+  if (i >= 0 && i < n) return i;
+  atomicCAS(&g_cem_dbg_status, 0, code);
+  return i < 0 ? 0 : n - 1;
+}
+#define CEM_DIDX(i, n, code) ::cem::cem_didx((i), (n), (code))
+// the host side of one translation unit's status word: read it (and zero it)
+#define CEM_DEBUG_STATUS_ACCESSOR(name)                                                    \
+  cudaError_t name(int* code, bool reset) {                                                \
+    cudaError_t e = cudaMemcpyFromSymbol(code, g_cem_dbg_status, sizeof(int));             \
+    if (e == cudaSuccess && reset) {                                                       \
+      const int zero = 0;                                                                  \
+      e = cudaMemcpyToSymbol(g_cem_dbg_status, &zero, sizeof(int));                        \
+    }                                                                                      \
+    return e;                                                                              \
+  }
+cudaError_t debug_status_rollout(int* code, bool reset);
+cudaError_t debug_status_refit(int* code, bool reset);
+// one thread indexes a 3-element shared array at 5 through CEM_DIDX (code
+// 99): the access lands on element 2 and rollout.cu's word records 99
+cudaError_t debug_selftest_rollout();
+#else
+#define CEM_DIDX(i, n, code) (i)
+#endif
+
 }  // namespace cem

@@ -220,7 +220,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
     if (a.elite_idx)
       for (int e = tid; e < keff; e += RT) a.elite_idx[e] = (int)(keys[e] & 0xFFFFF);
     // elite e's parameter row (read through L2; the keys stay in shared memory)
-    auto eth = [&](int e, int d) -> float { return a.theta[(size_t)(keys[e] & 0xFFFFF) * D + d]; };
+    auto eth = [&](int e, int d) -> float { return a.theta[(size_t)CEM_DIDX((int)(keys[e] & 0xFFFFF), a.N, 8) * D + d]; };
     // statistics in FP64: 4 threads per output, fixed reduction order
     const int grp = tid >> 2, part = tid & 3;
     if (keff == 1) {
@@ -328,7 +328,7 @@ __device__ __forceinline__ void refit_body(const RefitArgs& a) {
     if (a.track) {
       Track* t = a.track;
       if (keff > 0) {
-        const int b = (int)(reinterpret_cast<uint64_t*>(dyn)[0] & 0xFFFFF);
+        const int b = CEM_DIDX((int)(reinterpret_cast<uint64_t*>(dyn)[0] & 0xFFFFF), a.N, 8);
         const float jb = a.J[b];
         if (cstar < t->best_cls || (cstar == t->best_cls && jb < t->best_J)) {
           t->best_cls = cstar;
@@ -360,6 +360,10 @@ __global__ void __launch_bounds__(RT) refit_batch_kernel(const RefitArgs* __rest
 }
 
 }  // namespace
+
+#ifdef CEM_DEBUG
+CEM_DEBUG_STATUS_ACCESSOR(debug_status_refit)
+#endif
 
 size_t refit_smem_bytes(int K, int D) {
   int P = 1;

@@ -28,6 +28,7 @@ constexpr int TW = CEM_TRACE_W;
 // parameter i clamped to its bounds; a NaN stays NaN (its rollout then ends
 // with a non-finite cost, class 3)
 __device__ __forceinline__ float theta_at(const DevScene& s, const float* __restrict__ row, int i) {
+  i = CEM_DIDX(i, s.D, 7);
   const float x = row[i];
   return isnan(x) ? x : fminf(fmaxf(x, s.lo[i]), s.hi[i]);
 }
@@ -349,6 +350,7 @@ __device__ __noinline__ void planar_rollout(const DevScene& s, const float* __re
 template <bool PLANAR>
 __device__ __forceinline__ bool slab_contact(const DevScene& s, int g, float px, float py, float pz, float& nx,
                                              float& ny, float& nz, float& depth) {
+  g = CEM_DIDX(g, s.n_geoms, 6);
   bool any = false;
   float best = 0.0f;
   const int ns = PLANAR ? s.bslab_n[g] : s.geom_nslab[g];
@@ -1245,7 +1247,7 @@ __global__ void __launch_bounds__(kOrderThreads, 1) order_batch_kernel(const Dev
   }
   __syncthreads();
   for (int k = threadIdx.x; k < pb.N; k += blockDim.x)
-    out[atomicAdd(&count[k < kOrderKeep ? (int)sbin[k] : bin_of(k)], 1)] = k;
+    out[CEM_DIDX(atomicAdd(&count[CEM_DIDX(k < kOrderKeep ? (int)sbin[k] : bin_of(k), kOrderBins, 4)], 1), pb.N, 3)] = k;
 }
 
 // Persistent batched rollout: every warp of a resident CTA repeatedly takes
@@ -1277,7 +1279,7 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
     if (lane == 0) it = atomicAdd(counter, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= n_items) break;
-    const int src_it = dorder ? dorder[it] : it;  // the dispatch order (longest item first)
+    const int src_it = dorder ? CEM_DIDX(dorder[it], n_items, 1) : it;  // the dispatch order (longest item first)
     const BatchItem item = items[src_it];
     uint64_t t_item = 0;
     if (idur && lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_item));
@@ -1328,7 +1330,7 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
       for (int sub = 0; sub < G; ++sub) {
         const int k = item.first + sub * (32 / G) + lane / G;
         if (k < pb.N) {
-          const int n = perm ? perm[pb.sample_off + k] : k;
+          const int n = perm ? CEM_DIDX(perm[pb.sample_off + k], pb.N, 2) : k;
           const float* row = theta + pb.theta_off + (size_t)n * pb.D;
           float Jn;
           int c;
@@ -1343,7 +1345,7 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
     } else {
       const int k = item.first + lane;
       if (k < pb.N) {
-        const int n = perm ? perm[pb.sample_off + k] : k;
+        const int n = perm ? CEM_DIDX(perm[pb.sample_off + k], pb.N, 2) : k;
         const float* row = theta + pb.theta_off + (size_t)n * pb.D;
         float Jn;
         int c;
@@ -1368,6 +1370,34 @@ __global__ void __launch_bounds__(256) rollout_persistent_kernel(const DevScene*
 }
 
 }  // namespace
+
+#ifdef CEM_DEBUG
+CEM_DEBUG_STATUS_ACCESSOR(debug_status_rollout)
+
+namespace {
+__global__ void debug_selftest_kernel(int* out) {
+  __shared__ int a[3];
+  if (threadIdx.x == 0) {
+    a[0] = a[1] = a[2] = 0;
+    a[CEM_DIDX(5, 3, 99)] = 7;  // clamped to a[2]
+    *out = a[2];
+  }
+}
+}  // namespace
+
+cudaError_t debug_selftest_rollout() {
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e != cudaSuccess) return e;
+  debug_selftest_kernel<<<1, 32>>>(d);
+  e = cudaGetLastError();
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e == cudaSuccess && h != 7) e = cudaErrorUnknown;
+  return e;
+}
+#endif
 
 cudaError_t configure_rollout_batch() {
   const int bytes = (int)(sizeof(DevScene) * kMaxBatchWarps);
@@ -1469,7 +1499,8 @@ __global__ void __launch_bounds__(1024) dispatch_order_kernel(const uint32_t* __
     for (int i = 0; i < kDispatchBins / 32; ++i) count[lane * (kDispatchBins / 32) + i] = base + v[i];
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n_items; i += blockDim.x) dorder[atomicAdd(&count[bin_of(i)], 1)] = i;
+  for (int i = threadIdx.x; i < n_items; i += blockDim.x)
+    dorder[CEM_DIDX(atomicAdd(&count[CEM_DIDX(bin_of(i), kDispatchBins, 4)], 1), n_items, 5)] = i;
 }
 
 cudaError_t launch_dispatch_order(const uint32_t* idur, const BatchItem* items, int n_items, int32_t* dorder,

@@ -139,6 +139,18 @@ def test_validation_rejects_bad_descriptors(pkg):
     assert b"annulus" in L.cem_last_error()
 
 
+def test_release_build_has_no_bounds_checks(pkg):
+    # the release library answers the debug-status query without touching the device
+    code = C.c_int(-1)
+    rc = pkg.load().cem_debug_status(C.byref(code), 0)
+    assert pkg.STATUS[rc] == "CEM_ERR_UNSUPPORTED" and code.value == 0
+    assert "release build" in pkg.load().cem_last_error().decode()
+    with pytest.raises(pkg.CemError) as e:
+        pkg.cem_debug_status()
+    assert pkg.STATUS[e.value.code] == "CEM_ERR_UNSUPPORTED"
+    assert pkg.STATUS[pkg.load().cem_debug_selftest()] == "CEM_ERR_UNSUPPORTED"
+
+
 def test_n_env_schedule_matches_oracle(pkg):
     """The library's integer schedule against the oracle's (Sec. IV-A)."""
     import oracle

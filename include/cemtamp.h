@@ -281,8 +281,9 @@ int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* x
  * Synchronises the device, writes the first recorded code to *code_out (0:
  * none; 1 dispatch-order entry, 2 rollout-order entry, 3 rollout-order
  * position, 4 order bin, 5 dispatch-order position, 6 geometry index,
- * 7 parameter index, 8 elite index) and, if reset, clears the record.  A
- * release build writes 0 and returns CEM_ERR_UNSUPPORTED. */
+ * 7 parameter index, 8 elite index, 9 screened row index) and, if reset,
+ * clears the record.  A release build writes 0 and returns
+ * CEM_ERR_UNSUPPORTED. */
 int cem_debug_status(int* code_out, int reset);
 /* Debug build only: one in-bounds kernel indexes a 3-element array at 5
  * through the checks, which clamp it to element 2 and record code 99 for

@@ -930,12 +930,13 @@ int cem_debug_status(int* code_out, int reset) {
   if (!code_out) return fail(CEM_ERR_INVALID_ARG, "cem_debug_status: code_out is NULL");
   *code_out = 0;
 #ifdef CEM_DEBUG
-  int c_rollout = 0, c_refit = 0;  // rollout.cu (rollouts, orders) and refit.cu
+  int c[3] = {0, 0, 0};  // rollout.cu (rollouts, orders), refit.cu, surrogate.cu (screening)
   cudaError_t e = cudaDeviceSynchronize();
-  if (e == cudaSuccess) e = debug_status_rollout(&c_rollout, reset != 0);
-  if (e == cudaSuccess) e = debug_status_refit(&c_refit, reset != 0);
+  if (e == cudaSuccess) e = debug_status_rollout(&c[0], reset != 0);
+  if (e == cudaSuccess) e = debug_status_refit(&c[1], reset != 0);
+  if (e == cudaSuccess) e = debug_status_surrogate(&c[2], reset != 0);
   if (e != cudaSuccess) return cuda_fail(e, "cem_debug_status");
-  *code_out = c_rollout ? c_rollout : c_refit;
+  *code_out = c[0] ? c[0] : c[1] ? c[1] : c[2];
   return CEM_OK;
 #else
   (void)reset;

@@ -320,6 +320,7 @@ __device__ __forceinline__ int cem_didx(int i, int n, int code) {
   }
 cudaError_t debug_status_rollout(int* code, bool reset);
 cudaError_t debug_status_refit(int* code, bool reset);
+cudaError_t debug_status_surrogate(int* code, bool reset);
 // one thread indexes a 3-element shared array at 5 through CEM_DIDX (code
 // 99): the access lands on element 2 and rollout.cu's word records 99
 cudaError_t debug_selftest_rollout();

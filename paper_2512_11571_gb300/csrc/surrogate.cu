@@ -542,12 +542,12 @@ __global__ void score_target_kernel(const float* __restrict__ J, const uint8_t* 
   t[i] = isfinite(j) ? log1pf(fmaxf(j, 0.0f) + 10.0f * (float)cls[i]) : log1pf(1e6f);
 }
 
-__global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ idx, int n, int D,
-                                   float* __restrict__ dst) {
+__global__ void gather_rows_kernel(const float* __restrict__ src, int n_src, const int32_t* __restrict__ idx, int n,
+                                   int D, float* __restrict__ dst) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * D) return;
   const int r = t / D, c = t % D;
-  dst[t] = src[(size_t)idx[r] * D + c];
+  dst[t] = src[(size_t)CEM_DIDX(idx[r], n_src, 9) * D + c];
 }
 
 // ---- FP32 debug path (gemm path 3): every input, weight, activation and
@@ -1417,7 +1417,7 @@ cudaError_t screen_pool_tab(cem_surrogate_ctx* s, int P, int N, int n_explore, i
   topk_kernel<<<1, 1024, 0, st>>>(s->pool_score, P, N, s->keep_idx);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gather_rows_kernel<<<(N * D + 255) / 256, 256, 0, st>>>(s->pool_theta, s->keep_idx, N, D, theta_keep);
+  gather_rows_kernel<<<(N * D + 255) / 256, 256, 0, st>>>(s->pool_theta, P, s->keep_idx, N, D, theta_keep);
   return cudaGetLastError();
 }
 
@@ -1441,6 +1441,10 @@ int set_tables(cem_surrogate_ctx* s, const cem_skeleton_desc& k, const float* sc
 }  // namespace
 
 namespace cem {
+
+#ifdef CEM_DEBUG
+CEM_DEBUG_STATUS_ACCESSOR(debug_status_surrogate)
+#endif
 
 int surrogate_reserve_pool(cem_surrogate_handle s, int n_pool, int n_keep, int D) {
   if (!s) return fail(CEM_ERR_INVALID_ARG, "null surrogate");

@@ -3,13 +3,14 @@
 compute-sanitizer is not available on the GB300 pool, so the kernels carry
 their own checks in a debug build: every checked index (the dispatch and
 rollout orders, their output positions and bins, geometry and parameter
-indexes, elite indexes) that leaves its buffer is clamped into range and its
-code recorded.  A child process loads the debug library and runs the bench's
-64-problem batch, a mixed batch with ragged and tiny problems, and single
-solves of every task; the test asserts that no check fired and that every
-result equals the release library's bit for bit (the checks change no
-arithmetic), then makes one check fire on purpose through an in-bounds
-self-test (the clamp keeps the access inside its array)."""
+indexes, elite indexes, screened row indexes) that leaves its buffer is
+clamped into range and its code recorded.  A child process loads the debug
+library and runs the bench's 64-problem batch, a mixed batch with ragged and
+tiny problems, single solves of every task and a surrogate-screened solve;
+the test asserts that no check fired and that every result equals the
+release library's bit for bit (the checks change no arithmetic), then makes
+one check fire on purpose through an in-bounds self-test (the clamp keeps
+the access inside its array)."""
 import json
 import os
 import subprocess
@@ -67,6 +68,11 @@ def run():
             r = S.solve(50 + j, 512, 32, 3, problem=j, use_graph=False)
         out["single"].append([float(r["best_J"]), int(r["best_cls"]), np.asarray(r["mean"]).tolist(),
                               np.asarray(r["best_theta"]).tolist()])
+    sc, sk, _ = workload.config(2, seed=3)  # surrogate-screened: the kept rows gathered from the pool
+    with P.Scene(sc, sk, T=400) as Sc, P.Surrogate(256, 4, seed=4) as S:
+        r = Sc.solve_screened(S, workload.scene_features(sc), seed=1, N=512, K=32, iters=3, n_pool=4096)
+    out["screened"] = [[float(r["best_J"]), int(r["best_cls"]), np.asarray(r["mean"]).tolist(),
+                        np.asarray(r["best_theta"]).tolist()]]
     return out
 '''
 

@@ -285,6 +285,13 @@ int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* x
  * clears the record.  A release build writes 0 and returns
  * CEM_ERR_UNSUPPORTED. */
 int cem_debug_status(int* code_out, int reset);
+/* Test hook (host-side fault injection): the k-th device allocation the
+ * library makes from now on reports cudaErrorMemoryAllocation without
+ * allocating, as if the device were full, so every call's out-of-memory
+ * path can be exercised (it returns CEM_ERR_NO_MEMORY and releases what it
+ * had allocated).  k = 0 switches the hook off; it also goes off once the
+ * failure has happened.  CEM_ERR_INVALID_ARG for k < 0.  Host only. */
+int cem_test_fail_allocation(int k);
 /* Debug build only: one in-bounds kernel indexes a 3-element array at 5
  * through the checks, which clamp it to element 2 and record code 99 for
  * cem_debug_status (shows that the checks are compiled in and fire).

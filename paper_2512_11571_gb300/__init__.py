@@ -34,7 +34,7 @@ EXPORTS = [
     "cem_batch_create", "cem_batch_destroy", "cem_batch_reset", "cem_batch_iterate", "cem_batch_read",
     "cem_batch_set_launch", "cem_batch_autotune", "cem_batch_steps_per_iteration",
     "cem_batch_set_threads_per_rollout", "cem_batch_get_launch", "cem_set_threads_per_rollout", "cem_get_launch",
-    "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_debug_status", "cem_debug_selftest", "cem_surrogate_test_expire_wait",
+    "cem_solve_paper", "cem_sample_uniform", "cem_n_env", "cem_debug_status", "cem_debug_selftest", "cem_test_fail_allocation", "cem_surrogate_test_expire_wait",
     "cem_set_randomization",
     "cem_batch_set_active", "cem_multiplan_solve", "cem_base_path",
     "cem_batch_set_randomization", "cem_batch_set_state", "cem_batch_state_bytes", "cem_batch_set_timing",
@@ -253,6 +253,7 @@ def load(path: str = LIB_PATH):
     L.cem_n_env.argtypes = [C.c_int] * 4
     L.cem_debug_status.argtypes = [C.POINTER(C.c_int), C.c_int]
     L.cem_debug_selftest.argtypes = []
+    L.cem_test_fail_allocation.argtypes = [C.c_int]
     L.cem_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
     L.cem_batch_set_active.argtypes = [H, C.POINTER(C.c_int32)]
     L.cem_batch_set_randomization.argtypes = [H, C.c_int, C.c_float, C.c_float, C.c_uint64]
@@ -488,6 +489,11 @@ def cem_debug_status(reset=False):
 def cem_debug_selftest():
     """Debug library only: makes one clamped check fire (code 99)."""
     _check(load().cem_debug_selftest())
+
+
+def cem_test_fail_allocation(k):
+    """Test hook: the k-th next device allocation fails (0: off)."""
+    _check(load().cem_test_fail_allocation(int(k)))
 
 
 def cem_solve_static(scene: dict, skel: dict, params: cem_solve_params, stream=None):

@@ -27,7 +27,9 @@ int fail(int code, const std::string& m) { return set_last_error(code, m); }
 #define BATCH_CUDA(call)                                                                                     \
   do {                                                                                                       \
     cudaError_t e_ = (call);                                                                                 \
-    if (e_ != cudaSuccess) return fail(CEM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));      \
+    if (e_ != cudaSuccess)                                                                                   \
+      return fail(e_ == cudaErrorMemoryAllocation ? CEM_ERR_NO_MEMORY : CEM_ERR_CUDA,                        \
+                  std::string(#call ": ") + cudaGetErrorString(e_));                                         \
   } while (0)
 
 constexpr int kMS = CEM_MAX_D, kMC = CEM_MAX_D * CEM_MAX_D;
@@ -270,7 +272,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
   cudaError_t e = configure_refit();
   if (e == cudaSuccess) e = configure_rollout_batch();
   auto M = [&](void** ptr, size_t bytes) {
-    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) e = dev_malloc(ptr, bytes);
   };
   M((void**)&h->scenes_d, sizeof(DevScene) * P);
   M((void**)&h->probs_d, sizeof(BatchProblem) * P);
@@ -542,7 +544,7 @@ int cem_batch_set_screening(cem_batch_handle h, cem_surrogate_handle s, const fl
     if (n_explore < 0 || n_explore > b.N) return fail(CEM_ERR_INVALID_ARG, "0 <= n_explore <= N of every problem");
   int rc = surrogate_reserve_pool(s, n_pool, h->maxN, h->maxD);
   if (rc != CEM_OK) return rc;
-  if (!h->screen_tab_d) BATCH_CUDA(cudaMalloc(&h->screen_tab_d, sizeof(float) * kTab * (size_t)h->P));
+  if (!h->screen_tab_d) BATCH_CUDA(dev_malloc(&h->screen_tab_d, sizeof(float) * kTab * (size_t)h->P));
   std::vector<float> tab((size_t)kTab * h->P, 0.0f);
   for (int p = 0; p < h->P; ++p) {
     float* t = tab.data() + (size_t)p * kTab;

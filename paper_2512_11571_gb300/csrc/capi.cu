@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -28,8 +29,12 @@ int fail(int code, const std::string& msg) {
 }
 
 int cuda_fail(cudaError_t e, const char* where) {
-  return fail(CEM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return fail(e == cudaErrorMemoryAllocation ? CEM_ERR_NO_MEMORY : CEM_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+// the test hook's countdown: 0 = off, k = the k-th next device allocation fails
+std::atomic<int> g_fail_alloc{0};
 
 #define CEM_CUDA(call)                               \
   do {                                               \
@@ -468,9 +473,9 @@ int ensure_work(cem_ctx* h, int N, int iters) {
   free_work(h);
   const int n = N > 0 ? N : 1, it = iters > 0 ? iters : 1;
   const StateLayout L = state_layout(it);
-  if (cudaMalloc(&h->theta_d, sizeof(float) * (size_t)n * D) != cudaSuccess ||
-      cudaMalloc(&h->J_d, sizeof(float) * (size_t)n) != cudaSuccess ||
-      cudaMalloc(&h->cls_d, (size_t)n) != cudaSuccess || cudaMalloc(&h->state_d, L.end) != cudaSuccess ||
+  if (dev_malloc(&h->theta_d, sizeof(float) * (size_t)n * D) != cudaSuccess ||
+      dev_malloc(&h->J_d, sizeof(float) * (size_t)n) != cudaSuccess ||
+      dev_malloc(&h->cls_d, (size_t)n) != cudaSuccess || dev_malloc(&h->state_d, L.end) != cudaSuccess ||
       cudaMallocHost(&h->state_h, L.end) != cudaSuccess) {
     cudaGetLastError();
     free_work(h);
@@ -686,6 +691,22 @@ int default_rollout_block(int N, int kind, int tpr) {
 }
 }  // namespace cem
 
+namespace cem {
+cudaError_t dev_malloc_bytes(void** p, size_t bytes) {
+  int k = g_fail_alloc.load(std::memory_order_relaxed);
+  while (k > 0) {  // count this allocation down; the one that takes the count to 0 fails
+    if (g_fail_alloc.compare_exchange_weak(k, k - 1, std::memory_order_relaxed)) {
+      if (k == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+      }
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+}  // namespace cem
+
 extern "C" {
 
 const char* cem_last_error(void) { return g_err.c_str(); }
@@ -702,7 +723,7 @@ int cem_scene_create(const cem_scene_desc* scene, const cem_skeleton_desc* skel,
   h->skel = *skel;
   h->host = prepare(*scene, *skel);
   cudaError_t e = configure_refit();
-  if (e == cudaSuccess) e = cudaMalloc(&h->scene_d, sizeof(DevScene));
+  if (e == cudaSuccess) e = dev_malloc(&h->scene_d, sizeof(DevScene));
   if (e == cudaSuccess) e = cudaMemcpy(h->scene_d, &h->host, sizeof(DevScene), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
@@ -907,8 +928,8 @@ int cem_base_path(cem_handle h, float sx, float sy, float gx, float gy, float* x
   if (cap < 0 || (cap > 0 && !xy_h)) return fail(CEM_ERR_INVALID_ARG, "cap >= 0 and an output array");
   float* buf = nullptr;
   int* cnt = nullptr;
-  CEM_CUDA(cudaMalloc(&buf, sizeof(float) * 2 * kMaxWaypoints));
-  cudaError_t e = cudaMalloc(&cnt, sizeof(int));
+  CEM_CUDA(dev_malloc(&buf, sizeof(float) * 2 * kMaxWaypoints));
+  cudaError_t e = dev_malloc(&cnt, sizeof(int));
   if (e == cudaSuccess) {
     base_path_kernel<<<1, 1, 0, h->stream>>>(h->scene_d, sx, sy, gx, gy, buf, cnt);
     e = cudaGetLastError();
@@ -942,6 +963,12 @@ int cem_debug_status(int* code_out, int reset) {
   (void)reset;
   return fail(CEM_ERR_UNSUPPORTED, "cem_debug_status: a release build (no bounds checks)");
 #endif
+}
+
+int cem_test_fail_allocation(int k) {
+  if (k < 0) return fail(CEM_ERR_INVALID_ARG, "cem_test_fail_allocation: k must be >= 0");
+  g_fail_alloc.store(k, std::memory_order_relaxed);
+  return CEM_OK;
 }
 
 int cem_debug_selftest(void) {

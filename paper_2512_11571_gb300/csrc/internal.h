@@ -293,6 +293,17 @@ bool gemm_tc_supported(const GemmArgs& g);
 // pipeline wait that runs out sets *status (device int) non-zero
 cudaError_t gemm_tc(int epi, const GemmArgs& g, int* status, cudaStream_t st);
 
+// Every device allocation of the library goes through dev_malloc: a plain
+// cudaMalloc, except that the test hook cem_test_fail_allocation can make
+// the k-th next one report cudaErrorMemoryAllocation without allocating
+// (host-side fault injection: the out-of-memory paths run on a GPU without
+// exhausting its memory).
+cudaError_t dev_malloc_bytes(void** p, size_t bytes);
+template <class T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
+
 // Bounds checks of the debug build (compiled with -DCEM_DEBUG into
 // libcemtamp_debug.so by build.build(debug=True)).  CEM_DIDX(i, n, code)
 // is i when 0 <= i < n; otherwise it records `code` in the translation

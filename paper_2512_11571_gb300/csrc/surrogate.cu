@@ -39,7 +39,9 @@ int fail(int code, const std::string& m) { return set_last_error(code, m); }
 #define SUR_CUDA(call)                                                                                   \
   do {                                                                                                   \
     cudaError_t e_ = (call);                                                                             \
-    if (e_ != cudaSuccess) return fail(CEM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));  \
+    if (e_ != cudaSuccess)                                                                               \
+      return fail(e_ == cudaErrorMemoryAllocation ? CEM_ERR_NO_MEMORY : CEM_ERR_CUDA,                    \
+                  std::string(#call ": ") + cudaGetErrorString(e_));                                     \
   } while (0)
 
 
@@ -733,7 +735,7 @@ int ensure_rows(cem_surrogate_ctx* s, int M) {
   sur_free_work(s);
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t b) {
-    if (e == cudaSuccess) e = cudaMalloc(p, b);
+    if (e == cudaSuccess) e = dev_malloc(p, b);
   };
   A((void**)&s->xin, sizeof(bf16) * (size_t)M * s->in_dim);
   s->act.assign(s->depth, nullptr);
@@ -915,9 +917,9 @@ int gradient_f32(cem_surrogate_ctx* s, const float* x_d, const float* t_d, int M
   float* dz_next = nullptr;
   cudaError_t e = cudaSuccess;
   for (auto& a : act)
-    if (e == cudaSuccess) e = cudaMalloc(&a, sizeof(float) * (size_t)M * W);
-  if (e == cudaSuccess) e = cudaMalloc(&dz, sizeof(float) * (size_t)M * W);
-  if (e == cudaSuccess) e = cudaMalloc(&dz_next, sizeof(float) * (size_t)M * W);
+    if (e == cudaSuccess) e = dev_malloc(&a, sizeof(float) * (size_t)M * W);
+  if (e == cudaSuccess) e = dev_malloc(&dz, sizeof(float) * (size_t)M * W);
+  if (e == cudaSuccess) e = dev_malloc(&dz_next, sizeof(float) * (size_t)M * W);
   auto release = [&]() {
     for (auto* a : act) cudaFree(a);
     cudaFree(dz);
@@ -1088,7 +1090,7 @@ int cem_surrogate_create(int in_dim, int width, int depth, uint64_t seed, cem_su
   const float norm0[2] = {0.0f, 1.0f};
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t b) {
-    if (e == cudaSuccess) e = cudaMalloc(p, b);
+    if (e == cudaSuccess) e = dev_malloc(p, b);
   };
   A((void**)&s->p, sizeof(float) * o);
   A((void**)&s->pb, sizeof(bf16) * o);
@@ -1114,7 +1116,8 @@ int cem_surrogate_create(int in_dim, int width, int depth, uint64_t seed, cem_su
   if (e != cudaSuccess) {
     cudaGetLastError();
     cem_surrogate_destroy(s);
-    return fail(CEM_ERR_CUDA, std::string("cem_surrogate_create: ") + cudaGetErrorString(e));
+    return fail(e == cudaErrorMemoryAllocation ? CEM_ERR_NO_MEMORY : CEM_ERR_CUDA,
+                std::string("cem_surrogate_create: ") + cudaGetErrorString(e));
   }
   *out = s;
   return CEM_OK;
@@ -1274,8 +1277,8 @@ int cem_surrogate_train(cem_surrogate_handle s, const float* x_d, const float* t
   bf16* Xall = nullptr;
   float* hist_d = nullptr;  // per-step losses stay on the device until the end (no per-step sync)
   cudaStream_t st = nullptr;
-  if (cudaMalloc(&Xall, sizeof(bf16) * (size_t)M * s->in_dim) != cudaSuccess ||
-      (loss_hist_h && steps > 0 && cudaMalloc(&hist_d, sizeof(float) * (size_t)steps) != cudaSuccess)) {
+  if (dev_malloc(&Xall, sizeof(bf16) * (size_t)M * s->in_dim) != cudaSuccess ||
+      (loss_hist_h && steps > 0 && dev_malloc(&hist_d, sizeof(float) * (size_t)steps) != cudaSuccess)) {
     cudaGetLastError();
     cudaFree(Xall);
     return fail(CEM_ERR_NO_MEMORY, "training set does not fit");
@@ -1385,9 +1388,9 @@ int ensure_pool(cem_surrogate_ctx* s, int P, int N, int D) {
   s->pool_theta = nullptr;
   s->pool_score = nullptr;
   s->keep_idx = nullptr;
-  cudaError_t e = cudaMalloc(&s->pool_theta, sizeof(float) * (size_t)P * CEM_MAX_D);
-  if (e == cudaSuccess) e = cudaMalloc(&s->pool_score, sizeof(float) * P);
-  if (e == cudaSuccess) e = cudaMalloc(&s->keep_idx, sizeof(int32_t) * P);
+  cudaError_t e = dev_malloc(&s->pool_theta, sizeof(float) * (size_t)P * CEM_MAX_D);
+  if (e == cudaSuccess) e = dev_malloc(&s->pool_score, sizeof(float) * P);
+  if (e == cudaSuccess) e = dev_malloc(&s->keep_idx, sizeof(int32_t) * P);
   if (e != cudaSuccess) {
     cudaGetLastError();
     s->cap_pool = 0;
@@ -1528,8 +1531,8 @@ int solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h,
     if (ft->capacity < N || ft->capacity % N != 0 || ft->capacity > (1 << 22))
       return fail(CEM_ERR_INVALID_ARG, "fine-tune: capacity a multiple of N, at most 2^22");
     if (s->in_dim != 48) return fail(CEM_ERR_UNSUPPORTED, "fine-tune needs the 48-feature surrogate input");
-    if (cudaMalloc(&rb.x, sizeof(float) * (size_t)ft->capacity * 48) != cudaSuccess ||
-        cudaMalloc(&rb.t, sizeof(float) * (size_t)ft->capacity) != cudaSuccess) {
+    if (dev_malloc(&rb.x, sizeof(float) * (size_t)ft->capacity * 48) != cudaSuccess ||
+        dev_malloc(&rb.t, sizeof(float) * (size_t)ft->capacity) != cudaSuccess) {
       cudaGetLastError();
       return fail(CEM_ERR_NO_MEMORY, "fine-tune replay buffer does not fit");
     }

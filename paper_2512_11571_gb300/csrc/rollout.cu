@@ -1387,7 +1387,7 @@ __global__ void debug_selftest_kernel(int* out) {
 
 cudaError_t debug_selftest_rollout() {
   int* d = nullptr;
-  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  cudaError_t e = dev_malloc(&d, sizeof(int));
   if (e != cudaSuccess) return e;
   debug_selftest_kernel<<<1, 32>>>(d);
   e = cudaGetLastError();

@@ -4,11 +4,11 @@ cem_test_fail_allocation(k) makes the k-th next device allocation of the
 library report cudaErrorMemoryAllocation without allocating (no GPU memory
 is exhausted, nothing faults).  For every call that allocates -- scene
 creation, the solve workspace, batch creation, the surrogate and its
-screening pool -- the test fails its 1st, 2nd, ... allocation in turn until
-the call goes through: each failure returns CEM_ERR_NO_MEMORY, hands out no
-handle, leaves the device's free memory where it was (what the call had
-allocated is released), and the call then gives the result of a run that
-never failed."""
+screening pool, the A* path query -- the test fails its 1st, 2nd, ...
+allocation in turn until the call goes through: each failure returns
+CEM_ERR_NO_MEMORY, hands out no handle, leaves the device's free memory
+where it was (what the call had allocated is released), and the call then
+gives the result of a run that never failed."""
 import numpy as np
 import pytest
 
@@ -105,6 +105,15 @@ def test_surrogate_and_screening_pool(P):
     out, n = fail_each_allocation(P, run)
     assert n >= 8
     same(out, ref)
+
+
+def test_base_path_buffers(P):
+    sc, sk = workload.pickplace_scene(0, controller="astar")
+    with P.Scene(sc, sk) as S:
+        start, goal = tuple(sc["base_start"][:2]), tuple(sk["actions"][0]["nominal"][:2])
+        ref = S.base_path(start, goal)
+        out, n = fail_each_allocation(P, lambda: S.base_path(start, goal))
+    assert n == 2 and np.array_equal(out, ref)  # the waypoint buffer, then the count
 
 
 def test_hook_validation_and_reset(P):

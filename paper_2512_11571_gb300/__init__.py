@@ -229,12 +229,15 @@ def pack_scene(scene: dict, skel: dict, T: int | None = None):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libcemtamp.so (or DEBUG_LIB_PATH, the bounds-checked build) once
-    per process; raises if it has not been built (no fallback)."""
+def load(path: str | None = None):
+    """Load libcemtamp.so once per process (DEBUG_LIB_PATH, the bounds-checked
+    build, when path says so or when the environment sets CEMTAMP_DEBUG=1);
+    raises if it has not been built (no fallback)."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = DEBUG_LIB_PATH if os.environ.get("CEMTAMP_DEBUG") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{os.path.basename(path)} is not built ({path}); run paper_2512_11571_gb300/build.py")
     L = C.CDLL(path)

@@ -141,6 +141,8 @@ def test_validation_rejects_bad_descriptors(pkg):
 
 def test_release_build_has_no_bounds_checks(pkg):
     # the release library answers the debug-status query without touching the device
+    if os.environ.get("CEMTAMP_DEBUG") == "1":
+        pytest.skip("the session runs on the debug library")
     code = C.c_int(-1)
     rc = pkg.load().cem_debug_status(C.byref(code), 0)
     assert pkg.STATUS[rc] == "CEM_ERR_UNSUPPORTED" and code.value == 0

@@ -62,6 +62,7 @@ struct cem_batch_ctx {
   std::vector<int> order;          // problems by descending work (the queue order)
   std::vector<uint32_t> weight;    // per problem: the work estimate behind that order
   bool has_pickplace = false;
+  bool has_astar = false;  // some pick-place problem has the A* base: the persistent kernel with the A* rollout
   bool dr_on = false;  // domain randomisation of every problem's rollouts
   DrArgs dr{};
   cudaGraphExec_t graph = nullptr;
@@ -95,7 +96,7 @@ void batch_free(cem_batch_ctx* h) {
 int grid_size(const cem_batch_ctx* h) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr);
+  const int per_sm = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr, h->has_astar);
   return sms * per_sm;
 }
 
@@ -188,7 +189,7 @@ cudaError_t enqueue(cem_batch_ctx* h, cudaStream_t st, bool screened = false) {
   e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d, h->theta_d,
                                       h->J_d, h->cls_d, grid_size(h), h->warps, h->tpr, h->track_d,
                                       h->dr_on ? &h->dr : nullptr, st, order ? h->perm_d : nullptr, h->dorder_d,
-                                      h->idur_d);
+                                      h->idur_d, h->has_astar);
   if (e != cudaSuccess) return e;
   e = mark(h, 2, st);
   if (e != cudaSuccess) return e;
@@ -226,6 +227,7 @@ int cem_batch_create(const cem_scene_desc* scenes, const cem_skeleton_desc* skel
     }
     host[p] = prepare_scene(scenes[p], skels[p]);
     if (host[p].kind == CEM_SCENE_PICKPLACE) h->has_pickplace = true;
+    if (host[p].kind == CEM_SCENE_PICKPLACE && host[p].base_ctrl) h->has_astar = true;
     BatchProblem b;
     std::memset(&b, 0, sizeof(b));
     b.N = q.N;
@@ -453,7 +455,7 @@ int cem_batch_set_launch(cem_batch_handle h, int warps_per_cta, int ctas_per_sm)
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   if (warps_per_cta < 1 || warps_per_cta > 8 || ctas_per_sm < 0 || ctas_per_sm > 64)
     return fail(CEM_ERR_INVALID_ARG, "warps per CTA in 1..8, CTAs per SM in 0..64 (0 = occupancy)");
-  if (ctas_per_sm > rollout_batch_max_ctas_per_sm(warps_per_cta, h->tpr))
+  if (ctas_per_sm > rollout_batch_max_ctas_per_sm(warps_per_cta, h->tpr, h->has_astar))
     return fail(CEM_ERR_INVALID_ARG, "more CTAs per SM than can be resident: the persistent grid must fit");
   h->warps = warps_per_cta;
   h->ctas_per_sm = ctas_per_sm;
@@ -480,7 +482,7 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
     if (t > 1 && !h->has_pickplace) break;
     bool first = true, drop = false;
     for (int w : cand_w) {
-      const int maxc = rollout_batch_max_ctas_per_sm(w, t);
+      const int maxc = rollout_batch_max_ctas_per_sm(w, t, h->has_astar);
       for (int c = 1; c <= maxc && e == cudaSuccess && !drop; c *= 2) {
         h->warps = w;
         h->ctas_per_sm = c;
@@ -492,7 +494,7 @@ int cem_batch_autotune(cem_batch_handle h, int* warps_out, int* ctas_out, float*
           if (e == cudaSuccess)
             e = launch_rollout_batch_persistent(h->scenes_d, h->probs_d, h->items_d, h->n_items, h->counter_d,
                                                 h->theta_d, h->J_d, h->cls_d, grid_size(h), w, t, h->track_d,
-                                                h->dr_on ? &h->dr : nullptr, 0);
+                                                h->dr_on ? &h->dr : nullptr, 0, nullptr, nullptr, nullptr, h->has_astar);
           if (e == cudaSuccess) e = cudaEventRecord(b, 0);
           if (e == cudaSuccess) e = cudaEventSynchronize(b);
           float ms = 0.0f;
@@ -726,7 +728,7 @@ int cem_multiplan_solve(const cem_scene_desc* scene, const cem_skeleton_desc* pl
 int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   if (tpr != 1 && tpr != 8 && tpr != 32) return fail(CEM_ERR_INVALID_ARG, "threads per rollout must be 1, 8 or 32");
-  if (h->ctas_per_sm > rollout_batch_max_ctas_per_sm(h->warps, tpr)) h->ctas_per_sm = 0;
+  if (h->ctas_per_sm > rollout_batch_max_ctas_per_sm(h->warps, tpr, h->has_astar)) h->ctas_per_sm = 0;
   h->tpr = tpr;
   if (h->graph) {
     cudaGraphExecDestroy(h->graph);
@@ -738,7 +740,7 @@ int cem_batch_set_threads_per_rollout(cem_batch_handle h, int tpr) {
 int cem_batch_get_launch(cem_batch_handle h, int* warps_out, int* ctas_out, int* tpr_out) {
   if (!h) return fail(CEM_ERR_INVALID_ARG, "null handle");
   if (warps_out) *warps_out = h->warps;
-  if (ctas_out) *ctas_out = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr);
+  if (ctas_out) *ctas_out = h->ctas_per_sm > 0 ? h->ctas_per_sm : rollout_batch_max_ctas_per_sm(h->warps, h->tpr, h->has_astar);
   if (tpr_out) *tpr_out = h->tpr;
   return CEM_OK;
 }

@@ -160,12 +160,14 @@ cudaError_t launch_sample_batch(const BatchProblem* probs_d, int n_problems, int
 // sample perm[sample_off + k] (the randomised path keeps the identity);
 // dorder (may be null = identity): the k-th item taken is items[dorder[k]];
 // idur (may be null): a running average of each item's duration is kept there
+// astar: whether any problem of the batch has the A* base controller (false
+// launches the kernel without the A* rollout; it must then be true of none)
 cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const BatchProblem* probs_d,
                                             const BatchItem* items_d, int n_items, int* counter_d,
                                             const float* theta, float* J, uint8_t* cls, int grid, int warps,
                                             int tpr, const Track* tracks, const DrArgs* dr, cudaStream_t st,
                                             const int32_t* perm = nullptr, const int32_t* dorder = nullptr,
-                                            uint32_t* idur = nullptr);
+                                            uint32_t* idur = nullptr, bool astar = true);
 // the dispatch order of the work items, longest forecast duration first
 // (idur: per item, 128 ns units, a running average the persistent kernel
 // keeps; blended with the item's problem mean)
@@ -175,7 +177,8 @@ cudaError_t launch_dispatch_order(const uint32_t* idur, const BatchItem* items, 
 // perm[sample_off + k] for k < N, from the theta just sampled
 cudaError_t launch_order_batch(const DevScene* scenes_d, const BatchProblem* probs_d, int n_problems,
                                const float* theta, int32_t* perm, cudaStream_t st);
-int rollout_batch_max_ctas_per_sm(int warps, int tpr);
+// (astar selects the kernel instantiation whose occupancy is asked)
+int rollout_batch_max_ctas_per_sm(int warps, int tpr, bool astar = true);
 // opts the persistent kernel into its dynamic shared memory (one DevScene
 // per warp; before any capture)
 cudaError_t configure_rollout_batch();

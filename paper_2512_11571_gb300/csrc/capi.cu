@@ -532,7 +532,7 @@ cudaError_t enqueue_iteration(cem_ctx* h, uint64_t seed, uint32_t problem, int N
   if (e != cudaSuccess) return e;
   DrArgs tmp;
   e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->tpr,
-                     dr_for(h, tmp, problem, &h->track_d->iter, 0), h->stream);
+                     dr_for(h, tmp, problem, &h->track_d->iter, 0), h->stream, h->host.base_ctrl != 0);
   if (e != cudaSuccess) return e;
   RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, K, cov_mode);
   a.mean = h->mean_d;
@@ -572,6 +572,7 @@ int handle_solve_buffers(cem_handle h, int N, int iters, SolveBuffers* b) {
   b->ev1 = h->ev1;
   b->scene = h->scene_d;
   b->kind = h->host.kind;
+  b->astar = h->host.base_ctrl != 0;
   b->block = default_block(h, N);
   b->tpr = h->tpr;
   b->dr = h->dr_on ? &h->dr : nullptr;
@@ -833,7 +834,7 @@ int cem_rollout_batch(cem_handle h, const float* theta_d, int N, float* J_d, uin
   DrArgs tmp;
   cudaError_t e = launch_rollout(h->scene_d, h->host.kind, theta_d, N, J_d, cls_d, default_block(h, N), h->tpr,
                                  dr_for(h, tmp, 0, nullptr, 0),
-                                 (cudaStream_t)stream);
+                                 (cudaStream_t)stream, h->host.base_ctrl != 0);
   return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_rollout_batch");
 }
 
@@ -845,7 +846,8 @@ int cem_rollout_trace(cem_handle h, const float* theta_d, int N, int steps, floa
   if (h->host.kind == CEM_SCENE_QUADRATIC) return fail(CEM_ERR_UNSUPPORTED, "quadratic scenes have no state");
   if (!is_device_ptr(theta_d) || !is_device_ptr(states_d))
     return fail(CEM_ERR_INVALID_ARG, "theta and states must be device pointers");
-  cudaError_t e = launch_trace(h->scene_d, h->host.kind, theta_d, N, steps, states_d, (cudaStream_t)stream);
+  cudaError_t e = launch_trace(h->scene_d, h->host.kind, theta_d, N, steps, states_d, (cudaStream_t)stream,
+                               h->host.base_ctrl != 0);
   return e == cudaSuccess ? CEM_OK : cuda_fail(e, "cem_rollout_trace");
 }
 
@@ -1036,7 +1038,7 @@ int cem_solve_paper(cem_handle h, const cem_paper_params* p, cem_result* out) {
     DrArgs tmp;
     if (e == cudaSuccess)
       e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, default_block(h, N), h->tpr,
-                         dr_for(h, tmp, p->problem, &h->track_d->iter, 0), h->stream);
+                         dr_for(h, tmp, p->problem, &h->track_d->iter, 0), h->stream, h->host.base_ctrl != 0);
     if (e == cudaSuccess) {
       RefitArgs a = refit_args(h, h->theta_d, h->J_d, h->cls_d, N, p->K, p->cov_mode);
       a.mean = h->mean_d;
@@ -1123,7 +1125,8 @@ int cem_autotune(cem_handle h, int N, const char* cache_path, int* block_out) {
       float tot = 0.0f;
       for (int rep = 0; rep < 3; ++rep) {
         CEM_CUDA(cudaEventRecord(h->ev0, h->stream));
-        e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, t, nullptr, h->stream);
+        e = launch_rollout(h->scene_d, h->host.kind, h->theta_d, N, h->J_d, h->cls_d, b, t, nullptr, h->stream,
+                           h->host.base_ctrl != 0);
         if (e != cudaSuccess) return cuda_fail(e, "autotune rollout");
         CEM_CUDA(cudaEventRecord(h->ev1, h->stream));
         CEM_CUDA(cudaEventSynchronize(h->ev1));

@@ -140,11 +140,13 @@ struct DrArgs {
 // block = threads per CTA; tpr = lanes per rollout (1, 8 or 32; used for
 // pick-and-place scenes, the other kinds always run one lane per rollout);
 // dr = domain randomisation or null (then tpr applies; with dr, one lane per
-// environment)
+// environment); astar = the scene has the A* base controller (false takes
+// the kernel without the A* rollout for a pick-and-place scene with the PD
+// base: the same compiled rollout as the batched kernel's)
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
-                           int block, int tpr, const DrArgs* dr, cudaStream_t st);
+                           int block, int tpr, const DrArgs* dr, cudaStream_t st, bool astar = true);
 cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
-                         cudaStream_t st);
+                         cudaStream_t st, bool astar = true);
 cudaError_t launch_refit(const RefitArgs& a, cudaStream_t st);
 // opts the refit kernel into its dynamic shared memory (once per device, before any capture)
 cudaError_t configure_refit();
@@ -210,6 +212,7 @@ struct SolveBuffers {
   cudaEvent_t ev0, ev1;
   const DevScene* scene;
   int kind, block, tpr;
+  bool astar;        // the scene has the A* base controller
   const DrArgs* dr;  // the handle's domain randomisation (null when off)
 };
 const cem_skeleton_desc& handle_skeleton(cem_handle h);

@@ -1074,7 +1074,7 @@ constexpr int rollout_min_ctas() {
 
 // One rollout per group of G lanes (G > 1 only for pick-and-place); the
 // group's first lane writes the result.
-template <int KIND, bool TRACE, int G>
+template <int KIND, bool TRACE, int G, bool AS = true>
 __global__ void __launch_bounds__(256, rollout_min_ctas<KIND>()) rollout_kernel(const DevScene* __restrict__ scene_g,
                                                                                 const float* __restrict__ theta, int N,
                                                                                 int steps,
@@ -1091,7 +1091,10 @@ __global__ void __launch_bounds__(256, rollout_min_ctas<KIND>()) rollout_kernel(
   int c;
   if (KIND == CEM_SCENE_REACH) planar_rollout<false, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
   else if (KIND == CEM_SCENE_PUSH) planar_rollout<true, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
-  else if (KIND == CEM_SCENE_PICKPLACE) pickplace_any<G, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
+  else if (KIND == CEM_SCENE_PICKPLACE) {
+    if (AS) pickplace_any<G, TRACE>(s, row, T, 1.0f, 1.0f, Jn, c, tr);
+    else pickplace_rollout<G, TRACE, false>(s, row, T, 1.0f, 1.0f, Jn, c, tr);  // the scene has the PD base
+  }
   else quadratic_cost(s, row, Jn, c);
   if (!TRACE && (G == 1 || (threadIdx.x & (G - 1)) == 0)) {
     J[n] = Jn;
@@ -1140,7 +1143,7 @@ __global__ void __launch_bounds__(256, rollout_min_ctas<KIND>()) rollout_dr_kern
 
 template <bool TRACE>
 cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* J, uint8_t* cls,
-                     float* trace, int block, int tpr, cudaStream_t st) {
+                     float* trace, int block, int tpr, cudaStream_t st, bool astar) {
   if (N <= 0) return cudaSuccess;
   if (block <= 0) block = 128;
   const int grid = (N + block - 1) / block;
@@ -1164,8 +1167,10 @@ cudaError_t dispatch(const DevScene* s_d, int kind, const float* theta, int N, i
           rollout_kernel<CEM_SCENE_PICKPLACE, false, 8><<<g2, bt, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
         else
           rollout_kernel<CEM_SCENE_PICKPLACE, false, 32><<<g2, bt, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
-      } else {
+      } else if (astar) {
         rollout_kernel<CEM_SCENE_PICKPLACE, TRACE, 1><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
+      } else {
+        rollout_kernel<CEM_SCENE_PICKPLACE, TRACE, 1, false><<<grid, block, 0, st>>>(s_d, theta, N, steps, J, cls, trace);
       }
       break;
     default:
@@ -1573,8 +1578,9 @@ cudaError_t launch_rollout_batch_persistent(const DevScene* scenes_d, const Batc
 }
 
 cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, int N, float* J, uint8_t* cls,
-                           int block, int tpr, const DrArgs* dr, cudaStream_t st) {
-  if (!dr || kind == CEM_SCENE_QUADRATIC) return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, tpr, st);
+                           int block, int tpr, const DrArgs* dr, cudaStream_t st, bool astar) {
+  if (!dr || kind == CEM_SCENE_QUADRATIC)
+    return dispatch<false>(s_d, kind, theta, N, 0, J, cls, nullptr, block, tpr, st, astar);
   if (N <= 0) return cudaSuccess;
   if (dr->M < 1 || dr->M > 32 || (dr->M & (dr->M - 1))) return cudaErrorInvalidValue;
   const int bt = block < 32 ? 32 : block;  // whole warps, so environment groups stay aligned
@@ -1597,8 +1603,8 @@ cudaError_t launch_rollout(const DevScene* s_d, int kind, const float* theta, in
 }
 
 cudaError_t launch_trace(const DevScene* s_d, int kind, const float* theta, int N, int steps, float* states,
-                         cudaStream_t st) {
-  return dispatch<true>(s_d, kind, theta, N, steps, nullptr, nullptr, states, 64, 1, st);
+                         cudaStream_t st, bool astar) {
+  return dispatch<true>(s_d, kind, theta, N, steps, nullptr, nullptr, states, 64, 1, st, astar);
 }
 
 }  // namespace cem

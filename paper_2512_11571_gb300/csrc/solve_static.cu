@@ -231,7 +231,7 @@ extern "C" int cem_solve_static(const cem_scene_desc* scene, const cem_skeleton_
   const int block = default_rollout_block(p->N, host.kind, 1);
   for (int j = 0; j < p->iters; ++j) {
     STATIC_CUDA(launch_sample(mean_d, chol_d, p->seed, &track_d->iter, 0, p->problem, p->N, D, theta_d, st));
-    STATIC_CUDA(launch_rollout(scene_d, host.kind, theta_d, p->N, J_d, cls_d, block, 1, nullptr, st));
+    STATIC_CUDA(launch_rollout(scene_d, host.kind, theta_d, p->N, J_d, cls_d, block, 1, nullptr, st, host.base_ctrl != 0));
     STATIC_CUDA(launch_refit(a, st));
   }
   int32_t status = 0;

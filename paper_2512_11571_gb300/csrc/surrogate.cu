@@ -1579,7 +1579,7 @@ int solve_screened(cem_handle h, cem_surrogate_handle s, const float* scene16_h,
       dr.problem = p->problem;
       dr.iter_ptr = &b.track->iter;
     }
-    SUR_CUDA(launch_rollout(b.scene, b.kind, b.theta, N, b.J, b.cls, b.block, b.tpr, b.dr ? &dr : nullptr, st));
+    SUR_CUDA(launch_rollout(b.scene, b.kind, b.theta, N, b.J, b.cls, b.block, b.tpr, b.dr ? &dr : nullptr, st, b.astar));
     if (ft) {  // this iteration's simulated samples (features, score targets) into the ring
       const int pos = (int)(((long long)j * N) % ft->capacity);
       features_kernel<float><<<(N + 127) / 128, 128, 0, st>>>(b.theta, N, D, s->lohi, s->scene16, rb.x + (size_t)pos * 48);

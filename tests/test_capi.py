@@ -48,6 +48,18 @@ def test_library_exports_every_declared_symbol(pkg):
         assert re.search(rf"\bT {n}\b", out), n
 
 
+def test_debug_library_builds_with_the_same_exports(pkg):
+    # the bounds-checked build (CEM_DEBUG) compiles from the same sources and
+    # exports the same entry points as the release library
+    from paper_2512_11571_gb300 import build
+
+    path = build.build(debug=True)
+    assert path == pkg.DEBUG_LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True).stdout
+    for n in declared_functions():
+        assert re.search(rf"\bT {n}\b", out), n
+
+
 def test_binding_names_match_header(pkg):
     assert sorted(pkg.EXPORTS) == sorted(n for n in declared_functions())
     for n in pkg.EXPORTS:
